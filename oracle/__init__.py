@@ -1,0 +1,216 @@
+"""FP64 CPU oracle for the alpha-CNG hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg import this
+package.  The CUDA library under ``paper_2510_05975_gb300/`` never imports it and shares no
+code with it.
+
+``cng_oracle.c`` holds the graph arithmetic (canonical distance, exact candidate lists,
+Def. 2 / Alg. 2 pruning, Alg. 4 adaptive pruning, Alg. 3 phase 3 reverse merge, Alg. 1
+beam search); this module compiles it with gcc on first use (``-O2 -ffp-contract=off``,
+OpenMP when available) and wraps it with ctypes.  ``mlp.py`` holds the FP64 learned-stop
+network.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cng_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libcng_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library (gcc, OpenMP if the compiler has it). Returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    tmp = _LIB + f".tmp{os.getpid()}"
+    try:
+        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32, i64, dbl, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+            lib.or_sqdist.restype = dbl
+            lib.or_sqdist.argtypes = [vp, vp, ctypes.c_int]
+            lib.or_dist.restype = dbl
+            lib.or_dist.argtypes = [vp, vp, ctypes.c_int]
+            lib.or_knn.restype = ctypes.c_int
+            lib.or_knn.argtypes = [vp, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+            lib.or_centroid.restype = None
+            lib.or_centroid.argtypes = [vp, i64, ctypes.c_int, vp]
+            lib.or_entry.restype = i32
+            lib.or_entry.argtypes = [vp, i64, ctypes.c_int]
+            lib.or_prune.restype = ctypes.c_int
+            lib.or_prune.argtypes = [vp, i64, ctypes.c_int, i64, vp, ctypes.c_int, dbl, dbl,
+                                     ctypes.c_int, vp]
+            lib.or_prune_adaptive.restype = ctypes.c_int
+            lib.or_prune_adaptive.argtypes = [vp, i64, ctypes.c_int, i64, vp, ctypes.c_int, dbl,
+                                              dbl, dbl, dbl, ctypes.c_int, vp, vp]
+            lib.or_build.restype = ctypes.c_int
+            lib.or_build.argtypes = [vp, i64, ctypes.c_int, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                     vp, vp, vp, vp, vp, vp]
+            lib.or_search.restype = ctypes.c_int
+            lib.or_search.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, vp, i64,
+                                      ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+            lib.or_num_threads.restype = ctypes.c_int
+            lib.or_num_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _f32(x) -> np.ndarray:
+    x = np.asarray(x)
+    if x.dtype == np.float16:  # fp16 -> fp32 widening is exact
+        x = x.astype(np.float32)
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def sqdist(x, y) -> float:
+    """Canonical squared distance: left-to-right FP64 sum of squared differences."""
+    x, y = _f32(x).ravel(), _f32(y).ravel()
+    assert x.size == y.size
+    return float(_load().or_sqdist(_p(x), _p(y), x.size))
+
+
+def dist(x, y) -> float:
+    """Canonical distance sqrt(sqdist), IEEE double."""
+    x, y = _f32(x).ravel(), _f32(y).ravel()
+    assert x.size == y.size
+    return float(_load().or_dist(_p(x), _p(y), x.size))
+
+
+def knn(base, L: int, rows=None, exclude_self: bool | None = None):
+    """Exact (D, id)-ordered L nearest points of ``base`` for each row (default: base itself,
+    self excluded by id).  Returns (ids int32 [m, L], dist float64 [m, L])."""
+    base = _f32(base)
+    if rows is None:
+        rows, ex = base, True if exclude_self is None else exclude_self
+    else:
+        rows, ex = _f32(rows), bool(exclude_self)
+    n, d = base.shape
+    m = rows.shape[0]
+    ids = np.empty((m, L), np.int32)
+    ds = np.empty((m, L), np.float64)
+    rc = _load().or_knn(_p(base), n, _p(rows), m, d, L, int(ex), _p(ids), _p(ds))
+    if rc != 0:
+        raise ValueError(f"or_knn failed ({rc})")
+    return ids, ds
+
+
+def centroid(X) -> np.ndarray:
+    X = _f32(X)
+    c = np.empty(X.shape[1], np.float64)
+    _load().or_centroid(_p(X), X.shape[0], X.shape[1], _p(c))
+    return c
+
+
+def entry(X) -> int:
+    X = _f32(X)
+    return int(_load().or_entry(_p(X), X.shape[0], X.shape[1]))
+
+
+def prune(X, p: int, V, alpha: float, tau: float, R: int) -> np.ndarray:
+    """Alg. 2 (Def. 2 rule) for point p on candidate ids V (any order), cut at R kept."""
+    X = _f32(X)
+    V = np.ascontiguousarray(V, dtype=np.int32)
+    S = np.empty(max(R, 1), np.int32)
+    ns = _load().or_prune(_p(X), X.shape[0], X.shape[1], int(p), _p(V), V.size, float(alpha),
+                          float(tau), int(R), _p(S))
+    if ns < 0:
+        raise ValueError(f"or_prune failed ({ns})")
+    return S[:ns].copy()
+
+
+def prune_adaptive(X, p: int, V, alpha0: float, alpha_max: float, dalpha: float, tau: float,
+                   R: int):
+    """Alg. 4; returns (kept ids, alpha used)."""
+    X = _f32(X)
+    V = np.ascontiguousarray(V, dtype=np.int32)
+    S = np.empty(max(R, 1), np.int32)
+    a = ctypes.c_double(0.0)
+    ns = _load().or_prune_adaptive(_p(X), X.shape[0], X.shape[1], int(p), _p(V), V.size,
+                                   float(alpha0), float(alpha_max), float(dalpha), float(tau),
+                                   int(R), _p(S), ctypes.byref(a))
+    if ns < 0:
+        raise ValueError(f"or_prune_adaptive failed ({ns})")
+    return S[:ns].copy(), a.value
+
+
+class Graph:
+    """Oracle construction result (Alg. 3 phases 1-3 with exact candidates)."""
+
+    def __init__(self, entry, cand, fwd, fdeg, adj, deg):
+        self.entry, self.cand, self.fwd, self.fdeg, self.adj, self.deg = entry, cand, fwd, fdeg, adj, deg
+
+    def out(self, p: int) -> np.ndarray:
+        return self.adj[p, : self.deg[p]]
+
+
+def build_graph(X, alpha: float, tau: float, R: int, L: int) -> Graph:
+    X = _f32(X)
+    n, d = X.shape
+    e = ctypes.c_int32(-1)
+    cand = np.empty((n, L), np.int32)
+    fwd = np.empty((n, R), np.int32)
+    fdeg = np.empty(n, np.int32)
+    adj = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    rc = _load().or_build(_p(X), n, d, float(alpha), float(tau), int(R), int(L), ctypes.byref(e),
+                          _p(cand), _p(fwd), _p(fdeg), _p(adj), _p(deg))
+    if rc != 0:
+        raise ValueError(f"or_build failed ({rc})")
+    return Graph(int(e.value), cand, fwd, fdeg, adj, deg)
+
+
+def search(X, adj, deg, entry_id: int, Q, k: int, L: int):
+    """Alg. 1 for every query. Returns (ids [nq,k], dist [nq,k] float64, ndc [nq], hops [nq])."""
+    X, Q = _f32(X), _f32(Q)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    deg = np.ascontiguousarray(deg, dtype=np.int32)
+    n, d = X.shape
+    nq = Q.shape[0]
+    ids = np.empty((nq, k), np.int32)
+    ds = np.empty((nq, k), np.float64)
+    ndc = np.empty(nq, np.int32)
+    hops = np.empty(nq, np.int32)
+    rc = _load().or_search(_p(X), n, d, _p(adj), _p(deg), adj.shape[1], int(entry_id), _p(Q), nq,
+                           int(k), int(L), _p(ids), _p(ds), _p(ndc), _p(hops))
+    if rc != 0:
+        raise ValueError(f"or_search failed ({rc})")
+    return ids, ds, ndc, hops
+
+
+def recall(found_ids, true_ids) -> float:
+    """Recall@k = |KNN(q) & Res(q)| / k averaged over queries (Sec. 5.1, Metrics)."""
+    found_ids = np.asarray(found_ids)
+    true_ids = np.asarray(true_ids)
+    k = true_ids.shape[1]
+    hit = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(found_ids, true_ids))
+    return hit / (k * true_ids.shape[0])

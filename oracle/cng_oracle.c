@@ -1,0 +1,418 @@
+/*
+ * cng_oracle.c -- plain, slow, FP64 CPU oracle for the alpha-CNG hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the benchmark's CPU
+ * baseline may load this file's library.  The CUDA library shares no code with it.
+ *
+ * Every routine below follows one passage of the paper (arXiv 2510.05975,
+ * "Fast-Convergent Proximity Graphs for Approximate Nearest Neighbor Search"):
+ *
+ *   canonical distance      Sec. 2.1 (metric space); the numeric reading is ours:
+ *                           D(x,y) = sqrt(sum_{i=0}^{d-1} (x_i - y_i)^2) in IEEE double,
+ *                           summed left to right, one rounding per operation, no fused
+ *                           multiply-add (compile with -ffp-contract=off).
+ *   candidate lists         Alg. 3, phase 2 reads "the C closest points"; here the exact
+ *                           L nearest points of P \ {p} ordered by (D, id).
+ *   navigating node         Alg. 3, phase 1: nearest point to the centroid of P.
+ *   pruning                 Def. 2 (Eq. 1) and Alg. 2, fixed alpha, stop at R kept.
+ *   adaptive pruning        Alg. 4 with alpha_i = alpha0 + i * dalpha.
+ *   reverse merge           Alg. 3, phase 3 and the lazy-pruning paragraph of Sec. 4.3.
+ *   beam search             Alg. 1 (with a visited set; identical returned ids).
+ *
+ * Ties: every "sort by distance" orders by (D, id) lexicographically.
+ * Parallelism: OpenMP over independent points / queries only; each point's arithmetic is
+ * the sequential definition.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_E_INVAL -1
+#define OR_E_NOMEM -2
+
+/* ---- canonical distance (Sec. 2.1) -------------------------------------------------- */
+
+/* Squared distance: left-to-right sum of squared differences, all in double. */
+double or_sqdist(const float *x, const float *y, int d) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = (double)x[i] - (double)y[i];
+        s = s + t * t;
+    }
+    return s;
+}
+
+double or_dist(const float *x, const float *y, int d) { return sqrt(or_sqdist(x, y, d)); }
+
+/* Distance from a double-precision point (the centroid) to a float point. */
+double or_dist_dc(const double *c, const float *y, int d) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = c[i] - (double)y[i];
+        s = s + t * t;
+    }
+    return sqrt(s);
+}
+
+static int key_less(double da, int32_t ia, double db, int32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+/* ---- exact candidate lists (Alg. 3 phase 2, exact form) ---------------------------- */
+
+/*
+ * For each of the m rows, the L points of `base` with the smallest (D, id), ascending.
+ * If exclude_self, row i is base point i and is left out by id (duplicates stay).
+ * Rows with fewer than L eligible points are padded with id -1 and distance +inf.
+ */
+int or_knn(const float *base, int64_t n, const float *rows, int64_t m, int d, int L,
+           int exclude_self, int32_t *out_ids, double *out_d) {
+    if (n < 0 || m < 0 || d <= 0 || L <= 0) return OR_E_INVAL;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t *ids = out_ids + i * L;
+        double *ds = out_d + i * L;
+        int cnt = 0;
+        const float *x = rows + i * (int64_t)d;
+        for (int64_t j = 0; j < n; ++j) {
+            if (exclude_self && j == i) continue;
+            double D = or_dist(x, base + j * (int64_t)d, d);
+            if (cnt < L || key_less(D, (int32_t)j, ds[cnt - 1], ids[cnt - 1])) {
+                int pos = (cnt < L) ? cnt : L - 1;
+                while (pos > 0 && key_less(D, (int32_t)j, ds[pos - 1], ids[pos - 1])) {
+                    ds[pos] = ds[pos - 1];
+                    ids[pos] = ids[pos - 1];
+                    --pos;
+                }
+                ds[pos] = D;
+                ids[pos] = (int32_t)j;
+                if (cnt < L) ++cnt;
+            }
+        }
+        for (int t = cnt; t < L; ++t) {
+            ids[t] = -1;
+            ds[t] = INFINITY;
+        }
+    }
+    return err;
+}
+
+/* ---- navigating node (Alg. 3 phase 1, exact form) ---------------------------------- */
+
+/* Centroid: c_j = (sum_i x_ij) / n, each sum taken sequentially in i. */
+void or_centroid(const float *X, int64_t n, int d, double *c) {
+    for (int j = 0; j < d; ++j) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s = s + (double)X[i * (int64_t)d + j];
+        c[j] = s / (double)n;
+    }
+}
+
+/* Navigating node s = argmin_i (D(c, x_i), i). */
+int32_t or_entry(const float *X, int64_t n, int d) {
+    if (n <= 0 || d <= 0) return -1;
+    double *c = (double *)malloc(sizeof(double) * d);
+    if (!c) return -1;
+    or_centroid(X, n, d, c);
+    double best = INFINITY;
+    int32_t bi = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        double D = or_dist_dc(c, X + i * (int64_t)d, d);
+        if (bi < 0 || key_less(D, (int32_t)i, best, bi)) {
+            best = D;
+            bi = (int32_t)i;
+        }
+    }
+    free(c);
+    return bi;
+}
+
+/* ---- pruning (Def. 2, Alg. 2) ------------------------------------------------------ */
+
+typedef struct {
+    double D;
+    int32_t id;
+} or_pair;
+
+static int pair_cmp(const void *a, const void *b) {
+    const or_pair *x = (const or_pair *)a, *y = (const or_pair *)b;
+    if (x->D < y->D) return -1;
+    if (x->D > y->D) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Sort the ids in V by (D(p, .), id); writes the sorted pairs into `out`. */
+static void sort_by_distance(const float *X, int d, int64_t p, const int32_t *V, int nv,
+                             or_pair *out) {
+    const float *xp = X + p * (int64_t)d;
+    for (int i = 0; i < nv; ++i) {
+        out[i].id = V[i];
+        out[i].D = or_dist(xp, X + (int64_t)V[i] * d, d);
+    }
+    qsort(out, (size_t)nv, sizeof(or_pair), pair_cmp);
+}
+
+/*
+ * Def. 2 / Eq. 1: u is pruned by v iff D(p,u) > alpha * D(u,v) + (alpha + 1) * tau.
+ * Evaluated as t = (alpha + 1) * tau once, rhs = alpha * D(u,v) + t, strict '>'.
+ */
+static int rule_prunes(double Dpu, double Duv, double alpha, double t) {
+    double rhs = alpha * Duv + t;
+    return Dpu > rhs;
+}
+
+/* Alg. 2 on candidates already sorted by (D(p,.), id); stops when R points are kept. */
+static int prune_sorted(const float *X, int d, const or_pair *V, int nv, double alpha,
+                        double tau, int R, int32_t *S) {
+    double t = (alpha + 1.0) * tau;
+    int ns = 0;
+    for (int i = 0; i < nv && ns < R; ++i) {
+        int32_t u = V[i].id;
+        int pruned = 0;
+        for (int j = 0; j < ns && !pruned; ++j) {
+            double Duv = or_dist(X + (int64_t)u * d, X + (int64_t)S[j] * d, d);
+            pruned = rule_prunes(V[i].D, Duv, alpha, t);
+        }
+        if (!pruned) S[ns++] = u;
+    }
+    return ns;
+}
+
+/* pruning(p, V, alpha) of Alg. 2 with the out-degree cut at R.  Returns |S|. */
+int or_prune(const float *X, int64_t n, int d, int64_t p, const int32_t *V, int nv,
+             double alpha, double tau, int R, int32_t *S) {
+    (void)n;
+    if (nv < 0 || R <= 0) return OR_E_INVAL;
+    or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * (nv > 0 ? nv : 1));
+    if (!pv) return OR_E_NOMEM;
+    sort_by_distance(X, d, p, V, nv, pv);
+    int ns = prune_sorted(X, d, pv, nv, alpha, tau, R, S);
+    free(pv);
+    return ns;
+}
+
+/*
+ * adaptive-pruning of Alg. 4: alpha_i = alpha0 + i * dalpha for i = 0 .. imax with
+ * imax = round((alpha_max - alpha0) / dalpha); stop at the first S_i with |S_i| >= R/2
+ * (real division); return the R closest points of the last S_i computed.
+ */
+int or_prune_adaptive(const float *X, int64_t n, int d, int64_t p, const int32_t *V, int nv,
+                      double alpha0, double alpha_max, double dalpha, double tau, int R,
+                      int32_t *S, double *alpha_used) {
+    (void)n;
+    if (nv < 0 || R <= 0 || dalpha <= 0.0) return OR_E_INVAL;
+    or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * (nv > 0 ? nv : 1));
+    if (!pv) return OR_E_NOMEM;
+    sort_by_distance(X, d, p, V, nv, pv);
+    int imax = (int)floor((alpha_max - alpha0) / dalpha + 0.5);
+    int ns = 0;
+    double a = alpha0;
+    for (int i = 0; i <= imax; ++i) {
+        a = alpha0 + (double)i * dalpha;
+        /* S_i in full is not needed: its R closest points are its first R members. */
+        ns = prune_sorted(X, d, pv, nv, a, tau, R, S);
+        if ((double)ns >= (double)R / 2.0) break;
+    }
+    if (alpha_used) *alpha_used = a;
+    free(pv);
+    return ns;
+}
+
+/* ---- construction (Alg. 3 phases 1-3, exact candidates, fixed alpha) --------------- */
+
+/*
+ * entry            navigating node
+ * cand  [n][L]     exact candidate lists (may be NULL)
+ * fwd   [n][R]     phase-2 out-lists (pruned candidates), padded with -1
+ * fdeg  [n]
+ * adj   [n][R]     final out-lists after reverse merge + lazy pruning, padded with -1
+ * deg   [n]
+ * Returns 0, or a negative error.
+ */
+int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
+             int32_t *entry, int32_t *cand, int32_t *fwd, int32_t *fdeg, int32_t *adj,
+             int32_t *deg) {
+    if (n < 2 || d <= 0 || R <= 0 || L <= 0 || L >= n) return OR_E_INVAL;
+    int32_t *cl = cand ? cand : (int32_t *)malloc(sizeof(int32_t) * n * L);
+    double *cd = (double *)malloc(sizeof(double) * n * L);
+    if (!cl || !cd) return OR_E_NOMEM;
+    *entry = or_entry(X, n, d);
+    or_knn(X, n, X, n, d, L, 1, cl, cd);
+
+    /* phase 2: prune every candidate list (already sorted by (D, id)) */
+#pragma omp parallel
+    {
+        or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * L);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < n; ++p) {
+            for (int i = 0; i < L; ++i) {
+                pv[i].id = cl[p * L + i];
+                pv[i].D = cd[p * L + i];
+            }
+            int32_t *S = fwd + p * R;
+            int ns = prune_sorted(X, d, pv, L, alpha, tau, R, S);
+            for (int i = ns; i < R; ++i) S[i] = -1;
+            fdeg[p] = ns;
+        }
+        free(pv);
+    }
+    free(cd);
+    if (!cand) free(cl);
+
+    /* phase 3: reverse edges from the phase-2 snapshot, then lazy pruning */
+    int64_t *off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!off) return OR_E_NOMEM;
+    for (int64_t u = 0; u < n; ++u)
+        for (int j = 0; j < fdeg[u]; ++j) off[fwd[u * R + j] + 1] += 1;
+    for (int64_t p = 0; p < n; ++p) off[p + 1] += off[p];
+    int32_t *in = (int32_t *)malloc(sizeof(int32_t) * (off[n] > 0 ? off[n] : 1));
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * n);
+    if (!in || !cur) return OR_E_NOMEM;
+    for (int64_t p = 0; p < n; ++p) cur[p] = off[p];
+    for (int64_t u = 0; u < n; ++u) /* in-lists in ascending u */
+        for (int j = 0; j < fdeg[u]; ++j) in[cur[fwd[u * R + j]]++] = (int32_t)u;
+
+#pragma omp parallel
+    {
+        int cap = 0;
+        int32_t *V = NULL;
+        or_pair *pv = NULL;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < n; ++p) {
+            int nin = (int)(off[p + 1] - off[p]);
+            int need = fdeg[p] + nin;
+            if (need > cap) {
+                cap = need * 2;
+                V = (int32_t *)realloc(V, sizeof(int32_t) * cap);
+                pv = (or_pair *)realloc(pv, sizeof(or_pair) * cap);
+            }
+            int nv = 0;
+            for (int j = 0; j < fdeg[p]; ++j) V[nv++] = fwd[p * R + j];
+            for (int j = 0; j < nin; ++j) {
+                int32_t u = in[off[p] + j], dup = 0;
+                for (int t = 0; t < fdeg[p] && !dup; ++t) dup = (fwd[p * R + t] == u);
+                if (!dup) V[nv++] = u;
+            }
+            sort_by_distance(X, d, p, V, nv, pv);
+            int32_t *A = adj + p * R;
+            int na;
+            if (nv <= R) { /* assigned directly, kept in (D, id) order */
+                for (int i = 0; i < nv; ++i) A[i] = pv[i].id;
+                na = nv;
+            } else {
+                na = prune_sorted(X, d, pv, nv, alpha, tau, R, A);
+            }
+            for (int i = na; i < R; ++i) A[i] = -1;
+            deg[p] = na;
+        }
+        free(V);
+        free(pv);
+    }
+    free(in);
+    free(cur);
+    free(off);
+    return OR_OK;
+}
+
+/* ---- beam search (Alg. 1) ----------------------------------------------------------- */
+
+typedef struct {
+    double D;
+    int32_t id;
+    int32_t explored;
+} or_qent;
+
+/*
+ * Alg. 1 from entry s with queue size L, returning the k closest entries of Q.
+ * A visited set skips points whose distance was already computed; this returns the same
+ * ids as the set-union form of Alg. 1 because a point dropped from Q can never re-enter
+ * it (the L-th key of Q never increases once Q is full).
+ * ndc counts distance computations (the entry included); hops counts hop vertices.
+ * Rows of out_ids / out_d beyond |Q| are -1 / +inf.
+ */
+int or_search(const float *X, int64_t n, int d, const int32_t *adj, const int32_t *deg, int R,
+              int32_t s, const float *Qv, int64_t nq, int k, int L, int32_t *out_ids,
+              double *out_d, int32_t *ndc_out, int32_t *hops_out) {
+    if (n <= 0 || k <= 0 || L < k || s < 0 || s >= n) return OR_E_INVAL;
+    int err = 0;
+#pragma omp parallel
+    {
+        unsigned char *vis = (unsigned char *)calloc((size_t)n, 1);
+        int32_t *touched = NULL;
+        int64_t tcap = 0;
+        or_qent *Q = (or_qent *)malloc(sizeof(or_qent) * (L + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            const float *q = Qv + qi * (int64_t)d;
+            int64_t nt = 0;
+            int len = 1;
+            Q[0].D = or_dist(q, X + (int64_t)s * d, d);
+            Q[0].id = s;
+            Q[0].explored = 0;
+            vis[s] = 1;
+            if (nt >= tcap) {
+                tcap = tcap ? tcap * 2 : 4096;
+                touched = (int32_t *)realloc(touched, sizeof(int32_t) * tcap);
+            }
+            touched[nt++] = s;
+            int32_t ndc = 1, hops = 0;
+            for (;;) {
+                int i = 0;
+                while (i < len && Q[i].explored) ++i;
+                if (i == len) break;
+                Q[i].explored = 1;
+                ++hops;
+                int32_t u = Q[i].id;
+                for (int j = 0; j < deg[u]; ++j) {
+                    int32_t v = adj[(int64_t)u * R + j];
+                    if (vis[v]) continue;
+                    vis[v] = 1;
+                    if (nt >= tcap) {
+                        tcap *= 2;
+                        touched = (int32_t *)realloc(touched, sizeof(int32_t) * tcap);
+                    }
+                    touched[nt++] = v;
+                    ++ndc;
+                    double D = or_dist(q, X + (int64_t)v * d, d);
+                    if (len < L || key_less(D, v, Q[len - 1].D, Q[len - 1].id)) {
+                        int pos = (len < L) ? len : L - 1;
+                        while (pos > 0 && key_less(D, v, Q[pos - 1].D, Q[pos - 1].id)) {
+                            Q[pos] = Q[pos - 1];
+                            --pos;
+                        }
+                        Q[pos].D = D;
+                        Q[pos].id = v;
+                        Q[pos].explored = 0;
+                        if (len < L) ++len;
+                    }
+                }
+            }
+            for (int t = 0; t < k; ++t) {
+                out_ids[qi * k + t] = t < len ? Q[t].id : -1;
+                out_d[qi * k + t] = t < len ? Q[t].D : INFINITY;
+            }
+            if (ndc_out) ndc_out[qi] = ndc;
+            if (hops_out) hops_out[qi] = hops;
+            for (int64_t t = 0; t < nt; ++t) vis[touched[t]] = 0;
+        }
+        free(vis);
+        free(touched);
+        free(Q);
+    }
+    return err;
+}
+
+/* Number of OpenMP threads the oracle uses (1 without OpenMP). */
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,121 @@
+"""Seeded synthetic workloads shaped like the paper's evaluation data (Sec. 5.1, Table 2).
+
+The paper evaluates on public vector collections (SIFT, DEEP, GIST, BIGANN, ...).  None of
+them is available here, so every workload below is a seeded synthetic stand-in with the
+same size, dimensionality, value range and cluster structure.  No record of any of those
+collections is reproduced.
+
+This module holds only random-number recipes.  It contains none of the method's
+arithmetic, so both the CUDA path and the CPU oracle may read its output.
+
+Recipes (numpy ``Generator(PCG64(seed))``, rows generated in fixed chunks so the output
+does not depend on memory limits):
+
+* ``gauss``      i.i.d. N(0, 1) float32.
+* ``sift``       64 centres uniform on the integers 40..215 per dimension, isotropic
+                 N(0, 25^2) noise, clipped to [0, 255] and rounded to integers (float32).
+* ``deep``       256 centres mu = g / ||g||, g ~ N(0, I); x = normalise(mu + 0.5 g' / sqrt(d)).
+* ``gist``       100 centres N(0, I); per (centre, dimension) standard deviation
+                 sqrt(v), v log-uniform on [0.01, 1].
+* ``bigann16``   1,024 centres N(0, I), noise N(0, 0.5^2), stored as float16.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+_CHUNK = 1 << 16  # rows drawn per chunk; fixed so results are independent of memory
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One seeded workload: base points, query points and training queries."""
+
+    name: str
+    kind: str
+    n: int
+    d: int
+    nq: int
+    k: int
+    alpha: float
+    R: int
+    L: int
+    n_train: int
+    seed: int
+    dtype: str = "float32"
+
+    def base(self, n: int | None = None) -> np.ndarray:
+        return generate(self.kind, self.n if n is None else n, self.d, self.seed, self.dtype)
+
+    def queries(self, nq: int | None = None) -> np.ndarray:
+        return generate(self.kind, self.nq if nq is None else nq, self.d, 1000 + self.seed, self.dtype,
+                        centre_seed=self.seed)
+
+    def train_queries(self, nt: int | None = None) -> np.ndarray:
+        return generate(self.kind, self.n_train if nt is None else nt, self.d, 2000 + self.seed,
+                        self.dtype, centre_seed=self.seed)
+
+
+# The five workloads: sizes and parameters of the hot-path scope table.
+WORKLOADS = {
+    "gauss10k": Workload("gauss10k", "gauss", 10_000, 32, 100, 10, 1.2, 32, 64, 2_000, 0),
+    "sift1m": Workload("sift1m", "sift", 1_000_000, 128, 10_000, 10, 1.2, 32, 128, 20_000, 1),
+    "deep1m": Workload("deep1m", "deep", 1_000_000, 96, 10_000, 10, 1.3, 48, 160, 20_000, 2),
+    "gist1m": Workload("gist1m", "gist", 1_000_000, 960, 1_000, 10, 1.2, 32, 128, 2_000, 3),
+    "bigann10m": Workload("bigann10m", "bigann16", 10_000_000, 128, 100_000, 10, 1.2, 32, 128,
+                          200_000, 4, "float16"),
+}
+
+
+def _centres(kind: str, d: int, seed: int):
+    """Cluster centres (and per-centre scales) drawn from their own stream."""
+    rng = np.random.Generator(np.random.PCG64(seed * 7919 + 17))
+    if kind == "sift":
+        return rng.integers(40, 216, size=(64, d)).astype(np.float32), None
+    if kind == "deep":
+        g = rng.standard_normal((256, d))
+        return (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32), None
+    if kind == "gist":
+        c = rng.standard_normal((100, d)).astype(np.float32)
+        v = np.exp(rng.uniform(np.log(0.01), np.log(1.0), size=(100, d))).astype(np.float32)
+        return c, np.sqrt(v).astype(np.float32)
+    if kind == "bigann16":
+        return rng.standard_normal((1024, d)).astype(np.float32), None
+    return None, None
+
+
+def generate(kind: str, n: int, d: int, seed: int, dtype: str = "float32",
+             centre_seed: int | None = None) -> np.ndarray:
+    """Return ``n`` rows of workload ``kind`` in dimension ``d`` (C-contiguous)."""
+    if n < 0 or d <= 0:
+        raise ValueError("n must be >= 0 and d > 0")
+    centres, scales = _centres(kind, d, seed if centre_seed is None else centre_seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty((n, d), dtype=np.float16 if dtype == "float16" else np.float32)
+    for r0 in range(0, n, _CHUNK):
+        m = min(_CHUNK, n - r0)
+        if kind == "gauss":
+            blk = rng.standard_normal((m, d), dtype=np.float32)
+        elif kind == "sift":
+            a = rng.integers(0, centres.shape[0], size=m)
+            blk = centres[a] + 25.0 * rng.standard_normal((m, d), dtype=np.float32)
+            blk = np.rint(np.clip(blk, 0.0, 255.0))
+        elif kind == "deep":
+            a = rng.integers(0, centres.shape[0], size=m)
+            blk = centres[a] + (0.5 / np.sqrt(d)) * rng.standard_normal((m, d), dtype=np.float32)
+            blk = blk / np.linalg.norm(blk, axis=1, keepdims=True)
+        elif kind == "gist":
+            a = rng.integers(0, centres.shape[0], size=m)
+            blk = centres[a] + scales[a] * rng.standard_normal((m, d), dtype=np.float32)
+        elif kind == "bigann16":
+            a = rng.integers(0, centres.shape[0], size=m)
+            blk = centres[a] + 0.5 * rng.standard_normal((m, d), dtype=np.float32)
+        else:
+            raise ValueError(f"unknown workload kind {kind!r}")
+        out[r0:r0 + m] = blk
+    return out
+
+
+def small(kind: str, n: int, d: int, seed: int = 0) -> np.ndarray:
+    """Convenience: ``n`` base rows of ``kind`` for parity tests at reduced size."""
+    return generate(kind, n, d, seed)

@@ -1,0 +1,155 @@
+"""Pins for the oracle's pruning (Def. 2 / Eq. 1, Alg. 2, Alg. 4) and construction (Alg. 3)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_05975_gb300 import synth
+
+
+def _load(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as f:
+        return json.load(f)
+
+
+def test_hand_worked_2d_example(golden_dir):
+    g = _load(golden_dir, "prune_2d.json")
+    names = list(g["points"])
+    X = np.array([g["p"]] + [g["points"][k] for k in names], np.float32)
+    V = np.arange(1, len(names) + 1, dtype=np.int32)[::-1].copy()  # any input order
+    for case in g["cases"]:
+        S = oracle.prune(X, 0, V, case["alpha"], case["tau"], case["R"])
+        assert [names[i - 1] for i in S] == case["kept"], case["why"]
+    a = g["adaptive"]
+    S, alpha = oracle.prune_adaptive(X, 0, V, a["alpha0"], a["alpha_max"], a["dalpha"], a["tau"], a["R"])
+    assert [names[i - 1] for i in S] == a["kept"], a["why"]
+    assert alpha == pytest.approx(a["alpha"], abs=1e-12)
+
+
+def test_adaptive_reaches_alpha_max_exactly():
+    # 0.9 + 14 * 0.05 accumulated by repeated addition exceeds 1.6; the oracle must still try 1.6.
+    X = np.array([[0, 0], [1, 0], [1.2, 0.1], [1.3, -0.1]], np.float32)
+    S, alpha = oracle.prune_adaptive(X, 0, [1, 2, 3], 0.9, 1.6, 0.05, 0.0, 100)
+    assert alpha == pytest.approx(1.6, abs=1e-12)
+
+
+def test_equality_keeps_the_candidate():
+    # Eq. 1 is strict: D(p,u) == alpha * D(u,v) + (alpha+1) tau keeps u.
+    # p=0, v at 1, u at 2 on a line: D(p,u) = 2, D(u,v) = 1; alpha = 2, tau = 0 -> equality.
+    X = np.array([[0.0], [1.0], [2.0]], np.float32)
+    assert oracle.prune(X, 0, [1, 2], 2.0, 0.0, 10).tolist() == [1, 2]
+    assert oracle.prune(X, 0, [1, 2], 1.5, 0.0, 10).tolist() == [1]
+
+
+def test_merge_hand_worked(golden_dir):
+    g = _load(golden_dir, "merge_2d.json")
+    X = np.array(g["points"], np.float32)
+    for case in g["cases"]:
+        G = oracle.build_graph(X, g["alpha"], g["tau"], case["R"], g["L"])
+        assert G.cand.tolist() == g["cand"]
+        assert [G.fwd[p, : G.fdeg[p]].tolist() for p in range(len(X))] == g["fwd"]
+        assert [G.out(p).tolist() for p in range(len(X))] == case["adj"]
+
+
+def _alpha_cg(X, alpha, tau):
+    """alpha-CG of Def. 3: pruning over P \\ {p}, no degree bound."""
+    n = len(X)
+    return [oracle.prune(X, p, np.array([u for u in range(n) if u != p], np.int32), alpha, tau, n)
+            for p in range(n)]
+
+
+def _scaled_points(n, d, seed):
+    """Random points scaled so the minimum pairwise distance is exactly 1 (Sec. 2.1)."""
+    X = synth.generate("gauss", n, d, seed=seed).astype(np.float64)
+    D = np.linalg.norm(X[:, None] - X[None], axis=2)
+    D[np.diag_indices(n)] = np.inf
+    return (X / D.min()).astype(np.float32)
+
+
+@pytest.mark.parametrize("alpha,tau,seed", [(1.2, 1.0, 1), (1.5, 2.0, 2), (1.1, 1.5, 3)])
+def test_lemma1_alpha_reducible_and_lemma3_hops(alpha, tau, seed):
+    """Lemma 1 and Lemma 3 on the alpha-CG: for q with D(q, v*) <= tau every p != v* has v*
+    or a neighbour p' with D(p', q) <= D(p, q) / alpha, and greedy routing (L = 1) reaches v*
+    within log_alpha(4 Delta) + 2 hop vertices."""
+    n, d = 120, 3
+    X = _scaled_points(n, d, seed)
+    G = _alpha_cg(X, alpha, tau)
+    deg = np.array([len(s) for s in G], np.int32)
+    adj = np.full((n, max(deg)), -1, np.int32)
+    for p, s in enumerate(G):
+        adj[p, : len(s)] = s
+    X64 = X.astype(np.float64)
+    diam = max(np.linalg.norm(X64[i] - X64, axis=1).max() for i in range(n))
+    bound = math.log(4 * diam) / math.log(alpha) + 2
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for _ in range(60):
+        v = int(rng.integers(n))
+        off = rng.standard_normal(d)
+        q = X64[v] + off / np.linalg.norm(off) * rng.uniform(0, tau)
+        dq = np.linalg.norm(X64 - q, axis=1)
+        vstar = int(np.argmin(dq))
+        if dq[vstar] > tau:
+            continue
+        checked += 1
+        for p in range(n):
+            if p == vstar:
+                continue
+            nb = G[p]
+            assert vstar in nb or any(dq[u] <= dq[p] / alpha for u in nb)
+        for s in rng.integers(0, n, size=5):
+            ids, _, _, hops = oracle.search(X, adj, deg, int(s), q[None].astype(np.float32), 1, 1)
+            assert ids[0, 0] == vstar
+            assert hops[0] <= bound
+    assert checked >= 20
+
+
+@pytest.mark.parametrize("alpha,tau", [(1.2, 0.0), (1.3, 0.5)])
+def test_alpha_shortcut_reachability(alpha, tau):
+    """Every non-edge (p, z) of the alpha-CG has an out-neighbour p' of p with
+    D(p', z) < D(p, z) / alpha (the shortcut-reachability argument of Sec. 3.3)."""
+    n = 90
+    X = _scaled_points(n, 2, 7)
+    X64 = X.astype(np.float64)
+    G = _alpha_cg(X, alpha, tau)
+    for p in range(n):
+        nb = set(G[p])
+        for z in range(n):
+            if z == p or z in nb:
+                continue
+            dz = np.linalg.norm(X64[list(nb)] - X64[z], axis=1)
+            assert dz.min() < np.linalg.norm(X64[p] - X64[z]) / alpha
+
+
+def test_build_invariants_random():
+    X = synth.generate("gauss", 600, 8, seed=9)
+    R, L, alpha, tau = 8, 24, 1.2, 0.05
+    G = oracle.build_graph(X, alpha, tau, R, L)
+    n = len(X)
+    # phase 2 lists are exactly Alg. 2 on the exact candidate lists
+    for p in range(0, n, 37):
+        assert G.fwd[p, : G.fdeg[p]].tolist() == oracle.prune(X, p, G.cand[p], alpha, tau, R).tolist()
+    inl = [[] for _ in range(n)]
+    for u in range(n):
+        for v in G.fwd[u, : G.fdeg[u]]:
+            inl[v].append(u)
+    for p in range(n):
+        out = G.out(p).tolist()
+        assert len(out) == G.deg[p] <= R and len(set(out)) == len(out) and p not in out
+        V = list(dict.fromkeys(G.fwd[p, : G.fdeg[p]].tolist() + inl[p]))
+        if len(V) <= R:
+            assert sorted(out) == sorted(V)  # assigned directly
+        else:
+            assert set(out) <= set(V)
+
+
+def test_phase2_equals_alpha_cg_when_unbounded():
+    X = _scaled_points(60, 2, 4)
+    n = len(X)
+    G = oracle.build_graph(X, 1.3, 0.2, n, n - 1)
+    cg = _alpha_cg(X, 1.3, 0.2)
+    for p in range(n):
+        assert G.fwd[p, : G.fdeg[p]].tolist() == cg[p].tolist()
