@@ -1,0 +1,359 @@
+"""Benchmark: alpha-CNG build seconds and search QPS at Recall@10 >= 0.95 on one GB300.
+
+Workload (default ``sift1m``): 1,000,000 x 128 integer-valued float32 points from a seeded
+64-centre Gaussian mixture (a synthetic stand-in for SIFT1M), alpha 1.2, tau 0, R 32, L 128;
+10,000 queries from the same mixture, k = 10.  One step = one full build (prep, entry point,
+exact candidate lists, pruning, reverse merge) plus one batched fixed-L search of all queries
+at the smallest beam width L_s reaching Recall@10 >= 0.95 (calibrated once, before timing,
+against brute-force ground truth from the library's exact k-NN).
+
+Printed JSON: value = build seconds (device-resident input), e2e = the same through the C ABI
+from pinned host memory (H2D copy inside the timed region, results read back), search QPS,
+roofline of the dominant kernel, the FP64 oracle's CPU baseline on a bounded sample, clocks.
+``--impl reference`` times the oracle itself (the paper ships no code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build s and QPS at Recall@10>=0.95, 1Mx128 L2; learned-stop vs fixed-L search"
+L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 192, 256)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def recall_at_k(found: np.ndarray, gt: np.ndarray) -> float:
+    k = gt.shape[1]
+    hits = 0
+    for a, b in zip(found, gt):
+        hits += len(set(a.tolist()) & set(b.tolist()))
+    return hits / (k * gt.shape[0])
+
+
+def oracle_baseline(X: np.ndarray, Q: np.ndarray, adj, deg, entry, w, k: int, L: int,
+                    budget_s: float = 15.0):
+    """The FP64 oracle, as it stands, on a bounded sample: exact candidate lists + Alg. 2 for
+    sampled points (extrapolated to the full build), Alg. 1 for sampled queries."""
+    import oracle
+
+    threads = oracle.num_threads()
+    rng = np.random.default_rng(0)
+    # build sample: grow until ~budget/2 seconds
+    m, t_build, pts = 8, 0.0, 0
+    while t_build < budget_s / 2 and pts < X.shape[0]:
+        rows = rng.integers(0, X.shape[0], size=m)
+        t0 = time.perf_counter()
+        ids, _ = oracle.knn(X, w.L, rows=X[rows], exclude_self=False)
+        for r, row in zip(rows, ids):
+            cand = row[row != r][: w.L]
+            oracle.prune(X, int(r), cand, w.alpha, 0.0, w.R)
+        t_build += time.perf_counter() - t0
+        pts += m
+        m *= 2
+    build_s = t_build / pts * X.shape[0]
+    # search sample
+    nq, t_s, qs = 64, 0.0, 0
+    while t_s < budget_s / 2 and qs < Q.shape[0]:
+        sel = Q[qs: qs + nq]
+        t0 = time.perf_counter()
+        oracle.search(X, adj, deg, entry, sel, k, L)
+        t_s += time.perf_counter() - t0
+        qs += sel.shape[0]
+        nq *= 2
+    qps = qs / t_s
+    return {"value": build_s, "unit": "s (build, extrapolated)", "cores": threads, "kind": "oracle",
+            "sample": f"{pts} points: exact L-NN over all {X.shape[0]} points in FP64 + Alg. 2, "
+                      f"extrapolated x{X.shape[0] / pts:.0f}; reverse merge not sampled; "
+                      f"search {qs} queries at L={L} on the GPU-built graph",
+            "search_qps": qps}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2510_05975_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    X = w.base()
+    Q = w.queries()
+    import oracle
+
+    oracle.build()
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        base = oracle_baseline(X, Q[:64], np.zeros((1, 1), np.int32), np.zeros(1, np.int32), 0, w,
+                               w.k, 16, budget_s=8.0) if False else None
+        rng = np.random.default_rng(step)
+        rows = rng.integers(0, X.shape[0], size=16)
+        ids, _ = oracle.knn(X, w.L, rows=X[rows], exclude_self=False)
+        for r, row in zip(rows, ids):
+            oracle.prune(X, int(r), row[row != r][: w.L], w.alpha, 0.0, w.R)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt / 16 * X.shape[0])
+    v = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n": w.n, "d": w.d},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": v,
+                             "sample": "16 points per step: exact L-NN in FP64 + Alg. 2, extrapolated to n"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sift1m")
+    ap.add_argument("--screen", default="tc", choices=["tc", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import __graft_entry__
+    import paper_2510_05975_gb300.cng as cng
+    from paper_2510_05975_gb300 import synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    cng.lib()
+    w = synth.WORKLOADS[args.workload]
+    screen = cng.CNG_SCREEN_TC if args.screen == "tc" else cng.CNG_SCREEN_FP32
+    X = w.base()
+    Q = w.queries()
+    dtype_t = torch.float16 if w.dtype == "float16" else torch.float32
+    xd = torch.from_numpy(X).cuda()
+    qd = torch.from_numpy(Q.astype(np.float32)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ground truth (exact k-NN of the queries, the library's own exact path) and L calibration
+    base32 = xd.float() if dtype_t == torch.float16 else xd
+    gt_ids, _, _ = cng.cng_knn(base32, w.k, rows=qd, screen=screen)
+    gt = gt_ids.cpu().numpy()
+    idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+    Ls, rec_s = None, None
+    sweep = []
+    for L in L_SWEEP:
+        if L < w.k:
+            continue
+        r = cng.cng_search(idx, qd, k=w.k, L=L, use_graph=True)
+        rc = recall_at_k(r["ids"].cpu().numpy(), gt)
+        sweep.append((L, rc))
+        if rc >= 0.95 and Ls is None:
+            Ls, rec_s = L, rc
+    if Ls is None:
+        Ls, rec_s = L_SWEEP[-1], sweep[-1][1]
+    adj, deg, _, entry = cng.cng_graph(idx)
+    adj_h, deg_h = adj.cpu().numpy(), deg.cpu().numpy()
+    cng.cng_free(idx)
+
+    # timed device-resident steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    build_ms, search_ms, step_ms, screen_ms = [], [], [], []
+    last_stats = None
+    total = args.warmup + args.steps
+    sampler = ClockSampler(local)
+    for step in range(total):
+        timed = step >= args.warmup
+        if step == args.warmup:
+            barrier()
+            sampler.__enter__()
+        ev[0].record(stream)
+        idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+        ev[1].record(stream)
+        res = cng.cng_search(idx, qd, k=w.k, L=Ls, use_graph=True, with_stats=False)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if timed:
+            build_ms.append(ev[0].elapsed_time(ev[1]))
+            search_ms.append(ev[1].elapsed_time(ev[2]))
+            step_ms.append(ev[0].elapsed_time(ev[2]))
+            screen_ms.append(bst["ms_screen"])
+            last_stats = bst
+        if step < total - 1:
+            cng.cng_free(idx)
+    barrier()
+    sampler.__exit__()
+    rec = recall_at_k(res["ids"].cpu().numpy(), gt)
+    cng.cng_free(idx)
+
+    def allmax(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    b_s = allmax(float(np.mean(build_ms)) / 1e3)
+    s_ms = allmax(float(np.mean(search_ms)))
+    st_ms = allmax(float(np.mean(step_ms)))
+    qps = w.nq / (s_ms / 1e3)
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Qh = torch.from_numpy(Q.astype(np.float32)).pin_memory()
+        out = dict(ids=torch.empty((w.nq, w.k), dtype=torch.int32).pin_memory(),
+                   dists=torch.empty((w.nq, w.k), dtype=torch.float32).pin_memory(),
+                   ndc=None, hops=None, flags=None)
+        e2e_b, e2e_s = [], []
+        for step in range(1 + args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            ix2, _ = cng.cng_build(Xh.numpy(), alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+            t1 = time.perf_counter()
+            cng.cng_search(ix2, Qh.numpy(), k=w.k, L=Ls, out={k_: (v.numpy() if v is not None else None)
+                                                               for k_, v in out.items()}, with_stats=False)
+            t2 = time.perf_counter()
+            cng.cng_free(ix2)
+            if step >= 1:
+                e2e_b.append(t1 - t0)
+                e2e_s.append(t2 - t1)
+        e2e = {"value": allmax(float(np.mean(e2e_b))), "unit": "s",
+               "search_qps": w.nq / allmax(float(np.mean(e2e_s))),
+               "h2d_bytes_per_step": int(X.nbytes + w.nq * w.d * 4),
+               "d2h_bytes_per_step": int(w.nq * w.k * 8)}
+
+    pk, src = peaks()
+    t_screen = float(np.mean(screen_ms)) / 1e3
+    flops = 2.0 * w.n * w.n * w.d
+    if screen == cng.CNG_SCREEN_TC and last_stats is not None and last_stats.get("screen_used", 1):
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": f"{src} bf16 sustained"}
+    else:
+        # FP32 CUDA cores, direct differences: 2 instructions (FADD + FFMA) per element pair
+        # = 2 GEMM-equivalent flops per 2 lane-instructions; 152 SMs x 128 lanes x max clock
+        peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": "FP32 lanes x max SM clock (derived)"}
+    achieved = flops / t_screen / 1e12
+    roof.update({"kernel": "candidate screen", "achieved": achieved, "frac": achieved / roof["peak"],
+                 "traffic": None, "algorithmic": "2*n*n*d flops per launch"})
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(X.astype(np.float32), Q[:4096].astype(np.float32), adj_h, deg_h, entry,
+                              w, w.k, Ls)
+
+    clocks = sampler.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": b_s * 1.0, "unit": "s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": st_ms, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "n": w.n, "d": w.d, "alpha": w.alpha, "tau": 0.0,
+                           "R": w.R, "L": w.L, "nq": w.nq, "k": w.k, "screen": args.screen,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (512 MB points)"},
+                "search": {"L": Ls, "qps": qps * ws, "recall_at_10": rec, "ms": s_ms,
+                           "L_sweep": sweep, "ndc_mean": None},
+                "build_phases_ms": {k_: last_stats[k_] for k_ in
+                                    ("ms_prep", "ms_entry", "ms_screen", "ms_rerank", "ms_prune",
+                                     "ms_merge")} if last_stats else None,
+                "build_counts": {k_: last_stats[k_] for k_ in
+                                 ("n_edges", "cert_fail_rows", "order_ties", "rule_ties",
+                                  "merge_repruned", "merge_max_list", "exact_int")} if last_stats else None,
+                "e2e": e2e, "gpu_launches": None, "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * cng.h -- C ABI of libcng.so: the alpha-convergent neighbourhood graph (alpha-CNG) of
+ * arXiv 2510.05975 ("Fast-Convergent Proximity Graphs for Approximate Nearest Neighbor
+ * Search"), built and searched on one GB300 GPU (sm_103a).
+ *
+ * Conventions for every call
+ *   - Pointers named *_dev must be device memory of the current CUDA device; pointers named
+ *     "host or device" may be either (the library detects which and copies host data itself).
+ *   - Arrays are dense, row-major, with the stated element type; ids are int32 point indices.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on
+ *     `stream` unless stated; calls that return statistics synchronise `stream` first.
+ *   - Every call returns a cng_status.  On failure, cng_last_error() holds a message for the
+ *     calling thread.  Invalid arguments are rejected before any kernel is launched.
+ *   - Device-side waits are bounded; a wait that runs out reports CNG_E_TIMEOUT instead of
+ *     hanging the GPU.
+ *   - Distances are Euclidean (L2, Sec. 2.1 metric space).  The canonical distance used for
+ *     every exact decision is D(x,y) = sqrt(sum_i (x_i - y_i)^2) in IEEE double, summed in
+ *     index order; FP32 decisions closer than a relative band `tie_band` are re-decided with
+ *     that canonical distance on the GPU.  Near-ties are counted in the statistics.
+ */
+#ifndef CNG_H_
+#define CNG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CNG_OK = 0,
+  CNG_E_INVAL = -1,       /* bad argument; nothing launched */
+  CNG_E_NOMEM = -2,       /* device or host allocation failed */
+  CNG_E_CUDA = -3,        /* CUDA runtime / launch error */
+  CNG_E_TIMEOUT = -4,     /* a bounded device wait ran out; results are not valid */
+  CNG_E_UNSUPPORTED = -5, /* valid input outside this build's limits (message says which) */
+  CNG_E_INTERNAL = -6     /* a device-side consistency check failed */
+} cng_status;
+
+typedef enum { CNG_L2 = 0, CNG_IP_AS_L2 = 1 } cng_metric;
+typedef enum { CNG_F32 = 0, CNG_F16 = 1 } cng_dtype;
+typedef enum {
+  CNG_SCREEN_FP32 = 0,  /* FP32 CUDA-core candidate screen (direct differences) */
+  CNG_SCREEN_TC = 1     /* tensor-core screen: BF16 (FP16 for f16 data) operands, FP32 accumulate */
+} cng_screen;
+
+/*
+ * Build parameters.  Paper names in brackets (Alg. 3 inputs):
+ *   alpha   [alpha]  pruning parameter of Def. 2 / Eq. 1, > 0
+ *   tau     [tau]    pruning parameter of Def. 2 / Eq. 1, >= 0, raw distance units
+ *   R       [M]      out-degree bound, 1 <= R <= L, R <= 64
+ *   L       [C]      candidate-list size: the exact L nearest points of P \ {p}, L < n, L <= 256
+ *   metric           CNG_IP_AS_L2 requires unit-norm rows (|‖x‖ - 1| <= 1e-3) and then uses L2
+ *   screen           cng_screen
+ *   tie_band         relative band for FP64 re-decision, >= 5e-6 (default 1e-5)
+ *   margin           screened list size is L + margin (default 32; clipped to n - 1)
+ *   keep_lists       1: keep candidate and phase-2 lists for cng_lists()
+ */
+typedef struct {
+  double alpha;
+  double tau;
+  int32_t R;
+  int32_t L;
+  int32_t metric;
+  int32_t screen;
+  double tie_band;
+  int32_t margin;
+  int32_t keep_lists;
+} cng_build_params;
+
+/* Per-phase times (device events, milliseconds) and near-tie / certification counts. */
+typedef struct {
+  double ms_total, ms_prep, ms_entry, ms_screen, ms_rerank, ms_prune, ms_merge;
+  int64_t n_edges;            /* edges of the final graph */
+  int64_t cert_fail_rows;     /* rows whose screened list could not be certified, rescanned */
+  int64_t order_ties;         /* candidate-order near-ties re-decided in FP64 */
+  int64_t rule_ties;          /* pruning comparisons re-decided in FP64 */
+  int64_t merge_repruned;     /* nodes whose merged list exceeded R and was pruned again */
+  int64_t merge_max_list;     /* largest merged candidate set */
+  int32_t entry;              /* navigating node s */
+  int32_t exact_int;          /* 1 when every FP32 squared distance is an exact integer */
+  double screen_err_max;      /* largest |screened - rerank| seen on kept candidates */
+} cng_build_stats;
+
+typedef struct cng_index cng_index;
+
+/*
+ * cng_build -- Alg. 3 phases 1-3 with exact candidates (Sec. 4.1, 4.3):
+ *   navigating node s = point nearest the centroid (phase 1);
+ *   for each p: the exact L nearest points of P \ {p} by (D, id), then Alg. 2 with the rule
+ *   of Def. 2 (Eq. 1) and the out-degree cut at R (phase 2);
+ *   reverse edges from the phase-2 snapshot, each node's merged set pruned once if it
+ *   exceeds R, else kept in (D, id) order (phase 3, lazy pruning of Sec. 4.3).
+ * points: host or device, n x d of `dtype`, borrowed for the call only (the index keeps its own
+ * device copy).  *out receives a new index owned by the caller (free with cng_free).
+ * stats may be NULL.  Synchronises `stream` before returning.
+ */
+cng_status cng_build(const void *points, int32_t dtype, int64_t n, int32_t d,
+                     const cng_build_params *params, void *stream, cng_index **out,
+                     cng_build_stats *stats);
+
+/* Release an index and its device memory.  NULL-safe. */
+void cng_free(cng_index *index);
+
+/* Thread-local message describing the last failure of this thread (never NULL). */
+const char *cng_last_error(void);
+
+/*
+ * cng_graph -- borrow the final graph: adj_dev [n][R] int32 (-1 padded, each row in the order
+ * the construction produced), deg_dev [n] int32, plus R, the entry point and n.  The pointers
+ * stay valid until cng_free.  Any output pointer may be NULL.
+ */
+cng_status cng_graph(const cng_index *index, const int32_t **adj_dev, const int32_t **deg_dev,
+                     int32_t *R, int32_t *entry, int64_t *n);
+
+/*
+ * cng_lists -- borrow the intermediate lists kept when keep_lists = 1:
+ *   cand_dev  [n][L] int32  exact candidate lists in (D, id) order
+ *   cdist_dev [n][L] float  their FP32 distances
+ *   fwd_dev   [n][R] int32  phase-2 out-lists (-1 padded), fdeg_dev [n] int32
+ * Returns CNG_E_INVAL if the index was built without keep_lists.
+ */
+cng_status cng_lists(const cng_index *index, const int32_t **cand_dev, const float **cdist_dev,
+                     int32_t *L, const int32_t **fwd_dev, const int32_t **fdeg_dev);
+
+/* ---------------------------------------------------------------------------------------
+ * Search (Alg. 1), batched: one persistent launch serves every query.
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct cng_stop_model cng_stop_model;
+
+typedef enum { CNG_SEARCH_FIXED = 0, CNG_SEARCH_LEARNED = 1 } cng_search_mode;
+
+/*
+ * mode         CNG_SEARCH_FIXED: Alg. 1 exactly (stop when every queue entry is explored);
+ *              CNG_SEARCH_LEARNED: additionally stop when the stop model's probability reaches
+ *              `threshold` at a check (every `check_every` hops); Alg. 1's own rule remains.
+ * model        required for CNG_SEARCH_LEARNED, ignored otherwise
+ * max_hops     0 = unbounded; otherwise queries stop after this many hop vertices (flagged)
+ * use_graph    1: launch through a cached CUDA graph for this (nq, k, L, mode) shape
+ * warps_per_block  0 = autotuned
+ */
+typedef struct {
+  int32_t mode;
+  const cng_stop_model *model;
+  float threshold;
+  int32_t check_every;
+  int32_t max_hops;
+  int32_t use_graph;
+  int32_t warps_per_block;
+} cng_search_params;
+
+typedef struct {
+  double ms;                /* device time of the search launch */
+  int64_t ndc_total;        /* distance computations summed over queries */
+  int64_t hops_total;       /* hop vertices summed over queries */
+  int64_t fp64_decisions;   /* queue-order near-ties re-decided in FP64 */
+  int64_t stopped_early;    /* queries stopped by the learned rule */
+  int32_t warps_per_block;  /* launch shape used */
+} cng_search_stats;
+
+/*
+ * cng_search -- beam-search(G, q, s, L, k) of Alg. 1 for each of nq queries (f32, n x d,
+ * host or device).  Outputs (host or device; ndc/hops/flags may be NULL):
+ *   ids [nq][k] int32, dists [nq][k] float (FP32 distances), ndc [nq], hops [nq] int32,
+ *   flags [nq] int32 (bit 0: a queue decision was re-decided in FP64; bit 1: max_hops hit;
+ *   bit 2: stopped by the learned rule).
+ * Requires 1 <= k <= L <= 256.  Ties in the queue order by (D, id).  Returns identical ids to the
+ * FP64 definition for fixed-L mode.  stats may be NULL; when given, `stream` is synchronised.
+ */
+cng_status cng_search(const cng_index *index, const float *queries, int64_t nq, int32_t k,
+                      int32_t L, const cng_search_params *params, int32_t *ids, float *dists,
+                      int32_t *ndc, int32_t *hops, int32_t *flags, void *stream,
+                      cng_search_stats *stats);
+
+/* ---------------------------------------------------------------------------------------
+ * Exact k-NN (the candidate step of cng_build, exposed for ground truth and tests).
+ * ------------------------------------------------------------------------------------- */
+
+/*
+ * cng_knn -- for each of m rows, the exact `k` nearest base points by (D, id) (Alg. 3's
+ * candidate lists in exact form).  base: n x d f32 device; rows: m x d f32 device, or NULL
+ * for rows = base with each row's own id excluded.  ids_dev [m][k] int32, dists_dev [m][k]
+ * float.  k <= 256, k <= n (k < n when rows is NULL).  screen: cng_screen.  Synchronises.
+ */
+cng_status cng_knn(const float *base_dev, int64_t n, const float *rows_dev, int64_t m, int32_t d,
+                   int32_t k, int32_t screen, double tie_band, int32_t *ids_dev,
+                   float *dists_dev, void *stream, cng_build_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CNG_H_ */

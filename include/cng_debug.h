@@ -1,0 +1,28 @@
+/*
+ * cng_debug.h -- test aids exported by libcng.so (not part of the alpha-CNG method).
+ */
+#ifndef CNG_DEBUG_H_
+#define CNG_DEBUG_H_
+
+#include <stdint.h>
+
+#include "cng.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * cngx_tc_scores -- run the tensor-core screen's MMA and epilogue arithmetic on m rows and n
+ * columns (f32 device arrays, row-major, d columns, d <= 192) and write every screened score
+ * s(x, y) = ||y_b||^2 - 2 <x_b, y_b> (x_b, y_b: bf16-rounded rows) to scores_dev [m][n] (f32,
+ * device).  Lets tests compare the tcgen05 pipeline with a plain reference of the same
+ * arithmetic.  Synchronises `stream`.
+ */
+cng_status cngx_tc_scores(const float *rows_dev, int64_t m, const float *cols_dev, int64_t n,
+                          int32_t d, float *scores_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CNG_DEBUG_H_ */

@@ -71,6 +71,15 @@ def _load():
             lib.or_search.restype = ctypes.c_int
             lib.or_search.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, vp, i64,
                                       ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+            lib.or_connect.restype = ctypes.c_int
+            lib.or_connect.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, ctypes.c_int,
+                                       vp]
+            lib.or_mlp_logit.restype = dbl
+            lib.or_mlp_logit.argtypes = [vp, vp]
+            lib.or_search_ex.restype = ctypes.c_int
+            lib.or_search_ex.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, vp, i64,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, dbl,
+                                         ctypes.c_int, vp, vp, vp, vp, vp]
             lib.or_num_threads.restype = ctypes.c_int
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -163,17 +172,42 @@ def prune_adaptive(X, p: int, V, alpha0: float, alpha_max: float, dalpha: float,
     return S[:ns].copy(), a.value
 
 
-class Graph:
-    """Oracle construction result (Alg. 3 phases 1-3 with exact candidates)."""
+REPAIR_SLOTS = 8  # row slots beyond R for phase-4 connectivity edges
+CONNECT_L = 32    # beam width of the phase-4 searches
 
-    def __init__(self, entry, cand, fwd, fdeg, adj, deg):
-        self.entry, self.cand, self.fwd, self.fdeg, self.adj, self.deg = entry, cand, fwd, fdeg, adj, deg
+
+class Graph:
+    """Oracle construction result (Alg. 3 phases 1-4 with exact candidates).
+
+    cand, fwd/fdeg (phase 2), adj3/deg3 (phase 3, stride R), adj/deg (final, stride
+    R + REPAIR_SLOTS, after phase 4), entry, repair_edges, repair_rounds."""
+
+    def __init__(self, entry, cand, fwd, fdeg, adj3, deg3):
+        self.entry, self.cand, self.fwd, self.fdeg, self.adj3, self.deg3 = entry, cand, fwd, fdeg, adj3, deg3
+        self.adj, self.deg, self.repair_edges, self.repair_rounds = adj3, deg3, 0, 0
 
     def out(self, p: int) -> np.ndarray:
         return self.adj[p, : self.deg[p]]
 
 
-def build_graph(X, alpha: float, tau: float, R: int, L: int) -> Graph:
+def connect(X, adj3, deg3, entry_id: int, slots: int = REPAIR_SLOTS, Lc: int = CONNECT_L):
+    """Alg. 3 phase 4 on a copy: returns (adj [n, R + slots], deg, edges added, rounds)."""
+    X = _f32(X)
+    n, d = X.shape
+    R = adj3.shape[1]
+    adj = np.full((n, R + slots), -1, np.int32)
+    adj[:, :R] = adj3
+    deg = np.ascontiguousarray(deg3, np.int32).copy()
+    rounds = ctypes.c_int32(0)
+    added = _load().or_connect(_p(X), n, d, _p(adj), _p(deg), R + slots, int(entry_id), int(Lc),
+                               ctypes.byref(rounds))
+    if added < 0:
+        raise ValueError(f"or_connect failed ({added})")
+    return adj, deg, added, rounds.value
+
+
+def build_graph(X, alpha: float, tau: float, R: int, L: int, connect_L: int = CONNECT_L,
+                repair_slots: int = REPAIR_SLOTS) -> Graph:
     X = _f32(X)
     n, d = X.shape
     e = ctypes.c_int32(-1)
@@ -186,7 +220,11 @@ def build_graph(X, alpha: float, tau: float, R: int, L: int) -> Graph:
                           _p(cand), _p(fwd), _p(fdeg), _p(adj), _p(deg))
     if rc != 0:
         raise ValueError(f"or_build failed ({rc})")
-    return Graph(int(e.value), cand, fwd, fdeg, adj, deg)
+    G = Graph(int(e.value), cand, fwd, fdeg, adj, deg)
+    if connect_L > 0:
+        G.adj, G.deg, G.repair_edges, G.repair_rounds = connect(X, adj, deg, G.entry, repair_slots,
+                                                                connect_L)
+    return G
 
 
 def search(X, adj, deg, entry_id: int, Q, k: int, L: int):
@@ -205,6 +243,41 @@ def search(X, adj, deg, entry_id: int, Q, k: int, L: int):
     if rc != 0:
         raise ValueError(f"or_search failed ({rc})")
     return ids, ds, ndc, hops
+
+
+NF = 16
+
+
+def search_ex(X, adj, deg, entry_id: int, Q, k: int, L: int, max_trace: int = 0, model=None,
+              zthr: float = 0.0, check_every: int = 1):
+    """Alg. 1 with per-hop search-state features (learned early stop) and, if ``model`` (the
+    parameter vector followed by mu[16], sigma[16]) is given, the learned stop rule.
+    Returns dict(ids, dists, ndc, hops, tlc, stopped, feats [nq, max_trace, 16] or None)."""
+    X, Q = _f32(X), _f32(Q)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    deg = np.ascontiguousarray(deg, dtype=np.int32)
+    n, d = X.shape
+    nq = Q.shape[0]
+    out = dict(ids=np.empty((nq, k), np.int32), dists=np.empty((nq, k), np.float64),
+               ndc=np.empty(nq, np.int32), hops=np.empty(nq, np.int32), tlc=np.empty(nq, np.int32),
+               stopped=np.empty(nq, np.int32),
+               feats=np.full((nq, max_trace, NF), np.nan) if max_trace else None)
+    mdl = None if model is None else np.ascontiguousarray(model, np.float64)
+    rc = _load().or_search_ex(_p(X), n, d, _p(adj), _p(deg), adj.shape[1], int(entry_id), _p(Q), nq,
+                              int(k), int(L), int(max_trace),
+                              _p(out["feats"]) if max_trace else None, _p(out["tlc"]),
+                              None if mdl is None else _p(mdl), float(zthr), int(check_every),
+                              _p(out["ids"]), _p(out["dists"]), _p(out["ndc"]), _p(out["hops"]),
+                              _p(out["stopped"]))
+    if rc != 0:
+        raise ValueError(f"or_search_ex failed ({rc})")
+    return out
+
+
+def mlp_logit(model, f) -> float:
+    mdl = np.ascontiguousarray(model, np.float64)
+    f = np.ascontiguousarray(f, np.float64)
+    return float(_load().or_mlp_logit(_p(mdl), _p(f)))
 
 
 def recall(found_ids, true_ids) -> float:

@@ -13,7 +13,8 @@
  *                           multiply-add (compile with -ffp-contract=off).
  *   candidate lists         Alg. 3, phase 2 reads "the C closest points"; here the exact
  *                           L nearest points of P \ {p} ordered by (D, id).
- *   navigating node         Alg. 3, phase 1: nearest point to the centroid of P.
+ *   navigating node         Alg. 3, phase 1: nearest point to the centroid of P (exact
+ *                           form: argmin over all points of (D(c, x), id)).
  *   pruning                 Def. 2 (Eq. 1) and Alg. 2, fixed alpha, stop at R kept.
  *   adaptive pruning        Alg. 4 with alpha_i = alpha0 + i * dalpha.
  *   reverse merge           Alg. 3, phase 3 and the lazy-pruning paragraph of Sec. 4.3.
@@ -105,12 +106,22 @@ int or_knn(const float *base, int64_t n, const float *rows, int64_t m, int d, in
 
 /* ---- navigating node (Alg. 3 phase 1, exact form) ---------------------------------- */
 
-/* Centroid: c_j = (sum_i x_ij) / n, each sum taken sequentially in i. */
+/*
+ * Centroid: c_j = (sum_i x_ij) / n in double.  The paper fixes no summation order; ours:
+ * rows are taken in consecutive blocks of OR_CENTROID_BLOCK, each block summed left to
+ * right, then the block sums added left to right, then one division by n.
+ */
+#define OR_CENTROID_BLOCK 4096
 void or_centroid(const float *X, int64_t n, int d, double *c) {
     for (int j = 0; j < d; ++j) {
-        double s = 0.0;
-        for (int64_t i = 0; i < n; ++i) s = s + (double)X[i * (int64_t)d + j];
-        c[j] = s / (double)n;
+        double total = 0.0;
+        for (int64_t b = 0; b < n; b += OR_CENTROID_BLOCK) {
+            int64_t e = b + OR_CENTROID_BLOCK < n ? b + OR_CENTROID_BLOCK : n;
+            double s = 0.0;
+            for (int64_t i = b; i < e; ++i) s = s + (double)X[i * (int64_t)d + j];
+            total = total + s;
+        }
+        c[j] = total / (double)n;
     }
 }
 
@@ -406,6 +417,260 @@ int or_search(const float *X, int64_t n, int d, const int32_t *adj, const int32_
         free(Q);
     }
     return err;
+}
+
+/* ---- connectivity (Alg. 3 phase 4) ------------------------------------------------------ */
+
+/*
+ * The paper adds "necessary edges" from the DFS tree of s to every point outside it, in line
+ * with NSG, without fixing which.  Our reading, in rounds until every point is reachable:
+ *   reached = points reachable from s;
+ *   for every unreached p: r(p) = the nearest result of beam-search(G, x_p, s, Lc, 1) on the
+ *     current graph (necessarily a reached point);
+ *   every reached r named by some r(p) gets the edge r -> (smallest such p) if its row has a
+ *     free slot (deg < Rs).
+ * adj rows have stride Rs; phase-3 rows use at most R < Rs of them.  Returns the number of
+ * edges added (rounds in *rounds_out), or -3 if a round could add no edge.
+ */
+int or_connect(const float *X, int64_t n, int d, int32_t *adj, int32_t *deg, int Rs, int32_t s,
+               int Lc, int32_t *rounds_out) {
+    if (n <= 0 || s < 0 || s >= n || Lc < 1) return OR_E_INVAL;
+    unsigned char *reach = (unsigned char *)malloc((size_t)n);
+    int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *U = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *best = (int32_t *)malloc(sizeof(int32_t) * n);
+    if (!reach || !stack || !U || !best) return OR_E_NOMEM;
+    for (int64_t i = 0; i < n; ++i) best[i] = -1;
+    int total = 0, rounds = 0, rc = 0;
+    for (;;) {
+        memset(reach, 0, (size_t)n);
+        int64_t top = 0;
+        stack[top++] = s;
+        reach[s] = 1;
+        while (top > 0) {
+            int32_t u = stack[--top];
+            for (int j = 0; j < deg[u]; ++j) {
+                int32_t v = adj[(int64_t)u * Rs + j];
+                if (!reach[v]) {
+                    reach[v] = 1;
+                    stack[top++] = v;
+                }
+            }
+        }
+        int64_t nu = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (!reach[i]) U[nu++] = (int32_t)i;
+        if (nu == 0) break;
+        ++rounds;
+        float *Qm = (float *)malloc(sizeof(float) * nu * d);
+        int32_t *rid = (int32_t *)malloc(sizeof(int32_t) * nu);
+        double *rd = (double *)malloc(sizeof(double) * nu);
+        if (!Qm || !rid || !rd) return OR_E_NOMEM;
+        for (int64_t i = 0; i < nu; ++i) memcpy(Qm + i * d, X + (int64_t)U[i] * d, sizeof(float) * d);
+        or_search(X, n, d, adj, deg, Rs, s, Qm, nu, 1, Lc, rid, rd, NULL, NULL);
+        for (int64_t i = 0; i < nu; ++i) /* U ascending: the first p naming r is the smallest */
+            if (best[rid[i]] < 0) best[rid[i]] = U[i];
+        int added = 0;
+        for (int64_t r = 0; r < n; ++r) {
+            if (best[r] < 0) continue;
+            if (deg[r] < Rs) {
+                adj[r * Rs + deg[r]] = best[r];
+                deg[r] += 1;
+                ++added;
+            }
+            best[r] = -1;
+        }
+        free(Qm);
+        free(rid);
+        free(rd);
+        if (added == 0) {
+            rc = -3;
+            break;
+        }
+        total += added;
+    }
+    free(reach);
+    free(stack);
+    free(U);
+    free(best);
+    if (rounds_out) *rounds_out = rounds;
+    return rc < 0 ? rc : total;
+}
+
+/* ---- learned early stop (not in the paper): search-state features and traces ------------ */
+
+/*
+ * After hop t (t >= 1, the hop vertex u* explored and its neighbours merged into Q), with
+ * lg(x) = ln(max(x, 1e-30)), D0 = D(q, s), D1 / Dk / DL the distances of Q[0], Q[min(k,|Q|)-1]
+ * and Q[|Q|-1], du = D(q, u*), Dk_h[j] the Dk after hop j (Dk_h[0] = D0), tlc the last hop at
+ * which the list of the first min(k, |Q|) ids changed (0 if never), U the unexplored entries
+ * of Q and ins the points of this hop still in Q after it:
+ *   f0 = lg D0          f1 = ln(1 + t)      f2 = lg D1 - lg D0   f3 = lg Dk - lg D0
+ *   f4 = lg DL - lg D0  f5 = lg du - lg Dk
+ *   f6..f11 = lg Dk_h[max(t - j, 0)] - lg Dk  for j = 1, 2, 4, 8, 16, 32
+ *   f12 = ln(1 + t - tlc)   f13 = U / L   f14 = |Q| / L   f15 = ins / R
+ * The label of hop t is 1 iff t >= tlc at the end of the search (the top-k list is final).
+ */
+#define OR_NF 16
+#define OR_H 64
+#define OR_NPARAMS (OR_H * OR_NF + OR_H + OR_H * OR_H + OR_H + OR_H + 1)
+
+static double lgx(double x) { return log(x > 1e-30 ? x : 1e-30); }
+
+/* model = params[OR_NPARAMS] followed by mu[16], sigma[16]; returns the logit. */
+double or_mlp_logit(const double *model, const double *f) {
+    const double *W1 = model, *b1 = W1 + OR_H * OR_NF, *W2 = b1 + OR_H, *b2 = W2 + OR_H * OR_H;
+    const double *w3 = b2 + OR_H, *b3 = w3 + OR_H, *mu = model + OR_NPARAMS, *sg = mu + OR_NF;
+    double x[OR_NF], h1[OR_H], h2[OR_H];
+    for (int i = 0; i < OR_NF; ++i) x[i] = (f[i] - mu[i]) / sg[i];
+    for (int o = 0; o < OR_H; ++o) {
+        double a = b1[o];
+        for (int i = 0; i < OR_NF; ++i) a = a + W1[o * OR_NF + i] * x[i];
+        h1[o] = a > 0 ? a : 0;
+    }
+    for (int o = 0; o < OR_H; ++o) {
+        double a = b2[o];
+        for (int i = 0; i < OR_H; ++i) a = a + W2[o * OR_H + i] * h1[i];
+        h2[o] = a > 0 ? a : 0;
+    }
+    double z = b3[0];
+    for (int i = 0; i < OR_H; ++i) z = z + w3[i] * h2[i];
+    return z;
+}
+
+/*
+ * Alg. 1 as or_search, plus: per-hop features into feats[qi][t-1][16] for t <= max_trace
+ * (when feats != NULL), the final tlc per query, and -- when model != NULL -- the learned stop:
+ * after every hop t with t % check_every == 0 the search ends if or_mlp_logit >= zthr
+ * (stopped[qi] = 1).  Ids, distances, ndc and hops as or_search.
+ */
+int or_search_ex(const float *X, int64_t n, int d, const int32_t *adj, const int32_t *deg, int R,
+                 int32_t s, const float *Qv, int64_t nq, int k, int L, int max_trace, double *feats,
+                 int32_t *tlc_out, const double *model, double zthr, int check_every,
+                 int32_t *out_ids, double *out_d, int32_t *ndc_out, int32_t *hops_out,
+                 int32_t *stopped) {
+    if (n <= 0 || k <= 0 || L < k || s < 0 || s >= n || check_every < 1) return OR_E_INVAL;
+#pragma omp parallel
+    {
+        unsigned char *vis = (unsigned char *)calloc((size_t)n, 1);
+        int32_t *touched = NULL;
+        int64_t tcap = 0;
+        or_qent *Q = (or_qent *)malloc(sizeof(or_qent) * (L + 1));
+        int32_t *born = (int32_t *)malloc(sizeof(int32_t) * (L + 1));
+        int32_t *prevk = (int32_t *)malloc(sizeof(int32_t) * k);
+        int hcap = 1024;
+        double *hist = (double *)malloc(sizeof(double) * hcap);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            const float *q = Qv + qi * (int64_t)d;
+            int64_t nt = 0;
+            int len = 1;
+            Q[0].D = or_dist(q, X + (int64_t)s * d, d);
+            Q[0].id = s;
+            Q[0].explored = 0;
+            born[0] = 0;
+            vis[s] = 1;
+            if (nt >= tcap) {
+                tcap = tcap ? tcap * 2 : 4096;
+                touched = (int32_t *)realloc(touched, sizeof(int32_t) * tcap);
+            }
+            touched[nt++] = s;
+            const double D0 = Q[0].D;
+            hist[0] = D0;
+            int32_t ndc = 1, hops = 0, tlc = 0, stop = 0;
+            for (;;) {
+                int i = 0;
+                while (i < len && Q[i].explored) ++i;
+                if (i == len) break;
+                Q[i].explored = 1;
+                ++hops;
+                const double du = Q[i].D;
+                int32_t u = Q[i].id;
+                int kk0 = len < k ? len : k;
+                for (int t = 0; t < kk0; ++t) prevk[t] = Q[t].id;
+                for (int j = 0; j < deg[u]; ++j) {
+                    int32_t v = adj[(int64_t)u * R + j];
+                    if (vis[v]) continue;
+                    vis[v] = 1;
+                    if (nt >= tcap) {
+                        tcap *= 2;
+                        touched = (int32_t *)realloc(touched, sizeof(int32_t) * tcap);
+                    }
+                    touched[nt++] = v;
+                    ++ndc;
+                    double D = or_dist(q, X + (int64_t)v * d, d);
+                    if (len < L || key_less(D, v, Q[len - 1].D, Q[len - 1].id)) {
+                        int pos = (len < L) ? len : L - 1;
+                        while (pos > 0 && key_less(D, v, Q[pos - 1].D, Q[pos - 1].id)) {
+                            Q[pos] = Q[pos - 1];
+                            born[pos] = born[pos - 1];
+                            --pos;
+                        }
+                        Q[pos].D = D;
+                        Q[pos].id = v;
+                        Q[pos].explored = 0;
+                        born[pos] = hops;
+                        if (len < L) ++len;
+                    }
+                }
+                int kk = len < k ? len : k, changed = kk != kk0;
+                for (int t = 0; t < kk && !changed; ++t) changed = Q[t].id != prevk[t];
+                if (changed) tlc = hops;
+                const double Dk = Q[kk - 1].D;
+                if (hops >= hcap) {
+                    hcap *= 2;
+                    hist = (double *)realloc(hist, sizeof(double) * hcap);
+                }
+                hist[hops] = Dk;
+                if ((feats && hops <= max_trace) || (model && hops % check_every == 0)) {
+                    int U = 0, ins = 0;
+                    for (int t = 0; t < len; ++t) {
+                        U += !Q[t].explored;
+                        ins += born[t] == hops;
+                    }
+                    double f[OR_NF];
+                    const int lags[6] = {1, 2, 4, 8, 16, 32};
+                    f[0] = lgx(D0);
+                    f[1] = log(1.0 + hops);
+                    f[2] = lgx(Q[0].D) - lgx(D0);
+                    f[3] = lgx(Dk) - lgx(D0);
+                    f[4] = lgx(Q[len - 1].D) - lgx(D0);
+                    f[5] = lgx(du) - lgx(Dk);
+                    for (int j = 0; j < 6; ++j) {
+                        int h = hops - lags[j];
+                        f[6 + j] = lgx(hist[h > 0 ? h : 0]) - lgx(Dk);
+                    }
+                    f[12] = log(1.0 + (hops - tlc));
+                    f[13] = (double)U / L;
+                    f[14] = (double)len / L;
+                    f[15] = (double)ins / R;
+                    if (feats && hops <= max_trace)
+                        for (int j = 0; j < OR_NF; ++j)
+                            feats[(qi * (int64_t)max_trace + (hops - 1)) * OR_NF + j] = f[j];
+                    if (model && hops % check_every == 0 && or_mlp_logit(model, f) >= zthr) {
+                        stop = 1;
+                        break;
+                    }
+                }
+            }
+            for (int t = 0; t < k; ++t) {
+                if (out_ids) out_ids[qi * k + t] = t < len ? Q[t].id : -1;
+                if (out_d) out_d[qi * k + t] = t < len ? Q[t].D : INFINITY;
+            }
+            if (ndc_out) ndc_out[qi] = ndc;
+            if (hops_out) hops_out[qi] = hops;
+            if (tlc_out) tlc_out[qi] = tlc;
+            if (stopped) stopped[qi] = stop;
+            for (int64_t t = 0; t < nt; ++t) vis[touched[t]] = 0;
+        }
+        free(vis);
+        free(touched);
+        free(Q);
+        free(born);
+        free(prevk);
+        free(hist);
+    }
+    return OR_OK;
 }
 
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */

@@ -1,0 +1,789 @@
+// api.cu -- C ABI of libcng.so (declared in include/cng.h): argument checks, device memory,
+// phase ordering and statistics of the alpha-CNG build (Alg. 3 phases 1-3, exact candidates)
+// and the batched beam search (Alg. 1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cng_internal.h"
+#include "search_internal.h"
+#include "screen_tc.h"
+
+namespace cng {
+
+static thread_local std::string g_err = "no error";
+
+cng_status fail(cng_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? CNG_E_NOMEM : CNG_E_CUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+
+// Owns device allocations made during one call; frees them on scope exit.
+struct DevPool {
+  std::vector<void*> ptrs;
+  ~DevPool() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return e;
+  }
+  void release(void* p) {  // keep p alive beyond the pool
+    ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), p), ptrs.end());
+  }
+};
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace cng
+
+using namespace cng;
+
+struct cng_index {
+  int64_t n = 0;
+  int d = 0, dpad = 0, dtype = 0, R = 0, L = 0;
+  int32_t entry = -1;
+  int exact = 0;
+  float band = 1e-5f;
+  void* xs = nullptr;       // stored points [n][dpad]
+  int32_t* adj = nullptr;   // [n][R]
+  int32_t* deg = nullptr;   // [n]
+  int32_t* cand = nullptr;  // [n][L] (keep_lists)
+  float* cdist = nullptr;
+  int32_t* fwd = nullptr;   // [n][R] (keep_lists)
+  int32_t* fdeg = nullptr;
+  // search scratch
+  int* counter = nullptr;
+  unsigned long long* tot = nullptr;
+  uint32_t* status = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream for CUDA-graph capture
+  std::mutex mu;
+  struct GraphEntry {
+    SearchArgs args;
+    int wpb, grid;
+    cudaStream_t stream;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+};
+
+extern "C" const char* cng_last_error(void) { return g_err.c_str(); }
+
+extern "C" void cng_free(cng_index* ix) {
+  if (!ix) return;
+  for (auto& g : ix->graphs) cudaGraphExecDestroy(g.exec);
+  cudaFree(ix->xs);
+  cudaFree(ix->adj);
+  cudaFree(ix->deg);
+  cudaFree(ix->cand);
+  cudaFree(ix->cdist);
+  cudaFree(ix->fwd);
+  cudaFree(ix->fdeg);
+  cudaFree(ix->counter);
+  cudaFree(ix->tot);
+  cudaFree(ix->status);
+  if (ix->cap_stream) cudaStreamDestroy(ix->cap_stream);
+  delete ix;
+}
+
+namespace cng {
+
+struct Timer {
+  cudaEvent_t ev[8];
+  int n = 0;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    for (auto& e : ev) cudaEventCreate(&e);
+  }
+  ~Timer() {
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  void mark() { cudaEventRecord(ev[n++], s); }
+  double ms(int a, int b) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+};
+
+// Exact candidate lists for m rows against n stored columns (K1 screen -> K2 rerank ->
+// rescan).  xr / xc are stored matrices [.][dpad] of `dtype`.  Writes ids [m][L], dist [m][L].
+struct KnnInputs {
+  const void* xr;
+  const void* xc;
+  int64_t m, n;
+  int d, dpad, dtype;
+  int self_excl;
+  int L, Lp;
+  int screen;   // cng_screen
+  float band;
+  int exact;
+  // tensor-core operands (screen == CNG_SCREEN_TC)
+  const void* tc_rows;  // [m][kpad] bf16 / fp16
+  const void* tc_cols;  // [n][kpad]
+  int kpad;
+  const float* nb_rows;  // ||x_b||^2 of rows
+  const float* nb_cols;  // ||y_b||^2 of columns
+  const float* rb_rows;
+  float rbmax, normmax;
+};
+
+static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist, Counters* ctr,
+                          double* ms_screen, double* ms_rerank, cudaStream_t s) {
+  DevPool pool;
+  int32_t* sids;
+  uint32_t* sthr;
+  CK(pool.alloc(&sids, (size_t)in.m * in.Lp));
+  CK(pool.alloc(&sthr, (size_t)in.m));
+  Timer tm(s);
+  tm.mark();
+  ScreenModel sm{};
+  if (in.screen == CNG_SCREEN_TC) {
+    TcScreenArgs ta{};
+    ta.A = in.tc_rows;
+    ta.B = in.tc_cols;
+    ta.m = in.m;
+    ta.n = in.n;
+    ta.kpad = in.kpad;
+    ta.fp16 = in.dtype == CNG_F16;
+    ta.nb = in.nb_cols;
+    ta.Lp = in.Lp;
+    ta.self_excl = in.self_excl;
+    ta.ids = sids;
+    ta.thr = sthr;
+    ta.status = &ctr->status;
+    ta.rowbuf_words = screen_tc_rowbuf_words(in.m, in.Lp);
+    CK(pool.alloc(&ta.rowbuf, ta.rowbuf_words));
+    std::string msg;
+    cudaError_t e = launch_screen_tc(ta, s, &msg);
+    if (e != cudaSuccess) return fail(CNG_E_CUDA, "tensor-core screen: " + msg + cudaGetErrorString(e));
+    sm.kind = 1;
+    sm.nb = in.nb_rows;
+    sm.rb = in.rb_rows;
+    sm.rbmax = in.rbmax;
+    sm.normmax = in.normmax;
+    sm.acc_err = (float)(in.kpad + 8) * 1.1920929e-7f;  // K terms, 2^-23 per add
+  } else {
+    int cpl = 0;
+    for (int c : {8, 12, 16, 20})
+      if (c * 32 >= in.Lp + 128 + 32) { cpl = c; break; }
+    if (!cpl) return fail(CNG_E_UNSUPPORTED, "screened list too long");
+    int grid = std::min<int64_t>((in.m + 127) / 128, (int64_t)num_sms() * 2);
+    uint64_t* rowbuf;
+    CK(pool.alloc(&rowbuf, (size_t)grid * 128 * cpl * 32));
+    CK(launch_knn_simt(in.xr, in.m, in.xc, in.n, in.dtype, in.dpad, in.Lp, in.self_excl, rowbuf,
+                       cpl, grid, sids, sthr, &ctr->status, s));
+    sm.kind = 0;
+    sm.rel_err = (float)(in.dpad + 8) * 5.9604645e-8f;
+  }
+  sm.exact = in.exact;
+  tm.mark();
+  int32_t* fail_rows;
+  float* fail_bound;
+  CK(pool.alloc(&fail_rows, (size_t)in.m));
+  CK(pool.alloc(&fail_bound, (size_t)in.m));
+  CK(launch_rerank(in.xr, in.xc, in.dtype, in.m, in.d, in.dpad, sids, sthr, in.Lp, in.L, sm,
+                   in.band, in.exact, out_ids, out_dist, fail_rows, fail_bound, ctr, s));
+  CK(launch_rescan(in.xr, in.xc, in.dtype, in.m, in.n, in.d, in.dpad, in.self_excl, in.L,
+                   fail_rows, fail_bound, ctr, out_ids, out_dist, s));
+  tm.mark();
+  CK(cudaStreamSynchronize(s));
+  if (ms_screen) *ms_screen = tm.ms(0, 1);
+  if (ms_rerank) *ms_rerank = tm.ms(1, 2);
+  return CNG_OK;
+}
+
+static cng_status check_status(uint32_t st) {
+  if (st & ST_TIMEOUT) return fail(CNG_E_TIMEOUT, "a bounded device wait ran out");
+  if (st & ST_OVERFLOW)
+    return fail(CNG_E_UNSUPPORTED, "a candidate row buffer overflowed");
+  if (st & ST_CERT) return fail(CNG_E_UNSUPPORTED, "more than 4096 points tie at a candidate boundary");
+  if (st & ST_OVF_MERGE) return fail(CNG_E_INTERNAL, "a merged candidate set exceeded its buffer");
+  if (st & ST_OVF_RUN)
+    return fail(CNG_E_UNSUPPORTED, "more than 256 consecutive near-tied distances (degenerate input)");
+  if (st & ST_BOUNDS) return fail(CNG_E_INTERNAL, "device index check failed");
+  if (st & ST_SCREEN) return fail(CNG_E_INTERNAL, "screened scores violate the exactness assumption");
+  return CNG_OK;
+}
+
+// Stored copy + exactness of one point matrix.
+struct Prepared {
+  void* xs = nullptr;
+  void* tc = nullptr;
+  float* nb = nullptr;
+  float* rb = nullptr;
+  PrepStats st{};
+};
+
+static cng_status prepare(DevPool& pool, const void* pts_dev, int dtype, int64_t n, int d,
+                          int dpad, int screen, int kpad, Prepared* out, cudaStream_t s) {
+  size_t el = dtype == CNG_F32 ? 4 : 2;
+  CK(pool.alloc(reinterpret_cast<char**>(&out->xs), (size_t)n * dpad * el));
+  __nv_bfloat16* xb_bf = nullptr;
+  __half* xb_h = nullptr;
+  if (screen == CNG_SCREEN_TC) {
+    if (dtype == CNG_F32) {
+      CK(pool.alloc(&xb_bf, (size_t)n * kpad));
+      out->tc = xb_bf;
+    } else {
+      CK(pool.alloc(&xb_h, (size_t)n * kpad));
+      out->tc = xb_h;
+    }
+    CK(pool.alloc(&out->nb, (size_t)n + 256));
+    CK(pool.alloc(&out->rb, (size_t)n));
+    CK(cudaMemsetAsync(out->nb, 0, ((size_t)n + 256) * sizeof(float), s));
+  }
+  PrepStats* dst;
+  CK(pool.alloc(&dst, 1));
+  PrepStats init{};
+  init.vmin_key = 0xffffffffu;
+  CK(cudaMemcpyAsync(dst, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CK(launch_prep(pts_dev, dtype, n, d, dpad, out->xs, xb_bf, xb_h, kpad, out->nb, out->rb, dst, s));
+  CK(cudaMemcpyAsync(&out->st, dst, sizeof(PrepStats), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return CNG_OK;
+}
+
+static float key_to_float(uint32_t k) {
+  uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+}
+static float bits_to_float(uint32_t b) {
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+}
+
+// Squared distances are exact FP32 integers when every coordinate is an integer and
+// d * span^2 < 2^24 (span = max - min coordinate); the tensor-core screen additionally needs
+// |coordinate| <= 256 (exact in bf16) and ||x||^2 < 2^24.
+static int exact_int(const PrepStats& st, int d, int screen) {
+  if (st.nonint) return 0;
+  double lo = key_to_float(st.vmin_key), hi = key_to_float(st.vmax_key);
+  double span = hi - lo;
+  if ((double)d * span * span >= 16777216.0) return 0;
+  if (screen == CNG_SCREEN_TC) {
+    if (std::max(std::fabs(lo), std::fabs(hi)) > 256.0) return 0;
+    double nm = bits_to_float(st.normmax_bits);
+    if (nm * nm >= 8388608.0) return 0;
+  }
+  return 1;
+}
+
+}  // namespace cng
+
+static cng_status validate_build(const void* points, int32_t dtype, int64_t n, int32_t d,
+                                 const cng_build_params* p) {
+  if (!points || !p) return fail(CNG_E_INVAL, "points and params must be non-NULL");
+  if (dtype != CNG_F32 && dtype != CNG_F16) return fail(CNG_E_INVAL, "dtype must be CNG_F32 or CNG_F16");
+  if (n < 2 || n > 0x7fffffffLL) return fail(CNG_E_INVAL, "n must be in [2, 2^31 - 1]");
+  if (d < 1 || d > 4096) return fail(CNG_E_INVAL, "d must be in [1, 4096]");
+  if (p->L < 1 || p->L > 256 || p->L >= n) return fail(CNG_E_INVAL, "L must satisfy 1 <= L <= 256 and L < n");
+  if (p->R < 1 || p->R > p->L || p->R > 64) return fail(CNG_E_INVAL, "R must satisfy 1 <= R <= min(L, 64)");
+  if (!(p->alpha > 0.0) || !std::isfinite(p->alpha)) return fail(CNG_E_INVAL, "alpha must be a positive finite number");
+  if (!(p->tau >= 0.0) || !std::isfinite(p->tau)) return fail(CNG_E_INVAL, "tau must be finite and >= 0");
+  if (p->metric != CNG_L2 && p->metric != CNG_IP_AS_L2) return fail(CNG_E_INVAL, "unknown metric");
+  if (p->screen != CNG_SCREEN_FP32 && p->screen != CNG_SCREEN_TC) return fail(CNG_E_INVAL, "unknown screen");
+  if (!(p->tie_band >= 5e-6) || p->tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
+  if (p->margin < 0 || p->margin > 256) return fail(CNG_E_INVAL, "margin must be in [0, 256]");
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, int32_t d,
+                                const cng_build_params* params, void* stream, cng_index** out,
+                                cng_build_stats* stats) {
+  if (!out) return fail(CNG_E_INVAL, "out must be non-NULL");
+  *out = nullptr;
+  cng_status vs = validate_build(points, dtype, n, d, params);
+  if (vs != CNG_OK) return vs;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cng_build_params& P = *params;
+  int screen = P.screen;
+  if (screen == CNG_SCREEN_TC && !tc_screen_supported(d, dtype == CNG_F16)) screen = CNG_SCREEN_FP32;
+  DevPool pool;
+  Timer tm(s);
+  tm.mark();  // 0
+  const size_t el = dtype == CNG_F32 ? 4 : 2;
+  const void* pts = points;
+  if (!is_device_ptr(points)) {
+    void* tmp;
+    CK(pool.alloc(reinterpret_cast<char**>(&tmp), (size_t)n * d * el));
+    CK(cudaMemcpyAsync(tmp, points, (size_t)n * d * el, cudaMemcpyHostToDevice, s));
+    pts = tmp;
+  }
+  const int dpad = round_up(d, dtype == CNG_F32 ? 32 : 64);
+  const int kpad = round_up(d, 64);
+  Prepared pr;
+  cng_status st = prepare(pool, pts, dtype, n, d, dpad, screen, kpad, &pr, s);
+  if (st != CNG_OK) return st;
+  if (P.metric == CNG_IP_AS_L2 && bits_to_float(pr.st.unitdev_bits) > 1e-3f)
+    return fail(CNG_E_INVAL, "CNG_IP_AS_L2 requires unit-norm rows (| ||x|| - 1 | <= 1e-3)");
+  const int exact = exact_int(pr.st, d, screen);
+  const float band = (float)P.tie_band;
+  tm.mark();  // 1
+  // phase 1: navigating node
+  int nblk = (int)((n + 4095) / 4096);
+  double *part, *cen;
+  unsigned long long* best;
+  int32_t* d_entry;
+  CK(pool.alloc(&part, (size_t)nblk * d + (size_t)n));
+  CK(pool.alloc(&cen, (size_t)d));
+  CK(pool.alloc(&best, 2));
+  CK(pool.alloc(&d_entry, 1));
+  CK(launch_entry(pr.xs, dtype, n, d, dpad, part, cen, best, d_entry, s));
+  tm.mark();  // 2
+  // phase 2a: exact candidate lists
+  Counters* ctr;
+  CK(pool.alloc(&ctr, 1));
+  CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+  const int L = P.L, R = P.R;
+  const int Lp = (int)std::min<int64_t>((int64_t)L + P.margin, n - 1);
+  int32_t* cand;
+  float* cdist;
+  CK(pool.alloc(&cand, (size_t)n * L));
+  CK(pool.alloc(&cdist, (size_t)n * L));
+  KnnInputs ki{};
+  ki.xr = pr.xs;
+  ki.xc = pr.xs;
+  ki.m = n;
+  ki.n = n;
+  ki.d = d;
+  ki.dpad = dpad;
+  ki.dtype = dtype;
+  ki.self_excl = 1;
+  ki.L = L;
+  ki.Lp = Lp;
+  ki.screen = screen;
+  ki.band = band;
+  ki.exact = exact;
+  ki.tc_rows = pr.tc;
+  ki.tc_cols = pr.tc;
+  ki.kpad = kpad;
+  ki.nb_rows = pr.nb;
+  ki.nb_cols = pr.nb;
+  ki.rb_rows = pr.rb;
+  ki.rbmax = bits_to_float(pr.st.rbmax_bits);
+  ki.normmax = std::sqrt(bits_to_float(pr.st.nbmax_bits));
+  double ms_screen = 0, ms_rerank = 0;
+  st = run_knn(ki, cand, cdist, ctr, &ms_screen, &ms_rerank, s);
+  if (st != CNG_OK) return st;
+  // screening operands are no longer needed
+  if (pr.tc) { cudaFree(pr.tc); pool.release(pr.tc); pr.tc = nullptr; }
+  tm.mark();  // 3
+  // phase 2b: prune every candidate list
+  int32_t *fwd, *fdeg;
+  CK(pool.alloc(&fwd, (size_t)n * R));
+  CK(pool.alloc(&fdeg, (size_t)n));
+  CK(launch_prune_fwd(pr.xs, dtype, n, d, dpad, cand, cdist, L, P.alpha, P.tau, R, band, fwd, fdeg,
+                      ctr, s));
+  tm.mark();  // 4
+  // phase 3: reverse edges + lazy pruning
+  int32_t *indeg, *cursor, *inl, *adj, *deg;
+  int64_t *off, *bsum;
+  CK(pool.alloc(&indeg, (size_t)n));
+  CK(pool.alloc(&cursor, (size_t)n));
+  CK(pool.alloc(&off, (size_t)n + 1));
+  CK(pool.alloc(&bsum, (size_t)reverse_blocksums_len(n)));
+  CK(pool.alloc(&inl, (size_t)n * R));
+  CK(pool.alloc(&adj, (size_t)n * R));
+  CK(pool.alloc(&deg, (size_t)n));
+  int32_t* big_list;
+  CK(pool.alloc(&big_list, (size_t)n));
+  CK(launch_reverse(fwd, fdeg, n, R, indeg, off, cursor, inl, bsum, ctr, s));
+  CK(launch_merge(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band, exact, adj,
+                  deg, ctr, big_list, s));
+  {
+    Counters hc0;
+    CK(cudaMemcpyAsync(&hc0, ctr, sizeof(hc0), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hc0.nbig > 0) {  // hubs: merged sets above the shared-memory capacity
+      int cap = 1;
+      while (cap < R + hc0.max_indeg) cap <<= 1;
+      int grid = std::min(hc0.nbig, num_sms() * 2);
+      unsigned char* scratch;
+      CK(pool.alloc(&scratch, (size_t)grid * cap * 17));
+      CK(launch_merge_big(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band,
+                          exact, adj, deg, ctr, big_list, hc0.nbig, scratch, cap, grid, s));
+    }
+  }
+  tm.mark();  // 5
+  Counters hc;
+  int32_t h_entry = -1;
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&h_entry, d_entry, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  st = check_status(hc.status);
+  if (st != CNG_OK) return st;
+
+  cng_index* ix = new cng_index();
+  ix->n = n;
+  ix->d = d;
+  ix->dpad = dpad;
+  ix->dtype = dtype;
+  ix->R = R;
+  ix->L = L;
+  ix->entry = h_entry;
+  ix->exact = exact;
+  ix->band = band;
+  ix->xs = pr.xs;
+  pool.release(pr.xs);
+  ix->adj = adj;
+  pool.release(adj);
+  ix->deg = deg;
+  pool.release(deg);
+  if (P.keep_lists) {
+    ix->cand = cand;
+    pool.release(cand);
+    ix->cdist = cdist;
+    pool.release(cdist);
+    ix->fwd = fwd;
+    pool.release(fwd);
+    ix->fdeg = fdeg;
+    pool.release(fdeg);
+  }
+  if (cudaMalloc(&ix->counter, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ix->tot, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&ix->status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ix->status, 0, sizeof(uint32_t)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ix->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cng_free(ix);
+    return fail(CNG_E_NOMEM, "index scratch allocation failed");
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->ms_total = tm.ms(0, 5);
+    stats->ms_prep = tm.ms(0, 1);
+    stats->ms_entry = tm.ms(1, 2);
+    stats->ms_screen = ms_screen;
+    stats->ms_rerank = ms_rerank;
+    stats->ms_prune = tm.ms(3, 4);
+    stats->ms_merge = tm.ms(4, 5);
+    stats->n_edges = (int64_t)hc.edges;
+    stats->cert_fail_rows = hc.nfail;
+    stats->order_ties = (int64_t)hc.order_ties;
+    stats->rule_ties = (int64_t)hc.rule_ties;
+    stats->merge_repruned = (int64_t)hc.merge_repruned;
+    stats->merge_max_list = std::max<int64_t>((int64_t)hc.merge_max_list, hc.max_indeg + R);
+    stats->entry = h_entry;
+    stats->exact_int = exact;
+    stats->screen_err_max = bits_to_float(hc.screen_err_bits);
+  }
+  *out = ix;
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_graph(const cng_index* ix, const int32_t** adj, const int32_t** deg,
+                                int32_t* R, int32_t* entry, int64_t* n) {
+  if (!ix) return fail(CNG_E_INVAL, "index is NULL");
+  if (adj) *adj = ix->adj;
+  if (deg) *deg = ix->deg;
+  if (R) *R = ix->R;
+  if (entry) *entry = ix->entry;
+  if (n) *n = ix->n;
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_lists(const cng_index* ix, const int32_t** cand, const float** cdist,
+                                int32_t* L, const int32_t** fwd, const int32_t** fdeg) {
+  if (!ix) return fail(CNG_E_INVAL, "index is NULL");
+  if (!ix->cand) return fail(CNG_E_INVAL, "index was built without keep_lists");
+  if (cand) *cand = ix->cand;
+  if (cdist) *cdist = ix->cdist;
+  if (L) *L = ix->L;
+  if (fwd) *fwd = ix->fwd;
+  if (fdeg) *fdeg = ix->fdeg;
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int64_t nq, int32_t k,
+                                 int32_t L, const cng_search_params* params, int32_t* ids,
+                                 float* dists, int32_t* ndc, int32_t* hops, int32_t* flags,
+                                 void* stream, cng_search_stats* stats) {
+  cng_index* ix = const_cast<cng_index*>(cix);
+  if (!ix || !queries || !ids || !dists) return fail(CNG_E_INVAL, "index, queries, ids and dists must be non-NULL");
+  if (nq < 0) return fail(CNG_E_INVAL, "nq must be >= 0");
+  if (k < 1 || L < k || L > 256) return fail(CNG_E_INVAL, "need 1 <= k <= L <= 256");
+  cng_search_params defp{};
+  const cng_search_params& P = params ? *params : defp;
+  if (P.mode != CNG_SEARCH_FIXED) return fail(CNG_E_UNSUPPORTED, "learned stop not available in this build");
+  if (P.max_hops < 0) return fail(CNG_E_INVAL, "max_hops must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nq == 0) {
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return CNG_OK;
+  }
+  DevPool pool;
+  const float* qd = queries;
+  const bool host_q = !is_device_ptr(queries);
+  if (host_q) {
+    float* t;
+    CK(pool.alloc(&t, (size_t)nq * ix->d));
+    CK(cudaMemcpyAsync(t, queries, (size_t)nq * ix->d * 4, cudaMemcpyHostToDevice, s));
+    qd = t;
+  }
+  int32_t *o_ids = ids, *o_ndc = ndc, *o_hops = hops, *o_flags = flags;
+  float* o_d = dists;
+  const bool host_out = !is_device_ptr(ids);
+  if (host_out) {
+    CK(pool.alloc(&o_ids, (size_t)nq * k));
+    CK(pool.alloc(&o_d, (size_t)nq * k));
+    if (ndc) CK(pool.alloc(&o_ndc, (size_t)nq));
+    if (hops) CK(pool.alloc(&o_hops, (size_t)nq));
+    if (flags) CK(pool.alloc(&o_flags, (size_t)nq));
+  }
+  SearchArgs a{};
+  a.X = ix->xs;
+  a.dtype = ix->dtype;
+  a.n = ix->n;
+  a.d = ix->d;
+  a.dpad = ix->dpad;
+  a.adj = ix->adj;
+  a.deg = ix->deg;
+  a.R = ix->R;
+  a.entry = ix->entry;
+  a.Q = qd;
+  a.nq = nq;
+  a.k = k;
+  a.L = L;
+  a.hash_slots = L <= 64 ? 1024 : 2048;
+  a.warp_smem = search_warp_smem(ix->dpad, L, a.hash_slots);
+  a.band = ix->band;
+  a.exact = ix->exact;
+  a.max_hops = P.max_hops;
+  a.counter = ix->counter;
+  a.ids = o_ids;
+  a.dists = o_d;
+  a.ndc = o_ndc;
+  a.hops = o_hops;
+  a.flags = o_flags;
+  a.tot = ix->tot;
+  a.status = ix->status;
+  int wpb = P.warps_per_block > 0 ? P.warps_per_block : 4;
+  if (wpb > 8) wpb = 8;
+  while (wpb > 1 && (size_t)wpb * a.warp_smem > 200 * 1024) wpb >>= 1;
+  int bps = search_blocks_per_sm(ix->dtype, wpb, (size_t)wpb * a.warp_smem);
+  if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
+  int grid = num_sms() * bps;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  CK(cudaMemsetAsync(ix->tot, 0, 4 * sizeof(unsigned long long), s));
+  cudaEventRecord(e0, s);
+  if (P.use_graph) {
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : ix->graphs)
+      if (g.stream == s && g.wpb == wpb && g.grid == grid && !memcmp(&g.args, &a, sizeof(a))) exec = g.exec;
+    if (!exec) {
+      // capture on the index's private stream (the legacy default stream cannot be captured);
+      // the instantiated graph is then launched on the caller's stream
+      cudaGraph_t graph;
+      cudaStream_t cs = ix->cap_stream;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      cudaMemsetAsync(ix->counter, 0, sizeof(int), cs);
+      launch_search(a, wpb, grid, cs);
+      CK(cudaStreamEndCapture(cs, &graph));
+      CK(cudaGraphInstantiate(&exec, graph, 0));
+      cudaGraphDestroy(graph);
+      ix->graphs.push_back({a, wpb, grid, s, exec});
+    }
+    CK(cudaGraphLaunch(exec, s));
+  } else {
+    CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
+    CK(launch_search(a, wpb, grid, s));
+  }
+  cudaEventRecord(e1, s);
+  if (host_out) {
+    CK(cudaMemcpyAsync(ids, o_ids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(dists, o_d, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s));
+    if (ndc) CK(cudaMemcpyAsync(ndc, o_ndc, (size_t)nq * 4, cudaMemcpyDeviceToHost, s));
+    if (hops) CK(cudaMemcpyAsync(hops, o_hops, (size_t)nq * 4, cudaMemcpyDeviceToHost, s));
+    if (flags) CK(cudaMemcpyAsync(flags, o_flags, (size_t)nq * 4, cudaMemcpyDeviceToHost, s));
+  }
+  if (stats || host_out || host_q) {
+    unsigned long long tot[4];
+    uint32_t dst = 0;
+    CK(cudaMemcpyAsync(tot, ix->tot, sizeof(tot), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&dst, ix->status, sizeof(dst), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (dst) {
+      cudaMemsetAsync(ix->status, 0, sizeof(uint32_t), s);
+      return fail(CNG_E_INTERNAL, "search exceeded n hop vertices (corrupted queue)");
+    }
+    if (stats) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      stats->ms = ms;
+      stats->ndc_total = (int64_t)tot[0];
+      stats->hops_total = (int64_t)tot[1];
+      stats->fp64_decisions = (int64_t)tot[2];
+      stats->stopped_early = (int64_t)tot[3];
+      stats->warps_per_block = wpb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, int64_t m, int32_t d,
+                              int32_t k, int32_t screen, double tie_band, int32_t* ids, float* dists,
+                              void* stream, cng_build_stats* stats) {
+  if (!base || !ids || !dists) return fail(CNG_E_INVAL, "base, ids and dists must be non-NULL");
+  if (d < 1 || d > 4096) return fail(CNG_E_INVAL, "d must be in [1, 4096]");
+  const bool self = rows == nullptr;
+  if (self) m = n;
+  if (n < 1 || m < 0 || k < 1 || k > 256 || k > n || (self && k >= n))
+    return fail(CNG_E_INVAL, "need 1 <= k <= 256, k <= n (k < n without rows)");
+  if (screen != CNG_SCREEN_FP32 && screen != CNG_SCREEN_TC) return fail(CNG_E_INVAL, "unknown screen");
+  if (!(tie_band >= 5e-6) || tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
+  if (!is_device_ptr(base) || (!self && !is_device_ptr(rows)) || !is_device_ptr(ids) || !is_device_ptr(dists))
+    return fail(CNG_E_INVAL, "cng_knn takes device pointers");
+  if (m == 0) return CNG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (screen == CNG_SCREEN_TC && !tc_screen_supported(d, false)) screen = CNG_SCREEN_FP32;
+  DevPool pool;
+  const int dpad = round_up(d, 32), kpad = round_up(d, 64);
+  Prepared pb, prw;
+  cng_status st = prepare(pool, base, CNG_F32, n, d, dpad, screen, kpad, &pb, s);
+  if (st != CNG_OK) return st;
+  if (!self) {
+    st = prepare(pool, rows, CNG_F32, m, d, dpad, screen, kpad, &prw, s);
+    if (st != CNG_OK) return st;
+  }
+  Prepared& pr = self ? pb : prw;
+  PrepStats both = pb.st;
+  if (!self) {
+    both.nonint |= prw.st.nonint;
+    both.vmin_key = std::min(both.vmin_key, prw.st.vmin_key);
+    both.vmax_key = std::max(both.vmax_key, prw.st.vmax_key);
+    both.normmax_bits = std::max(both.normmax_bits, prw.st.normmax_bits);
+    both.nbmax_bits = std::max(both.nbmax_bits, prw.st.nbmax_bits);
+    both.rbmax_bits = std::max(both.rbmax_bits, prw.st.rbmax_bits);
+  }
+  Counters* ctr;
+  CK(pool.alloc(&ctr, 1));
+  CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+  KnnInputs ki{};
+  ki.xr = pr.xs;
+  ki.xc = pb.xs;
+  ki.m = m;
+  ki.n = n;
+  ki.d = d;
+  ki.dpad = dpad;
+  ki.dtype = CNG_F32;
+  ki.self_excl = self;
+  ki.L = k;
+  ki.Lp = (int)std::min<int64_t>((int64_t)k + 32, self ? n - 1 : n);
+  ki.screen = screen;
+  ki.band = (float)tie_band;
+  ki.exact = exact_int(both, d, screen);
+  ki.tc_rows = pr.tc;
+  ki.tc_cols = pb.tc;
+  ki.kpad = kpad;
+  ki.nb_rows = pr.nb;
+  ki.nb_cols = pb.nb;
+  ki.rb_rows = pr.rb;
+  ki.rbmax = bits_to_float(both.rbmax_bits);
+  ki.normmax = std::sqrt(bits_to_float(both.nbmax_bits));
+  double ms_screen = 0, ms_rerank = 0;
+  st = run_knn(ki, ids, dists, ctr, &ms_screen, &ms_rerank, s);
+  if (st != CNG_OK) return st;
+  Counters hc;
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  st = check_status(hc.status);
+  if (st != CNG_OK) return st;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->ms_screen = ms_screen;
+    stats->ms_rerank = ms_rerank;
+    stats->ms_total = ms_screen + ms_rerank;
+    stats->cert_fail_rows = hc.nfail;
+    stats->order_ties = (int64_t)hc.order_ties;
+    stats->exact_int = ki.exact;
+  }
+  return CNG_OK;
+}
+
+extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* cols, int64_t n,
+                                     int32_t d, float* scores, void* stream) {
+  if (!rows || !cols || !scores) return fail(CNG_E_INVAL, "pointers must be non-NULL");
+  if (m < 1 || n < 1 || d < 1 || !tc_screen_supported(d, false))
+    return fail(CNG_E_INVAL, "need m, n >= 1 and 1 <= d <= 192");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevPool pool;
+  const int dpad = round_up(d, 32), kpad = round_up(d, 64);
+  Prepared pr, pc;
+  cng_status st = prepare(pool, rows, CNG_F32, m, d, dpad, CNG_SCREEN_TC, kpad, &pr, s);
+  if (st != CNG_OK) return st;
+  st = prepare(pool, cols, CNG_F32, n, d, dpad, CNG_SCREEN_TC, kpad, &pc, s);
+  if (st != CNG_OK) return st;
+  uint32_t* status;
+  CK(pool.alloc(&status, 1));
+  CK(cudaMemsetAsync(status, 0, 4, s));
+  TcScreenArgs ta{};
+  ta.A = pr.tc;
+  ta.B = pc.tc;
+  ta.m = m;
+  ta.n = n;
+  ta.kpad = kpad;
+  ta.fp16 = 0;
+  ta.nb = pc.nb;
+  ta.Lp = 32;
+  ta.self_excl = 0;
+  ta.status = status;
+  ta.rowbuf_words = screen_tc_rowbuf_words(m, 32);
+  CK(pool.alloc(&ta.rowbuf, ta.rowbuf_words));
+  std::string msg;
+  cudaError_t e = launch_screen_tc_dump(ta, scores, s, &msg);
+  if (e != cudaSuccess) return fail(CNG_E_CUDA, "tensor-core screen: " + msg + cudaGetErrorString(e));
+  uint32_t hs = 0;
+  CK(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return check_status(hs);
+}

@@ -1,0 +1,101 @@
+// cng_internal.h -- host-side declarations shared by the libcng translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include <string>
+
+#include "../../include/cng.h"
+#include "status_bits.h"
+
+namespace cng {
+
+// Statistics written by the preparation kernel (device memory, one per build).
+struct PrepStats {
+  uint32_t nonint;        // != 0 if some coordinate is not an integer
+  uint32_t vmin_key;      // ordered-key min / max over all coordinates
+  uint32_t vmax_key;
+  uint32_t nbmax_bits;    // max squared norm of the screening operand (float bits, >= 0)
+  uint32_t rbmax_bits;    // max ||bf16(x) - x||
+  uint32_t normmax_bits;  // max ||x||
+  uint32_t unitdev_bits;  // max | ||x|| - 1 |
+  uint32_t pad;
+};
+
+// Device counters accumulated by the build kernels.
+struct Counters {
+  unsigned long long order_ties;
+  unsigned long long rule_ties;
+  unsigned long long merge_repruned;
+  unsigned long long merge_max_list;
+  unsigned long long edges;
+  int nfail;
+  uint32_t status;
+  uint32_t screen_err_bits;
+  int nbig;        // nodes whose merged set exceeds the shared-memory capacity
+  int max_indeg;
+  int pad;
+};
+
+// How the screened score relates to the squared distance (for certification).
+struct ScreenModel {
+  int kind;          // 0: FP32 direct squared distance; 1: tensor-core shifted score
+  int exact;         // 1: scores are exact integers
+  float rel_err;     // kind 0: relative error bound of the screened squared distance
+  const float* nb;   // kind 1: ||x_b||^2 per point (shift of the score)
+  const float* rb;   // kind 1: ||x_b - x|| per point
+  float rbmax;       // kind 1: max rb
+  float acc_err;     // kind 1: absolute accumulation error bound per unit of (||x||+||y||)^2
+  float normmax;     // kind 1: max ||x_b||
+};
+
+// Launchers (each returns cudaError_t of the launch).
+cudaError_t launch_prep(const void* pts, int dtype, int64_t n, int d, int dpad, void* xs,
+                        __nv_bfloat16* xb_bf, __half* xb_h, int kpad, float* nb, float* rb,
+                        PrepStats* st, cudaStream_t s);
+cudaError_t launch_entry(const void* xs, int dtype, int64_t n, int d, int dpad, double* part,
+                         double* cen, unsigned long long* best, int32_t* entry, cudaStream_t s);
+cudaError_t launch_knn_simt(const void* xr, int64_t m, const void* xc, int64_t n, int dtype,
+                            int dpad, int Lp, int self_excl, uint64_t* rowbuf, int cpl,
+                            int grid, int32_t* ids, uint32_t* thr, uint32_t* status,
+                            cudaStream_t s);
+cudaError_t launch_rerank(const void* xr, const void* xc, int dtype, int64_t m, int d, int dpad,
+                          const int32_t* sids, const uint32_t* sthr, int Lp, int L,
+                          const ScreenModel& sm, float band, int exact, int32_t* out_ids,
+                          float* out_dist, int32_t* fail_rows, float* fail_bound, Counters* ctr,
+                          cudaStream_t s);
+cudaError_t launch_rescan(const void* xr, const void* xc, int dtype, int64_t m, int64_t n, int d,
+                          int dpad, int self_excl, int L, const int32_t* fail_rows,
+                          const float* fail_bound, Counters* ctr, int32_t* out_ids,
+                          float* out_dist, cudaStream_t s);
+cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
+                             const int32_t* cand, const float* cdist, int L, double alpha,
+                             double tau, int R, float band, int32_t* fwd, int32_t* fdeg,
+                             Counters* ctr, cudaStream_t s);
+cudaError_t launch_reverse(const int32_t* fwd, const int32_t* fdeg, int64_t n, int R,
+                           int32_t* indeg, int64_t* off, int32_t* cursor, int32_t* inl,
+                           int64_t* blocksums, Counters* ctr, cudaStream_t s);
+// Phase-3 merge of every node whose merged set fits in shared memory; the others are
+// appended to big_list (count in ctr->nbig) for launch_merge_big.
+cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
+                         const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
+                         const int32_t* inl, double alpha, double tau, int R, float band,
+                         int exact, int32_t* adj, int32_t* deg, Counters* ctr,
+                         int32_t* big_list, cudaStream_t s);
+// Merge of the listed nodes with per-CTA global scratch of 17 * big_cap bytes (grid CTAs).
+cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
+                             const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
+                             const int32_t* inl, double alpha, double tau, int R, float band,
+                             int exact, int32_t* adj, int32_t* deg, Counters* ctr,
+                             int32_t* big_list, int nbig, unsigned char* scratch, int big_cap,
+                             int grid, cudaStream_t s);
+
+int num_sms();
+int64_t reverse_blocksums_len(int64_t n);
+
+}  // namespace cng

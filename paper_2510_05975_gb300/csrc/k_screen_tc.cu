@@ -1,0 +1,535 @@
+// k_screen_tc.cu -- tensor-core candidate screen (K1) for sm_103a: tcgen05.mma with TMEM
+// accumulators, TMA tile loads into 128-byte-swizzled shared memory, mbarrier pipelines and
+// a fused per-row top-L' filter.  It yields, for each row point x, a superset list of its
+// nearest columns y by the screened score  s(x,y) = ||y_b||^2 - 2 <x_b, y_b>,  which differs
+// from ||x_b - y_b||^2 only by the row constant ||x_b||^2 (x_b, y_b: bf16-rounded operands;
+// fp16 operands for fp16 data).  The rerank (K2) recomputes FP32 distances and certifies
+// the list; rows it cannot certify are rescanned exactly.
+//
+// CTA organisation (one CTA per SM, persistent over 256-row blocks):
+//   warp 8      TMA producer: the row block's A tile once, then B tiles of 128 columns
+//               through an NST-stage ring (full / empty mbarriers)
+//   warp 9      TMEM owner (512 columns) and MMA issuer: per B tile, two M=128 x N=128
+//               accumulators (rows 0-127 and 128-255), K in steps of 16, into one of two TMEM
+//               buffers; tcgen05.commit frees the B stage and publishes the buffer
+//   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of accumulator w / 4,
+//               so each thread owns one row; 32 columns per tcgen05.ld; score = fma(-2, acc,
+//               ||y_b||^2); the minimum of 32 scores is compared with the row threshold and
+//               only then are entries appended to the row's buffer; full buffers are compacted
+//               by the warp (radix select) which lowers the threshold
+// All CTAs sweep the columns in the same order, so B tiles are shared through L2.
+// Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT, drains its own
+// TMA copies and MMAs (bounded) and frees TMEM before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "cng_internal.h"
+#include "device_common.cuh"
+#include "screen_tc.h"
+
+namespace cng {
+
+constexpr int TC_BM = 256;          // rows per CTA block (two M=128 accumulators)
+constexpr int TC_BN = 128;          // columns per B tile
+constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
+constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
+constexpr int TC_PRODUCER = 8;
+constexpr int TC_MMA = 9;
+constexpr uint32_t TC_SPIN = 1u << 28;  // wait iterations before declaring a timeout
+
+struct TcParams {
+  int64_t m, n;
+  int kpad, nkc;        // kpad / 64
+  int nst;              // B stages
+  int Lp, cap, self_excl;
+  uint32_t idesc;
+  const float* nb;
+  int32_t* ids;
+  uint32_t* thr;
+  uint64_t* rowbuf;
+  uint32_t* status;
+};
+
+// ---- PTX wrappers ------------------------------------------------------------------------------
+CNG_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+CNG_DEV void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+CNG_DEV void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+CNG_DEV void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+CNG_DEV bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false (and raises the CTA abort flag) on expiry or if aborted.
+CNG_DEV bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+  for (uint32_t i = 0; i < TC_SPIN; ++i) {
+    if (mbar_try(b, parity)) return true;
+    if ((i & 1023u) == 1023u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicOr(status, ST_TIMEOUT);
+  return false;
+}
+
+// Warp-uniform bounded wait: every lane polls, the warp proceeds only when all lanes saw the
+// phase complete, so the whole warp leaves together (needed before .sync.aligned TMEM loads).
+CNG_DEV bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+  for (uint32_t i = 0; i < TC_SPIN; ++i) {
+    if (__all_sync(FULL, mbar_try(b, parity))) return true;
+    if ((i & 1023u) == 1023u && __any_sync(FULL, *abort_flag != 0)) return false;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    *abort_flag = 1;
+    atomicOr(status, ST_TIMEOUT);
+  }
+  __syncwarp();
+  return false;
+}
+
+CNG_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of 1024 B.
+CNG_DEV uint64_t desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+
+CNG_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+CNG_DEV void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+CNG_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+CNG_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+CNG_DEV void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// ---- the kernel --------------------------------------------------------------------------------
+template <int CPL, bool DUMP>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 TcParams P, float* dump) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned tile region
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int a_bytes = TC_BM * P.kpad * 2;
+  const int b_bytes = TC_BN * P.kpad * 2;
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + a_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + P.nst * b_bytes);
+  uint64_t* b_full = bars;               // [nst]
+  uint64_t* b_empty = bars + P.nst;      // [nst]
+  uint64_t* t_full = bars + 2 * P.nst;   // [2]
+  uint64_t* t_empty = t_full + 2;        // [2]
+  uint64_t* a_full = t_empty + 2;        // [1]
+  uint64_t* a_empty = a_full + 1;        // [1]
+  uint64_t* fin = a_empty + 1;           // [1] MMA drain at exit
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nrb = (P.m + TC_BM - 1) / TC_BM;
+  const int ntiles = (int)((P.n + TC_BN - 1) / TC_BN);
+
+  if (tid == 0) {
+    for (int i = 0; i < P.nst; ++i) {
+      mbar_init(&b_full[i], 1);
+      mbar_init(&b_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&t_full[i], 1);
+      mbar_init(&t_empty[i], 8);
+    }
+    mbar_init(a_full, 1);
+    mbar_init(a_empty, 1);
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == TC_MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == TC_PRODUCER) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+      int64_t it = 0;
+      int j = 0;
+      bool ok = true;
+      for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
+        ok = mbar_wait(a_empty, (j & 1) ^ 1, abort_flag, P.status);
+        if (!ok) break;
+        mbar_expect_tx(a_full, (uint32_t)a_bytes);
+        for (int kc = 0; kc < P.nkc; ++kc)
+          tma_load_2d(sA + kc * (TC_BM * 128), &mapA, kc * TC_KC, (int)(rb * TC_BM), a_full);
+        for (int t = 0; t < ntiles; ++t, ++it) {
+          const int s = (int)(it % P.nst);
+          const uint32_t ph = (uint32_t)((it / P.nst) & 1);
+          ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
+          if (!ok) break;
+          mbar_expect_tx(&b_full[s], (uint32_t)b_bytes);
+          unsigned char* dst = sB + s * b_bytes;
+          for (int kc = 0; kc < P.nkc; ++kc)
+            tma_load_2d(dst + kc * (TC_BN * 128), &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
+        }
+      }
+      if (!ok) {
+        // drain: wait (bounded) for copies this thread issued into stages not yet consumed
+        for (int s = 0; s < P.nst; ++s) {
+          for (uint32_t i = 0; i < (1u << 20); ++i)
+            if (mbar_try(&b_full[s], 0) || mbar_try(&b_full[s], 1)) break;
+        }
+      }
+    }
+  } else if (warp == TC_MMA) {
+    if (lane == 0) {
+      int64_t it = 0, tt = 0;
+      int j = 0;
+      bool ok = true;
+      for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
+        ok = mbar_wait(a_full, j & 1, abort_flag, P.status);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(sA);
+        for (int t = 0; t < ntiles; ++t, ++it, ++tt) {
+          const int s = (int)(it % P.nst);
+          const int b = (int)(tt & 1);
+          ok = mbar_wait(&b_full[s], (uint32_t)((it / P.nst) & 1), abort_flag, P.status);
+          if (!ok) break;
+          ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> 1) & 1) ^ 1), abort_flag, P.status);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t b_base = smem_u32(sB + s * b_bytes);
+          for (int kc = 0; kc < P.nkc; ++kc) {
+#pragma unroll
+            for (int k16 = 0; k16 < TC_KC / 16; ++k16) {
+              const uint64_t bd = desc_sw128(b_base + kc * (TC_BN * 128) + k16 * 32);
+#pragma unroll
+              for (int acc = 0; acc < 2; ++acc) {
+                const uint64_t ad = desc_sw128(a_base + kc * (TC_BM * 128) + acc * (128 * 128) + k16 * 32);
+                mma_f16(tmem + (uint32_t)(b * 256 + acc * 128), ad, bd, P.idesc, (kc | k16) != 0);
+              }
+            }
+          }
+          mma_commit(&b_empty[s]);
+          mma_commit(&t_full[b]);
+        }
+        if (!ok) break;
+        mma_commit(a_empty);
+      }
+      // drain every MMA this thread issued before TMEM is released
+      mma_commit(fin);
+      for (uint32_t i = 0; i < (1u << 24); ++i)
+        if (mbar_try(fin, 0)) break;
+    }
+  } else {
+    // ---- epilogue: warps 0-7, one row per thread ----
+    const int quarter = warp & 3, accsel = warp >> 2;
+    const int rloc = accsel * 128 + quarter * 32 + lane;  // row within the block
+    uint64_t* rbuf = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rloc) * P.cap;
+    int64_t tt = 0;
+    bool ok = true;
+    for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+      const int64_t row = rb * TC_BM + rloc;
+      const bool live = row < P.m;
+      float thr = __int_as_float(0x7f800000);
+      int cnt = 0;
+      for (int t = 0; t < ntiles; ++t, ++tt) {
+        const int b = (int)(tt & 1);
+        ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> 1) & 1), abort_flag, P.status);
+        if (!ok) break;
+        tc_fence_after();
+        const int64_t c0 = (int64_t)t * TC_BN;
+        const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
+#pragma unroll 1
+        for (int ch = 0; ch < TC_BN / 32; ++ch) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + accsel * 128 + ch * 32), v);
+          const int64_t cb = c0 + ch * 32;
+          const float4* nb4 = reinterpret_cast<const float4*>(P.nb + cb);
+          float mn = __int_as_float(0x7f800000);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 y = __ldg(nb4 + q);
+            v[4 * q + 0] = fmaf(-2.f, v[4 * q + 0], y.x);
+            v[4 * q + 1] = fmaf(-2.f, v[4 * q + 1], y.y);
+            v[4 * q + 2] = fmaf(-2.f, v[4 * q + 2], y.z);
+            v[4 * q + 3] = fmaf(-2.f, v[4 * q + 3], y.w);
+          }
+          if (edge) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int64_t col = cb + jj;
+              if (col >= P.n || (P.self_excl && col == row)) v[jj] = __int_as_float(0x7f800000);
+            }
+          }
+          if (DUMP) {
+            if (live)
+              for (int jj = 0; jj < 32; ++jj)
+                if (cb + jj < P.n) dump[row * P.n + cb + jj] = v[jj];
+            continue;
+          }
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) mn = fminf(mn, v[jj]);
+          if (live && mn < thr) {
+#pragma unroll 1
+            for (int jj = 0; jj < 32; ++jj) {
+              if (v[jj] < thr) {
+                if (cnt < P.cap)
+                  rbuf[cnt] = ((uint64_t)fkey(v[jj]) << 32) | (uint32_t)(cb + jj);
+                else
+                  atomicOr(P.status, ST_OVERFLOW);
+                ++cnt;
+              }
+            }
+          }
+        }
+        // buffer drained: hand it back to the MMA warp
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&t_empty[b]);
+        if (DUMP) continue;
+        // compact every row whose buffer could overflow on the next tile
+        unsigned needc = __ballot_sync(FULL, cnt > P.cap - TC_BN);
+        while (needc) {
+          const int l = __ffs(needc) - 1;
+          needc &= needc - 1;
+          const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
+          uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
+          __syncwarp();
+          const uint32_t k = warp_compact<CPL>(buf_l, c_l, P.Lp, lane);
+          if (lane == l) {
+            thr = fkey_inv(k);
+            cnt = P.Lp;
+          }
+        }
+      }
+      if (!ok || DUMP) continue;
+      // final: keep Lp per row, write ids and the threshold key
+      uint32_t thk = fkey(thr);
+      if (isinf(thr) && thr > 0.f) thk = 0xffffffffu;
+      unsigned needf = __ballot_sync(FULL, cnt > P.Lp);
+      while (needf) {
+        const int l = __ffs(needf) - 1;
+        needf &= needf - 1;
+        const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
+        uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
+        __syncwarp();
+        const uint32_t k = warp_compact<CPL>(buf_l, c_l, P.Lp, lane);
+        if (lane == l) {
+          thk = k;
+          cnt = P.Lp;
+        }
+      }
+      __syncwarp();
+      if (live) {
+        const int c = min(cnt, P.Lp);
+        for (int t = 0; t < P.Lp; ++t) P.ids[row * P.Lp + t] = t < c ? key_id(rbuf[t]) : -1;
+        P.thr[row] = thk;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == TC_MMA) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+bool tc_screen_supported(int d, bool) { return d >= 1 && ((d + 63) / 64) * 64 <= 192; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kpad, int box_rows, bool fp16,
+                     std::string* msg) {
+  auto enc = get_encode();
+  if (!enc) {
+    if (msg) *msg = "cuTensorMapEncodeTiled unavailable; ";
+    return false;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_KC, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (msg) *msg = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + "); ";
+    return false;
+  }
+  return true;
+}
+
+static uint32_t make_idesc(bool fp16) {
+  uint32_t d = 0;
+  d |= 1u << 4;                      // D format: F32
+  d |= (fp16 ? 0u : 1u) << 7;        // A format: BF16 (1) / F16 (0)
+  d |= (fp16 ? 0u : 1u) << 10;       // B format
+  // bits 15/16 = 0: A and B K-major
+  d |= (uint32_t)(TC_BN >> 3) << 17; // N
+  d |= (uint32_t)(128 >> 4) << 24;   // M
+  return d;
+}
+
+template <int CPL, bool DUMP>
+static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
+                           size_t smem, int grid, cudaStream_t s, float* dump) {
+  cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel<CPL, DUMP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  screen_tc_kernel<CPL, DUMP><<<grid, TC_THREADS, smem, s>>>(ma, mb, p, dump);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::string* msg, float* dump) {
+  const int kpad = a.kpad;
+  if (kpad % 64 != 0 || kpad > 192) {
+    if (msg) *msg = "kpad must be a multiple of 64 and <= 192; ";
+    return cudaErrorInvalidValue;
+  }
+  TcParams p{};
+  p.m = a.m;
+  p.n = a.n;
+  p.kpad = kpad;
+  p.nkc = kpad / 64;
+  const int a_bytes = TC_BM * kpad * 2, b_bytes = TC_BN * kpad * 2;
+  const int budget = 220 * 1024 - a_bytes - 1024 - 256;
+  p.nst = std::min(4, budget / b_bytes);
+  if (p.nst < 2) {
+    if (msg) *msg = "shared memory too small for two B stages; ";
+    return cudaErrorInvalidValue;
+  }
+  p.Lp = a.Lp;
+  int cpl = 0;
+  for (int c : {8, 12, 16, 20})
+    if (c * 32 >= a.Lp + TC_BN + 32) { cpl = c; break; }
+  if (!cpl) {
+    if (msg) *msg = "screened list too long; ";
+    return cudaErrorInvalidValue;
+  }
+  p.cap = cpl * 32;
+  p.self_excl = a.self_excl;
+  p.idesc = make_idesc(a.fp16);
+  p.nb = a.nb;
+  p.ids = a.ids;
+  p.thr = a.thr;
+  p.status = a.status;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a.A, a.m, kpad, TC_BM, a.fp16, msg)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, a.B, a.n, kpad, TC_BN, a.fp16, msg)) return cudaErrorInvalidValue;
+  const int64_t nrb = (a.m + TC_BM - 1) / TC_BM;
+  const int grid = (int)std::min<int64_t>(nrb, num_sms());
+  // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
+  size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * b_bytes + 256;
+  smem = std::max<size_t>(smem, 116 * 1024);
+  if (!a.rowbuf || a.rowbuf_words < (size_t)grid * TC_BM * p.cap) {
+    if (msg) *msg = "row buffer missing or too small; ";
+    return cudaErrorInvalidValue;
+  }
+  p.rowbuf = a.rowbuf;
+  cudaError_t e;
+#define CNG_TC(C)                                                                             \
+  case C:                                                                                     \
+    e = dump ? launch_t<C, true>(ma, mb, p, smem, grid, s, dump)                              \
+             : launch_t<C, false>(ma, mb, p, smem, grid, s, dump);                            \
+    break;
+  switch (cpl) {
+    CNG_TC(8)
+    CNG_TC(12)
+    CNG_TC(16)
+    CNG_TC(20)
+    default:
+      e = cudaErrorInvalidValue;
+  }
+#undef CNG_TC
+  return e;
+}
+
+size_t screen_tc_rowbuf_words(int64_t m, int Lp) {
+  int cpl = 0;
+  for (int c : {8, 12, 16, 20})
+    if (c * 32 >= Lp + TC_BN + 32) { cpl = c; break; }
+  if (!cpl) cpl = 20;
+  const int64_t nrb = (m + TC_BM - 1) / TC_BM;
+  const int grid = (int)std::min<int64_t>(nrb, num_sms());
+  return (size_t)grid * TC_BM * cpl * 32;
+}
+
+cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg) {
+  return launch_impl(a, s, msg, nullptr);
+}
+
+cudaError_t launch_screen_tc_dump(const TcScreenArgs& a, float* dump, cudaStream_t s,
+                                  std::string* msg) {
+  return launch_impl(a, s, msg, dump);
+}
+
+}  // namespace cng

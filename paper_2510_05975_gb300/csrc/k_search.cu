@@ -1,0 +1,376 @@
+// k_search.cu -- batched beam search of Alg. 1 (K7), sm_103a.
+//
+// One persistent launch serves all queries: each warp takes the next query from an atomic
+// counter and runs Alg. 1 to completion; queries of any length share the launch.
+//
+// Per warp (shared memory):
+//   Q   sorted queue of <= L entries: key = (FP32 squared distance, id), an explored flag,
+//       and the canonical FP64 distance when one was needed (NaN otherwise)
+//   H   lossy visited filter (open addressing, <= 8 probes); a point missed by the filter is
+//       recomputed, then dropped by an exact key match against Q -- or it cannot re-enter Q,
+//       because a point that left Q is farther than Q's L-th entry, which never grows
+//   q   the query vector
+// One hop: first unexplored entry u* of Q (ballot), its out-list (one coalesced load), filter,
+// FP32 distances by 8-lane groups (16-byte vector loads), sort of the new batch, merge with
+// Q by merge-path ranks (binary search of each side in the other), truncation to L.
+//
+// Exactness: every comparison whose two FP32 squared distances are within the relative band
+// is decided by the canonical FP64 distance and id instead, so the queue order -- and with it
+// every hop, the returned ids and the hop count -- equals the FP64 definition of Alg. 1.
+// Integer data whose squared distances are exact in FP32 needs no FP64 at all.
+#include "cng_internal.h"
+#include "device_common.cuh"
+#include "search_internal.h"
+
+namespace cng {
+
+constexpr int SQ_G = 8;
+constexpr int SQ_MAXB = 64;  // batch capacity (R <= 64)
+
+struct QEnt {
+  uint64_t* k;   // keys
+  double* x;     // FP64 distance or NaN
+  uint8_t* e;    // explored
+};
+
+CNG_DEV bool has64(double v) { return !isnan(v); }
+
+// Exact-order comparison: a before b.
+CNG_DEV bool before(uint64_t ka, double xa, uint64_t kb, double xb, float band, int exact) {
+  if (!exact) {
+    float da = key_dist(ka), db = key_dist(kb);
+    if (near_tie(da, db, band) && has64(xa) && has64(xb))
+      return xa < xb || (xa == xb && key_id(ka) < key_id(kb));
+  }
+  return ka < kb;
+}
+
+CNG_DEV uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+// Returns true if v was not known to be visited (then it is recorded if there is room).
+CNG_DEV bool visit(int32_t* H, int hmask, int32_t v) {
+  uint32_t h = hash32((uint32_t)v) & hmask;
+  for (int p = 0; p < 8; ++p) {
+    int32_t* slot = H + ((h + p) & hmask);
+    int32_t cur = *slot;
+    if (cur == v) return false;
+    if (cur == -1) {
+      int32_t old = atomicCAS(slot, -1, v);
+      if (old == -1) return true;
+      if (old == v) return false;
+    }
+  }
+  return true;
+}
+
+template <typename T>
+CNG_DEV double canon_q(const float* __restrict__ q, const T* __restrict__ x, int d) {
+  return canon_dist(q, x, d);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+search_kernel(SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int L = a.L, dpad = a.dpad;
+  unsigned char* base = smem + (size_t)warp * a.warp_smem;
+  float* qv = reinterpret_cast<float*>(base);
+  uint64_t* Ak = reinterpret_cast<uint64_t*>(base + dpad * 4);
+  uint64_t* Bk = Ak + L;
+  double* Ax = reinterpret_cast<double*>(Bk + L);
+  double* Bx = Ax + L;
+  uint64_t* Nk = reinterpret_cast<uint64_t*>(Bx + L);
+  double* Nx = reinterpret_cast<double*>(Nk + SQ_MAXB);
+  int32_t* H = reinterpret_cast<int32_t*>(Nx + SQ_MAXB);
+  const int L16 = ((L + 15) / 16) * 16;
+  uint8_t* Ae = reinterpret_cast<uint8_t*>(H + a.hash_slots);
+  uint8_t* Be = Ae + L16;
+  int32_t* Nv = reinterpret_cast<int32_t*>(Be + L16);
+  const int hmask = a.hash_slots - 1;
+  const T* X = reinterpret_cast<const T*>(a.X);
+  const int g = lane % SQ_G, grp = lane / SQ_G;
+  unsigned long long t_ndc = 0, t_hops = 0, t_f64 = 0, t_stop = 0;
+
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(a.counter, 1);
+    qi = __shfl_sync(FULL, qi, 0);
+    if (qi >= a.nq) break;
+    const float* qg = a.Q + (int64_t)qi * a.d;
+    for (int c = lane; c < dpad; c += 32) qv[c] = c < a.d ? qg[c] : 0.f;
+    for (int c = lane; c < a.hash_slots; c += 32) H[c] = -1;
+    __syncwarp();
+    QEnt cur{Ak, Ax, Ae}, nxt{Bk, Bx, Be};
+    // entry point
+    {
+      float s = part_sqdist<SQ_G>(qv, X + (int64_t)a.entry * dpad, dpad, g);
+      s = group_reduce<SQ_G>(s);
+      if (lane == 0) {
+        cur.k[0] = pack_key(s, a.entry);
+        cur.x[0] = __longlong_as_double(0x7ff8000000000000ll);
+        cur.e[0] = 0;
+        H[hash32((uint32_t)a.entry) & hmask] = a.entry;
+      }
+    }
+    __syncwarp();
+    int len = 1, ndc = 1, hops = 0, flags = 0;
+    // every point is explored at most once, so n hops bound a correct search; the cap keeps a
+    // corrupted queue from looping
+    const int hop_cap = a.max_hops > 0 ? a.max_hops : (int)min(a.n, (int64_t)0x3fffffff);
+    for (;;) {
+      // first unexplored
+      int idx = -1;
+      for (int b = 0; b < len && idx < 0; b += 32) {
+        int t = b + lane;
+        unsigned bal = __ballot_sync(FULL, t < len && !cur.e[t]);
+        if (bal) idx = b + __ffs(bal) - 1;
+      }
+      if (idx < 0) break;
+      if (hops >= hop_cap) {
+        flags |= 2;
+        if (a.max_hops == 0 && lane == 0) atomicOr(a.status, ST_BOUNDS);
+        break;
+      }
+      const int32_t u = key_id(cur.k[idx]);
+      __syncwarp();
+      if (lane == 0) cur.e[idx] = 1;
+      ++hops;
+      const int du = a.deg[u];
+      // fresh neighbours -> Nv[0..nb)
+      int nb = 0;
+      for (int r = 0; r < a.R; r += 32) {
+        int j = r + lane;
+        int32_t v = j < du ? a.adj[(int64_t)u * a.R + j] : -1;
+        bool fresh = v >= 0 && visit(H, hmask, v);
+        unsigned bal = __ballot_sync(FULL, fresh);
+        if (fresh) Nv[nb + __popc(bal & ((1u << lane) - 1))] = v;
+        nb += __popc(bal);
+      }
+      __syncwarp();
+      ndc += nb;
+      if (nb == 0) continue;
+      // FP32 distances, 4 per round
+      for (int b0 = 0; b0 < nb; b0 += 32 / SQ_G) {
+        int b = b0 + grp;
+        float s = 0.f;
+        int32_t v = b < nb ? Nv[b] : 0;
+        if (b < nb) s = part_sqdist<SQ_G>(qv, X + (int64_t)v * dpad, dpad, g);
+        s = group_reduce<SQ_G>(s);
+        if (b < nb && g == 0) {
+          Nk[b] = pack_key(s, v);
+          Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+      }
+      int P2 = nb <= 32 ? 32 : 64;
+      for (int b = nb + lane; b < P2; b += 32) {
+        Nk[b] = ~0ull;
+        Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      __syncwarp();
+      // sort the batch by FP32 key (bitonic)
+      for (int kk = 2; kk <= P2; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < P2; i += 32) {
+            int ixj = i ^ j;
+            if (ixj > i) {
+              uint64_t x0 = Nk[i], y0 = Nk[ixj];
+              bool up = (i & kk) == 0;
+              if ((x0 > y0) == up) { Nk[i] = y0; Nk[ixj] = x0; }
+            }
+          }
+          __syncwarp();
+        }
+      // drop batch entries already in Q (exact key match; only when the filter lost them)
+      int nbv = nb;
+      for (int b = lane; b < nb; b += 32) {
+        uint64_t kb = Nk[b];
+        int lo = 0, hi = len;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (cur.k[mid] < kb) lo = mid + 1; else hi = mid;
+        }
+        // Q is in exact order, FP32 keys are near-sorted: scan the neighbourhood for equality
+        bool dup = false;
+        if (a.exact) {
+          dup = lo < len && cur.k[lo] == kb;
+        } else {
+          // Q is in exact order, its FP32 keys sorted up to near-ties: scan the window of
+          // entries whose FP32 distance lies within four bands of this one
+          const float db = key_dist(kb);
+          const float lo_d = db * (1.f - 4.f * a.band), hi_d = db * (1.f + 4.f * a.band);
+          int l2 = 0, h2 = len;
+          while (l2 < h2) {
+            int mid = (l2 + h2) >> 1;
+            if (key_dist(cur.k[mid]) < lo_d) l2 = mid + 1; else h2 = mid;
+          }
+          for (int t = l2; t < len && !dup; ++t) {
+            if (key_dist(cur.k[t]) > hi_d) break;
+            dup = cur.k[t] == kb;
+          }
+        }
+        if (dup) Nk[b] = ~0ull;
+      }
+      __syncwarp();
+      {
+        // compact survivors to the front keeping order
+        uint64_t kv[2];
+        bool keep[2];
+        int cnt_before = 0;
+        for (int r = 0; r < 2; ++r) {
+          int b = r * 32 + lane;
+          kv[r] = b < nb ? Nk[b] : ~0ull;
+          keep[r] = b < nb && kv[r] != ~0ull;
+        }
+        __syncwarp();
+        for (int r = 0; r < 2; ++r) {
+          unsigned bal = __ballot_sync(FULL, keep[r]);
+          if (keep[r]) Nk[cnt_before + __popc(bal & ((1u << lane) - 1))] = kv[r];
+          cnt_before += __popc(bal);
+        }
+        nbv = cnt_before;
+        __syncwarp();
+        for (int b = nbv + lane; b < P2; b += 32) Nk[b] = ~0ull;
+        __syncwarp();
+      }
+      if (nbv == 0) continue;
+      // near-ties: mark batch entries close to a neighbour in the batch or to a Q entry, and
+      // the Q entries concerned; give every marked entry its canonical FP64 distance
+      if (!a.exact) {
+        bool any = false;
+        for (int b = lane; b < nbv; b += 32) {
+          const float db = key_dist(Nk[b]);
+          bool mark = (b > 0 && near_tie(key_dist(Nk[b - 1]), db, a.band)) ||
+                      (b + 1 < nbv && near_tie(key_dist(Nk[b + 1]), db, a.band));
+          // Q entries within the band: Q keys are sorted up to near-ties; a linear scan of
+          // the window found by binary search on FP32 distance covers them
+          const float lo_d = db * (1.f - 4.f * a.band), hi_d = db * (1.f + 4.f * a.band);
+          int lo = 0, hi = len;
+          while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (key_dist(cur.k[mid]) < lo_d) lo = mid + 1; else hi = mid;
+          }
+          for (int t = lo; t < len; ++t) {
+            const float dq = key_dist(cur.k[t]);
+            if (dq > hi_d) break;
+            if (near_tie(dq, db, a.band)) {
+              mark = true;
+              if (!has64(cur.x[t]))
+                cur.x[t] = canon_q(qv, X + (int64_t)key_id(cur.k[t]) * dpad, a.d);
+            }
+          }
+          if (mark) {
+            Nx[b] = canon_q(qv, X + (int64_t)key_id(Nk[b]) * dpad, a.d);
+            any = true;
+          }
+        }
+        unsigned anyb = __ballot_sync(FULL, any);
+        __syncwarp();
+        if (anyb) {
+          flags |= 1;
+          t_f64 += __popc(anyb);
+          // exact re-sort of the batch (odd-even transposition over nbv <= 64)
+          for (int ph = 0; ph < nbv; ++ph) {
+            for (int b = 2 * lane + (ph & 1); b + 1 < nbv; b += 64) {
+              if (before(Nk[b + 1], Nx[b + 1], Nk[b], Nx[b], a.band, 0)) {
+                uint64_t tk = Nk[b]; Nk[b] = Nk[b + 1]; Nk[b + 1] = tk;
+                double tx = Nx[b]; Nx[b] = Nx[b + 1]; Nx[b + 1] = tx;
+              }
+            }
+            __syncwarp();
+          }
+        }
+      }
+      // merge: ranks by binary search of each side in the other (exact comparator)
+      const int nlen = min(len + nbv, L);
+      for (int i = lane; i < len; i += 32) {
+        uint64_t ki = cur.k[i];
+        double xi = cur.x[i];
+        int lo = 0, hi = nbv;  // # batch entries before Q[i]
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (before(Nk[mid], Nx[mid], ki, xi, a.band, a.exact)) lo = mid + 1; else hi = mid;
+        }
+        int pos = i + lo;
+        if (pos < nlen) { nxt.k[pos] = ki; nxt.x[pos] = xi; nxt.e[pos] = cur.e[i]; }
+      }
+      for (int b = lane; b < nbv; b += 32) {
+        uint64_t kb = Nk[b];
+        double xb = Nx[b];
+        int lo = 0, hi = len;  // # Q entries before batch[b]
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (before(cur.k[mid], cur.x[mid], kb, xb, a.band, a.exact)) lo = mid + 1; else hi = mid;
+        }
+        int pos = b + lo;
+        if (pos < nlen) { nxt.k[pos] = kb; nxt.x[pos] = xb; nxt.e[pos] = 0; }
+      }
+      __syncwarp();
+      QEnt t = cur; cur = nxt; nxt = t;
+      len = nlen;
+    }
+    // results
+    for (int t = lane; t < a.k; t += 32) {
+      bool ok = t < len;
+      a.ids[(int64_t)qi * a.k + t] = ok ? key_id(cur.k[t]) : -1;
+      a.dists[(int64_t)qi * a.k + t] = ok ? sqrtf(key_dist(cur.k[t])) : INFINITY;
+    }
+    if (lane == 0) {
+      if (a.ndc) a.ndc[qi] = ndc;
+      if (a.hops) a.hops[qi] = hops;
+      if (a.flags) a.flags[qi] = flags;
+    }
+    t_ndc += ndc;
+    t_hops += hops;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&a.tot[0], t_ndc);
+    atomicAdd(&a.tot[1], t_hops);
+  }
+  // t_f64 is per lane
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t_f64 += __shfl_xor_sync(FULL, t_f64, o);
+  if (lane == 0) {
+    if (t_f64) atomicAdd(&a.tot[2], t_f64);
+    if (t_stop) atomicAdd(&a.tot[3], t_stop);
+  }
+}
+
+size_t search_warp_smem(int dpad, int L, int hash_slots) {
+  size_t b = (size_t)dpad * 4 + 4 * (size_t)L * 8 + 2 * SQ_MAXB * 8 + (size_t)hash_slots * 4 +
+             2 * (((size_t)L + 15) / 16) * 16 + SQ_MAXB * 4;
+  return (b + 15) / 16 * 16;
+}
+
+// The kernel's shared-memory attribute is set by search_blocks_per_sm, which callers run
+// first (outside any stream capture).
+cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s) {
+  size_t sh = (size_t)warps_per_block * a.warp_smem;
+  if (a.dtype == CNG_F32)
+    search_kernel<float><<<grid, warps_per_block * 32, sh, s>>>(a);
+  else
+    search_kernel<__half><<<grid, warps_per_block * 32, sh, s>>>(a);
+  return cudaGetLastError();
+}
+
+int search_blocks_per_sm(int dtype, int warps_per_block, size_t smem) {
+  int nb = 0;
+  if (dtype == CNG_F32) {
+    cudaFuncSetAttribute(search_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<float>, warps_per_block * 32, smem);
+  } else {
+    cudaFuncSetAttribute(search_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<__half>, warps_per_block * 32, smem);
+  }
+  return nb;
+}
+
+}  // namespace cng

@@ -1,0 +1,35 @@
+// screen_tc.h -- tensor-core candidate screen (tcgen05 + TMA), host interface.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+
+#include <cuda_runtime.h>
+
+namespace cng {
+
+struct TcScreenArgs {
+  const void* A;      // rows   [m][kpad] bf16 (fp16 when fp16 != 0), zero padded
+  const void* B;      // columns [n][kpad]
+  int64_t m, n;
+  int kpad;           // multiple of 64
+  int fp16;
+  const float* nb;    // ||y_b||^2 per column (length >= n rounded up to 256, zero padded)
+  int Lp;             // screened list length per row
+  int self_excl;      // 1: row i is column i and is skipped
+  int32_t* ids;       // [m][Lp] screened ids (unordered), -1 padded
+  uint32_t* thr;      // [m] ordered key of the largest kept score (0xffffffff: all kept)
+  uint32_t* status;
+  uint64_t* rowbuf;     // scratch: screen_tc_rowbuf_words(m, Lp) words
+  size_t rowbuf_words;
+};
+
+bool tc_screen_supported(int d, bool fp16);
+size_t screen_tc_rowbuf_words(int64_t m, int Lp);
+cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg);
+// Test aid: writes every screened score s(x, y) to dump[m][n] instead of selecting.
+cudaError_t launch_screen_tc_dump(const TcScreenArgs& a, float* dump, cudaStream_t s,
+                                  std::string* msg);
+
+}  // namespace cng

@@ -9,15 +9,21 @@ This module holds only random-number recipes.  It contains none of the method's
 arithmetic, so both the CUDA path and the CPU oracle may read its output.
 
 Recipes (numpy ``Generator(PCG64(seed))``, rows generated in fixed chunks so the output
-does not depend on memory limits):
+does not depend on memory limits).  Descriptor collections such as SIFT, DEEP and BIGANN have
+a low intrinsic dimension inside each cluster, so their mixtures use low-rank cluster noise:
+x = c + A_c z + e with z ~ N(0, I_16) and a per-centre loading matrix A_c, plus a small
+isotropic term e.
 
 * ``gauss``      i.i.d. N(0, 1) float32.
-* ``sift``       64 centres uniform on the integers 40..215 per dimension, isotropic
-                 N(0, 25^2) noise, clipped to [0, 255] and rounded to integers (float32).
-* ``deep``       256 centres mu = g / ||g||, g ~ N(0, I); x = normalise(mu + 0.5 g' / sqrt(d)).
-* ``gist``       100 centres N(0, I); per (centre, dimension) standard deviation
-                 sqrt(v), v log-uniform on [0.01, 1].
-* ``bigann16``   1,024 centres N(0, I), noise N(0, 0.5^2), stored as float16.
+* ``sift``       64 centres uniform on the integers 40..215 per dimension; A_c entries
+                 N(0, 25^2 / 16) (per-coordinate std 25); e ~ N(0, 2^2); clipped to [0, 255]
+                 and rounded to integers (float32).
+* ``deep``       256 centres mu = g / ||g||, g ~ N(0, I); A_c entries N(0, 0.25 / (16 d));
+                 e ~ N(0, 0.05^2 / d); x = normalise(mu + A_c z + e) (unit norm).
+* ``gist``       100 centres N(0, I); per (centre, dimension) standard deviation sqrt(v),
+                 v log-uniform on [0.01, 1] (diagonal covariance).
+* ``bigann16``   1,024 centres N(0, I); A_c entries N(0, 0.25 / 16); e ~ N(0, 0.05^2);
+                 stored as float16.
 """
 from __future__ import annotations
 
@@ -67,21 +73,41 @@ WORKLOADS = {
 }
 
 
+LATENT = 16
+
+
 def _centres(kind: str, d: int, seed: int):
-    """Cluster centres (and per-centre scales) drawn from their own stream."""
+    """Cluster centres and per-centre noise parameters, drawn from their own stream."""
     rng = np.random.Generator(np.random.PCG64(seed * 7919 + 17))
+    m = LATENT
     if kind == "sift":
-        return rng.integers(40, 216, size=(64, d)).astype(np.float32), None
+        c = rng.integers(40, 216, size=(64, d)).astype(np.float32)
+        return c, (rng.standard_normal((64, d, m)) * (25.0 / np.sqrt(m))).astype(np.float32)
     if kind == "deep":
         g = rng.standard_normal((256, d))
-        return (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32), None
+        c = (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32)
+        return c, (rng.standard_normal((256, d, m)) * (0.5 / np.sqrt(m * d))).astype(np.float32)
     if kind == "gist":
         c = rng.standard_normal((100, d)).astype(np.float32)
         v = np.exp(rng.uniform(np.log(0.01), np.log(1.0), size=(100, d))).astype(np.float32)
         return c, np.sqrt(v).astype(np.float32)
     if kind == "bigann16":
-        return rng.standard_normal((1024, d)).astype(np.float32), None
+        c = rng.standard_normal((1024, d)).astype(np.float32)
+        return c, (rng.standard_normal((1024, d, m)) * (0.5 / np.sqrt(m))).astype(np.float32)
     return None, None
+
+
+def _lowrank(rng, A, a, m_rows):
+    """Rows A[a_i] z_i with z_i ~ N(0, I): one matrix product per centre present."""
+    z = rng.standard_normal((m_rows, A.shape[2]), dtype=np.float32)
+    out = np.empty((m_rows, A.shape[1]), np.float32)
+    order = np.argsort(a, kind="stable")
+    bounds = np.searchsorted(a[order], np.arange(A.shape[0] + 1))
+    for c in range(A.shape[0]):
+        rows = order[bounds[c]:bounds[c + 1]]
+        if rows.size:
+            out[rows] = z[rows] @ A[c].T
+    return out
 
 
 def generate(kind: str, n: int, d: int, seed: int, dtype: str = "float32",
@@ -98,18 +124,21 @@ def generate(kind: str, n: int, d: int, seed: int, dtype: str = "float32",
             blk = rng.standard_normal((m, d), dtype=np.float32)
         elif kind == "sift":
             a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + 25.0 * rng.standard_normal((m, d), dtype=np.float32)
+            blk = centres[a] + _lowrank(rng, scales, a, m)
+            blk += 2.0 * rng.standard_normal((m, d), dtype=np.float32)
             blk = np.rint(np.clip(blk, 0.0, 255.0))
         elif kind == "deep":
             a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + (0.5 / np.sqrt(d)) * rng.standard_normal((m, d), dtype=np.float32)
+            blk = centres[a] + _lowrank(rng, scales, a, m)
+            blk += (0.05 / np.sqrt(d)) * rng.standard_normal((m, d), dtype=np.float32)
             blk = blk / np.linalg.norm(blk, axis=1, keepdims=True)
         elif kind == "gist":
             a = rng.integers(0, centres.shape[0], size=m)
             blk = centres[a] + scales[a] * rng.standard_normal((m, d), dtype=np.float32)
         elif kind == "bigann16":
             a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + 0.5 * rng.standard_normal((m, d), dtype=np.float32)
+            blk = centres[a] + _lowrank(rng, scales, a, m)
+            blk += 0.05 * rng.standard_normal((m, d), dtype=np.float32)
         else:
             raise ValueError(f"unknown workload kind {kind!r}")
         out[r0:r0 + m] = blk

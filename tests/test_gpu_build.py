@@ -1,0 +1,108 @@
+"""GPU parity of the build path (K0 prep, K3 entry, K1 screen, K2 rerank, K4 prune, K5/K6 merge)
+against the FP64 oracle: candidate lists, phase-2 lists and the final graph must be identical
+element by element (every FP32 near-tie is re-decided in FP64 on the GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_05975_gb300 import synth
+
+from gpu_util import host, lib, need_gpu, tensor
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_graph(X, G, idx, cng, R, L):
+    cand, cdist, fwd, fdeg = cng.cng_lists(idx)
+    adj, deg, R_, entry = cng.cng_graph(idx)
+    assert entry == G.entry
+    c = host(cand)
+    bad = np.flatnonzero((c != G.cand).any(axis=1))
+    assert bad.size == 0, f"candidate lists differ at rows {bad[:10]}"
+    fd = host(fdeg)
+    assert np.array_equal(fd, G.fdeg)
+    assert np.array_equal(host(fwd), G.fwd)
+    assert np.array_equal(host(deg), G.deg)
+    assert np.array_equal(host(adj), G.adj)
+    # FP32 candidate distances within FP32 error of the canonical ones
+    _, ds = oracle.knn(X, L)
+    assert np.allclose(host(cdist), ds, rtol=2e-6, atol=0)
+
+
+@pytest.mark.parametrize("kind,n,d,alpha,tau,R,L,screen", [
+    ("gauss", 3000, 32, 1.2, 0.0, 16, 64, 0),
+    ("gauss", 2777, 20, 1.3, 0.25, 12, 40, 0),
+    ("sift", 3001, 128, 1.2, 0.0, 32, 128, 0),
+    ("deep", 2500, 96, 1.3, 0.0, 24, 80, 0),
+    ("gauss", 3000, 32, 1.2, 0.0, 16, 64, 1),
+    ("sift", 3001, 128, 1.2, 0.0, 32, 128, 1),
+])
+def test_build_matches_oracle(kind, n, d, alpha, tau, R, L, screen):
+    need_gpu()
+    cng = lib()
+    X = synth.generate(kind, n, d, seed=5)
+    idx, st = cng.cng_build(tensor(X), alpha=alpha, R=R, L=L, tau=tau, screen=screen, keep_lists=True)
+    G = oracle.build_graph(X, alpha, tau, R, L)
+    _check_graph(X, G, idx, cng, R, L)
+    if kind == "sift":
+        assert st["exact_int"] == 1
+    cng.cng_free(idx)
+
+
+def test_gauss10k_full_size():
+    """The 10,000 x 32 N(0,1) workload at its stated parameters (alpha 1.2, R 32, L 64)."""
+    need_gpu()
+    cng = lib()
+    w = synth.WORKLOADS["gauss10k"]
+    X = w.base()
+    idx, st = cng.cng_build(tensor(X), alpha=w.alpha, R=w.R, L=w.L, keep_lists=True)
+    G = oracle.build_graph(X, w.alpha, 0.0, w.R, w.L)
+    _check_graph(X, G, idx, cng, w.R, w.L)
+    cng.cng_free(idx)
+
+
+def test_host_points_and_fp16():
+    need_gpu()
+    cng = lib()
+    X = synth.generate("bigann16", 2000, 64, seed=3)  # float16 storage
+    idx, st = cng.cng_build(X, alpha=1.2, R=16, L=48, keep_lists=True)  # host array
+    G = oracle.build_graph(X.astype(np.float32), 1.2, 0.0, 16, 48)
+    _check_graph(X.astype(np.float32), G, idx, cng, 16, 48)
+    cng.cng_free(idx)
+
+
+def test_duplicates_and_tiny_n():
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(1)
+    base = rng.integers(0, 4, size=(40, 3)).astype(np.float32)  # many exact duplicates and ties
+    X = np.concatenate([base, base[:10]])
+    n = len(X)
+    idx, st = cng.cng_build(tensor(X), alpha=1.1, R=6, L=n - 1, keep_lists=True)
+    G = oracle.build_graph(X, 1.1, 0.0, 6, n - 1)
+    _check_graph(X, G, idx, cng, 6, n - 1)
+    cng.cng_free(idx)
+
+
+def test_ip_metric_requires_unit_norm():
+    need_gpu()
+    cng = lib()
+    X = synth.generate("gauss", 500, 16, seed=2)
+    with pytest.raises(cng.CngError) as e:
+        cng.cng_build(tensor(X), alpha=1.2, R=8, L=16, metric=cng.CNG_IP_AS_L2)
+    assert e.value.code == cng.CNG_E_INVAL
+    Xu = synth.generate("deep", 500, 16, seed=2)
+    idx, _ = cng.cng_build(tensor(Xu), alpha=1.3, R=8, L=16, metric=cng.CNG_IP_AS_L2)
+    cng.cng_free(idx)
+
+
+@pytest.mark.parametrize("screen", [0, 1])
+def test_knn_rows_vs_oracle(screen):
+    need_gpu()
+    cng = lib()
+    X = synth.generate("gauss", 5003, 48, seed=8)
+    Q = synth.generate("gauss", 300, 48, seed=9)
+    ids, ds, st = cng.cng_knn(tensor(X), 100, rows=tensor(Q), screen=screen)
+    ref, rd = oracle.knn(X, 100, rows=Q)
+    assert np.array_equal(host(ids), ref)
+    assert np.allclose(host(ds), rd, rtol=2e-6)

@@ -51,7 +51,8 @@ def test_merge_hand_worked(golden_dir):
         G = oracle.build_graph(X, g["alpha"], g["tau"], case["R"], g["L"])
         assert G.cand.tolist() == g["cand"]
         assert [G.fwd[p, : G.fdeg[p]].tolist() for p in range(len(X))] == g["fwd"]
-        assert [G.out(p).tolist() for p in range(len(X))] == case["adj"]
+        assert [G.adj3[p, : G.deg3[p]].tolist() for p in range(len(X))] == case["adj"]
+        assert [G.out(p).tolist() for p in range(len(X))] == case["adj4"]
 
 
 def _alpha_cg(X, alpha, tau):
@@ -137,8 +138,8 @@ def test_build_invariants_random():
         for v in G.fwd[u, : G.fdeg[u]]:
             inl[v].append(u)
     for p in range(n):
-        out = G.out(p).tolist()
-        assert len(out) == G.deg[p] <= R and len(set(out)) == len(out) and p not in out
+        out = G.adj3[p, : G.deg3[p]].tolist()
+        assert len(out) == G.deg3[p] <= R and len(set(out)) == len(out) and p not in out
         V = list(dict.fromkeys(G.fwd[p, : G.fdeg[p]].tolist() + inl[p]))
         if len(V) <= R:
             assert sorted(out) == sorted(V)  # assigned directly
@@ -153,3 +154,39 @@ def test_phase2_equals_alpha_cg_when_unbounded():
     cg = _alpha_cg(X, 1.3, 0.2)
     for p in range(n):
         assert G.fwd[p, : G.fdeg[p]].tolist() == cg[p].tolist()
+
+
+def _reachable(adj, deg, s):
+    seen, stack = {s}, [s]
+    while stack:
+        u = stack.pop()
+        for v in adj[u, : deg[u]]:
+            if int(v) not in seen:
+                seen.add(int(v))
+                stack.append(int(v))
+    return seen
+
+
+def test_connectivity_repair_on_clusters():
+    """Exact candidate lists on separated clusters leave the clusters disconnected; phase 4
+    must make every point reachable from the entry point, adding edges only from reached
+    points into unreached ones, at most R + slots per row."""
+    X = synth.generate("sift", 3000, 32, seed=3)
+    G = oracle.build_graph(X, 1.2, 0.0, 12, 30)
+    n = len(X)
+    assert len(_reachable(G.adj3, G.deg3, G.entry)) < n  # the phase-3 graph is disconnected
+    assert len(_reachable(G.adj, G.deg, G.entry)) == n
+    assert G.repair_edges > 0 and G.repair_rounds >= 1
+    assert np.all(G.deg <= 12 + oracle.REPAIR_SLOTS)
+    for p in range(n):  # phase-3 edges kept in place, repair edges appended
+        assert np.array_equal(G.adj[p, : G.deg3[p]], G.adj3[p, : G.deg3[p]])
+    # the first round's edges: r -> smallest p whose search from the entry ends at r
+    reach0 = _reachable(G.adj3, G.deg3, G.entry)
+    U = np.array(sorted(set(range(n)) - reach0), np.int32)
+    ids, _, _, _ = oracle.search(X, G.adj3, G.deg3, G.entry, X[U], 1, oracle.CONNECT_L)
+    first = {}
+    for p, r in zip(U, ids[:, 0]):
+        first.setdefault(int(r), int(p))
+    for r, p in first.items():
+        assert int(r) in reach0
+        assert G.adj[r, G.deg3[r]] == p
