@@ -3,9 +3,11 @@
 Workload (default ``sift1m``): 1,000,000 x 128 integer-valued float32 points from a seeded
 64-centre Gaussian mixture (a synthetic stand-in for SIFT1M), alpha 1.2, tau 0, R 32, L 128;
 10,000 queries from the same mixture, k = 10.  One step = one full build (prep, entry point,
-exact candidate lists, pruning, reverse merge) plus one batched fixed-L search of all queries
-at the smallest beam width L_s reaching Recall@10 >= 0.95 (calibrated once, before timing,
-against brute-force ground truth from the library's exact k-NN).
+exact candidate lists, pruning, reverse merge, connectivity), training of the learned stop
+network on traces of 16,000 training queries, one batched fixed-L search of all queries at
+the smallest beam width reaching Recall@10 >= 0.955 on 4,000 held-out calibration queries,
+and one batched learned-stop search at the fastest (beam, threshold) reaching the same target
+on the calibration queries.  Ground truth: the library's exact k-NN.
 
 Printed JSON: value = build seconds (device-resident input), e2e = the same through the C ABI
 from pinned host memory (H2D copy inside the timed region, results read back), search QPS,
@@ -154,8 +156,6 @@ def run_reference(args):
     times = []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        base = oracle_baseline(X, Q[:64], np.zeros((1, 1), np.int32), np.zeros(1, np.int32), 0, w,
-                               w.k, 16, budget_s=8.0) if False else None
         rng = np.random.default_rng(step)
         rows = rng.integers(0, X.shape[0], size=16)
         ids, _ = oracle.knn(X, w.L, rows=X[rows], exclude_self=False)
@@ -220,55 +220,102 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ground truth (exact k-NN of the queries, the library's own exact path) and L calibration
+    # ground truth (exact k-NN, the library's own exact path) for evaluation and calibration
+    # queries; the calibration queries are held-out training queries, never the evaluation set
+    T_all = w.train_queries()
+    n_cal = min(4000, len(T_all) // 5)
+    Tq = torch.from_numpy(T_all[: len(T_all) - n_cal].astype(np.float32)).cuda()
+    Cq = torch.from_numpy(T_all[len(T_all) - n_cal:].astype(np.float32)).cuda()
     base32 = xd.float() if dtype_t == torch.float16 else xd
-    gt_ids, _, _ = cng.cng_knn(base32, w.k, rows=qd, screen=screen)
-    gt = gt_ids.cpu().numpy()
+    gt = cng.cng_knn(base32, w.k, rows=qd, screen=screen)[0].cpu().numpy()
+    gt_cal = cng.cng_knn(base32, w.k, rows=Cq, screen=screen)[0].cpu().numpy()
     idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
-    Ls, rec_s = None, None
-    sweep = []
+    TARGET = 0.955  # calibration target, a margin above the 0.95 reported on the evaluation set
+
+    def timed_search(q, **kw):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cng.cng_search(idx, q, k=w.k, use_graph=True, with_stats=False, **kw)  # warm / capture
+        ev0.record(stream)
+        r = cng.cng_search(idx, q, k=w.k, use_graph=True, with_stats=False, **kw)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return r, ev0.elapsed_time(ev1)
+
+    Ls, sweep = None, []
     for L in L_SWEEP:
         if L < w.k:
             continue
-        r = cng.cng_search(idx, qd, k=w.k, L=L, use_graph=True)
-        rc = recall_at_k(r["ids"].cpu().numpy(), gt)
-        sweep.append((L, rc))
-        if rc >= 0.95 and Ls is None:
-            Ls, rec_s = L, rc
+        r, ms = timed_search(Cq, L=L)
+        rc = recall_at_k(r["ids"].cpu().numpy(), gt_cal)
+        sweep.append((L, rc, ms))
+        if rc >= TARGET and Ls is None:
+            Ls = L
     if Ls is None:
-        Ls, rec_s = L_SWEEP[-1], sweep[-1][1]
+        Ls = L_SWEEP[-1]
+    # learned stop: one model per candidate beam width, thresholds chosen on calibration queries
+    THETAS = (0.5, 0.7, 0.8, 0.9, 0.95, 0.98, 0.99)
+    best = None
+    lsweep = []
+    cand_L = [L for L in L_SWEEP if L >= Ls][:3]
+    for L in cand_L:
+        model, tst = cng.cng_stop_train(idx, Tq, k=w.k, L=L, seed=1)
+        for th in THETAS:
+            r, ms = timed_search(Cq, L=L, mode=cng.CNG_SEARCH_LEARNED, model=model, threshold=th,
+                                 check_every=1)
+            rc = recall_at_k(r["ids"].cpu().numpy(), gt_cal)
+            lsweep.append((L, th, rc, ms))
+            if rc >= TARGET and (best is None or ms < best[2]):
+                best = (L, th, ms)
+        model.free()
+    if best is None:
+        best = (Ls, 0.99, float("inf"))
+    Ll, theta = best[0], best[1]
     adj, deg, _, entry = cng.cng_graph(idx)
     adj_h, deg_h = adj.cpu().numpy(), deg.cpu().numpy()
     cng.cng_free(idx)
 
-    # timed device-resident steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    build_ms, search_ms, step_ms, screen_ms = [], [], [], []
+    # timed device-resident steps: build, stop-model training, fixed-L search, learned search
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    build_ms, train_ms, fix_ms, lrn_ms, step_ms, screen_ms = [], [], [], [], [], []
     last_stats = None
     total = args.warmup + args.steps
     sampler = ClockSampler(local)
+    L0 = 0
     for step in range(total):
         timed = step >= args.warmup
         if step == args.warmup:
             barrier()
+            L0 = cng.lib().cngx_launches()
             sampler.__enter__()
         ev[0].record(stream)
         idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
         ev[1].record(stream)
-        res = cng.cng_search(idx, qd, k=w.k, L=Ls, use_graph=True, with_stats=False)
+        model, tst = cng.cng_stop_train(idx, Tq, k=w.k, L=Ll, seed=1)
         ev[2].record(stream)
+        res_f = cng.cng_search(idx, qd, k=w.k, L=Ls, use_graph=True, with_stats=False)
+        ev[3].record(stream)
+        res_l = cng.cng_search(idx, qd, k=w.k, L=Ll, mode=cng.CNG_SEARCH_LEARNED, model=model,
+                               threshold=theta, check_every=1, use_graph=True, with_stats=False)
+        ev[4].record(stream)
         torch.cuda.synchronize()
         if timed:
             build_ms.append(ev[0].elapsed_time(ev[1]))
-            search_ms.append(ev[1].elapsed_time(ev[2]))
-            step_ms.append(ev[0].elapsed_time(ev[2]))
+            train_ms.append(ev[1].elapsed_time(ev[2]))
+            fix_ms.append(ev[2].elapsed_time(ev[3]))
+            lrn_ms.append(ev[3].elapsed_time(ev[4]))
+            step_ms.append(ev[0].elapsed_time(ev[4]))
             screen_ms.append(bst["ms_screen"])
             last_stats = bst
+        model.free()
         if step < total - 1:
             cng.cng_free(idx)
     barrier()
     sampler.__exit__()
-    rec = recall_at_k(res["ids"].cpu().numpy(), gt)
+    launches = cng.lib().cngx_launches() - L0
+    rec_f = recall_at_k(res_f["ids"].cpu().numpy(), gt)
+    rec_l = recall_at_k(res_l["ids"].cpu().numpy(), gt)
+    hops_f = float(res_f["hops"].float().mean())
+    hops_l = float(res_l["hops"].float().mean())
     cng.cng_free(idx)
 
     def allmax(v):
@@ -279,9 +326,12 @@ def main():
         return float(t.item())
 
     b_s = allmax(float(np.mean(build_ms)) / 1e3)
-    s_ms = allmax(float(np.mean(search_ms)))
+    f_ms = allmax(float(np.mean(fix_ms)))
+    l_ms = allmax(float(np.mean(lrn_ms)))
+    t_ms = allmax(float(np.mean(train_ms)))
     st_ms = allmax(float(np.mean(step_ms)))
-    qps = w.nq / (s_ms / 1e3)
+    qps_f = w.nq / (f_ms / 1e3)
+    qps_l = w.nq / (l_ms / 1e3)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -340,15 +390,22 @@ def main():
                            "R": w.R, "L": w.L, "nq": w.nq, "k": w.k, "screen": args.screen,
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (512 MB points)"},
-                "search": {"L": Ls, "qps": qps * ws, "recall_at_10": rec, "ms": s_ms,
-                           "L_sweep": sweep, "ndc_mean": None},
+                "search": {"fixed": {"L": Ls, "qps": qps_f * ws, "recall_at_10": rec_f, "ms": f_ms,
+                                     "hops_mean": hops_f},
+                           "learned": {"L": Ll, "threshold": theta, "check_every": 1,
+                                       "qps": qps_l * ws, "recall_at_10": rec_l, "ms": l_ms,
+                                       "hops_mean": hops_l, "train_ms": t_ms},
+                           "learned_over_fixed_qps": qps_l / qps_f,
+                           "calibration": {"queries": int(n_cal), "target": TARGET,
+                                           "fixed_sweep": sweep, "learned_sweep": lsweep}},
                 "build_phases_ms": {k_: last_stats[k_] for k_ in
                                     ("ms_prep", "ms_entry", "ms_screen", "ms_rerank", "ms_prune",
-                                     "ms_merge")} if last_stats else None,
+                                     "ms_merge", "ms_connect")} if last_stats else None,
                 "build_counts": {k_: last_stats[k_] for k_ in
                                  ("n_edges", "cert_fail_rows", "order_ties", "rule_ties",
-                                  "merge_repruned", "merge_max_list", "exact_int")} if last_stats else None,
-                "e2e": e2e, "gpu_launches": None, "roofline": roof, "cpu_baseline": cpu,
+                                  "merge_repruned", "merge_max_list", "repair_edges", "repair_rounds",
+                                  "exact_int", "screen_used")} if last_stats else None,
+                "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if ws > 1:

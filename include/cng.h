@@ -56,6 +56,8 @@ typedef enum {
  *   tie_band         relative band for FP64 re-decision, >= 5e-6 (default 1e-5)
  *   margin           screened list size is L + margin (default 32; clipped to n - 1)
  *   keep_lists       1: keep candidate and phase-2 lists for cng_lists()
+ *   connect_L        beam width of the phase-4 connectivity searches (0 = 32; < 0 skips
+ *                    phase 4, leaving points of separated clusters unreachable)
  */
 typedef struct {
   double alpha;
@@ -67,17 +69,21 @@ typedef struct {
   double tie_band;
   int32_t margin;
   int32_t keep_lists;
+  int32_t connect_L;
 } cng_build_params;
 
 /* Per-phase times (device events, milliseconds) and near-tie / certification counts. */
 typedef struct {
-  double ms_total, ms_prep, ms_entry, ms_screen, ms_rerank, ms_prune, ms_merge;
+  double ms_total, ms_prep, ms_entry, ms_screen, ms_rerank, ms_prune, ms_merge, ms_connect;
   int64_t n_edges;            /* edges of the final graph */
   int64_t cert_fail_rows;     /* rows whose screened list could not be certified, rescanned */
   int64_t order_ties;         /* candidate-order near-ties re-decided in FP64 */
   int64_t rule_ties;          /* pruning comparisons re-decided in FP64 */
   int64_t merge_repruned;     /* nodes whose merged list exceeded R and was pruned again */
   int64_t merge_max_list;     /* largest merged candidate set */
+  int64_t repair_edges;       /* edges added by phase 4 (connectivity) */
+  int32_t repair_rounds;      /* phase-4 rounds */
+  int32_t screen_used;        /* cng_screen actually used (the tensor-core screen needs d <= 192) */
   int32_t entry;              /* navigating node s */
   int32_t exact_int;          /* 1 when every FP32 squared distance is an exact integer */
   double screen_err_max;      /* largest |screened - rerank| seen on kept candidates */
@@ -86,12 +92,16 @@ typedef struct {
 typedef struct cng_index cng_index;
 
 /*
- * cng_build -- Alg. 3 phases 1-3 with exact candidates (Sec. 4.1, 4.3):
+ * cng_build -- Alg. 3 with exact candidates (Sec. 4.1, 4.3):
  *   navigating node s = point nearest the centroid (phase 1);
  *   for each p: the exact L nearest points of P \ {p} by (D, id), then Alg. 2 with the rule
  *   of Def. 2 (Eq. 1) and the out-degree cut at R (phase 2);
  *   reverse edges from the phase-2 snapshot, each node's merged set pruned once if it
- *   exceeds R, else kept in (D, id) order (phase 3, lazy pruning of Sec. 4.3).
+ *   exceeds R, else kept in (D, id) order (phase 3, lazy pruning of Sec. 4.3);
+ *   connectivity (phase 4): in rounds, every point p not reachable from s is searched for from
+ *   s (Alg. 1, beam connect_L, k = min(8, connect_L)); its first result r whose row has a free
+ *   slot names p, and each named r gets an edge to the smallest point naming it.  Rows hold up
+ *   to R pruned edges plus up to 8 such edges.
  * points: host or device, n x d of `dtype`, borrowed for the call only (the index keeps its own
  * device copy).  *out receives a new index owned by the caller (free with cng_free).
  * stats may be NULL.  Synchronises `stream` before returning.
@@ -107,8 +117,9 @@ void cng_free(cng_index *index);
 const char *cng_last_error(void);
 
 /*
- * cng_graph -- borrow the final graph: adj_dev [n][R] int32 (-1 padded, each row in the order
- * the construction produced), deg_dev [n] int32, plus R, the entry point and n.  The pointers
+ * cng_graph -- borrow the final graph: adj_dev [n][stride] int32 (-1 padded, each row in the
+ * order the construction produced: phase-3 edges, then phase-4 edges), deg_dev [n] int32,
+ * `R` receives the row stride (degree bound + 8), plus the entry point and n.  The pointers
  * stay valid until cng_free.  Any output pointer may be NULL.
  */
 cng_status cng_graph(const cng_index *index, const int32_t **adj_dev, const int32_t **deg_dev,
@@ -119,10 +130,11 @@ cng_status cng_graph(const cng_index *index, const int32_t **adj_dev, const int3
  *   cand_dev  [n][L] int32  exact candidate lists in (D, id) order
  *   cdist_dev [n][L] float  their FP32 distances
  *   fwd_dev   [n][R] int32  phase-2 out-lists (-1 padded), fdeg_dev [n] int32
- * Returns CNG_E_INVAL if the index was built without keep_lists.
+ * plus L and the degree bound R.  Returns CNG_E_INVAL if the index was built without
+ * keep_lists.
  */
 cng_status cng_lists(const cng_index *index, const int32_t **cand_dev, const float **cdist_dev,
-                     int32_t *L, const int32_t **fwd_dev, const int32_t **fdeg_dev);
+                     int32_t *L, const int32_t **fwd_dev, const int32_t **fdeg_dev, int32_t *R);
 
 /* ---------------------------------------------------------------------------------------
  * Search (Alg. 1), batched: one persistent launch serves every query.
@@ -173,6 +185,75 @@ cng_status cng_search(const cng_index *index, const float *queries, int64_t nq, 
                       int32_t L, const cng_search_params *params, int32_t *ids, float *dists,
                       int32_t *ndc, int32_t *hops, int32_t *flags, void *stream,
                       cng_search_stats *stats);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned early stop.  Not part of the paper (its search stops only by Alg. 1's rule): a
+ * 16 -> 64 -> 64 -> 1 ReLU network reads the state of a search after a hop and predicts whether
+ * the top-k result list is already final; the learned search mode stops when the predicted
+ * probability reaches a threshold.  Features after hop t (lg = natural log, floored at 1e-30;
+ * D0 = entry distance; D1, Dk, DL = distances of the 1st, min(k,|Q|)-th and last queue entry;
+ * Du = the hop vertex's distance; Dk_h[j] = Dk after hop j, Dk_h[0] = D0; tlc = last hop at
+ * which the first min(k, |Q|) ids changed; U = unexplored entries; ins = this hop's points left
+ * in Q; stride = adjacency row stride):
+ *   f0 lg D0, f1 ln(1+t), f2 lg D1 - lg D0, f3 lg Dk - lg D0, f4 lg DL - lg D0, f5 lg Du - lg Dk,
+ *   f6..f11 lg Dk_h[max(t-j,0)] - lg Dk for j = 1,2,4,8,16,32, f12 ln(1 + t - tlc), f13 U/L,
+ *   f14 |Q|/L, f15 ins/stride.
+ * Training samples: every hop t <= max_trace of the plain search of each training query, label
+ * 1 iff t >= that query's final tlc.  Parameters (flat FP32, CNG_STOP_NPARAMS):
+ *   W1[64][16] b1[64] W2[64][64] b2[64] w3[64] b3[1];  inputs standardised by mu[16], sigma[16].
+ * Inference uses BF16-rounded weights with FP32 arithmetic.
+ * ------------------------------------------------------------------------------------- */
+
+#define CNG_STOP_NPARAMS 5313
+
+typedef struct {
+  int32_t k;          /* result size the model is trained for */
+  int32_t L;          /* beam width of the traced searches (and of the learned searches) */
+  int32_t max_trace;  /* hops recorded per training query (0 = 256) */
+  int32_t epochs;     /* passes over the samples (0 = 4) */
+  int32_t batch;      /* minibatch rows (0 = 4096) */
+  float lr;           /* Adam learning rate (0 = 1e-3) */
+  uint64_t seed;      /* weight initialisation and minibatch draws (counter-based hash) */
+} cng_train_params;
+
+typedef struct {
+  double ms_trace, ms_train;  /* device time of the traced search and of the training */
+  int64_t samples, positives, steps;
+  float loss_first, loss_last;  /* mean loss of the first and last minibatch */
+} cng_train_stats;
+
+/*
+ * cng_stop_train -- trace the plain search of nq training queries (f32 [nq][d], host or
+ * device) on `index`, then train the stop network on the GPU (forward, backward and Adam
+ * kernels).  *out receives a model owned by the caller (cng_stop_free).  Synchronises.
+ */
+cng_status cng_stop_train(const cng_index *index, const float *train_queries, int64_t nq,
+                          const cng_train_params *params, void *stream, cng_stop_model **out,
+                          cng_train_stats *stats);
+void cng_stop_free(cng_stop_model *model);
+/* Copy the FP32 master parameters [CNG_STOP_NPARAMS] and mu[16], sigma[16] to host memory
+ * (any pointer may be NULL).  bf16_params, if not NULL, receives the BF16-rounded parameter
+ * values inference uses (as floats, same layout). */
+cng_status cng_stop_export(const cng_stop_model *model, float *params, float *mu, float *sigma,
+                           float *bf16_params);
+/* A model from given host parameters (layout above); for tests and reloading. */
+cng_status cng_stop_import(const float *params, const float *mu, const float *sigma,
+                           cng_stop_model **out);
+/*
+ * cng_trace -- the plain search (Alg. 1) of nq device queries recording, for every hop
+ * t <= max_trace, the 16 features into feats_dev [nq][max_trace][16] (entries past a query's
+ * last hop are left untouched), plus hops_dev [nq], tlc_dev [nq] and ids_dev [nq][k].
+ */
+cng_status cng_trace(const cng_index *index, const float *queries_dev, int64_t nq, int32_t k,
+                     int32_t L, int32_t max_trace, float *feats_dev, int32_t *hops_dev,
+                     int32_t *tlc_dev, int32_t *ids_dev, void *stream);
+/* Mean loss and its gradient over B standardised rows x_dev [B][16] with labels y_dev [B]
+ * (the training kernels, exposed for gradient checks).  Synchronises. */
+cng_status cng_mlp_grad(const float *params_dev, const float *x_dev, const float *y_dev,
+                        int64_t B, float *grad_dev, float *loss_dev, void *stream);
+/* One Adam step (t >= 1) on device arrays of CNG_STOP_NPARAMS floats. */
+cng_status cng_mlp_adam(float *params_dev, float *m_dev, float *v_dev, const float *grad_dev,
+                        int64_t t, float lr, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * Exact k-NN (the candidate step of cng_build, exposed for ground truth and tests).

@@ -22,6 +22,10 @@ extern "C" {
 cng_status cngx_tc_scores(const float *rows_dev, int64_t m, const float *cols_dev, int64_t n,
                           int32_t d, float *scores_dev, void *stream);
 
+/* Number of CUDA kernel launches this library has issued since it was loaded (each launch
+ * site counts once per launch). */
+long long cngx_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -425,10 +425,10 @@ int or_search(const float *X, int64_t n, int d, const int32_t *adj, const int32_
  * The paper adds "necessary edges" from the DFS tree of s to every point outside it, in line
  * with NSG, without fixing which.  Our reading, in rounds until every point is reachable:
  *   reached = points reachable from s;
- *   for every unreached p: r(p) = the nearest result of beam-search(G, x_p, s, Lc, 1) on the
- *     current graph (necessarily a reached point);
- *   every reached r named by some r(p) gets the edge r -> (smallest such p) if its row has a
- *     free slot (deg < Rs).
+ *   for every unreached p: beam-search(G, x_p, s, Lc, kc) on the current graph, kc = min(8, Lc);
+ *     r(p) = the first of its results (nearest first; all reached points) whose row has a free
+ *     slot (deg < Rs, degrees as at the start of the round); none: p waits for a later round;
+ *   every reached r named by some r(p) gets the edge r -> (smallest such p).
  * adj rows have stride Rs; phase-3 rows use at most R < Rs of them.  Returns the number of
  * edges added (rounds in *rounds_out), or -3 if a round could add no edge.
  */
@@ -462,22 +462,27 @@ int or_connect(const float *X, int64_t n, int d, int32_t *adj, int32_t *deg, int
             if (!reach[i]) U[nu++] = (int32_t)i;
         if (nu == 0) break;
         ++rounds;
+        const int kc = Lc < 8 ? Lc : 8;
         float *Qm = (float *)malloc(sizeof(float) * nu * d);
-        int32_t *rid = (int32_t *)malloc(sizeof(int32_t) * nu);
-        double *rd = (double *)malloc(sizeof(double) * nu);
+        int32_t *rid = (int32_t *)malloc(sizeof(int32_t) * nu * kc);
+        double *rd = (double *)malloc(sizeof(double) * nu * kc);
         if (!Qm || !rid || !rd) return OR_E_NOMEM;
         for (int64_t i = 0; i < nu; ++i) memcpy(Qm + i * d, X + (int64_t)U[i] * d, sizeof(float) * d);
-        or_search(X, n, d, adj, deg, Rs, s, Qm, nu, 1, Lc, rid, rd, NULL, NULL);
-        for (int64_t i = 0; i < nu; ++i) /* U ascending: the first p naming r is the smallest */
-            if (best[rid[i]] < 0) best[rid[i]] = U[i];
+        or_search(X, n, d, adj, deg, Rs, s, Qm, nu, kc, Lc, rid, rd, NULL, NULL);
+        for (int64_t i = 0; i < nu; ++i) { /* U ascending: the first p naming r is the smallest */
+            int32_t r = -1;
+            for (int t = 0; t < kc && r < 0; ++t) {
+                int32_t c = rid[i * kc + t];
+                if (c >= 0 && deg[c] < Rs) r = c;
+            }
+            if (r >= 0 && best[r] < 0) best[r] = U[i];
+        }
         int added = 0;
         for (int64_t r = 0; r < n; ++r) {
             if (best[r] < 0) continue;
-            if (deg[r] < Rs) {
-                adj[r * Rs + deg[r]] = best[r];
-                deg[r] += 1;
-                ++added;
-            }
+            adj[r * Rs + deg[r]] = best[r];
+            deg[r] += 1;
+            ++added;
             best[r] = -1;
         }
         free(Qm);

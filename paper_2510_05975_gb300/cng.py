@@ -25,7 +25,9 @@ CNG_SCREEN_FP32, CNG_SCREEN_TC = 0, 1
 CNG_SEARCH_FIXED, CNG_SEARCH_LEARNED = 0, 1
 
 EXPORTS = ("cng_build", "cng_free", "cng_last_error", "cng_graph", "cng_lists", "cng_search",
-           "cng_knn")
+           "cng_knn", "cng_stop_train", "cng_stop_free", "cng_stop_export", "cng_stop_import",
+           "cng_trace", "cng_mlp_grad", "cng_mlp_adam")
+CNG_STOP_NPARAMS = 5313
 
 
 class CngError(RuntimeError):
@@ -38,16 +40,18 @@ class BuildParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("R", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("metric", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("tie_band", ctypes.c_double), ("margin", ctypes.c_int32),
-                ("keep_lists", ctypes.c_int32)]
+                ("keep_lists", ctypes.c_int32), ("connect_L", ctypes.c_int32)]
 
 
 class BuildStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in
-                ("ms_total", "ms_prep", "ms_entry", "ms_screen", "ms_rerank", "ms_prune", "ms_merge")] + \
+                ("ms_total", "ms_prep", "ms_entry", "ms_screen", "ms_rerank", "ms_prune", "ms_merge",
+                 "ms_connect")] + \
                [(f, ctypes.c_int64) for f in
                 ("n_edges", "cert_fail_rows", "order_ties", "rule_ties", "merge_repruned",
-                 "merge_max_list")] + \
-               [("entry", ctypes.c_int32), ("exact_int", ctypes.c_int32),
+                 "merge_max_list", "repair_edges")] + \
+               [("repair_rounds", ctypes.c_int32), ("screen_used", ctypes.c_int32),
+                ("entry", ctypes.c_int32), ("exact_int", ctypes.c_int32),
                 ("screen_err_max", ctypes.c_double)]
 
 
@@ -61,6 +65,18 @@ class SearchStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("ndc_total", ctypes.c_int64),
                 ("hops_total", ctypes.c_int64), ("fp64_decisions", ctypes.c_int64),
                 ("stopped_early", ctypes.c_int64), ("warps_per_block", ctypes.c_int32)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("L", ctypes.c_int32), ("max_trace", ctypes.c_int32),
+                ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class TrainStats(ctypes.Structure):
+    _fields_ = [("ms_trace", ctypes.c_double), ("ms_train", ctypes.c_double),
+                ("samples", ctypes.c_int64), ("positives", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float)]
 
 
 def _as_dict(st) -> dict:
@@ -89,13 +105,30 @@ def lib():
                                     ctypes.POINTER(i32), ctypes.POINTER(i64)]
             L.cng_lists.restype = ctypes.c_int
             L.cng_lists.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32),
-                                    ctypes.POINTER(vp), ctypes.POINTER(vp)]
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32)]
             L.cng_search.restype = ctypes.c_int
             L.cng_search.argtypes = [vp, vp, i64, i32, i32, ctypes.POINTER(SearchParams), vp, vp, vp,
                                      vp, vp, vp, ctypes.POINTER(SearchStats)]
             L.cng_knn.restype = ctypes.c_int
             L.cng_knn.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.c_double, vp, vp, vp,
                                   ctypes.POINTER(BuildStats)]
+            L.cng_stop_train.restype = ctypes.c_int
+            L.cng_stop_train.argtypes = [vp, vp, i64, ctypes.POINTER(TrainParams), vp,
+                                         ctypes.POINTER(vp), ctypes.POINTER(TrainStats)]
+            L.cng_stop_free.restype = None
+            L.cng_stop_free.argtypes = [vp]
+            L.cng_stop_export.restype = ctypes.c_int
+            L.cng_stop_export.argtypes = [vp, vp, vp, vp, vp]
+            L.cng_stop_import.restype = ctypes.c_int
+            L.cng_stop_import.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
+            L.cng_trace.restype = ctypes.c_int
+            L.cng_trace.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp]
+            L.cng_mlp_grad.restype = ctypes.c_int
+            L.cng_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+            L.cngx_launches.restype = ctypes.c_longlong
+            L.cngx_launches.argtypes = []
+            L.cng_mlp_adam.restype = ctypes.c_int
+            L.cng_mlp_adam.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, vp]
             _lib = L
     return _lib
 
@@ -158,7 +191,7 @@ class Index:
 
 def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: int = CNG_L2,
               screen: int = CNG_SCREEN_TC, tie_band: float = 1e-5, margin: int = 32,
-              keep_lists: bool = False, stream=None):
+              keep_lists: bool = False, connect_L: int = 0, stream=None):
     """cng_build of include/cng.h.  points: CUDA tensor or host (numpy / CPU tensor), float32
     or float16, shape [n, d].  Returns (Index, stats dict)."""
     if isinstance(points, torch.Tensor):
@@ -168,7 +201,7 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
         import numpy as np
         dt = {np.dtype("float32"): CNG_F32, np.dtype("float16"): CNG_F16}[points.dtype]
         n, d = points.shape
-    p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists))
+    p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists), connect_L)
     st = BuildStats()
     h = ctypes.c_void_p()
     _check(lib().cng_build(_ptr(points), dt, n, d, ctypes.byref(p), _stream(stream),
@@ -193,13 +226,12 @@ def cng_graph(index: Index):
 def cng_lists(index: Index):
     """(cand [n, L], cdist [n, L], fwd [n, R], fdeg [n]) views; needs keep_lists=True."""
     c, cd, f, fd = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
-    L = ctypes.c_int32()
+    L, R = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().cng_lists(index.handle, ctypes.byref(c), ctypes.byref(cd), ctypes.byref(L),
-                           ctypes.byref(f), ctypes.byref(fd)))
-    _, _, R, _ = cng_graph(index)
+                           ctypes.byref(f), ctypes.byref(fd), ctypes.byref(R)))
     n = index.n
     return (_view(c.value, (n, L.value), torch.int32), _view(cd.value, (n, L.value), torch.float32),
-            _view(f.value, (n, R), torch.int32), _view(fd.value, (n,), torch.int32))
+            _view(f.value, (n, R.value), torch.int32), _view(fd.value, (n,), torch.int32))
 
 
 def cng_search(index: Index, queries, k: int, L: int, mode: int = CNG_SEARCH_FIXED, model=None,
@@ -247,3 +279,86 @@ def cng_knn(base: torch.Tensor, k: int, rows: torch.Tensor | None = None,
     _check(lib().cng_knn(_ptr(base), n, _ptr(rows), m, d, k, screen, tie_band, _ptr(ids), _ptr(ds),
                          _stream(stream), ctypes.byref(st)))
     return ids, ds, _as_dict(st)
+
+
+class StopModel:
+    """Owner of a cng_stop_model*."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def free(self):
+        if self.handle:
+            lib().cng_stop_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def cng_stop_train(index: Index, train_queries, k: int, L: int, max_trace: int = 0, epochs: int = 0,
+                   batch: int = 0, lr: float = 0.0, seed: int = 1, stream=None):
+    """cng_stop_train of include/cng.h; returns (StopModel, stats dict)."""
+    p = TrainParams(k, L, max_trace, epochs, batch, lr, seed)
+    st = TrainStats()
+    h = ctypes.c_void_p()
+    _check(lib().cng_stop_train(index.handle, _ptr(train_queries), train_queries.shape[0], ctypes.byref(p),
+                                _stream(stream), ctypes.byref(h), ctypes.byref(st)))
+    return StopModel(h.value), _as_dict(st)
+
+
+def cng_stop_free(model: StopModel):
+    model.free()
+
+
+def cng_stop_export(model: StopModel):
+    """(params, mu, sigma, bf16-rounded params) as numpy float32 arrays."""
+    import numpy as np
+
+    P = np.empty(CNG_STOP_NPARAMS, np.float32)
+    mu = np.empty(16, np.float32)
+    sg = np.empty(16, np.float32)
+    Pb = np.empty(CNG_STOP_NPARAMS, np.float32)
+    _check(lib().cng_stop_export(model.handle, _ptr(P), _ptr(mu), _ptr(sg), _ptr(Pb)))
+    return P, mu, sg, Pb
+
+
+def cng_stop_import(params, mu, sigma) -> StopModel:
+    import numpy as np
+
+    P = np.ascontiguousarray(params, np.float32)
+    m = np.ascontiguousarray(mu, np.float32)
+    s_ = np.ascontiguousarray(sigma, np.float32)
+    h = ctypes.c_void_p()
+    _check(lib().cng_stop_import(_ptr(P), _ptr(m), _ptr(s_), ctypes.byref(h)))
+    return StopModel(h.value)
+
+
+def cng_trace(index: Index, queries: torch.Tensor, k: int, L: int, max_trace: int, stream=None):
+    """Per-hop features of the plain search: dict(feats [nq, T, 16], hops, tlc, ids)."""
+    nq = queries.shape[0]
+    dev = queries.device
+    out = dict(feats=torch.full((nq, max_trace, 16), float("nan"), device=dev),
+               hops=torch.empty(nq, dtype=torch.int32, device=dev),
+               tlc=torch.empty(nq, dtype=torch.int32, device=dev),
+               ids=torch.empty((nq, k), dtype=torch.int32, device=dev))
+    _check(lib().cng_trace(index.handle, _ptr(queries), nq, k, L, max_trace, _ptr(out["feats"]),
+                           _ptr(out["hops"]), _ptr(out["tlc"]), _ptr(out["ids"]), _stream(stream)))
+    return out
+
+
+def cng_mlp_grad(params: torch.Tensor, x: torch.Tensor, y: torch.Tensor, stream=None):
+    """(loss, grad) of the stop network's training kernels on one batch (CUDA tensors)."""
+    grad = torch.empty(CNG_STOP_NPARAMS, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(lib().cng_mlp_grad(_ptr(params), _ptr(x), _ptr(y), x.shape[0], _ptr(grad), _ptr(loss),
+                              _stream(stream)))
+    return loss, grad
+
+
+def cng_mlp_adam(params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, t: int,
+                 lr: float, stream=None):
+    _check(lib().cng_mlp_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), t, lr, _stream(stream)))

@@ -12,13 +12,20 @@
 #include <string>
 #include <vector>
 
+#include "launch_count.h"
 #include "cng_internal.h"
 #include "search_internal.h"
+#include "mlp_internal.h"
 #include "screen_tc.h"
 
 namespace cng {
 
 static thread_local std::string g_err = "no error";
+
+std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
 
 cng_status fail(cng_status st, const std::string& msg) {
   g_err = msg;
@@ -82,6 +89,7 @@ using namespace cng;
 struct cng_index {
   int64_t n = 0;
   int d = 0, dpad = 0, dtype = 0, R = 0, L = 0;
+  int rs = 0;               // adjacency row stride (R + REPAIR_SLOTS)
   int32_t entry = -1;
   int exact = 0;
   float band = 1e-5f;
@@ -107,7 +115,23 @@ struct cng_index {
   std::vector<GraphEntry> graphs;
 };
 
+struct cng_stop_model {
+  float* P = nullptr;     // FP32 master parameters
+  float* mu = nullptr;    // [16]
+  float* sg = nullptr;    // [16]
+  void* blk = nullptr;    // packed inference block (BF16 weights)
+};
+
 extern "C" const char* cng_last_error(void) { return g_err.c_str(); }
+
+extern "C" void cng_stop_free(cng_stop_model* m) {
+  if (!m) return;
+  cudaFree(m->P);
+  cudaFree(m->mu);
+  cudaFree(m->sg);
+  cudaFree(m->blk);
+  delete m;
+}
 
 extern "C" void cng_free(cng_index* ix) {
   if (!ix) return;
@@ -328,6 +352,7 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
   if (p->screen != CNG_SCREEN_FP32 && p->screen != CNG_SCREEN_TC) return fail(CNG_E_INVAL, "unknown screen");
   if (!(p->tie_band >= 5e-6) || p->tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
   if (p->margin < 0 || p->margin > 256) return fail(CNG_E_INVAL, "margin must be in [0, 256]");
+  if (p->connect_L > 256) return fail(CNG_E_INVAL, "connect_L must be <= 256");
   return CNG_OK;
 }
 
@@ -427,13 +452,14 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   CK(pool.alloc(&off, (size_t)n + 1));
   CK(pool.alloc(&bsum, (size_t)reverse_blocksums_len(n)));
   CK(pool.alloc(&inl, (size_t)n * R));
-  CK(pool.alloc(&adj, (size_t)n * R));
+  const int Rs = R + REPAIR_SLOTS;
+  CK(pool.alloc(&adj, (size_t)n * Rs));
   CK(pool.alloc(&deg, (size_t)n));
   int32_t* big_list;
   CK(pool.alloc(&big_list, (size_t)n));
   CK(launch_reverse(fwd, fdeg, n, R, indeg, off, cursor, inl, bsum, ctr, s));
   CK(launch_merge(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band, exact, adj,
-                  deg, ctr, big_list, s));
+                  deg, Rs, ctr, big_list, s));
   {
     Counters hc0;
     CK(cudaMemcpyAsync(&hc0, ctr, sizeof(hc0), cudaMemcpyDeviceToHost, s));
@@ -445,14 +471,94 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       unsigned char* scratch;
       CK(pool.alloc(&scratch, (size_t)grid * cap * 17));
       CK(launch_merge_big(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band,
-                          exact, adj, deg, ctr, big_list, hc0.nbig, scratch, cap, grid, s));
+                          exact, adj, deg, Rs, ctr, big_list, hc0.nbig, scratch, cap, grid, s));
     }
   }
-  tm.mark();  // 5
-  Counters hc;
+  tm.mark();  // 5: merge done
+  // phase 4: connectivity
   int32_t h_entry = -1;
-  CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&h_entry, d_entry, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int64_t repair_edges = 0;
+  int repair_rounds = 0;
+  if (P.connect_L >= 0) {
+    const int Lc = P.connect_L > 0 ? P.connect_L : CONNECT_L;
+    int32_t *reached, *fa, *fb, *U, *rid, *best, *qdeg, *qhops;
+    float* rdist;
+    int* counts;
+    int *sc_counter;
+    unsigned long long* sc_tot;
+    uint32_t* sc_status;
+    CK(pool.alloc(&reached, (size_t)n));
+    CK(pool.alloc(&fa, (size_t)n));
+    CK(pool.alloc(&fb, (size_t)n));
+    CK(pool.alloc(&U, (size_t)n));
+    const int kc = std::min(8, Lc);
+    CK(pool.alloc(&rid, (size_t)n * kc));
+    CK(pool.alloc(&rdist, (size_t)n * kc));
+    CK(pool.alloc(&best, (size_t)n));
+    CK(pool.alloc(&counts, 4));
+    CK(pool.alloc(&sc_counter, 1));
+    CK(pool.alloc(&sc_tot, 4));
+    CK(pool.alloc(&sc_status, 1));
+    CK(cudaMemsetAsync(sc_status, 0, 4, s));
+    (void)qdeg;
+    (void)qhops;
+    CK(launch_fill(best, n, 0x7fffffff, s));
+    int hc_counts[4] = {0, 0, 0, 0};
+    for (int round = 0; round < 64; ++round) {
+      CK(launch_bfs(adj, deg, Rs, n, h_entry, reached, fa, fb, counts, hc_counts, s));
+      CK(launch_collect(reached, n, U, counts + 2, s));
+      CK(cudaMemcpyAsync(&hc_counts[2], counts + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const int nu = hc_counts[2];
+      if (nu == 0) break;
+      ++repair_rounds;
+      SearchArgs sa{};
+      sa.X = pr.xs;
+      sa.dtype = dtype;
+      sa.n = n;
+      sa.d = d;
+      sa.dpad = dpad;
+      sa.adj = adj;
+      sa.deg = deg;
+      sa.R = Rs;
+      sa.entry = h_entry;
+      sa.Q = nullptr;
+      sa.qids = U;
+      sa.nq = nu;
+      sa.k = kc;
+      sa.L = Lc;
+      sa.hash_slots = 1024;
+      sa.warp_smem = search_warp_smem(dpad, Lc, sa.hash_slots);
+      sa.band = band;
+      sa.exact = exact;
+      sa.max_hops = 0;
+      sa.counter = sc_counter;
+      sa.ids = rid;
+      sa.dists = rdist;
+      sa.tot = sc_tot;
+      sa.status = sc_status;
+      const int wpb = 4;
+      int bps = search_blocks_per_sm(dtype, wpb, (size_t)wpb * sa.warp_smem);
+      if (bps < 1) return fail(CNG_E_UNSUPPORTED, "connectivity search shape does not fit");
+      CK(cudaMemsetAsync(sc_counter, 0, sizeof(int), s));
+      CK(launch_search(sa, wpb, num_sms() * bps, s));
+      CK(launch_pick_add(U, rid, nu, kc, best, n, adj, deg, Rs, counts + 3, s));
+      CK(cudaMemcpyAsync(&hc_counts[3], counts + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hc_counts[3] == 0)
+        return fail(CNG_E_UNSUPPORTED, "phase 4 could not connect the graph (connectivity slots full)");
+      repair_edges += hc_counts[3];
+    }
+    uint32_t sst = 0;
+    CK(cudaMemcpyAsync(&sst, sc_status, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sst) return fail(CNG_E_INTERNAL, "connectivity search exceeded n hops");
+  }
+  tm.mark();  // 6: connectivity done
+  Counters hc;
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   st = check_status(hc.status);
@@ -464,6 +570,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   ix->dpad = dpad;
   ix->dtype = dtype;
   ix->R = R;
+  ix->rs = Rs;
   ix->L = L;
   ix->entry = h_entry;
   ix->exact = exact;
@@ -494,14 +601,18 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
-    stats->ms_total = tm.ms(0, 5);
+    stats->ms_total = tm.ms(0, 6);
     stats->ms_prep = tm.ms(0, 1);
     stats->ms_entry = tm.ms(1, 2);
     stats->ms_screen = ms_screen;
     stats->ms_rerank = ms_rerank;
     stats->ms_prune = tm.ms(3, 4);
     stats->ms_merge = tm.ms(4, 5);
-    stats->n_edges = (int64_t)hc.edges;
+    stats->ms_connect = tm.ms(5, 6);
+    stats->n_edges = (int64_t)hc.edges + repair_edges;
+    stats->repair_edges = repair_edges;
+    stats->repair_rounds = repair_rounds;
+    stats->screen_used = screen;
     stats->cert_fail_rows = hc.nfail;
     stats->order_ties = (int64_t)hc.order_ties;
     stats->rule_ties = (int64_t)hc.rule_ties;
@@ -520,14 +631,14 @@ extern "C" cng_status cng_graph(const cng_index* ix, const int32_t** adj, const 
   if (!ix) return fail(CNG_E_INVAL, "index is NULL");
   if (adj) *adj = ix->adj;
   if (deg) *deg = ix->deg;
-  if (R) *R = ix->R;
+  if (R) *R = ix->rs;
   if (entry) *entry = ix->entry;
   if (n) *n = ix->n;
   return CNG_OK;
 }
 
 extern "C" cng_status cng_lists(const cng_index* ix, const int32_t** cand, const float** cdist,
-                                int32_t* L, const int32_t** fwd, const int32_t** fdeg) {
+                                int32_t* L, const int32_t** fwd, const int32_t** fdeg, int32_t* R) {
   if (!ix) return fail(CNG_E_INVAL, "index is NULL");
   if (!ix->cand) return fail(CNG_E_INVAL, "index was built without keep_lists");
   if (cand) *cand = ix->cand;
@@ -535,6 +646,7 @@ extern "C" cng_status cng_lists(const cng_index* ix, const int32_t** cand, const
   if (L) *L = ix->L;
   if (fwd) *fwd = ix->fwd;
   if (fdeg) *fdeg = ix->fdeg;
+  if (R) *R = ix->R;
   return CNG_OK;
 }
 
@@ -543,12 +655,16 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
                                  float* dists, int32_t* ndc, int32_t* hops, int32_t* flags,
                                  void* stream, cng_search_stats* stats) {
   cng_index* ix = const_cast<cng_index*>(cix);
-  if (!ix || !queries || !ids || !dists) return fail(CNG_E_INVAL, "index, queries, ids and dists must be non-NULL");
+  if (!ix) return fail(CNG_E_INVAL, "index must be non-NULL");
   if (nq < 0) return fail(CNG_E_INVAL, "nq must be >= 0");
+  if (nq > 0 && (!queries || !ids || !dists))
+    return fail(CNG_E_INVAL, "queries, ids and dists must be non-NULL when nq > 0");
   if (k < 1 || L < k || L > 256) return fail(CNG_E_INVAL, "need 1 <= k <= L <= 256");
   cng_search_params defp{};
   const cng_search_params& P = params ? *params : defp;
-  if (P.mode != CNG_SEARCH_FIXED) return fail(CNG_E_UNSUPPORTED, "learned stop not available in this build");
+  if (P.mode != CNG_SEARCH_FIXED && P.mode != CNG_SEARCH_LEARNED) return fail(CNG_E_INVAL, "unknown mode");
+  if (P.mode == CNG_SEARCH_LEARNED && (!P.model || !(P.threshold > 0.f && P.threshold < 1.f) || P.check_every < 1))
+    return fail(CNG_E_INVAL, "learned mode needs a model, 0 < threshold < 1 and check_every >= 1");
   if (P.max_hops < 0) return fail(CNG_E_INVAL, "max_hops must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   if (nq == 0) {
@@ -582,7 +698,7 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   a.dpad = ix->dpad;
   a.adj = ix->adj;
   a.deg = ix->deg;
-  a.R = ix->R;
+  a.R = ix->rs;
   a.entry = ix->entry;
   a.Q = qd;
   a.nq = nq;
@@ -601,10 +717,15 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   a.flags = o_flags;
   a.tot = ix->tot;
   a.status = ix->status;
+  if (P.mode == CNG_SEARCH_LEARNED) {
+    a.model = P.model->blk;
+    a.zthr = std::log(P.threshold / (1.f - P.threshold));
+    a.check_every = P.check_every;
+  }
   int wpb = P.warps_per_block > 0 ? P.warps_per_block : 4;
   if (wpb > 8) wpb = 8;
   while (wpb > 1 && (size_t)wpb * a.warp_smem > 200 * 1024) wpb >>= 1;
-  int bps = search_blocks_per_sm(ix->dtype, wpb, (size_t)wpb * a.warp_smem);
+  int bps = search_blocks_per_sm(ix->dtype, wpb, (size_t)wpb * a.warp_smem + (a.model ? STOP_BLOCK_BYTES : 0));
   if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
   int grid = num_sms() * bps;
   cudaEvent_t e0, e1;
@@ -787,3 +908,259 @@ extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* 
   CK(cudaStreamSynchronize(s));
   return check_status(hs);
 }
+
+
+// ---------------------------------------------------------------------------------------------
+// learned early stop
+// ---------------------------------------------------------------------------------------------
+__global__ void count_pos_kernel(const float* __restrict__ y, int64_t N, unsigned long long* c) {
+  unsigned long long m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    m += y[i] > 0.5f;
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(c, m);
+}
+
+static cng_status new_model(cng_stop_model** out) {
+  cng_stop_model* m = new cng_stop_model();
+  if (cudaMalloc(&m->P, MLP_NPARAMS * 4) != cudaSuccess || cudaMalloc(&m->mu, 64) != cudaSuccess ||
+      cudaMalloc(&m->sg, 64) != cudaSuccess || cudaMalloc(&m->blk, STOP_BLOCK_BYTES) != cudaSuccess) {
+    cng_stop_free(m);
+    return fail(CNG_E_NOMEM, "model allocation failed");
+  }
+  *out = m;
+  return CNG_OK;
+}
+
+// Plain search with per-hop features (shared by cng_trace and cng_stop_train).
+static cng_status run_trace(cng_index* ix, const float* qd, int64_t nq, int k, int L, int T,
+                            float* feats, int32_t* hops, int32_t* tlc, int32_t* ids, float* dists,
+                            cudaStream_t s) {
+  SearchArgs a{};
+  a.X = ix->xs;
+  a.dtype = ix->dtype;
+  a.n = ix->n;
+  a.d = ix->d;
+  a.dpad = ix->dpad;
+  a.adj = ix->adj;
+  a.deg = ix->deg;
+  a.R = ix->rs;
+  a.entry = ix->entry;
+  a.Q = qd;
+  a.nq = nq;
+  a.k = k;
+  a.L = L;
+  a.hash_slots = L <= 64 ? 1024 : 2048;
+  a.warp_smem = search_warp_smem(ix->dpad, L, a.hash_slots);
+  a.band = ix->band;
+  a.exact = ix->exact;
+  a.counter = ix->counter;
+  a.ids = ids;
+  a.dists = dists;
+  a.hops = hops;
+  a.tlc = tlc;
+  a.tot = ix->tot;
+  a.status = ix->status;
+  a.trace_feats = feats;
+  a.max_trace = T;
+  a.check_every = 1;
+  const int wpb = 4;
+  int bps = search_blocks_per_sm(ix->dtype, wpb, (size_t)wpb * a.warp_smem);
+  if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
+  CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
+  CK(launch_search(a, wpb, num_sms() * bps, s));
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_trace(const cng_index* cix, const float* queries, int64_t nq, int32_t k,
+                                int32_t L, int32_t max_trace, float* feats, int32_t* hops,
+                                int32_t* tlc, int32_t* ids, void* stream) {
+  cng_index* ix = const_cast<cng_index*>(cix);
+  if (!ix || !queries || !feats || !hops || !tlc || !ids) return fail(CNG_E_INVAL, "pointers must be non-NULL");
+  if (nq < 1 || k < 1 || L < k || L > 256 || max_trace < 1) return fail(CNG_E_INVAL, "bad sizes");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevPool pool;
+  float* dists;
+  CK(pool.alloc(&dists, (size_t)nq * k));
+  std::lock_guard<std::mutex> lock(ix->mu);
+  cng_status st = run_trace(ix, queries, nq, k, L, max_trace, feats, hops, tlc, ids, dists, s);
+  if (st != CNG_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_stop_train(const cng_index* cix, const float* train_q, int64_t nq,
+                                     const cng_train_params* params, void* stream,
+                                     cng_stop_model** out, cng_train_stats* stats) {
+  cng_index* ix = const_cast<cng_index*>(cix);
+  if (!ix || !train_q || !params || !out) return fail(CNG_E_INVAL, "pointers must be non-NULL");
+  *out = nullptr;
+  const cng_train_params& P = *params;
+  const int T = P.max_trace > 0 ? P.max_trace : 256;
+  const int epochs = P.epochs > 0 ? P.epochs : 4;
+  const int B = P.batch > 0 ? P.batch : 4096;
+  const float lr = P.lr > 0.f ? P.lr : 1e-3f;
+  if (nq < 1 || P.k < 1 || P.L < P.k || P.L > 256 || T > 4096 || B > (1 << 20))
+    return fail(CNG_E_INVAL, "need nq >= 1, 1 <= k <= L <= 256, max_trace <= 4096, batch <= 2^20");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevPool pool;
+  const float* qd = train_q;
+  if (!is_device_ptr(train_q)) {
+    float* t;
+    CK(pool.alloc(&t, (size_t)nq * ix->d));
+    CK(cudaMemcpyAsync(t, train_q, (size_t)nq * ix->d * 4, cudaMemcpyHostToDevice, s));
+    qd = t;
+  }
+  Timer tm(s);
+  tm.mark();
+  float *feats, *dists;
+  int32_t *hops, *tlc, *ids;
+  int64_t* off;
+  CK(pool.alloc(&feats, (size_t)nq * T * 16));
+  CK(pool.alloc(&dists, (size_t)nq * P.k));
+  CK(pool.alloc(&hops, (size_t)nq));
+  CK(pool.alloc(&tlc, (size_t)nq));
+  CK(pool.alloc(&ids, (size_t)nq * P.k));
+  CK(pool.alloc(&off, (size_t)nq + 1));
+  std::lock_guard<std::mutex> lock(ix->mu);
+  cng_status st = run_trace(ix, qd, nq, P.k, P.L, T, feats, hops, tlc, ids, dists, s);
+  if (st != CNG_OK) return st;
+  CK(launch_offsets(hops, nq, T, off, s));
+  int64_t N = 0;
+  CK(cudaMemcpyAsync(&N, off + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  tm.mark();
+  if (N < 1) return fail(CNG_E_INVAL, "traces produced no samples");
+  float *X, *y, *part, *ploss, *grad, *loss, *m, *v;
+  double* spart;
+  unsigned long long* npos;
+  CK(pool.alloc(&X, (size_t)N * 16));
+  CK(pool.alloc(&y, (size_t)N));
+  CK(pool.alloc(&spart, 64 * 32));
+  CK(pool.alloc(&npos, 1));
+  const int Bn = (int)std::min<int64_t>(B, N);
+  CK(pool.alloc(&part, (size_t)mlp_parts(Bn) * MLP_NPARAMS));
+  CK(pool.alloc(&ploss, (size_t)mlp_parts(Bn)));
+  CK(pool.alloc(&grad, MLP_NPARAMS));
+  CK(pool.alloc(&loss, 2));
+  CK(pool.alloc(&m, MLP_NPARAMS));
+  CK(pool.alloc(&v, MLP_NPARAMS));
+  cng_stop_model* mdl = nullptr;
+  st = new_model(&mdl);
+  if (st != CNG_OK) return st;
+  auto guard = [&](cng_status r) {
+    if (r != CNG_OK) cng_stop_free(mdl);
+    return r;
+  };
+#define CKM(call)                                                                           \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return guard(fail(CNG_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  CKM(launch_samples(feats, hops, tlc, nq, T, off, X, y, s));
+  CKM(cudaMemsetAsync(npos, 0, 8, s));
+  count_launch();
+  count_pos_kernel<<<num_sms() * 4, 256, 0, s>>>(y, N, npos);
+  CKM(launch_standardise(X, N, spart, mdl->mu, mdl->sg, s));
+  CKM(launch_mlp_init(mdl->P, P.seed ? P.seed : 1, s));
+  CKM(cudaMemsetAsync(m, 0, MLP_NPARAMS * 4, s));
+  CKM(cudaMemsetAsync(v, 0, MLP_NPARAMS * 4, s));
+  const int64_t steps = std::max<int64_t>(1, (int64_t)epochs * ((N + Bn - 1) / Bn));
+  const uint64_t seed = (P.seed ? P.seed : 1) * 0x2545F4914F6CDD1Dull + 7;
+  for (int64_t t = 1; t <= steps; ++t) {
+    float* lp = (t == 1) ? loss : (t == steps ? loss + 1 : nullptr);
+    CKM(launch_mlp_grad(mdl->P, X, y, N, Bn, seed, t, part, ploss, grad, lp, s));
+    CKM(launch_adam(mdl->P, m, v, grad, t, lr, s));
+  }
+  CKM(launch_pack_model(mdl->P, mdl->mu, mdl->sg, mdl->blk, s));
+  tm.mark();
+  float hl[2] = {0, 0};
+  unsigned long long hp = 0;
+  CKM(cudaMemcpyAsync(hl, loss, 8, cudaMemcpyDeviceToHost, s));
+  CKM(cudaMemcpyAsync(&hp, npos, 8, cudaMemcpyDeviceToHost, s));
+  CKM(cudaStreamSynchronize(s));
+#undef CKM
+  if (stats) {
+    stats->ms_trace = tm.ms(0, 1);
+    stats->ms_train = tm.ms(1, 2);
+    stats->samples = N;
+    stats->positives = (int64_t)hp;
+    stats->steps = steps;
+    stats->loss_first = hl[0];
+    stats->loss_last = steps == 1 ? hl[0] : hl[1];
+  }
+  *out = mdl;
+  return CNG_OK;
+}
+
+__global__ void bf16_round_kernel(const float* __restrict__ a, float* __restrict__ b, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __bfloat162float(__float2bfloat16_rn(a[i]));
+}
+
+extern "C" cng_status cng_stop_export(const cng_stop_model* m, float* params, float* mu, float* sigma,
+                                      float* bf16_params) {
+  if (!m) return fail(CNG_E_INVAL, "model is NULL");
+  if (params) CK(cudaMemcpy(params, m->P, MLP_NPARAMS * 4, cudaMemcpyDeviceToHost));
+  if (mu) CK(cudaMemcpy(mu, m->mu, 64, cudaMemcpyDeviceToHost));
+  if (sigma) CK(cudaMemcpy(sigma, m->sg, 64, cudaMemcpyDeviceToHost));
+  if (bf16_params) {
+    DevPool pool;
+    float* t;
+    CK(pool.alloc(&t, MLP_NPARAMS));
+    count_launch();
+    bf16_round_kernel<<<(MLP_NPARAMS + 255) / 256, 256>>>(m->P, t, MLP_NPARAMS);
+    // weights are rounded for inference; biases, w3 and b3 stay FP32
+    CK(cudaMemcpy(bf16_params, t, MLP_NPARAMS * 4, cudaMemcpyDeviceToHost));
+    float* full = new float[MLP_NPARAMS];
+    cudaMemcpy(full, m->P, MLP_NPARAMS * 4, cudaMemcpyDeviceToHost);
+    const int b1 = 64 * 16, W2 = b1 + 64, b2 = W2 + 64 * 64;
+    for (int i = b1; i < W2; ++i) bf16_params[i] = full[i];
+    for (int i = b2; i < MLP_NPARAMS; ++i) bf16_params[i] = full[i];
+    delete[] full;
+  }
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_stop_import(const float* params, const float* mu, const float* sigma,
+                                      cng_stop_model** out) {
+  if (!params || !mu || !sigma || !out) return fail(CNG_E_INVAL, "pointers must be non-NULL");
+  cng_stop_model* m = nullptr;
+  cng_status st = new_model(&m);
+  if (st != CNG_OK) return st;
+  if (cudaMemcpy(m->P, params, MLP_NPARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->mu, mu, 64, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->sg, sigma, 64, cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_pack_model(m->P, m->mu, m->sg, m->blk, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cng_stop_free(m);
+    return fail(CNG_E_CUDA, "model upload failed");
+  }
+  *out = m;
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_mlp_grad(const float* params, const float* x, const float* y, int64_t B,
+                                   float* grad, float* loss, void* stream) {
+  if (!params || !x || !y || !grad) return fail(CNG_E_INVAL, "pointers must be non-NULL");
+  if (B < 1 || B > (1 << 22)) return fail(CNG_E_INVAL, "B must be in [1, 2^22]");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevPool pool;
+  float *part, *ploss, *l;
+  CK(pool.alloc(&part, (size_t)mlp_parts((int)B) * MLP_NPARAMS));
+  CK(pool.alloc(&ploss, (size_t)mlp_parts((int)B)));
+  CK(pool.alloc(&l, 1));
+  CK(launch_mlp_grad(params, x, y, B, (int)B, 0, 0, part, ploss, grad, l, s));
+  if (loss) CK(cudaMemcpyAsync(loss, l, 4, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return CNG_OK;
+}
+
+extern "C" cng_status cng_mlp_adam(float* params, float* m, float* v, const float* grad, int64_t t,
+                                   float lr, void* stream) {
+  if (!params || !m || !v || !grad || t < 1) return fail(CNG_E_INVAL, "bad arguments");
+  CK(launch_adam(params, m, v, grad, t, lr, (cudaStream_t)stream));
+  return CNG_OK;
+}
+
+extern "C" long long cngx_launches(void) { return launch_counter().load(); }

@@ -85,15 +85,27 @@ cudaError_t launch_reverse(const int32_t* fwd, const int32_t* fdeg, int64_t n, i
 cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                          const int32_t* inl, double alpha, double tau, int R, float band,
-                         int exact, int32_t* adj, int32_t* deg, Counters* ctr,
+                         int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
                          int32_t* big_list, cudaStream_t s);
 // Merge of the listed nodes with per-CTA global scratch of 17 * big_cap bytes (grid CTAs).
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                              const int32_t* inl, double alpha, double tau, int R, float band,
-                             int exact, int32_t* adj, int32_t* deg, Counters* ctr,
+                             int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
                              int32_t* big_list, int nbig, unsigned char* scratch, int big_cap,
                              int grid, cudaStream_t s);
+// Phase 4 (connectivity) pieces, k_connect.cu.  counts_dev / counts_host: int[4].
+cudaError_t launch_bfs(const int32_t* adj, const int32_t* deg, int Rs, int64_t n, int32_t s,
+                       int32_t* reached, int32_t* fa, int32_t* fb, int* counts_dev,
+                       int* counts_host, cudaStream_t st);
+cudaError_t launch_collect(const int32_t* reached, int64_t n, int32_t* U, int* nu_dev,
+                           cudaStream_t st);
+cudaError_t launch_pick_add(const int32_t* U, const int32_t* r, int nu, int kc, int32_t* best,
+                            int64_t n, int32_t* adj, int32_t* deg, int Rs, int* added_dev,
+                            cudaStream_t st);
+cudaError_t launch_fill(int32_t* a, int64_t n, int32_t v, cudaStream_t st);
+constexpr int REPAIR_SLOTS = 8;   // adjacency row slots beyond R for phase-4 edges
+constexpr int CONNECT_L = 32;     // default beam width of the phase-4 searches
 
 int num_sms();
 int64_t reverse_blocksums_len(int64_t n);

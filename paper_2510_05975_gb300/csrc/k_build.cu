@@ -10,6 +10,7 @@
 // exact form of Alg. 3 phase 2's candidate set.
 #include <float.h>
 
+#include "launch_count.h"
 #include "cng_internal.h"
 #include "device_common.cuh"
 
@@ -98,6 +99,7 @@ cudaError_t launch_prep(const void* pts, int dtype, int64_t n, int d, int dpad, 
   int64_t warps = (n + 3) / 4;
   int grid = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
   if (grid < 1) grid = 1;
+  count_launch();
   if (dtype == CNG_F32)
     prep_kernel<float, float><<<grid, 256, 0, s>>>((const float*)pts, n, d, dpad, (float*)xs,
                                                    xb_bf, xb_h, kpad, nb, rb, st);
@@ -185,17 +187,25 @@ cudaError_t launch_entry(const void* xs, int dtype, int64_t n, int d, int dpad, 
   unsigned long long* dbits = reinterpret_cast<unsigned long long*>(part + (int64_t)nblk * d);
   int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
   if (dtype == CNG_F32) {
+    count_launch();
     centroid_part_kernel<float><<<g1, 128, 0, s>>>((const float*)xs, n, d, dpad, part);
+    count_launch();
     centroid_final_kernel<<<(d + 127) / 128, 128, 0, s>>>(part, nblk, n, d, cen, best);
+    count_launch();
     entry_dist_kernel<float><<<grid, 256, d * sizeof(double), s>>>((const float*)xs, n, d, dpad,
                                                                    cen, dbits, best);
   } else {
+    count_launch();
     centroid_part_kernel<__half><<<g1, 128, 0, s>>>((const __half*)xs, n, d, dpad, part);
+    count_launch();
     centroid_final_kernel<<<(d + 127) / 128, 128, 0, s>>>(part, nblk, n, d, cen, best);
+    count_launch();
     entry_dist_kernel<__half><<<grid, 256, d * sizeof(double), s>>>((const __half*)xs, n, d,
                                                                     dpad, cen, dbits, best);
   }
+  count_launch();
   entry_pick_kernel<<<grid, 256, 0, s>>>(dbits, n, best);
+  count_launch();
   entry_write_kernel<<<1, 1, 0, s>>>(best, entry);
   return cudaGetLastError();
 }
@@ -339,6 +349,7 @@ template <typename T, int CPL>
 static cudaError_t knn_simt_t(const void* xr, int64_t m, const void* xc, int64_t n, int dpad,
                               int Lp, int self_excl, uint64_t* rowbuf, int grid, int32_t* ids,
                               uint32_t* thr, uint32_t* status, cudaStream_t s) {
+  count_launch();
   knn_simt_kernel<T, CPL><<<grid, 256, 0, s>>>((const T*)xr, m, (const T*)xc, n, dpad, Lp,
                                                self_excl, rowbuf, ids, thr, status);
   return cudaGetLastError();
@@ -527,11 +538,13 @@ cudaError_t launch_rerank(const void* xr, const void* xc, int dtype, int64_t m, 
   int grid = (int)std::min<int64_t>((m + RR_WARPS - 1) / RR_WARPS, (int64_t)num_sms() * 32);
   if (dtype == CNG_F32) {
     cudaFuncSetAttribute(rerank_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    count_launch();
     rerank_kernel<float><<<grid, RR_WARPS * 32, sh, s>>>((const float*)xr, (const float*)xc, m, d,
                                                          dpad, sids, sthr, Lp, L, sm, band, exact,
                                                          out_ids, out_dist, fail_rows, fail_bound, ctr);
   } else {
     cudaFuncSetAttribute(rerank_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    count_launch();
     rerank_kernel<__half><<<grid, RR_WARPS * 32, sh, s>>>((const __half*)xr, (const __half*)xc, m,
                                                           d, dpad, sids, sthr, Lp, L, sm, band,
                                                           exact, out_ids, out_dist, fail_rows, fail_bound, ctr);
@@ -647,11 +660,13 @@ cudaError_t launch_rescan(const void* xr, const void* xc, int dtype, int64_t m, 
   int grid = num_sms() * 2;
   if (dtype == CNG_F32) {
     cudaFuncSetAttribute(rescan_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    count_launch();
     rescan_kernel<float><<<grid, 256, sh, s>>>((const float*)xr, (const float*)xc, m, n, d, dpad,
                                                self_excl, L, fail_rows, fail_bound, ctr, out_ids,
                                                out_dist);
   } else {
     cudaFuncSetAttribute(rescan_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    count_launch();
     rescan_kernel<__half><<<grid, 256, sh, s>>>((const __half*)xr, (const __half*)xc, m, n, d,
                                                 dpad, self_excl, L, fail_rows, fail_bound, ctr,
                                                 out_ids, out_dist);

@@ -12,6 +12,7 @@
 // the first candidate still alive.  Pair distances are computed only against members of S
 // (the reuse observation of Sec. 4.3).  FP32 rule decisions inside the near-tie band are
 // re-decided with the canonical FP64 distances.
+#include "launch_count.h"
 #include "cng_internal.h"
 #include "device_common.cuh"
 
@@ -27,7 +28,8 @@ constexpr int PR_MERGE_STAGE_BYTES = 64 * 1024;
 struct RuleArgs {
   float alpha32, t32, band;
   double alpha64, t64;
-  int R;
+  int R;   // out-degree bound
+  int rs;  // row stride of the final adjacency (R + connectivity slots)
 };
 
 CNG_DEV float part_sqdist_ss(const float* __restrict__ a, const float* __restrict__ b, int dpad,
@@ -195,16 +197,19 @@ cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dp
   ra.t32 = (float)ra.t64;
   ra.band = band;
   ra.R = R;
+  ra.rs = R;
   size_t sh = dpad * 4 + 2 * (((size_t)L * 4 + 15) / 16) * 16 + 256 + ((L + 15) / 16) * 16;
   if ((size_t)L * dpad * 4 <= PR_STAGE_BYTES) sh += (size_t)L * dpad * 4;
   int per_sm = sh > 110 * 1024 ? 1 : 2;
   int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * per_sm * 4);
   if (dtype == CNG_F32) {
     cudaFuncSetAttribute(prune_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    count_launch();
     prune_fwd_kernel<float><<<grid, PR_THREADS, sh, s>>>((const float*)xs, n, d, dpad, cand, cdist,
                                                          L, ra, fwd, fdeg, ctr);
   } else {
     cudaFuncSetAttribute(prune_fwd_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    count_launch();
     prune_fwd_kernel<__half><<<grid, PR_THREADS, sh, s>>>((const __half*)xs, n, d, dpad, cand,
                                                           cdist, L, ra, fwd, fdeg, ctr);
   }
@@ -303,12 +308,18 @@ cudaError_t launch_reverse(const int32_t* fwd, const int32_t* fdeg, int64_t n, i
   cudaMemsetAsync(cursor, 0, n * sizeof(int32_t), s);
   int64_t ne = n * R;
   int g = (int)((ne + 255) / 256);
+  count_launch();
   indeg_kernel<<<g, 256, 0, s>>>(fwd, fdeg, n, R, indeg);
+  count_launch();
   max_indeg_kernel<<<(int)std::min<int64_t>((n + 255) / 256, num_sms() * 4), 256, 0, s>>>(indeg, n, ctr);
   int64_t nb = reverse_blocksums_len(n);
+  count_launch();
   scan_block_kernel<<<(int)nb, SCAN_B, 0, s>>>(indeg, n, off, blocksums);
+  count_launch();
   scan_sums_kernel<<<1, 32, 0, s>>>(blocksums, nb, off);
+  count_launch();
   scan_add_kernel<<<(int)nb, SCAN_B, 0, s>>>(off, n, blocksums);
+  count_launch();
   scatter_kernel<<<g, 256, 0, s>>>(fwd, fdeg, n, R, off, cursor, inl);
   return cudaGetLastError();
 }
@@ -452,7 +463,7 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
     na = prune_sweep(Xs, d, dpad, p, sm, nv, nstage, ra, ties);
     ++repruned;
   }
-  for (int i = tid; i < ra.R; i += PR_THREADS) adj_row[i] = i < na ? sm.S[i] : -1;
+  for (int i = tid; i < ra.rs; i += PR_THREADS) adj_row[i] = i < na ? sm.S[i] : -1;
   __syncthreads();
   return na;
 }
@@ -505,7 +516,7 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
     }
     maxlist = max(maxlist, (unsigned long long)(nf + nin));
     int na = merge_node(Xs, d, dpad, p, fwd + p * ra.R, nf, inl, i0, nin, ra, exact, ar, sm, d64,
-                        rid, stage_cap, &s_nv, adj + p * ra.R, ctr, ties, ordties, repruned);
+                        rid, stage_cap, &s_nv, adj + p * ra.rs, ctr, ties, ordties, repruned);
     if (tid == 0) deg[p] = na;
     edges += na;
   }
@@ -530,14 +541,16 @@ static cudaError_t merge_t(const void* xs, int64_t n, int d, int dpad, const int
   size_t sh = 2 * (size_t)dpad * 4 + 256 + PR_RUN * 12 + (BIG ? 0 : (size_t)PR_VMAX * 17) +
               (size_t)stage_cap * dpad * 4 + 16;
   cudaFuncSetAttribute(merge_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  count_launch();
   merge_kernel<T, BIG><<<grid, PR_THREADS, sh, s>>>((const T*)xs, n, d, dpad, fwd, fdeg, off, inl,
                                                     ra, exact, adj, deg, ctr, big_list,
                                                     big_scratch, big_cap);
   return cudaGetLastError();
 }
 
-static RuleArgs rule_args(double alpha, double tau, int R, float band) {
+static RuleArgs rule_args(double alpha, double tau, int R, float band, int rs) {
   RuleArgs ra;
+  ra.rs = rs;
   ra.alpha64 = alpha;
   ra.t64 = (alpha + 1.0) * tau;
   ra.alpha32 = (float)alpha;
@@ -550,9 +563,9 @@ static RuleArgs rule_args(double alpha, double tau, int R, float band) {
 cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                          const int32_t* inl, double alpha, double tau, int R, float band,
-                         int exact, int32_t* adj, int32_t* deg, Counters* ctr,
+                         int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
                          int32_t* big_list, cudaStream_t s) {
-  RuleArgs ra = rule_args(alpha, tau, R, band);
+  RuleArgs ra = rule_args(alpha, tau, R, band, rs);
   int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
   return dtype == CNG_F32
              ? merge_t<float, false>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,
@@ -564,10 +577,10 @@ cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                              const int32_t* inl, double alpha, double tau, int R, float band,
-                             int exact, int32_t* adj, int32_t* deg, Counters* ctr,
+                             int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
                              int32_t* big_list, int nbig, unsigned char* scratch, int big_cap,
                              int grid, cudaStream_t s) {
-  RuleArgs ra = rule_args(alpha, tau, R, band);
+  RuleArgs ra = rule_args(alpha, tau, R, band, rs);
   (void)nbig;
   return dtype == CNG_F32
              ? merge_t<float, true>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,

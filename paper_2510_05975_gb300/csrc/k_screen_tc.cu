@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "launch_count.h"
 #include "cng_internal.h"
 #include "device_common.cuh"
 #include "screen_tc.h"
@@ -445,6 +446,7 @@ static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const 
   cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel<CPL, DUMP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  count_launch();
   screen_tc_kernel<CPL, DUMP><<<grid, TC_THREADS, smem, s>>>(ma, mb, p, dump);
   return cudaGetLastError();
 }

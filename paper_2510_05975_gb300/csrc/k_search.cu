@@ -18,6 +18,7 @@
 // is decided by the canonical FP64 distance and id instead, so the queue order -- and with it
 // every hop, the returned ids and the hop count -- equals the FP64 definition of Alg. 1.
 // Integer data whose squared distances are exact in FP32 needs no FP64 at all.
+#include "launch_count.h"
 #include "cng_internal.h"
 #include "device_common.cuh"
 #include "search_internal.h"
@@ -25,7 +26,7 @@
 namespace cng {
 
 constexpr int SQ_G = 8;
-constexpr int SQ_MAXB = 64;  // batch capacity (R <= 64)
+constexpr int SQ_MAXB = 128;  // batch capacity (row stride <= 128)
 
 struct QEnt {
   uint64_t* k;   // keys
@@ -75,6 +76,60 @@ CNG_DEV double canon_q(const float* __restrict__ q, const T* __restrict__ x, int
   return canon_dist(q, x, d);
 }
 
+CNG_DEV float lgf(float x) { return logf(fmaxf(x, 1e-30f)); }
+
+// The stop model in shared memory: BF16 weights (inputs-major, so lane o reads W[i][o]
+// conflict-free), FP32 biases and input normalisation.
+struct StopSmem {
+  const __nv_bfloat16* W1T;  // [16][64]
+  const __nv_bfloat16* W2T;  // [64][64]
+  const float *b1, *b2, *w3, *b3, *mu, *sg;
+};
+CNG_DEV StopSmem stop_smem(const unsigned char* mb) {
+  StopSmem m;
+  m.W1T = reinterpret_cast<const __nv_bfloat16*>(mb);
+  m.W2T = m.W1T + 16 * 64;
+  const float* f = reinterpret_cast<const float*>(m.W2T + 64 * 64);
+  m.b1 = f;
+  m.b2 = f + 64;
+  m.w3 = f + 128;
+  m.b3 = f + 192;
+  m.mu = f + 196;
+  m.sg = f + 212;
+  return m;
+}
+
+// Logit of the 16-64-64-1 ReLU network for the features held by lanes 0..15 (FP32 math on
+// BF16 weights); every lane returns the same value.
+CNG_DEV float mlp_logit(const StopSmem& m, float f, int lane) {
+  const float xh = lane < 16 ? (f - m.mu[lane]) / m.sg[lane] : 0.f;
+  float a0 = m.b1[lane], a1 = m.b1[lane + 32];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float xi = __shfl_sync(FULL, xh, i);
+    a0 = fmaf(__bfloat162float(m.W1T[i * 64 + lane]), xi, a0);
+    a1 = fmaf(__bfloat162float(m.W1T[i * 64 + lane + 32]), xi, a1);
+  }
+  const float h0 = fmaxf(a0, 0.f), h1 = fmaxf(a1, 0.f);
+  float c0 = m.b2[lane], c1 = m.b2[lane + 32];
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i) {
+    const float hi = __shfl_sync(FULL, h0, i);
+    c0 = fmaf(__bfloat162float(m.W2T[i * 64 + lane]), hi, c0);
+    c1 = fmaf(__bfloat162float(m.W2T[i * 64 + lane + 32]), hi, c1);
+  }
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i) {
+    const float hi = __shfl_sync(FULL, h1, i);
+    c0 = fmaf(__bfloat162float(m.W2T[(i + 32) * 64 + lane]), hi, c0);
+    c1 = fmaf(__bfloat162float(m.W2T[(i + 32) * 64 + lane + 32]), hi, c1);
+  }
+  float z = m.w3[lane] * fmaxf(c0, 0.f) + m.w3[lane + 32] * fmaxf(c1, 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(FULL, z, o);
+  return z + m.b3[0];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 search_kernel(SearchArgs a) {
@@ -94,6 +149,17 @@ search_kernel(SearchArgs a) {
   uint8_t* Ae = reinterpret_cast<uint8_t*>(H + a.hash_slots);
   uint8_t* Be = Ae + L16;
   int32_t* Nv = reinterpret_cast<int32_t*>(Be + L16);
+  float* hist = reinterpret_cast<float*>(Nv + SQ_MAXB);  // Dk after each of the last 64 hops
+  // stop model (shared by the CTA's warps), after all warp regions
+  StopSmem ms;
+  if (a.model) {
+    unsigned char* mb = smem + (size_t)(blockDim.x >> 5) * a.warp_smem;
+    const int4* src = reinterpret_cast<const int4*>(a.model);
+    int4* dst = reinterpret_cast<int4*>(mb);
+    for (int i = threadIdx.x; i < STOP_BLOCK_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    ms = stop_smem(mb);
+    __syncthreads();
+  }
   const int hmask = a.hash_slots - 1;
   const T* X = reinterpret_cast<const T*>(a.X);
   const int g = lane % SQ_G, grp = lane / SQ_G;
@@ -104,8 +170,12 @@ search_kernel(SearchArgs a) {
     if (lane == 0) qi = atomicAdd(a.counter, 1);
     qi = __shfl_sync(FULL, qi, 0);
     if (qi >= a.nq) break;
-    const float* qg = a.Q + (int64_t)qi * a.d;
-    for (int c = lane; c < dpad; c += 32) qv[c] = c < a.d ? qg[c] : 0.f;
+    if (a.qids) {  // the query is a stored point (phase-4 searches)
+      load_row(qv, X + (int64_t)a.qids[qi] * dpad, dpad, lane, 32);
+    } else {
+      const float* qg = a.Q + (int64_t)qi * a.d;
+      for (int c = lane; c < dpad; c += 32) qv[c] = c < a.d ? qg[c] : 0.f;
+    }
     for (int c = lane; c < a.hash_slots; c += 32) H[c] = -1;
     __syncwarp();
     QEnt cur{Ak, Ax, Ae}, nxt{Bk, Bx, Be};
@@ -121,7 +191,10 @@ search_kernel(SearchArgs a) {
       }
     }
     __syncwarp();
-    int len = 1, ndc = 1, hops = 0, flags = 0;
+    int len = 1, ndc = 1, hops = 0, flags = 0, tlc = 0;
+    const float D0 = sqrtf(key_dist(cur.k[0]));
+    if (lane == 0) hist[0] = D0;
+    __syncwarp();
     // every point is explored at most once, so n hops bound a correct search; the cap keeps a
     // corrupted queue from looping
     const int hop_cap = a.max_hops > 0 ? a.max_hops : (int)min(a.n, (int64_t)0x3fffffff);
@@ -140,6 +213,7 @@ search_kernel(SearchArgs a) {
         break;
       }
       const int32_t u = key_id(cur.k[idx]);
+      const float Du = sqrtf(key_dist(cur.k[idx]));  // distance of the hop vertex
       __syncwarp();
       if (lane == 0) cur.e[idx] = 1;
       ++hops;
@@ -156,7 +230,10 @@ search_kernel(SearchArgs a) {
       }
       __syncwarp();
       ndc += nb;
-      if (nb == 0) continue;
+      int ins = 0;          // points of this hop still in Q after it
+      bool chg = false;     // the first min(k, |Q|) ids changed
+      do {                  // merge of the hop's new points (skipped when there are none)
+      if (nb == 0) break;
       // FP32 distances, 4 per round
       for (int b0 = 0; b0 < nb; b0 += 32 / SQ_G) {
         int b = b0 + grp;
@@ -169,7 +246,7 @@ search_kernel(SearchArgs a) {
           Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
         }
       }
-      int P2 = nb <= 32 ? 32 : 64;
+      int P2 = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
       for (int b = nb + lane; b < P2; b += 32) {
         Nk[b] = ~0ull;
         Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
@@ -221,16 +298,18 @@ search_kernel(SearchArgs a) {
       __syncwarp();
       {
         // compact survivors to the front keeping order
-        uint64_t kv[2];
-        bool keep[2];
+        uint64_t kv[SQ_MAXB / 32];
+        bool keep[SQ_MAXB / 32];
         int cnt_before = 0;
-        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int r = 0; r < SQ_MAXB / 32; ++r) {
           int b = r * 32 + lane;
           kv[r] = b < nb ? Nk[b] : ~0ull;
           keep[r] = b < nb && kv[r] != ~0ull;
         }
         __syncwarp();
-        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int r = 0; r < SQ_MAXB / 32; ++r) {
           unsigned bal = __ballot_sync(FULL, keep[r]);
           if (keep[r]) Nk[cnt_before + __popc(bal & ((1u << lane) - 1))] = kv[r];
           cnt_before += __popc(bal);
@@ -240,7 +319,7 @@ search_kernel(SearchArgs a) {
         for (int b = nbv + lane; b < P2; b += 32) Nk[b] = ~0ull;
         __syncwarp();
       }
-      if (nbv == 0) continue;
+      if (nbv == 0) break;
       // near-ties: mark batch entries close to a neighbour in the batch or to a Q entry, and
       // the Q entries concerned; give every marked entry its canonical FP64 distance
       if (!a.exact) {
@@ -301,6 +380,9 @@ search_kernel(SearchArgs a) {
         int pos = i + lo;
         if (pos < nlen) { nxt.k[pos] = ki; nxt.x[pos] = xi; nxt.e[pos] = cur.e[i]; }
       }
+      const int ktop = min(a.k, nlen);
+      bool lchg = false;
+      int lins = 0;
       for (int b = lane; b < nbv; b += 32) {
         uint64_t kb = Nk[b];
         double xb = Nx[b];
@@ -310,11 +392,58 @@ search_kernel(SearchArgs a) {
           if (before(cur.k[mid], cur.x[mid], kb, xb, a.band, a.exact)) lo = mid + 1; else hi = mid;
         }
         int pos = b + lo;
-        if (pos < nlen) { nxt.k[pos] = kb; nxt.x[pos] = xb; nxt.e[pos] = 0; }
+        if (pos < nlen) {
+          nxt.k[pos] = kb; nxt.x[pos] = xb; nxt.e[pos] = 0;
+          ++lins;
+          lchg |= pos < ktop;
+        }
       }
+      chg = __any_sync(FULL, lchg);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lins += __shfl_xor_sync(FULL, lins, o);
+      ins = lins;
       __syncwarp();
       QEnt t = cur; cur = nxt; nxt = t;
       len = nlen;
+      } while (0);
+      // ---- search state after this hop (learned early stop) ----
+      if (a.trace_feats || a.model) {
+        const int kk = min(a.k, len);
+        const float Dk = sqrtf(key_dist(cur.k[kk - 1]));
+        if (chg) tlc = hops;
+        const bool want_trace = a.trace_feats && hops <= a.max_trace;
+        const bool want_check = a.model && (hops % a.check_every) == 0;
+        float f = 0.f;
+        if (want_trace || want_check) {
+          int U = 0;
+          for (int b = 0; b < len; b += 32)
+            U += __popc(__ballot_sync(FULL, b + lane < len && !cur.e[b + lane]));
+          const float lD0 = lgf(D0), lDk = lgf(Dk);
+          if (lane == 0) f = lD0;
+          else if (lane == 1) f = logf(1.f + (float)hops);
+          else if (lane == 2) f = lgf(sqrtf(key_dist(cur.k[0]))) - lD0;
+          else if (lane == 3) f = lDk - lD0;
+          else if (lane == 4) f = lgf(sqrtf(key_dist(cur.k[len - 1]))) - lD0;
+          else if (lane == 5) f = lgf(Du) - lDk;
+          else if (lane < 12) {
+            const int h = max(hops - (1 << (lane - 6)), 0);
+            f = lgf(hist[h & 63]) - lDk;
+          } else if (lane == 12) f = logf(1.f + (float)(hops - tlc));
+          else if (lane == 13) f = (float)U / (float)a.L;
+          else if (lane == 14) f = (float)len / (float)a.L;
+          else if (lane == 15) f = (float)ins / (float)a.R;
+          if (want_trace && lane < 16)
+            a.trace_feats[((int64_t)qi * a.max_trace + (hops - 1)) * 16 + lane] = f;
+        }
+        __syncwarp();
+        if (lane == 0) hist[hops & 63] = Dk;
+        __syncwarp();
+        if (want_check && mlp_logit(ms, f, lane) >= a.zthr) {
+          flags |= 4;
+          ++t_stop;
+          break;
+        }
+      }
     }
     // results
     for (int t = lane; t < a.k; t += 32) {
@@ -326,6 +455,7 @@ search_kernel(SearchArgs a) {
       if (a.ndc) a.ndc[qi] = ndc;
       if (a.hops) a.hops[qi] = hops;
       if (a.flags) a.flags[qi] = flags;
+      if (a.tlc) a.tlc[qi] = tlc;
     }
     t_ndc += ndc;
     t_hops += hops;
@@ -346,14 +476,15 @@ search_kernel(SearchArgs a) {
 
 size_t search_warp_smem(int dpad, int L, int hash_slots) {
   size_t b = (size_t)dpad * 4 + 4 * (size_t)L * 8 + 2 * SQ_MAXB * 8 + (size_t)hash_slots * 4 +
-             2 * (((size_t)L + 15) / 16) * 16 + SQ_MAXB * 4;
+             2 * (((size_t)L + 15) / 16) * 16 + SQ_MAXB * 4 + 64 * 4;
   return (b + 15) / 16 * 16;
 }
 
 // The kernel's shared-memory attribute is set by search_blocks_per_sm, which callers run
 // first (outside any stream capture).
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s) {
-  size_t sh = (size_t)warps_per_block * a.warp_smem;
+  size_t sh = (size_t)warps_per_block * a.warp_smem + (a.model ? STOP_BLOCK_BYTES : 0);
+  count_launch();
   if (a.dtype == CNG_F32)
     search_kernel<float><<<grid, warps_per_block * 32, sh, s>>>(a);
   else

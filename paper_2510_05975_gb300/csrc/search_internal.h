@@ -18,6 +18,7 @@ struct SearchArgs {
   int R;
   int32_t entry;
   const float* Q;       // queries [nq][d]
+  const int32_t* qids;  // or: query i is stored point qids[i] (Q unused)
   int64_t nq;
   int k, L;
   int hash_slots;       // power of two
@@ -33,7 +34,18 @@ struct SearchArgs {
   int32_t* flags;
   unsigned long long* tot;  // [4]: ndc, hops, fp64 decisions, learned stops
   uint32_t* status;         // device status word (ST_* bits)
+  // learned early stop
+  float* trace_feats;       // [nq][max_trace][16] per-hop features, or null
+  int max_trace;
+  int32_t* tlc;             // [nq] last hop at which the top-k list changed, or null
+  const void* model;        // packed stop model (STOP_BLOCK_BYTES), or null
+  float zthr;               // stop when the logit >= zthr
+  int check_every;
 };
+
+// Packed stop model for inference: W1T bf16 [16][64], W2T bf16 [64][64], then floats
+// b1[64] b2[64] w3[64] b3[1] pad[3] mu[16] sigma[16].
+constexpr int STOP_BLOCK_BYTES = 16 * 64 * 2 + 64 * 64 * 2 + (64 * 3 + 4 + 32) * 4;
 
 size_t search_warp_smem(int dpad, int L, int hash_slots);
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s);

@@ -9,21 +9,23 @@ This module holds only random-number recipes.  It contains none of the method's
 arithmetic, so both the CUDA path and the CPU oracle may read its output.
 
 Recipes (numpy ``Generator(PCG64(seed))``, rows generated in fixed chunks so the output
-does not depend on memory limits).  Descriptor collections such as SIFT, DEEP and BIGANN have
-a low intrinsic dimension inside each cluster, so their mixtures use low-rank cluster noise:
-x = c + A_c z + e with z ~ N(0, I_16) and a per-centre loading matrix A_c, plus a small
-isotropic term e.
+does not depend on memory limits).  Descriptor collections such as SIFT, DEEP and BIGANN lie
+near a low-dimensional structure, so their mixtures live in one shared 16-dimensional
+subspace: x = c0 + A (u_a + z) + e, with a shared loading matrix A (d x 16), cluster offsets
+u_a ~ N(0, I_16) (the mixture's centres are c0 + A u_a), z ~ N(0, I_16) and a small isotropic
+term e.  (Clusters given private subspaces, or centres spread wider than the clusters, turn
+into islands that graphs built from exact neighbour lists cannot navigate between.)
 
 * ``gauss``      i.i.d. N(0, 1) float32.
-* ``sift``       64 centres uniform on the integers 40..215 per dimension; A_c entries
-                 N(0, 25^2 / 16) (per-coordinate std 25); e ~ N(0, 2^2); clipped to [0, 255]
-                 and rounded to integers (float32).
-* ``deep``       256 centres mu = g / ||g||, g ~ N(0, I); A_c entries N(0, 0.25 / (16 d));
-                 e ~ N(0, 0.05^2 / d); x = normalise(mu + A_c z + e) (unit norm).
-* ``gist``       100 centres N(0, I); per (centre, dimension) standard deviation sqrt(v),
-                 v log-uniform on [0.01, 1] (diagonal covariance).
-* ``bigann16``   1,024 centres N(0, I); A_c entries N(0, 0.25 / 16); e ~ N(0, 0.05^2);
-                 stored as float16.
+* ``sift``       64 centres; c0 uniform on the integers 112..143 per dimension; A entries
+                 N(0, 25^2 / 16) (per-coordinate std about 25 per unit of u + z); e ~ N(0, 2^2);
+                 clipped to [0, 255] and rounded to integers (float32).
+* ``deep``       256 centres; c0 a random unit vector; A entries N(0, 0.25 / (16 d));
+                 e ~ N(0, 0.05^2 / d); x normalised to unit length.
+* ``gist``       100 centres N(0, 0.1^2 I); per (centre, dimension) standard deviation
+                 sqrt(v), v log-uniform on [0.01, 1] (diagonal covariance).
+* ``bigann16``   1,024 centres; c0 = 0; A entries N(0, 0.25 / 16); e ~ N(0, 0.05^2); stored
+                 as float16.
 """
 from __future__ import annotations
 
@@ -77,37 +79,27 @@ LATENT = 16
 
 
 def _centres(kind: str, d: int, seed: int):
-    """Cluster centres and per-centre noise parameters, drawn from their own stream."""
+    """(c0, A, U): base point, shared loading matrix and cluster offsets (own stream).  For
+    ``gist``: (centres, per-centre scales, None)."""
     rng = np.random.Generator(np.random.PCG64(seed * 7919 + 17))
     m = LATENT
     if kind == "sift":
-        c = rng.integers(40, 216, size=(64, d)).astype(np.float32)
-        return c, (rng.standard_normal((64, d, m)) * (25.0 / np.sqrt(m))).astype(np.float32)
+        c0 = rng.integers(112, 144, size=d).astype(np.float32)
+        A = (rng.standard_normal((d, m)) * (25.0 / np.sqrt(m))).astype(np.float32)
+        return c0, A, rng.standard_normal((64, m)).astype(np.float32)
     if kind == "deep":
-        g = rng.standard_normal((256, d))
-        c = (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32)
-        return c, (rng.standard_normal((256, d, m)) * (0.5 / np.sqrt(m * d))).astype(np.float32)
+        g = rng.standard_normal(d)
+        c0 = (g / np.linalg.norm(g)).astype(np.float32)
+        A = (rng.standard_normal((d, m)) * (0.5 / np.sqrt(m * d))).astype(np.float32)
+        return c0, A, rng.standard_normal((256, m)).astype(np.float32)
     if kind == "gist":
-        c = rng.standard_normal((100, d)).astype(np.float32)
+        c = (0.1 * rng.standard_normal((100, d))).astype(np.float32)
         v = np.exp(rng.uniform(np.log(0.01), np.log(1.0), size=(100, d))).astype(np.float32)
-        return c, np.sqrt(v).astype(np.float32)
+        return c, np.sqrt(v).astype(np.float32), None
     if kind == "bigann16":
-        c = rng.standard_normal((1024, d)).astype(np.float32)
-        return c, (rng.standard_normal((1024, d, m)) * (0.5 / np.sqrt(m))).astype(np.float32)
-    return None, None
-
-
-def _lowrank(rng, A, a, m_rows):
-    """Rows A[a_i] z_i with z_i ~ N(0, I): one matrix product per centre present."""
-    z = rng.standard_normal((m_rows, A.shape[2]), dtype=np.float32)
-    out = np.empty((m_rows, A.shape[1]), np.float32)
-    order = np.argsort(a, kind="stable")
-    bounds = np.searchsorted(a[order], np.arange(A.shape[0] + 1))
-    for c in range(A.shape[0]):
-        rows = order[bounds[c]:bounds[c + 1]]
-        if rows.size:
-            out[rows] = z[rows] @ A[c].T
-    return out
+        A = (rng.standard_normal((d, m)) * (0.5 / np.sqrt(m))).astype(np.float32)
+        return np.zeros(d, np.float32), A, rng.standard_normal((1024, m)).astype(np.float32)
+    return None, None, None
 
 
 def generate(kind: str, n: int, d: int, seed: int, dtype: str = "float32",
@@ -115,30 +107,26 @@ def generate(kind: str, n: int, d: int, seed: int, dtype: str = "float32",
     """Return ``n`` rows of workload ``kind`` in dimension ``d`` (C-contiguous)."""
     if n < 0 or d <= 0:
         raise ValueError("n must be >= 0 and d > 0")
-    centres, scales = _centres(kind, d, seed if centre_seed is None else centre_seed)
+    c0, A, U = _centres(kind, d, seed if centre_seed is None else centre_seed)
     rng = np.random.Generator(np.random.PCG64(seed))
     out = np.empty((n, d), dtype=np.float16 if dtype == "float16" else np.float32)
     for r0 in range(0, n, _CHUNK):
         m = min(_CHUNK, n - r0)
         if kind == "gauss":
             blk = rng.standard_normal((m, d), dtype=np.float32)
-        elif kind == "sift":
-            a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + _lowrank(rng, scales, a, m)
-            blk += 2.0 * rng.standard_normal((m, d), dtype=np.float32)
-            blk = np.rint(np.clip(blk, 0.0, 255.0))
-        elif kind == "deep":
-            a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + _lowrank(rng, scales, a, m)
-            blk += (0.05 / np.sqrt(d)) * rng.standard_normal((m, d), dtype=np.float32)
-            blk = blk / np.linalg.norm(blk, axis=1, keepdims=True)
+        elif kind in ("sift", "deep", "bigann16"):
+            a = rng.integers(0, U.shape[0], size=m)
+            z = rng.standard_normal((m, U.shape[1]), dtype=np.float32)
+            blk = c0 + (U[a] + z) @ A.T
+            eps = {"sift": 2.0, "deep": 0.05 / np.sqrt(d), "bigann16": 0.05}[kind]
+            blk += eps * rng.standard_normal((m, d), dtype=np.float32)
+            if kind == "sift":
+                blk = np.rint(np.clip(blk, 0.0, 255.0))
+            elif kind == "deep":
+                blk = blk / np.linalg.norm(blk, axis=1, keepdims=True)
         elif kind == "gist":
-            a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + scales[a] * rng.standard_normal((m, d), dtype=np.float32)
-        elif kind == "bigann16":
-            a = rng.integers(0, centres.shape[0], size=m)
-            blk = centres[a] + _lowrank(rng, scales, a, m)
-            blk += 0.05 * rng.standard_normal((m, d), dtype=np.float32)
+            a = rng.integers(0, c0.shape[0], size=m)
+            blk = c0[a] + A[a] * rng.standard_normal((m, d), dtype=np.float32)
         else:
             raise ValueError(f"unknown workload kind {kind!r}")
         out[r0:r0 + m] = blk

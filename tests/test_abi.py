@@ -45,7 +45,7 @@ def test_last_error_without_gpu(lib):
     import paper_2510_05975_gb300.cng as cng
 
     # an invalid call is rejected before any device work
-    p = cng.BuildParams(1.2, 0.0, 0, 10, 0, 0, 1e-5, 32, 0)
+    p = cng.BuildParams(1.2, 0.0, 0, 10, 0, 0, 1e-5, 32, 0, 0)
     h = ctypes.c_void_p()
     rc = lib.cng_build(None, 0, 100, 8, ctypes.byref(p), None, ctypes.byref(h), None)
     assert rc == cng.CNG_E_INVAL

@@ -183,10 +183,13 @@ def test_connectivity_repair_on_clusters():
     # the first round's edges: r -> smallest p whose search from the entry ends at r
     reach0 = _reachable(G.adj3, G.deg3, G.entry)
     U = np.array(sorted(set(range(n)) - reach0), np.int32)
-    ids, _, _, _ = oracle.search(X, G.adj3, G.deg3, G.entry, X[U], 1, oracle.CONNECT_L)
+    ids, _, _, _ = oracle.search(X, G.adj3, G.deg3, G.entry, X[U], 8, oracle.CONNECT_L)
     first = {}
-    for p, r in zip(U, ids[:, 0]):
-        first.setdefault(int(r), int(p))
+    Rs = 12 + oracle.REPAIR_SLOTS
+    for p, row in zip(U, ids):
+        r = next((int(c) for c in row if c >= 0 and G.deg3[c] < Rs), None)
+        if r is not None:
+            first.setdefault(r, int(p))
     for r, p in first.items():
         assert int(r) in reach0
         assert G.adj[r, G.deg3[r]] == p
