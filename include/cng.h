@@ -110,6 +110,23 @@ cng_status cng_build(const void *points, int32_t dtype, int64_t n, int32_t d,
                      const cng_build_params *params, void *stream, cng_index **out,
                      cng_build_stats *stats);
 
+/*
+ * cng_entry_noalloc -- the navigating node of cng_build (the point nearest the centroid, ties
+ * to the smaller id) without allocating any memory, for callers that cannot allocate device
+ * memory when they need it: code running while a stream is captured into a CUDA graph,
+ * processes whose device memory belongs to another allocator, latency-bound loops.  The paper
+ * has no counterpart to this call; it is an engineering addition.
+ * points_dev: device, n x d of `dtype`, row-major without padding; entry_dev: device int32
+ * receiving the id.  Asynchronous on `stream`; calls no allocator.  Scratch is a fixed 4 MiB
+ * device array held by every GPU that loads the library until exit: a call needs
+ * ceil(n / 4096) * d + d + 2 doubles of it, at most 524,288 (n <= 16.7 million at d = 128);
+ * larger inputs are rejected with CNG_E_INVAL.  The first call on a device looks up the
+ * array's address, so make it before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU race.
+ */
+cng_status cng_entry_noalloc(const void *points_dev, int32_t dtype, int64_t n, int32_t d,
+                             int32_t *entry_dev, void *stream);
+
 /* Release an index and its device memory.  NULL-safe. */
 void cng_free(cng_index *index);
 

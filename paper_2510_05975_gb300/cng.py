@@ -26,7 +26,7 @@ CNG_SEARCH_FIXED, CNG_SEARCH_LEARNED = 0, 1
 
 EXPORTS = ("cng_build", "cng_free", "cng_last_error", "cng_graph", "cng_lists", "cng_search",
            "cng_knn", "cng_stop_train", "cng_stop_free", "cng_stop_export", "cng_stop_import",
-           "cng_trace", "cng_mlp_grad", "cng_mlp_adam")
+           "cng_trace", "cng_mlp_grad", "cng_mlp_adam", "cng_entry_noalloc")
 CNG_STOP_NPARAMS = 5313
 
 
@@ -125,6 +125,8 @@ def lib():
             L.cng_trace.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp]
             L.cng_mlp_grad.restype = ctypes.c_int
             L.cng_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+            L.cng_entry_noalloc.restype = ctypes.c_int
+            L.cng_entry_noalloc.argtypes = [vp, i32, i64, i32, vp, vp]
             L.cngx_launches.restype = ctypes.c_longlong
             L.cngx_launches.argtypes = []
             L.cng_mlp_adam.restype = ctypes.c_int
@@ -362,3 +364,11 @@ def cng_mlp_grad(params: torch.Tensor, x: torch.Tensor, y: torch.Tensor, stream=
 def cng_mlp_adam(params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, t: int,
                  lr: float, stream=None):
     _check(lib().cng_mlp_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), t, lr, _stream(stream)))
+
+
+def cng_entry_noalloc(points: torch.Tensor, out: torch.Tensor, stream=None):
+    """cng_entry_noalloc of include/cng.h: the navigating node of `points` (CUDA float32 or
+    float16 [n, d]) written to `out` (CUDA int32 [1]); allocates nothing."""
+    dt = {torch.float32: CNG_F32, torch.float16: CNG_F16}[points.dtype]
+    n, d = points.shape
+    _check(lib().cng_entry_noalloc(_ptr(points), dt, n, d, _ptr(out), _stream(stream)))

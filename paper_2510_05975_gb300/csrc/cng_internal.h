@@ -108,6 +108,11 @@ constexpr int REPAIR_SLOTS = 8;   // adjacency row slots beyond R for phase-4 ed
 constexpr int CONNECT_L = 32;     // default beam width of the phase-4 searches
 
 int num_sms();
+// k_entry_noalloc.cu: the navigating node using a fixed file-scope device array as scratch.
+int64_t entry_noalloc_need(int64_t n, int d);      // doubles of scratch a call needs
+int64_t entry_noalloc_capacity();                  // doubles the array holds
+cudaError_t launch_entry_noalloc(const void* X, int dtype, int64_t n, int d, int32_t* out,
+                                 cudaStream_t s);
 int64_t reverse_blocksums_len(int64_t n);
 
 }  // namespace cng
