@@ -149,6 +149,97 @@ CNG_DEV void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+CNG_DEV void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Warp-cooperative selection (same contract as warp_compact): keeps the Lp smallest of the
+// cnt buffered keys, moves them to the front and returns the largest kept key.  Radix select
+// on 8-bit digits with a 256-bin shared histogram per warp (4 passes).
+template <int CAP_PER_LANE>
+CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uint32_t* hist) {
+  uint32_t k[CAP_PER_LANE];
+  uint64_t e[CAP_PER_LANE];
+#pragma unroll
+  for (int i = 0; i < CAP_PER_LANE; ++i) {
+    int idx = i * 32 + lane;
+    e[i] = idx < cnt ? buf[idx] : ~0ull;
+    k[i] = (uint32_t)(e[i] >> 32);
+  }
+  __syncwarp();
+  uint32_t prefix = 0;
+  int need = Lp;
+#pragma unroll 1
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < CAP_PER_LANE; ++i) {
+      const bool valid = i * 32 + lane < cnt;
+      const bool match = pass == 0 || ((k[i] ^ prefix) >> (shift + 8)) == 0;
+      if (valid && match) atomicAdd(&hist[(k[i] >> shift) & 255u], 1u);
+    }
+    __syncwarp();
+    uint32_t h[8], tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = hist[lane * 8 + i];
+      tot += h[i];
+    }
+    uint32_t inc = tot;  // inclusive scan of lane totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const uint32_t excl = inc - tot;
+    const unsigned hit = __ballot_sync(FULL, excl < (uint32_t)need && inc >= (uint32_t)need);
+    const int src = __ffs(hit) - 1;
+    int digit = 0, below = 0;
+    if (lane == src) {
+      uint32_t acc = excl;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (acc + h[i] >= (uint32_t)need) { digit = lane * 8 + i; break; }
+        acc += h[i];
+      }
+      below = (int)acc;
+    }
+    digit = __shfl_sync(FULL, digit, src);
+    below = __shfl_sync(FULL, below, src);
+    need -= below;
+    prefix |= (uint32_t)digit << shift;
+    __syncwarp();
+  }
+  const uint32_t kth = prefix;  // `need` entries equal to kth are kept
+  int out = 0, eq_taken = 0;
+#pragma unroll
+  for (int i = 0; i < CAP_PER_LANE; ++i) {
+    bool valid = i * 32 + lane < cnt;
+    bool lt = valid && k[i] < kth;
+    bool eq = valid && k[i] == kth;
+    unsigned beq = __ballot_sync(FULL, eq);
+    int eq_rank = eq_taken + __popc(beq & ((1u << lane) - 1));
+    bool keep = lt || (eq && eq_rank < need);
+    eq_taken += __popc(beq);
+    unsigned bk = __ballot_sync(FULL, keep);
+    if (keep) buf[out + __popc(bk & ((1u << lane) - 1))] = e[i];
+    out += __popc(bk);
+  }
+  __syncwarp();
+  return kth;
+}
+
 // ---- the kernel --------------------------------------------------------------------------------
 template <int CPL, bool DUMP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -172,6 +263,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   uint64_t* fin = a_empty + 1;           // [1] MMA drain at exit
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint32_t* hist_all = reinterpret_cast<uint32_t*>(tmem_slot + 4);  // [8 warps][256]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nrb = (P.m + TC_BM - 1) / TC_BM;
@@ -281,6 +373,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     const int quarter = warp & 3, accsel = warp >> 2;
     const int rloc = accsel * 128 + quarter * 32 + lane;  // row within the block
     uint64_t* rbuf = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rloc) * P.cap;
+    uint32_t* hist = hist_all + warp * 256;
     int64_t tt = 0;
     bool ok = true;
     for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
@@ -295,42 +388,60 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         tc_fence_after();
         const int64_t c0 = (int64_t)t * TC_BN;
         const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + accsel * 128);
+        // four chunks of 32 columns; the buffer goes back to the MMA warp after the last load
 #pragma unroll 1
         for (int ch = 0; ch < TC_BN / 32; ++ch) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + accsel * 128 + ch * 32), v);
+          uint32_t r[32];
+          tmem_ld32_nowait(ta + ch * 32, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (ch == TC_BN / 32 - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[b]);
+          }
           const int64_t cb = c0 + ch * 32;
           const float4* nb4 = reinterpret_cast<const float4*>(P.nb + cb);
-          float mn = __int_as_float(0x7f800000);
+          float4 y[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) y[q] = __ldg(nb4 + q);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const float4 y = __ldg(nb4 + q);
-            v[4 * q + 0] = fmaf(-2.f, v[4 * q + 0], y.x);
-            v[4 * q + 1] = fmaf(-2.f, v[4 * q + 1], y.y);
-            v[4 * q + 2] = fmaf(-2.f, v[4 * q + 2], y.z);
-            v[4 * q + 3] = fmaf(-2.f, v[4 * q + 3], y.w);
+            r[4 * q + 0] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 0]), y[q].x));
+            r[4 * q + 1] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 1]), y[q].y));
+            r[4 * q + 2] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 2]), y[q].z));
+            r[4 * q + 3] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 3]), y[q].w));
           }
           if (edge) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
               const int64_t col = cb + jj;
-              if (col >= P.n || (P.self_excl && col == row)) v[jj] = __int_as_float(0x7f800000);
+              if (col >= P.n || (P.self_excl && col == row)) r[jj] = 0x7f800000u;
             }
           }
           if (DUMP) {
             if (live)
+#pragma unroll
               for (int jj = 0; jj < 32; ++jj)
-                if (cb + jj < P.n) dump[row * P.n + cb + jj] = v[jj];
+                if (cb + jj < P.n) dump[row * P.n + cb + jj] = __uint_as_float(r[jj]);
             continue;
           }
+          float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
+          float m2 = __uint_as_float(r[2]), m3 = __uint_as_float(r[3]);
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) mn = fminf(mn, v[jj]);
-          if (live && mn < thr) {
-#pragma unroll 1
+          for (int jj = 4; jj < 32; jj += 4) {
+            m0 = fminf(m0, __uint_as_float(r[jj]));
+            m1 = fminf(m1, __uint_as_float(r[jj + 1]));
+            m2 = fminf(m2, __uint_as_float(r[jj + 2]));
+            m3 = fminf(m3, __uint_as_float(r[jj + 3]));
+          }
+          if (live && fminf(fminf(m0, m1), fminf(m2, m3)) < thr) {
+#pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
-              if (v[jj] < thr) {
+              const float vj = __uint_as_float(r[jj]);
+              if (vj < thr) {
                 if (cnt < P.cap)
-                  rbuf[cnt] = ((uint64_t)fkey(v[jj]) << 32) | (uint32_t)(cb + jj);
+                  rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + jj);
                 else
                   atomicOr(P.status, ST_OVERFLOW);
                 ++cnt;
@@ -338,10 +449,6 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             }
           }
         }
-        // buffer drained: hand it back to the MMA warp
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&t_empty[b]);
         if (DUMP) continue;
         // compact every row whose buffer could overflow on the next tile
         unsigned needc = __ballot_sync(FULL, cnt > P.cap - TC_BN);
@@ -351,7 +458,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
           uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
           __syncwarp();
-          const uint32_t k = warp_compact<CPL>(buf_l, c_l, P.Lp, lane);
+          const uint32_t k = warp_compact_hist<CPL>(buf_l, c_l, P.Lp, lane, hist);
           if (lane == l) {
             thr = fkey_inv(k);
             cnt = P.Lp;
@@ -369,7 +476,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
         uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
         __syncwarp();
-        const uint32_t k = warp_compact<CPL>(buf_l, c_l, P.Lp, lane);
+        const uint32_t k = warp_compact_hist<CPL>(buf_l, c_l, P.Lp, lane, hist);
         if (lane == l) {
           thk = k;
           cnt = P.Lp;
@@ -463,7 +570,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   p.kpad = kpad;
   p.nkc = kpad / 64;
   const int a_bytes = TC_BM * kpad * 2, b_bytes = TC_BN * kpad * 2;
-  const int budget = 220 * 1024 - a_bytes - 1024 - 256;
+  const int budget = 220 * 1024 - a_bytes - 1024 - 256 - 8 * 256 * 4;
   p.nst = std::min(4, budget / b_bytes);
   if (p.nst < 2) {
     if (msg) *msg = "shared memory too small for two B stages; ";
@@ -490,7 +597,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   const int64_t nrb = (a.m + TC_BM - 1) / TC_BM;
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
-  size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * b_bytes + 256;
+  size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * b_bytes + 256 + 8 * 256 * 4;
   smem = std::max<size_t>(smem, 116 * 1024);
   if (!a.rowbuf || a.rowbuf_words < (size_t)grid * TC_BM * p.cap) {
     if (msg) *msg = "row buffer missing or too small; ";
