@@ -95,6 +95,20 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values: dict, dist=None) -> dict:
+    """Max of each timing over the ranks of the default process group (identity without one).
+    Each rank runs an independent replica, so the slowest rank's time is the job's time."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return dict(values)
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    keys = sorted(values)
+    t = torch.tensor([float(values[k]) for k in keys], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return {k: float(v) for k, v in zip(keys, t.tolist())}
+
+
 def recall_at_k(found: np.ndarray, gt: np.ndarray) -> float:
     k = gt.shape[1]
     hits = 0
@@ -336,11 +350,7 @@ def main():
     cng.cng_free(idx)
 
     def allmax(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks({"v": v}, dist if ws > 1 else None)["v"]
 
     b_s = allmax(float(np.mean(build_ms)) / 1e3)
     f_ms = allmax(float(np.mean(fix_ms)))

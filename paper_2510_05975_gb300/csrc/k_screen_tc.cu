@@ -36,7 +36,8 @@ constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
 constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
 constexpr int TC_PRODUCER = 8;
 constexpr int TC_MMA = 9;
-constexpr uint32_t TC_SPIN = 1u << 28;  // wait iterations before declaring a timeout
+constexpr uint32_t TC_SPIN = 1u << 17;     // wait iterations before declaring a timeout
+constexpr uint32_t TC_SUSPEND_NS = 20000;  // try_wait suspend-time hint (wakes on completion)
 
 struct TcParams {
   int64_t m, n;
@@ -67,9 +68,9 @@ CNG_DEV void mbar_arrive(uint64_t* b) {
 CNG_DEV bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
+      : "r"(smem_u32(b)), "r"(parity), "r"(TC_SUSPEND_NS)
       : "memory");
   return ok != 0;
 }
@@ -77,7 +78,7 @@ CNG_DEV bool mbar_try(uint64_t* b, uint32_t parity) {
 CNG_DEV bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
   for (uint32_t i = 0; i < TC_SPIN; ++i) {
     if (mbar_try(b, parity)) return true;
-    if ((i & 1023u) == 1023u && *abort_flag) return false;
+    if ((i & 15u) == 15u && *abort_flag) return false;
   }
   *abort_flag = 1;
   atomicOr(status, ST_TIMEOUT);
@@ -89,7 +90,7 @@ CNG_DEV bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, u
 CNG_DEV bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
   for (uint32_t i = 0; i < TC_SPIN; ++i) {
     if (__all_sync(FULL, mbar_try(b, parity))) return true;
-    if ((i & 1023u) == 1023u && __any_sync(FULL, *abort_flag != 0)) return false;
+    if ((i & 15u) == 15u && __any_sync(FULL, *abort_flag != 0)) return false;
   }
   if ((threadIdx.x & 31) == 0) {
     *abort_flag = 1;
@@ -104,6 +105,14 @@ CNG_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+CNG_DEV void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -240,6 +249,61 @@ CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uin
   return kth;
 }
 
+// One row's 32 accumulator columns [cb, cb + 32): screened scores, masking of out-of-range
+// and self columns, minimum against the row threshold, appends below the threshold.
+template <bool DUMP>
+CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_t row,
+                           const TcParams& P, const float* nbs, float thr, int& cnt,
+                           uint64_t* rbuf, float* dump) {
+  const float4* nb4 = reinterpret_cast<const float4*>(nbs);
+  float4 y[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) y[q] = nb4[q];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    r[4 * q + 0] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 0]), y[q].x));
+    r[4 * q + 1] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 1]), y[q].y));
+    r[4 * q + 2] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 2]), y[q].z));
+    r[4 * q + 3] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 3]), y[q].w));
+  }
+  if (edge) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int64_t col = cb + jj;
+      if (col >= P.n || (P.self_excl && col == row)) r[jj] = 0x7f800000u;
+    }
+  }
+  if (DUMP) {
+    if (live)
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj)
+        if (cb + jj < P.n) dump[row * P.n + cb + jj] = __uint_as_float(r[jj]);
+    return;
+  }
+  float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
+  float m2 = __uint_as_float(r[2]), m3 = __uint_as_float(r[3]);
+#pragma unroll
+  for (int jj = 4; jj < 32; jj += 4) {
+    m0 = fminf(m0, __uint_as_float(r[jj]));
+    m1 = fminf(m1, __uint_as_float(r[jj + 1]));
+    m2 = fminf(m2, __uint_as_float(r[jj + 2]));
+    m3 = fminf(m3, __uint_as_float(r[jj + 3]));
+  }
+  if (live && fminf(fminf(m0, m1), fminf(m2, m3)) < thr) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const float vj = __uint_as_float(r[jj]);
+      if (vj < thr) {
+        if (cnt < P.cap)
+          rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + jj);
+        else
+          atomicOr(P.status, ST_OVERFLOW);
+        ++cnt;
+      }
+    }
+  }
+}
+
 // ---- the kernel --------------------------------------------------------------------------------
 template <int CPL, bool DUMP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -253,7 +317,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   const int b_bytes = TC_BN * P.kpad * 2;
   unsigned char* sA = smem;
   unsigned char* sB = smem + a_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + P.nst * b_bytes);
+  float* sNB = reinterpret_cast<float*>(sB + P.nst * b_bytes);  // [nst][TC_BN] column norms
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sNB + P.nst * TC_BN);
   uint64_t* b_full = bars;               // [nst]
   uint64_t* b_empty = bars + P.nst;      // [nst]
   uint64_t* t_full = bars + 2 * P.nst;   // [2]
@@ -272,7 +337,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   if (tid == 0) {
     for (int i = 0; i < P.nst; ++i) {
       mbar_init(&b_full[i], 1);
-      mbar_init(&b_empty[i], 1);
+      mbar_init(&b_empty[i], 1 + 8);  // MMA commit + the 8 epilogue warps (norms read)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&t_full[i], 1);
@@ -313,10 +378,11 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           const uint32_t ph = (uint32_t)((it / P.nst) & 1);
           ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
           if (!ok) break;
-          mbar_expect_tx(&b_full[s], (uint32_t)b_bytes);
+          mbar_expect_tx(&b_full[s], (uint32_t)(b_bytes + TC_BN * 4));
           unsigned char* dst = sB + s * b_bytes;
           for (int kc = 0; kc < P.nkc; ++kc)
             tma_load_2d(dst + kc * (TC_BN * 128), &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
+          bulk_load(sNB + s * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &b_full[s]);
         }
       }
       if (!ok) {
@@ -387,9 +453,13 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         if (!ok) break;
         tc_fence_after();
         const int64_t c0 = (int64_t)t * TC_BN;
+        const int stage = (int)(tt % P.nst);  // the B stage (and its norms) of this tile
+        // observe the stage's TMA completion too (already complete; the stage cannot be refilled
+        // before this warp releases it), so the norms written by the copy engine are visible
+        ok = mbar_wait_warp(&b_full[stage], (uint32_t)((tt / P.nst) & 1), abort_flag, P.status);
+        if (!ok) break;
         const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
         const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + accsel * 128);
-        // four chunks of 32 columns; the buffer goes back to the MMA warp after the last load
 #pragma unroll 1
         for (int ch = 0; ch < TC_BN / 32; ++ch) {
           uint32_t r[32];
@@ -400,55 +470,11 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&t_empty[b]);
           }
-          const int64_t cb = c0 + ch * 32;
-          const float4* nb4 = reinterpret_cast<const float4*>(P.nb + cb);
-          float4 y[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) y[q] = __ldg(nb4 + q);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            r[4 * q + 0] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 0]), y[q].x));
-            r[4 * q + 1] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 1]), y[q].y));
-            r[4 * q + 2] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 2]), y[q].z));
-            r[4 * q + 3] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 3]), y[q].w));
-          }
-          if (edge) {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              const int64_t col = cb + jj;
-              if (col >= P.n || (P.self_excl && col == row)) r[jj] = 0x7f800000u;
-            }
-          }
-          if (DUMP) {
-            if (live)
-#pragma unroll
-              for (int jj = 0; jj < 32; ++jj)
-                if (cb + jj < P.n) dump[row * P.n + cb + jj] = __uint_as_float(r[jj]);
-            continue;
-          }
-          float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
-          float m2 = __uint_as_float(r[2]), m3 = __uint_as_float(r[3]);
-#pragma unroll
-          for (int jj = 4; jj < 32; jj += 4) {
-            m0 = fminf(m0, __uint_as_float(r[jj]));
-            m1 = fminf(m1, __uint_as_float(r[jj + 1]));
-            m2 = fminf(m2, __uint_as_float(r[jj + 2]));
-            m3 = fminf(m3, __uint_as_float(r[jj + 3]));
-          }
-          if (live && fminf(fminf(m0, m1), fminf(m2, m3)) < thr) {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              const float vj = __uint_as_float(r[jj]);
-              if (vj < thr) {
-                if (cnt < P.cap)
-                  rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + jj);
-                else
-                  atomicOr(P.status, ST_OVERFLOW);
-                ++cnt;
-              }
-            }
-          }
+          process_chunk<DUMP>(r, c0 + ch * 32, edge, live, row, P, sNB + stage * TC_BN + ch * 32, thr, cnt, rbuf, dump);
         }
+        // norms of this stage no longer needed: release the stage (with the MMA's commit)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&b_empty[stage]);
         if (DUMP) continue;
         // compact every row whose buffer could overflow on the next tile
         unsigned needc = __ballot_sync(FULL, cnt > P.cap - TC_BN);
@@ -571,14 +597,14 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   p.nkc = kpad / 64;
   const int a_bytes = TC_BM * kpad * 2, b_bytes = TC_BN * kpad * 2;
   const int budget = 220 * 1024 - a_bytes - 1024 - 256 - 8 * 256 * 4;
-  p.nst = std::min(4, budget / b_bytes);
+  p.nst = std::min(4, budget / (b_bytes + TC_BN * 4));
   if (p.nst < 2) {
     if (msg) *msg = "shared memory too small for two B stages; ";
     return cudaErrorInvalidValue;
   }
   p.Lp = a.Lp;
   int cpl = 0;
-  for (int c : {8, 12, 16, 20})
+  for (int c : {12, 16, 20, 24})
     if (c * 32 >= a.Lp + TC_BN + 32) { cpl = c; break; }
   if (!cpl) {
     if (msg) *msg = "screened list too long; ";
@@ -597,7 +623,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   const int64_t nrb = (a.m + TC_BM - 1) / TC_BM;
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
-  size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * b_bytes + 256 + 8 * 256 * 4;
+  size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * (b_bytes + TC_BN * 4) + 256 + 8 * 256 * 4;
   smem = std::max<size_t>(smem, 116 * 1024);
   if (!a.rowbuf || a.rowbuf_words < (size_t)grid * TC_BM * p.cap) {
     if (msg) *msg = "row buffer missing or too small; ";
@@ -611,10 +637,10 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
              : launch_t<C, false>(ma, mb, p, smem, grid, s, dump);                            \
     break;
   switch (cpl) {
-    CNG_TC(8)
     CNG_TC(12)
     CNG_TC(16)
     CNG_TC(20)
+    CNG_TC(24)
     default:
       e = cudaErrorInvalidValue;
   }
@@ -623,10 +649,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
 }
 
 size_t screen_tc_rowbuf_words(int64_t m, int Lp) {
-  int cpl = 0;
-  for (int c : {8, 12, 16, 20})
-    if (c * 32 >= Lp + TC_BN + 32) { cpl = c; break; }
-  if (!cpl) cpl = 20;
+  const int cpl = 24;  // the largest capacity launch_impl may choose
   const int64_t nrb = (m + TC_BM - 1) / TC_BM;
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
   return (size_t)grid * TC_BM * cpl * 32;
