@@ -233,7 +233,8 @@ def main():
         torch.cuda.synchronize()
         fl = 2.0 * args.knn_n * args.knn_n * w.d
         print(json.dumps({"knn_n": args.knn_n, "d": w.d, "L": w.L, "screen": args.screen,
-                          "ms_screen": st["ms_screen"], "ms_rerank": st["ms_rerank"],
+                          "ms_order": st["ms_order"], "ms_screen": st["ms_screen"],
+                          "ms_rerank": st["ms_rerank"],
                           "screen_tflops": fl / (st["ms_screen"] / 1e3) / 1e12,
                           "cert_fail_rows": st["cert_fail_rows"]}), flush=True)
         return

@@ -58,6 +58,9 @@ typedef enum {
  *   keep_lists       1: keep candidate and phase-2 lists for cng_lists()
  *   connect_L        beam width of the phase-4 connectivity searches (0 = 32; < 0 skips
  *                    phase 4, leaving points of separated clusters unreachable)
+ *   input_order      0 (default): the tensor-core screen sweeps the points in a k-d locality
+ *                    order, which makes it faster; 1: in input order.  The results are the
+ *                    same either way (an engineering option, not in the paper).
  */
 typedef struct {
   double alpha;
@@ -70,6 +73,7 @@ typedef struct {
   int32_t margin;
   int32_t keep_lists;
   int32_t connect_L;
+  int32_t input_order;
 } cng_build_params;
 
 /* Per-phase times (device events, milliseconds) and near-tie / certification counts. */
@@ -87,6 +91,7 @@ typedef struct {
   int32_t entry;              /* navigating node s */
   int32_t exact_int;          /* 1 when every FP32 squared distance is an exact integer */
   double screen_err_max;      /* largest |screened - rerank| seen on kept candidates */
+  double ms_order;            /* locality order of the screen's operands (part of ms_total) */
 } cng_build_stats;
 
 typedef struct cng_index cng_index;

@@ -40,7 +40,8 @@ class BuildParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("R", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("metric", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("tie_band", ctypes.c_double), ("margin", ctypes.c_int32),
-                ("keep_lists", ctypes.c_int32), ("connect_L", ctypes.c_int32)]
+                ("keep_lists", ctypes.c_int32), ("connect_L", ctypes.c_int32),
+                ("input_order", ctypes.c_int32)]
 
 
 class BuildStats(ctypes.Structure):
@@ -52,7 +53,7 @@ class BuildStats(ctypes.Structure):
                  "merge_max_list", "repair_edges")] + \
                [("repair_rounds", ctypes.c_int32), ("screen_used", ctypes.c_int32),
                 ("entry", ctypes.c_int32), ("exact_int", ctypes.c_int32),
-                ("screen_err_max", ctypes.c_double)]
+                ("screen_err_max", ctypes.c_double), ("ms_order", ctypes.c_double)]
 
 
 class SearchParams(ctypes.Structure):
@@ -193,7 +194,8 @@ class Index:
 
 def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: int = CNG_L2,
               screen: int = CNG_SCREEN_TC, tie_band: float = 1e-5, margin: int = 32,
-              keep_lists: bool = False, connect_L: int = 0, stream=None):
+              keep_lists: bool = False, connect_L: int = 0, input_order: bool = False,
+              stream=None):
     """cng_build of include/cng.h.  points: CUDA tensor or host (numpy / CPU tensor), float32
     or float16, shape [n, d].  Returns (Index, stats dict)."""
     if isinstance(points, torch.Tensor):
@@ -203,7 +205,8 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
         import numpy as np
         dt = {np.dtype("float32"): CNG_F32, np.dtype("float16"): CNG_F16}[points.dtype]
         n, d = points.shape
-    p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists), connect_L)
+    p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists), connect_L,
+                    int(input_order))
     st = BuildStats()
     h = ctypes.c_void_p()
     _check(lib().cng_build(_ptr(points), dt, n, d, ctypes.byref(p), _stream(stream),

@@ -50,7 +50,18 @@ struct TcParams {
   uint32_t* thr;
   uint64_t* rowbuf;
   uint32_t* status;
+  const int32_t* perm;  // rows and columns are positions of a locality order: perm[pos] = id
+  int wave_start;       // 1: each wave of row blocks starts its column sweep at its own rows
 };
+
+// First column tile of row block rb's sweep.  A wave is the gridDim.x consecutive row blocks
+// processed together; all its CTAs share the start, so B tiles stay shared through L2.
+CNG_DEV int sweep_start(const TcParams& P, int64_t rb, int ntiles) {
+  if (!P.wave_start) return 0;
+  const int64_t w0 = rb - rb % gridDim.x;
+  const int64_t t0 = (w0 * TC_BM) / TC_BN;
+  return t0 < ntiles ? (int)t0 : ntiles - 1;
+}
 
 // ---- PTX wrappers ------------------------------------------------------------------------------
 CNG_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -249,8 +260,25 @@ CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uin
   return kth;
 }
 
+CNG_DEV float min3f(float a, float b, float c) {
+  float m;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+  return m;
+}
+
+// (a0, a1) * (b0, b1) + (c0, c1), each lane an IEEE fma rounded to nearest (same bits as fmaf)
+CNG_DEV void fma2(uint32_t& d0, uint32_t& d1, uint32_t a0, uint32_t a1, float b, float c0, float c1) {
+  uint64_t a, bb, c, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "r"(a0), "r"(a1));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(bb) : "f"(b));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(c0), "f"(c1));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(bb), "l"(c));
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(d0), "=r"(d1) : "l"(r));
+}
+
 // One row's 32 accumulator columns [cb, cb + 32): screened scores, masking of out-of-range
-// and self columns, minimum against the row threshold, appends below the threshold.
+// and self columns, minimum against the row threshold, appends below the threshold.  The
+// minimum is taken per group of 4 columns first, so appends visit only groups that hold one.
 template <bool DUMP>
 CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_t row,
                            const TcParams& P, const float* nbs, float thr, int& cnt,
@@ -261,10 +289,8 @@ CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_
   for (int q = 0; q < 8; ++q) y[q] = nb4[q];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    r[4 * q + 0] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 0]), y[q].x));
-    r[4 * q + 1] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 1]), y[q].y));
-    r[4 * q + 2] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 2]), y[q].z));
-    r[4 * q + 3] = __float_as_uint(fmaf(-2.f, __uint_as_float(r[4 * q + 3]), y[q].w));
+    fma2(r[4 * q + 0], r[4 * q + 1], r[4 * q + 0], r[4 * q + 1], -2.f, y[q].x, y[q].y);
+    fma2(r[4 * q + 2], r[4 * q + 3], r[4 * q + 2], r[4 * q + 3], -2.f, y[q].z, y[q].w);
   }
   if (edge) {
 #pragma unroll
@@ -280,25 +306,28 @@ CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_
         if (cb + jj < P.n) dump[row * P.n + cb + jj] = __uint_as_float(r[jj]);
     return;
   }
-  float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
-  float m2 = __uint_as_float(r[2]), m3 = __uint_as_float(r[3]);
+  float gm[8];
 #pragma unroll
-  for (int jj = 4; jj < 32; jj += 4) {
-    m0 = fminf(m0, __uint_as_float(r[jj]));
-    m1 = fminf(m1, __uint_as_float(r[jj + 1]));
-    m2 = fminf(m2, __uint_as_float(r[jj + 2]));
-    m3 = fminf(m3, __uint_as_float(r[jj + 3]));
-  }
-  if (live && fminf(fminf(m0, m1), fminf(m2, m3)) < thr) {
+  for (int g = 0; g < 8; ++g)
+    gm[g] = fminf(min3f(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]),
+                        __uint_as_float(r[4 * g + 2])),
+                  __uint_as_float(r[4 * g + 3]));
+  const float mall = min3f(min3f(gm[0], gm[1], gm[2]), min3f(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
+  if (live && mall < thr) {
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-      const float vj = __uint_as_float(r[jj]);
-      if (vj < thr) {
-        if (cnt < P.cap)
-          rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + jj);
-        else
-          atomicOr(P.status, ST_OVERFLOW);
-        ++cnt;
+    for (int g = 0; g < 8; ++g) {
+      if (gm[g] < thr) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float vj = __uint_as_float(r[4 * g + k]);
+          if (vj < thr) {
+            if (cnt < P.cap)
+              rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + 4 * g + k);
+            else
+              atomicOr(P.status, ST_OVERFLOW);
+            ++cnt;
+          }
+        }
       }
     }
   }
@@ -370,10 +399,12 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
         ok = mbar_wait(a_empty, (j & 1) ^ 1, abort_flag, P.status);
         if (!ok) break;
+        const int t0 = sweep_start(P, rb, ntiles);
         mbar_expect_tx(a_full, (uint32_t)a_bytes);
         for (int kc = 0; kc < P.nkc; ++kc)
           tma_load_2d(sA + kc * (TC_BM * 128), &mapA, kc * TC_KC, (int)(rb * TC_BM), a_full);
-        for (int t = 0; t < ntiles; ++t, ++it) {
+        for (int ti = 0; ti < ntiles; ++ti, ++it) {
+          const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
           const int s = (int)(it % P.nst);
           const uint32_t ph = (uint32_t)((it / P.nst) & 1);
           ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
@@ -447,7 +478,9 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       const bool live = row < P.m;
       float thr = __int_as_float(0x7f800000);
       int cnt = 0;
-      for (int t = 0; t < ntiles; ++t, ++tt) {
+      const int t0 = sweep_start(P, rb, ntiles);
+      for (int ti = 0; ti < ntiles; ++ti, ++tt) {
+        const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
         const int b = (int)(tt & 1);
         ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> 1) & 1), abort_flag, P.status);
         if (!ok) break;
@@ -511,8 +544,13 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       __syncwarp();
       if (live) {
         const int c = min(cnt, P.Lp);
-        for (int t = 0; t < P.Lp; ++t) P.ids[row * P.Lp + t] = t < c ? key_id(rbuf[t]) : -1;
-        P.thr[row] = thk;
+        const int64_t orow = P.perm ? P.perm[row] : row;
+        for (int t = 0; t < P.Lp; ++t) {
+          int32_t id = -1;
+          if (t < c) id = P.perm ? P.perm[key_id(rbuf[t])] : key_id(rbuf[t]);
+          P.ids[orow * P.Lp + t] = id;
+        }
+        P.thr[orow] = thk;
       }
     }
   }
@@ -617,6 +655,8 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   p.ids = a.ids;
   p.thr = a.thr;
   p.status = a.status;
+  p.perm = dump ? nullptr : a.perm;
+  p.wave_start = dump ? 0 : a.wave_start;
   CUtensorMap ma, mb;
   if (!make_map(&ma, a.A, a.m, kpad, TC_BM, a.fp16, msg)) return cudaErrorInvalidValue;
   if (!make_map(&mb, a.B, a.n, kpad, TC_BN, a.fp16, msg)) return cudaErrorInvalidValue;

@@ -23,6 +23,11 @@ struct TcScreenArgs {
   uint32_t* status;
   uint64_t* rowbuf;     // scratch: screen_tc_rowbuf_words(m, Lp) words
   size_t rowbuf_words;
+  // Locality order (optional): A and B hold the points at positions of an order, perm[pos]
+  // the point id; ids and thr are then written for the point ids (row perm[pos], column
+  // perm[col]).  wave_start = 1 starts each wave of row blocks at its own column tile.
+  const int32_t* perm;
+  int wave_start;
 };
 
 bool tc_screen_supported(int d, bool fp16);

@@ -106,3 +106,26 @@ def test_knn_rows_vs_oracle(screen):
     ref, rd = oracle.knn(X, 100, rows=Q)
     assert np.array_equal(host(ids), ref)
     assert np.allclose(host(ds), rd, rtol=2e-6)
+
+
+@pytest.mark.parametrize("kind,n,d,R,L", [
+    ("sift", 60_001, 128, 32, 128),   # two waves of 152 row blocks and a ragged tail
+    ("deep", 41_000, 96, 24, 80),
+])
+def test_locality_order_same_lists(kind, n, d, R, L):
+    """The tensor-core screen's locality order changes speed only: candidate lists, distances,
+    phase-2 lists and the final graph equal those of the input-order sweep."""
+    need_gpu()
+    cng = lib()
+    X = tensor(synth.generate(kind, n, d, seed=9))
+    out = []
+    for input_order in (False, True):
+        idx, st = cng.cng_build(X, alpha=1.2, R=R, L=L, keep_lists=True, input_order=input_order)
+        assert st["screen_used"] == 1
+        assert (st["ms_order"] > 0) != input_order
+        cand, cdist, fwd, fdeg = cng.cng_lists(idx)
+        adj, deg, _, entry = cng.cng_graph(idx)
+        out.append([host(a) for a in (cand, cdist, fwd, fdeg, adj, deg)] + [entry])
+        cng.cng_free(idx)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
