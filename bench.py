@@ -201,6 +201,9 @@ def main():
     ap.add_argument("--knn-n", type=int, default=0,
                     help="only run the exact k-NN path (screen + rerank) on the first N points "
                          "of the workload, once, and print its timing (small case for profiling)")
+    ap.add_argument("--build-n", type=int, default=0,
+                    help="only run one graph build on the first N points of the workload (after a "
+                         "warm-up build) and print its phase timings (small case for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -237,6 +240,17 @@ def main():
                           "ms_rerank": st["ms_rerank"],
                           "screen_tflops": fl / (st["ms_screen"] / 1e3) / 1e12,
                           "cert_fail_rows": st["cert_fail_rows"]}), flush=True)
+        return
+    if args.build_n:
+        Xs = torch.from_numpy(w.base(args.build_n).astype(np.float32)).cuda()
+        for it in range(2):  # warm-up, then the reported build
+            idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+            torch.cuda.synchronize()
+            cng.cng_free(idx)
+        print(json.dumps({"build_n": args.build_n, "d": w.d, "L": w.L, "R": w.R,
+                          **{k: st[k] for k in ("ms_total", "ms_order", "ms_screen", "ms_rerank",
+                                                "ms_prune", "ms_merge", "ms_connect", "rule_ties", "cert_fail_rows", "order_ties",
+                                                "merge_repruned", "n_edges")}}), flush=True)
         return
     X = w.base()
     Q = w.queries()

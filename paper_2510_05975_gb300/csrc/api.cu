@@ -360,6 +360,15 @@ static float bits_to_float(uint32_t b) {
   return f;
 }
 
+// 8-bit rows u = x - min(x) hold the data exactly when every coordinate is an integer and the
+// span is at most 255; squared distances are then exact 32-bit integers below 2^24.
+static bool u8_rows_ok(const PrepStats& st, int d) {
+  if (st.nonint) return false;
+  const double lo = key_to_float(st.vmin_key), hi = key_to_float(st.vmax_key);
+  const double span = hi - lo;
+  return span >= 0.0 && span <= 255.0 && (double)d * span * span < 16777216.0 && u8_words(d) > 0;
+}
+
 // Squared distances are exact FP32 integers when every coordinate is an integer and
 // d * span^2 < 2^24 (span = max - min coordinate); the tensor-core screen additionally needs
 // |coordinate| <= 256 (exact in bf16) and ||x||^2 < 2^24.
@@ -482,13 +491,20 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   if (st != CNG_OK) return st;
   // screening operands are no longer needed
   if (pr.tc) { cudaFree(pr.tc); pool.release(pr.tc); pr.tc = nullptr; }
+  // integer data spanning <= 255: 8-bit rows for exact integer pair distances in K4 / K6
+  uint8_t* u8 = nullptr;
+  const int u8w = u8_rows_ok(pr.st, d) ? u8_words(d) : 0;
+  if (u8w) {
+    CK(pool.alloc(&u8, (size_t)n * u8w * 4));
+    CK(launch_to_u8(pr.xs, dtype, n, d, dpad, key_to_float(pr.st.vmin_key), u8w, u8, s));
+  }
   tm.mark();  // 3
   // phase 2b: prune every candidate list
   int32_t *fwd, *fdeg;
   CK(pool.alloc(&fwd, (size_t)n * R));
   CK(pool.alloc(&fdeg, (size_t)n));
   CK(launch_prune_fwd(pr.xs, dtype, n, d, dpad, cand, cdist, L, P.alpha, P.tau, R, band, fwd, fdeg,
-                      ctr, s));
+                      ctr, u8, u8w, s));
   tm.mark();  // 4
   // phase 3: reverse edges + lazy pruning
   int32_t *indeg, *cursor, *inl, *adj, *deg;
@@ -502,10 +518,10 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   CK(pool.alloc(&adj, (size_t)n * Rs));
   CK(pool.alloc(&deg, (size_t)n));
   int32_t* big_list;
-  CK(pool.alloc(&big_list, (size_t)n));
+  CK(pool.alloc(&big_list, 2 * (size_t)n));  // big list + the 8-bit merge's middle list
   CK(launch_reverse(fwd, fdeg, n, R, indeg, off, cursor, inl, bsum, ctr, s));
   CK(launch_merge(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band, exact, adj,
-                  deg, Rs, ctr, big_list, s));
+                  deg, Rs, ctr, big_list, u8, u8w, s));
   {
     Counters hc0;
     CK(cudaMemcpyAsync(&hc0, ctr, sizeof(hc0), cudaMemcpyDeviceToHost, s));

@@ -39,7 +39,7 @@ struct Counters {
   uint32_t screen_err_bits;
   int nbig;        // nodes whose merged set exceeds the shared-memory capacity
   int max_indeg;
-  int pad;
+  int nmid;        // 8-bit merge: nodes deferred from the 128-entry to the 256-entry pass
 };
 
 // How the screened score relates to the squared distance (for certification).
@@ -76,17 +76,22 @@ cudaError_t launch_rescan(const void* xr, const void* xc, int dtype, int64_t m, 
 cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* cand, const float* cdist, int L, double alpha,
                              double tau, int R, float band, int32_t* fwd, int32_t* fdeg,
-                             Counters* ctr, cudaStream_t s);
+                             Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s);
+// 8-bit rows (integer data spanning <= 255): words per row for d (0: unsupported), conversion.
+int u8_words(int d);
+cudaError_t launch_to_u8(const void* xs, int dtype, int64_t n, int d, int dpad, float vmin, int dw,
+                         uint8_t* U, cudaStream_t s);
 cudaError_t launch_reverse(const int32_t* fwd, const int32_t* fdeg, int64_t n, int R,
                            int32_t* indeg, int64_t* off, int32_t* cursor, int32_t* inl,
                            int64_t* blocksums, Counters* ctr, cudaStream_t s);
 // Phase-3 merge of every node whose merged set fits in shared memory; the others are
-// appended to big_list (count in ctr->nbig) for launch_merge_big.
+// appended to big_list (count in ctr->nbig) for launch_merge_big.  big_list holds 2 n entries
+// (the second half is the 8-bit path's list between its two passes).
 cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                          const int32_t* inl, double alpha, double tau, int R, float band,
                          int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
-                         int32_t* big_list, cudaStream_t s);
+                         int32_t* big_list, const uint8_t* u8, int u8_words, cudaStream_t s);
 // Merge of the listed nodes with per-CTA global scratch of 17 * big_cap bytes (grid CTAs).
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* fwd, const int32_t* fdeg, const int64_t* off,

@@ -124,6 +124,222 @@ CNG_DEV int prune_sweep(const T* __restrict__ Xs, int d, int dpad, int64_t p, co
   return ns;
 }
 
+// ---- register-resident sweep ------------------------------------------------------------------
+// Candidate i belongs to group i % PR_GROUPS, slot i / PR_GROUPS; each lane of the group keeps
+// DL4 16-byte chunks of the vector (float4 index f4_index(g, q)) in registers for the whole
+// sweep, so a pair distance reads nothing but the current S member's slice, which its owner
+// publishes in shared memory.  Slots without a live candidate in the warp are skipped.
+template <typename T>
+CNG_DEV int f4_index(int g, int q) {
+  // float rows: 16-byte chunks g, g + 8, ...; half rows: 16-byte half chunks g, g + 8, ...,
+  // each giving two float4
+  return sizeof(T) == 4 ? g + PR_G * q : 2 * (g + PR_G * (q >> 1)) + (q & 1);
+}
+
+template <typename T, int DL4>
+CNG_DEV void load_slice(const T* __restrict__ row, int g, float4* x) {
+  if (sizeof(T) == 4) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int q = 0; q < DL4; ++q) x[q] = __ldg(r4 + g + PR_G * q);
+  } else {
+    const uint4* r8 = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+    for (int q = 0; q < DL4; q += 2) {
+      const uint4 u = __ldg(r8 + g + PR_G * (q >> 1));
+      x[q] = h8lo(u);
+      x[q + 1] = h8hi(u);
+    }
+  }
+}
+
+// Alg. 2 over ids/dist [0, nv) (nv <= NSLOT * PR_GROUPS, dpad == 32 DL4); returns |S| (in S).
+template <typename T, int NSLOT, int DL4>
+CNG_DEV int prune_sweep_reg(const T* __restrict__ Xs, int d, int dpad, int64_t p,
+                            const int32_t* ids, const float* dist, uint8_t* flags, int32_t* S,
+                            float* vq, int nv, const RuleArgs& ra, unsigned long long& ties) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int g = tid % PR_G, grp = tid / PR_G;
+  float4 xr[NSLOT][DL4];
+#pragma unroll
+  for (int k = 0; k < NSLOT; ++k) {
+    const int i = k * PR_GROUPS + grp;
+    if (i < nv) {
+      load_slice<T, DL4>(Xs + (int64_t)ids[i] * dpad, g, xr[k]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < DL4; ++q) xr[k][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  for (int i = tid; i < nv; i += PR_THREADS) flags[i] = 0;
+  __syncthreads();
+  float4* vq4 = reinterpret_cast<float4*>(vq);
+  int ns = 0, cur = -1;
+  for (;;) {
+    // the next member of S: first candidate after cur not pruned yet (same in every warp)
+    int nxt = nv;
+    for (int b = cur + 1; b < nv; b += 32) {
+      const int t = b + lane;
+      const unsigned bal = __ballot_sync(FULL, t < nv && !flags[t]);
+      if (bal) {
+        nxt = b + __ffs(bal) - 1;
+        break;
+      }
+    }
+    if (nxt >= nv) break;
+    const int32_t v = ids[nxt];
+    if (tid == 0) S[ns] = v;
+    ++ns;
+    cur = nxt;
+    if (ns >= ra.R) break;
+    if (grp == nxt % PR_GROUPS) {
+      const int slot = nxt / PR_GROUPS;
+#pragma unroll
+      for (int k = 0; k < NSLOT; ++k)
+        if (k == slot)
+#pragma unroll
+          for (int q = 0; q < DL4; ++q) vq4[f4_index<T>(g, q)] = xr[k][q];
+    }
+    __syncthreads();
+    float4 vr[DL4];
+#pragma unroll
+    for (int q = 0; q < DL4; ++q) vr[q] = vq4[f4_index<T>(g, q)];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) {
+      const int w = k * PR_GROUPS + grp;
+      const bool live = w > cur && w < nv && !flags[w];
+      if (!__any_sync(FULL, live)) continue;
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < DL4; ++q) {
+        if (q & 1)
+          acc4(xr[k][q], vr[q], s1);
+        else
+          acc4(xr[k][q], vr[q], s0);
+      }
+      const float s = group_reduce<PR_G>(s0 + s1);
+      if (live && g == 0) {
+        const float Dwv = sqrtf(s);
+        const float lhs = dist[w];
+        const float rhs = ra.alpha32 * Dwv + ra.t32;
+        bool pr;
+        if (near_tie(lhs, rhs, ra.band)) {
+          const T* xw = Xs + (int64_t)ids[w] * dpad;
+          const double Dpw = canon_dist(Xs + p * dpad, xw, d);
+          const double Dwv64 = canon_dist(xw, Xs + (int64_t)v * dpad, d);
+          pr = rule64(Dpw, Dwv64, ra.alpha64, ra.t64);
+          ++ties;
+        } else {
+          pr = lhs > rhs;
+        }
+        if (pr) flags[w] = 1;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  return ns;
+}
+
+// ---- 8-bit integer sweep --------------------------------------------------------------------
+// For integer data whose coordinates span at most 255 (and d * span^2 < 2^24), the rows are
+// kept as bytes u = x - min(x).  D(w,v)^2 = |u_w|^2 + |u_v|^2 - 2 <u_w, u_v> is then computed
+// exactly in 32-bit integers (dp4a), so the FP32 D = sqrtf(D^2) equals the one of the direct
+// FP32 difference form bit for bit (that sum is exact too), and every rule decision is the same.
+// One candidate per thread (nv <= blockDim.x), its row in DW registers.  One barrier per member
+// of S: every warp publishes its live mask and the row of its first live candidate (buffers
+// alternate between steps), so after the barrier all threads know the next member and its row.
+template <int DW>
+struct U8Slot {
+  uint4 row[DW / 4];
+  uint32_t nrm, pad[3];
+};
+
+template <typename T, int DW>
+CNG_DEV int prune_sweep_u8(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int d, int dpad,
+                           int64_t p, const int32_t* ids, const float* dist, int32_t* S,
+                           U8Slot<DW>* slots /* [2][warps] */, unsigned* masks /* [2][warps] */,
+                           int nv, const RuleArgs& ra, unsigned long long& ties) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  uint4 wv[DW / 4];
+  uint32_t nrm = 0;
+  const bool have = tid < nv;
+  float mydist = 0.f;
+  int32_t myid = 0;
+  if (have) {
+    myid = ids[tid];
+    mydist = dist[tid];
+    const uint4* r = reinterpret_cast<const uint4*>(U + (int64_t)myid * (DW * 4));
+#pragma unroll
+    for (int q = 0; q < DW / 4; ++q) {
+      wv[q] = __ldg(r + q);
+      nrm = __dp4a(wv[q].x, wv[q].x, nrm);
+      nrm = __dp4a(wv[q].y, wv[q].y, nrm);
+      nrm = __dp4a(wv[q].z, wv[q].z, nrm);
+      nrm = __dp4a(wv[q].w, wv[q].w, nrm);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < DW / 4; ++q) wv[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  bool alive = have;
+  int ns = 0, cur = -1, par = 0;
+  for (;;) {
+    const unsigned m = __ballot_sync(FULL, alive && tid > cur);
+    if (m && lane == __ffs(m) - 1) {
+      U8Slot<DW>& sl = slots[par * nwarps + warp];
+#pragma unroll
+      for (int q = 0; q < DW / 4; ++q) sl.row[q] = wv[q];
+      sl.nrm = nrm;
+    }
+    if (lane == 0) masks[par * nwarps + warp] = m;
+    __syncthreads();
+    int nxt = -1;
+    for (int w = 0; w < nwarps; ++w) {
+      const unsigned mm = masks[par * nwarps + w];
+      if (mm) {
+        nxt = w * 32 + __ffs(mm) - 1;
+        break;
+      }
+    }
+    if (nxt < 0) break;
+    const int32_t v = ids[nxt];
+    if (tid == 0) S[ns] = v;
+    ++ns;
+    cur = nxt;
+    if (ns >= ra.R) break;
+    if (alive && tid > cur) {
+      const U8Slot<DW>& sv = slots[par * nwarps + (nxt >> 5)];
+      uint32_t dot = 0;
+#pragma unroll
+      for (int q = 0; q < DW / 4; ++q) {
+        const uint4 y = sv.row[q];
+        dot = __dp4a(wv[q].x, y.x, dot);
+        dot = __dp4a(wv[q].y, y.y, dot);
+        dot = __dp4a(wv[q].z, y.z, dot);
+        dot = __dp4a(wv[q].w, y.w, dot);
+      }
+      const int32_t d2 = (int32_t)(nrm + sv.nrm) - 2 * (int32_t)dot;
+      const float Dwv = sqrtf((float)d2);
+      const float rhs = ra.alpha32 * Dwv + ra.t32;
+      bool pr;
+      if (near_tie(mydist, rhs, ra.band)) {
+        const T* xw = Xs + (int64_t)myid * dpad;
+        const double Dpw = canon_dist(Xs + p * dpad, xw, d);
+        const double Dwv64 = canon_dist(xw, Xs + (int64_t)v * dpad, d);
+        pr = rule64(Dpw, Dwv64, ra.alpha64, ra.t64);
+        ++ties;
+      } else {
+        pr = mydist > rhs;
+      }
+      if (pr) alive = false;
+    }
+    par ^= 1;
+  }
+  __syncthreads();
+  return ns;
+}
+
 template <typename T>
 CNG_DEV void stage_vectors(const T* __restrict__ Xs, int dpad, const int32_t* ids, int nstage,
                            float* stage) {
@@ -186,10 +402,125 @@ prune_fwd_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
   (void)edges;
 }
 
+template <typename T, int NSLOT, int DL4>
+__global__ void __launch_bounds__(PR_THREADS)
+prune_fwd_reg_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
+                     const int32_t* __restrict__ cand, const float* __restrict__ cdist, int L,
+                     RuleArgs ra, int32_t* __restrict__ fwd, int32_t* __restrict__ fdeg,
+                     Counters* ctr) {
+  __shared__ int32_t s_ids[NSLOT * PR_GROUPS];
+  __shared__ float s_dist[NSLOT * PR_GROUPS];
+  __shared__ uint8_t s_flags[NSLOT * PR_GROUPS];
+  __shared__ int32_t s_S[64];
+  __shared__ __align__(16) float s_vq[DL4 * 32 * 4];
+  unsigned long long ties = 0;
+  for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
+    for (int i = threadIdx.x; i < L; i += PR_THREADS) {
+      s_ids[i] = cand[p * L + i];
+      s_dist[i] = cdist[p * L + i];
+    }
+    __syncthreads();
+    const int ns = prune_sweep_reg<T, NSLOT, DL4>(Xs, d, dpad, p, s_ids, s_dist, s_flags, s_S, s_vq,
+                                                  L, ra, ties);
+    for (int i = threadIdx.x; i < ra.R; i += PR_THREADS) fwd[p * ra.R + i] = i < ns ? s_S[i] : -1;
+    if (threadIdx.x == 0) fdeg[p] = ns;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
+  if ((threadIdx.x & 31) == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+}
+
+template <typename T, int DW>
+__global__ void __launch_bounds__(256)
+prune_fwd_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int64_t n, int d,
+                    int dpad, const int32_t* __restrict__ cand, const float* __restrict__ cdist,
+                    int L, RuleArgs ra, int32_t* __restrict__ fwd, int32_t* __restrict__ fdeg,
+                    Counters* ctr) {
+  __shared__ int32_t s_ids[256];
+  __shared__ float s_dist[256];
+  __shared__ int32_t s_S[64];
+  __shared__ U8Slot<DW> s_slots[2 * 8];
+  __shared__ unsigned s_masks[2 * 8];
+  unsigned long long ties = 0;
+  for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      s_ids[i] = cand[p * L + i];
+      s_dist[i] = cdist[p * L + i];
+    }
+    __syncthreads();
+    const int ns = prune_sweep_u8<T, DW>(U, Xs, d, dpad, p, s_ids, s_dist, s_S, s_slots, s_masks, L,
+                                         ra, ties);
+    for (int i = threadIdx.x; i < ra.R; i += blockDim.x) fwd[p * ra.R + i] = i < ns ? s_S[i] : -1;
+    if (threadIdx.x == 0) fdeg[p] = ns;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
+  if ((threadIdx.x & 31) == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+}
+
+template <typename T>
+static bool launch_prune_u8(const uint8_t* U, int dw, const T* xs, int64_t n, int d, int dpad,
+                            const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
+                            int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s) {
+  if (!U || L > 256) return false;
+  const int threads = (L + 31) / 32 * 32;
+  const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * (2048 / threads));
+#define CNG_PU(DW)                                                                                 \
+  if (dw == DW) {                                                                                  \
+    count_launch();                                                                                \
+    prune_fwd_u8_kernel<T, DW><<<grid, threads, 0, s>>>(U, xs, n, d, dpad, cand, cdist, L, ra, fwd, \
+                                                        fdeg, ctr);                                \
+    return true;                                                                                   \
+  }
+  CNG_PU(8)
+  CNG_PU(16)
+  CNG_PU(24)
+  CNG_PU(32)
+#undef CNG_PU
+  return false;
+}
+
+// Register-resident variants: (slots, 16-byte chunks per lane) with slots * chunks <= 18.
+template <typename T>
+static bool launch_prune_reg(const T* xs, int64_t n, int d, int dpad, const int32_t* cand,
+                             const float* cdist, int L, const RuleArgs& ra, int32_t* fwd,
+                             int32_t* fdeg, Counters* ctr, cudaStream_t s) {
+  const int dl4 = dpad / 32, ns = (L + PR_GROUPS - 1) / PR_GROUPS;
+  const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 16);
+#define CNG_PR(NS, DL)                                                                          \
+  if (dl4 == DL && ns <= NS) {                                                                  \
+    count_launch();                                                                             \
+    prune_fwd_reg_kernel<T, NS, DL><<<grid, PR_THREADS, 0, s>>>(xs, n, d, dpad, cand, cdist, L, \
+                                                                ra, fwd, fdeg, ctr);            \
+    return true;                                                                                \
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (dpad % 32 == 0) {
+      CNG_PR(4, 4)
+      CNG_PR(4, 3)
+      CNG_PR(6, 3)
+      CNG_PR(4, 2)
+      CNG_PR(8, 2)
+      CNG_PR(4, 1)
+      CNG_PR(8, 1)
+    }
+  } else {
+    if (dpad % 64 == 0) {
+      CNG_PR(4, 4)
+      CNG_PR(4, 2)
+      CNG_PR(8, 2)
+    }
+  }
+#undef CNG_PR
+  return false;
+}
+
 cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* cand, const float* cdist, int L, double alpha,
                              double tau, int R, float band, int32_t* fwd, int32_t* fdeg,
-                             Counters* ctr, cudaStream_t s) {
+                             Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s) {
   RuleArgs ra;
   ra.alpha64 = alpha;
   ra.t64 = (alpha + 1.0) * tau;
@@ -198,6 +529,16 @@ cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dp
   ra.band = band;
   ra.R = R;
   ra.rs = R;
+  if (dtype == CNG_F32 ? launch_prune_u8(u8, u8_words, (const float*)xs, n, d, dpad, cand, cdist, L,
+                                         ra, fwd, fdeg, ctr, s)
+                       : launch_prune_u8(u8, u8_words, (const __half*)xs, n, d, dpad, cand, cdist,
+                                         L, ra, fwd, fdeg, ctr, s))
+    return cudaGetLastError();
+  if (dtype == CNG_F32 ? launch_prune_reg((const float*)xs, n, d, dpad, cand, cdist, L, ra, fwd,
+                                          fdeg, ctr, s)
+                       : launch_prune_reg((const __half*)xs, n, d, dpad, cand, cdist, L, ra, fwd,
+                                          fdeg, ctr, s))
+    return cudaGetLastError();
   size_t sh = dpad * 4 + 2 * (((size_t)L * 4 + 15) / 16) * 16 + 256 + ((L + 15) / 16) * 16;
   if ((size_t)L * dpad * 4 <= PR_STAGE_BYTES) sh += (size_t)L * dpad * 4;
   int per_sm = sh > 110 * 1024 ? 1 : 2;
@@ -213,6 +554,37 @@ cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dp
     prune_fwd_kernel<__half><<<grid, PR_THREADS, sh, s>>>((const __half*)xs, n, d, dpad, cand,
                                                           cdist, L, ra, fwd, fdeg, ctr);
   }
+  return cudaGetLastError();
+}
+
+// ---- 8-bit rows for integer data ----------------------------------------------------------------
+// U[i][c] = x[i][c] - vmin (c < d), 0 in the padding up to 4 dw bytes; requires integer values
+// in [vmin, vmin + 255].
+template <typename T>
+__global__ void to_u8_kernel(const T* __restrict__ xs, int64_t n, int d, int dpad, float vmin,
+                             int dw, uint8_t* __restrict__ U) {
+  const int64_t total = n * (int64_t)(dw * 4);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / (dw * 4);
+    const int c = (int)(e - i * (dw * 4));
+    U[e] = c < d ? (uint8_t)(int)(to_f(xs[i * dpad + c]) - vmin) : (uint8_t)0;
+  }
+}
+
+int u8_words(int d) {
+  const int w = (d + 15) / 16 * 4;
+  return (w == 8 || w == 16 || w == 24 || w == 32) ? w : 0;
+}
+
+cudaError_t launch_to_u8(const void* xs, int dtype, int64_t n, int d, int dpad, float vmin, int dw,
+                         uint8_t* U, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((n * dw * 4 + 255) / 256, (int64_t)num_sms() * 16);
+  count_launch();
+  if (dtype == CNG_F32)
+    to_u8_kernel<float><<<grid, 256, 0, s>>>((const float*)xs, n, d, dpad, vmin, dw, U);
+  else
+    to_u8_kernel<__half><<<grid, 256, 0, s>>>((const __half*)xs, n, d, dpad, vmin, dw, U);
   return cudaGetLastError();
 }
 
@@ -355,7 +727,7 @@ struct MergeArrays {
 // One node of phase 3: V'(p) = fwd(p) U in(p) without duplicates, sorted by (D(p,.), id) --
 // FP32 keys, near-tied neighbours re-ordered by the canonical FP64 distance -- then kept as is
 // if |V'| <= R, else pruned once with the rule (Sec. 4.3, lazy pruning).  Returns |adj(p)|.
-template <typename T>
+template <typename T, int NS, int DL>
 CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
                        const int32_t* __restrict__ fwd, int nf, const int32_t* __restrict__ inl,
                        int64_t i0, int nin, const RuleArgs& ra, int exact, const MergeArrays& ar,
@@ -456,6 +828,10 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
     na = nv;
     for (int i = tid; i < nv; i += PR_THREADS) sm.S[i] = ar.ids[i];
     __syncthreads();
+  } else if (NS > 0 && nv <= NS * PR_GROUPS) {
+    na = prune_sweep_reg<T, (NS > 0 ? NS : 1), (DL > 0 ? DL : 1)>(Xs, d, dpad, p, ar.ids, ar.dist,
+                                                                  ar.flags, sm.S, sm.vq, nv, ra, ties);
+    ++repruned;
   } else {
     const int nstage = min(nv, stage_cap);
     stage_vectors(Xs, dpad, ar.ids, nstage, sm.stage);
@@ -469,7 +845,7 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
 }
 
 // Shared layout: vq, pq [dpad] | S [64] | d64 [PR_RUN] | rid [PR_RUN] | arrays | stage
-template <typename T, bool BIG>
+template <typename T, bool BIG, int NS, int DL>
 __global__ void __launch_bounds__(PR_THREADS)
 merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t* __restrict__ fwd,
              const int32_t* __restrict__ fdeg, const int64_t* __restrict__ off,
@@ -515,7 +891,7 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
       continue;
     }
     maxlist = max(maxlist, (unsigned long long)(nf + nin));
-    int na = merge_node(Xs, d, dpad, p, fwd + p * ra.R, nf, inl, i0, nin, ra, exact, ar, sm, d64,
+    int na = merge_node<T, NS, DL>(Xs, d, dpad, p, fwd + p * ra.R, nf, inl, i0, nin, ra, exact, ar, sm, d64,
                         rid, stage_cap, &s_nv, adj + p * ra.rs, ctr, ties, ordties, repruned);
     if (tid == 0) deg[p] = na;
     edges += na;
@@ -531,8 +907,115 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
   }
 }
 
-template <typename T, bool BIG>
-static cudaError_t merge_t(const void* xs, int64_t n, int d, int dpad, const int32_t* fwd,
+// Phase 3 from 8-bit integer rows: merged sets of up to CAP entries per CTA of CAP threads, one
+// entry per thread -- exact integer D(p,.)^2, (D, id) order by ranks, then the 8-bit sweep.
+// Pass 1 (CAP 128) takes every node and defers larger sets to mid_list; pass 2 (CAP 256) takes
+// mid_list and defers larger sets to big_list for the global-scratch pass.
+template <typename T, int DW, int CAP>
+__global__ void __launch_bounds__(CAP)
+merge_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int64_t n, int d, int dpad,
+                const int32_t* __restrict__ fwd, const int32_t* __restrict__ fdeg,
+                const int64_t* __restrict__ off, const int32_t* __restrict__ inl, RuleArgs ra,
+                int32_t* __restrict__ adj, int32_t* __restrict__ deg, Counters* ctr,
+                int32_t* __restrict__ mid_list, int32_t* __restrict__ big_list) {
+  constexpr bool SECOND = CAP > 128;
+  __shared__ int32_t s_raw[CAP];
+  __shared__ uint64_t s_key[CAP];
+  __shared__ int32_t s_ids[CAP];
+  __shared__ float s_dist[CAP];
+  __shared__ int32_t s_S[64];
+  __shared__ U8Slot<DW> s_slots[2 * (CAP / 32)];
+  __shared__ uint4 s_p[DW / 4];
+  __shared__ unsigned s_masks[2 * (CAP / 32)];
+  __shared__ int s_nv;
+  const int tid = threadIdx.x;
+  unsigned long long ties = 0, repruned = 0, edges = 0, maxlist = 0;
+  const int64_t count = SECOND ? (int64_t)ctr->nmid : n;
+  for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
+    const int64_t p = SECOND ? (int64_t)mid_list[q] : q;
+    const int nf = fdeg[p];
+    const int64_t i0 = off[p];
+    const int nin = (int)(off[p + 1] - i0);
+    if (nf + nin > CAP) {  // uniform: deferred to the next pass
+      if (tid == 0) {
+        if (SECOND)
+          big_list[atomicAdd(&ctr->nbig, 1)] = (int32_t)p;
+        else
+          mid_list[atomicAdd(&ctr->nmid, 1)] = (int32_t)p;
+      }
+      continue;
+    }
+    maxlist = max(maxlist, (unsigned long long)(nf + nin));
+    const int32_t* fp = fwd + p * ra.R;
+    if (tid < nf) s_raw[tid] = fp[tid];
+    if (tid == 0) s_nv = nf;
+    if (tid < DW / 4) s_p[tid] = __ldg(reinterpret_cast<const uint4*>(U + p * (DW * 4)) + tid);
+    __syncthreads();
+    if (tid < nin) {  // in-neighbours not already in fwd(p)
+      const int32_t u = inl[i0 + tid];
+      bool dup = false;
+      for (int j = 0; j < nf && !dup; ++j) dup = fp[j] == u;
+      if (!dup) s_raw[atomicAdd(&s_nv, 1)] = u;
+    }
+    __syncthreads();
+    const int nv = s_nv;
+    // exact D(p, u)^2 and the (D, id) key of entry tid
+    uint32_t d2 = 0;
+    int32_t u = 0;
+    if (tid < nv) {
+      u = s_raw[tid];
+      const uint4* r = reinterpret_cast<const uint4*>(U + (int64_t)u * (DW * 4));
+      uint32_t nu = 0, np = 0, dot = 0;
+#pragma unroll
+      for (int q = 0; q < DW / 4; ++q) {
+        const uint4 a = __ldg(r + q), b = s_p[q];
+        nu = __dp4a(a.x, a.x, nu); nu = __dp4a(a.y, a.y, nu);
+        nu = __dp4a(a.z, a.z, nu); nu = __dp4a(a.w, a.w, nu);
+        np = __dp4a(b.x, b.x, np); np = __dp4a(b.y, b.y, np);
+        np = __dp4a(b.z, b.z, np); np = __dp4a(b.w, b.w, np);
+        dot = __dp4a(a.x, b.x, dot); dot = __dp4a(a.y, b.y, dot);
+        dot = __dp4a(a.z, b.z, dot); dot = __dp4a(a.w, b.w, dot);
+      }
+      d2 = nu + np - 2u * dot;
+      s_key[tid] = pack_key((float)d2, u);
+    }
+    __syncthreads();
+    if (tid < nv) {  // rank among the distinct keys
+      const uint64_t k = s_key[tid];
+      int rank = 0;
+      for (int j = 0; j < nv; ++j) rank += s_key[j] < k;
+      s_ids[rank] = u;
+      s_dist[rank] = sqrtf((float)d2);
+    }
+    __syncthreads();
+    int na;
+    if (nv <= ra.R) {
+      na = nv;
+      if (tid < nv) s_S[tid] = s_ids[tid];
+      __syncthreads();
+    } else {
+      na = prune_sweep_u8<T, DW>(U, Xs, d, dpad, p, s_ids, s_dist, s_S, s_slots, s_masks, nv, ra,
+                                 ties);
+      ++repruned;
+    }
+    int32_t* row = adj + p * ra.rs;
+    for (int i = tid; i < ra.rs; i += blockDim.x) row[i] = i < na ? s_S[i] : -1;
+    if (tid == 0) deg[p] = na;
+    edges += na;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
+  if ((tid & 31) == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+  if (tid == 0) {
+    atomicAdd(&ctr->merge_repruned, repruned);
+    atomicAdd(&ctr->edges, edges);
+    atomicMax(&ctr->merge_max_list, maxlist);
+  }
+}
+
+template <typename T, bool BIG, int NS, int DL>
+static cudaError_t merge_t2(const void* xs, int64_t n, int d, int dpad, const int32_t* fwd,
                            const int32_t* fdeg, const int64_t* off, const int32_t* inl,
                            const RuleArgs& ra, int exact, int32_t* adj, int32_t* deg,
                            Counters* ctr, int32_t* big_list, unsigned char* big_scratch,
@@ -540,12 +1023,62 @@ static cudaError_t merge_t(const void* xs, int64_t n, int d, int dpad, const int
   const int stage_cap = PR_MERGE_STAGE_BYTES / (dpad * 4);
   size_t sh = 2 * (size_t)dpad * 4 + 256 + PR_RUN * 12 + (BIG ? 0 : (size_t)PR_VMAX * 17) +
               (size_t)stage_cap * dpad * 4 + 16;
-  cudaFuncSetAttribute(merge_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  cudaFuncSetAttribute(merge_kernel<T, BIG, NS, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sh);
   count_launch();
-  merge_kernel<T, BIG><<<grid, PR_THREADS, sh, s>>>((const T*)xs, n, d, dpad, fwd, fdeg, off, inl,
-                                                    ra, exact, adj, deg, ctr, big_list,
-                                                    big_scratch, big_cap);
+  merge_kernel<T, BIG, NS, DL><<<grid, PR_THREADS, sh, s>>>((const T*)xs, n, d, dpad, fwd, fdeg, off,
+                                                            inl, ra, exact, adj, deg, ctr, big_list,
+                                                            big_scratch, big_cap);
   return cudaGetLastError();
+}
+
+// Merged lists of up to 128 entries are pruned from registers when 16-byte chunks per lane
+// (dpad / 32) is 1..4 (even for half rows); longer lists and other widths use staged vectors.
+template <typename T, bool BIG>
+static cudaError_t merge_t(const uint8_t* U, int dw, const void* xs, int64_t n, int d, int dpad,
+                           const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
+                           const int32_t* inl, const RuleArgs& ra, int exact, int32_t* adj,
+                           int32_t* deg, Counters* ctr, int32_t* big_list,
+                           unsigned char* big_scratch, int big_cap, int grid, cudaStream_t s) {
+  const int dl4 = dpad % 32 == 0 ? dpad / 32 : 0;
+  constexpr bool half = sizeof(T) == 2;
+  if constexpr (!BIG) {
+    if (U) {  // 8-bit integer rows: two passes (the second reads its node count on the device)
+      const int g1 = (int)std::min<int64_t>(n, (int64_t)num_sms() * 16);
+      const int g2 = num_sms() * 4;
+      int32_t* mid_list = big_list + n;
+#define CNG_MU(DWV)                                                                                \
+  if (dw == DWV) {                                                                                 \
+    count_launch();                                                                                \
+    merge_u8_kernel<T, DWV, 128><<<g1, 128, 0, s>>>(U, (const T*)xs, n, d, dpad, fwd, fdeg, off,    \
+                                                    inl, ra, adj, deg, ctr, mid_list, big_list);   \
+    count_launch();                                                                                \
+    merge_u8_kernel<T, DWV, 256><<<g2, 256, 0, s>>>(U, (const T*)xs, n, d, dpad, fwd, fdeg, off,    \
+                                                    inl, ra, adj, deg, ctr, mid_list, big_list);   \
+    return cudaGetLastError();                                                                     \
+  }
+      CNG_MU(8)
+      CNG_MU(16)
+      CNG_MU(24)
+      CNG_MU(32)
+#undef CNG_MU
+    }
+  }
+#define CNG_MG(DLV)                                                                                \
+  if constexpr (!half || DLV % 2 == 0) {                                                           \
+    if (dl4 == DLV)                                                                                \
+      return merge_t2<T, BIG, 4, DLV>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg,    \
+                                      ctr, big_list, big_scratch, big_cap, grid, s);               \
+  }
+  if constexpr (!BIG) {
+    CNG_MG(1)
+    CNG_MG(2)
+    CNG_MG(3)
+    CNG_MG(4)
+  }
+#undef CNG_MG
+  return merge_t2<T, BIG, 0, 0>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,
+                                big_list, big_scratch, big_cap, grid, s);
 }
 
 static RuleArgs rule_args(double alpha, double tau, int R, float band, int rs) {
@@ -564,14 +1097,14 @@ cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                          const int32_t* inl, double alpha, double tau, int R, float band,
                          int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
-                         int32_t* big_list, cudaStream_t s) {
+                         int32_t* big_list, const uint8_t* u8, int u8_words, cudaStream_t s) {
   RuleArgs ra = rule_args(alpha, tau, R, band, rs);
   int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
   return dtype == CNG_F32
-             ? merge_t<float, false>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,
-                                     big_list, nullptr, 0, grid, s)
-             : merge_t<__half, false>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg,
-                                      ctr, big_list, nullptr, 0, grid, s);
+             ? merge_t<float, false>(u8, u8_words, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
+                                     adj, deg, ctr, big_list, nullptr, 0, grid, s)
+             : merge_t<__half, false>(u8, u8_words, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
+                                      adj, deg, ctr, big_list, nullptr, 0, grid, s);
 }
 
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
@@ -583,10 +1116,10 @@ cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dp
   RuleArgs ra = rule_args(alpha, tau, R, band, rs);
   (void)nbig;
   return dtype == CNG_F32
-             ? merge_t<float, true>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,
-                                    big_list, scratch, big_cap, grid, s)
-             : merge_t<__half, true>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,
-                                     big_list, scratch, big_cap, grid, s);
+             ? merge_t<float, true>(nullptr, 0, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj,
+                                    deg, ctr, big_list, scratch, big_cap, grid, s)
+             : merge_t<__half, true>(nullptr, 0, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
+                                     adj, deg, ctr, big_list, scratch, big_cap, grid, s);
 }
 
 }  // namespace cng
