@@ -22,6 +22,14 @@ extern "C" {
 cng_status cngx_tc_scores(const float *rows_dev, int64_t m, const float *cols_dev, int64_t n,
                           int32_t d, float *scores_dev, void *stream);
 
+/*
+ * cngx_tc_scores_f16 -- as cngx_tc_scores with the operands the build uses for f32 data:
+ * x_b = fp16(scale * x), y_b = fp16(scale * y) (scale a power of two, else CNG_E_INVAL), so the
+ * scores are in units of scale^2.
+ */
+cng_status cngx_tc_scores_f16(const float *rows_dev, int64_t m, const float *cols_dev, int64_t n,
+                              int32_t d, float scale, float *scores_dev, void *stream);
+
 /* Number of CUDA kernel launches this library has issued since it was loaded (each launch
  * site counts once per launch). */
 long long cngx_launches(void);

@@ -187,10 +187,12 @@ struct KnnInputs {
   const void* tc_rows;  // [m][kpad] bf16 / fp16
   const void* tc_cols;  // [n][kpad]
   int kpad;
+  int tc_fp16;          // operands are FP16 (else BF16)
   const float* nb_rows;  // ||x_b||^2 of rows
   const float* nb_cols;  // ||y_b||^2 of columns
   const float* rb_rows;
   float rbmax, normmax;
+  float scale2;  // operands are scale * x, scores in units of scale^2
   // locality order of the tensor-core operands (tc_rows / tc_cols / nb_cols hold positions)
   const int32_t* perm;
   int wave_start;
@@ -213,7 +215,7 @@ static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist
     ta.m = in.m;
     ta.n = in.n;
     ta.kpad = in.kpad;
-    ta.fp16 = in.dtype == CNG_F16;
+    ta.fp16 = in.tc_fp16;
     ta.nb = in.nb_cols;
     ta.Lp = in.Lp;
     ta.self_excl = in.self_excl;
@@ -233,6 +235,7 @@ static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist
     sm.rbmax = in.rbmax;
     sm.normmax = in.normmax;
     sm.acc_err = (float)(in.kpad + 8) * 1.1920929e-7f;  // K terms, 2^-23 per add
+    sm.scale2 = in.scale2;
   } else {
     int cpl = 0;
     for (int c : {8, 12, 16, 20})
@@ -285,14 +288,41 @@ struct Prepared {
   PrepStats st{};
 };
 
+// Tensor-core operand scale: 1 for integer data with |x| <= 2048 (exact in FP16) and for FP16
+// input; otherwise the power of two that puts max |s x| in (4096, 8192], which keeps the FP16
+// operands clear of overflow and of the subnormal range (relative rounding 2^-11).
+static cng_status operand_scale(const void* const* pts, const int64_t* ns, int count, int dtype,
+                                int d, float* scale, cudaStream_t s) {
+  *scale = 1.f;
+  if (dtype != CNG_F32) return CNG_OK;
+  DevPool pool;
+  uint32_t* dev;
+  CK(pool.alloc(&dev, 2));
+  CK(cudaMemsetAsync(dev, 0, 2 * sizeof(uint32_t), s));
+  for (int i = 0; i < count; ++i)
+    if (ns[i] > 0) CK(launch_absmax(pts[i], dtype, ns[i], d, dev, s));
+  uint32_t host[2];
+  CK(cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float amax;
+  memcpy(&amax, &host[0], 4);
+  if (!host[1] && amax <= 2048.f) return CNG_OK;
+  if (!(amax > 0.f) || !std::isfinite(amax)) return CNG_OK;
+  const int e = (int)std::ceil(std::log2((double)amax));
+  *scale = (float)std::ldexp(1.0, 13 - e);
+  return CNG_OK;
+}
+
+// fp16ops: tensor-core operands in FP16 (scaled by `scale`); else BF16 (unscaled).
 static cng_status prepare(DevPool& pool, const void* pts_dev, int dtype, int64_t n, int d,
-                          int dpad, int screen, int kpad, Prepared* out, cudaStream_t s) {
+                          int dpad, int screen, int kpad, Prepared* out, cudaStream_t s,
+                          int fp16ops = 1, float scale = 1.f) {
   size_t el = dtype == CNG_F32 ? 4 : 2;
   CK(pool.alloc(reinterpret_cast<char**>(&out->xs), (size_t)n * dpad * el));
   __nv_bfloat16* xb_bf = nullptr;
   __half* xb_h = nullptr;
   if (screen == CNG_SCREEN_TC) {
-    if (dtype == CNG_F32) {
+    if (dtype == CNG_F32 && !fp16ops) {
       CK(pool.alloc(&xb_bf, (size_t)n * kpad));
       out->tc = xb_bf;
     } else {
@@ -308,7 +338,8 @@ static cng_status prepare(DevPool& pool, const void* pts_dev, int dtype, int64_t
   PrepStats init{};
   init.vmin_key = 0xffffffffu;
   CK(cudaMemcpyAsync(dst, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  CK(launch_prep(pts_dev, dtype, n, d, dpad, out->xs, xb_bf, xb_h, kpad, out->nb, out->rb, dst, s));
+  CK(launch_prep(pts_dev, dtype, n, d, dpad, out->xs, xb_bf, xb_h, kpad, out->nb, out->rb,
+                 dtype == CNG_F32 ? scale : 1.f, dst, s));
   CK(cudaMemcpyAsync(&out->st, dst, sizeof(PrepStats), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return CNG_OK;
@@ -378,7 +409,7 @@ static int exact_int(const PrepStats& st, int d, int screen) {
   double span = hi - lo;
   if ((double)d * span * span >= 16777216.0) return 0;
   if (screen == CNG_SCREEN_TC) {
-    if (std::max(std::fabs(lo), std::fabs(hi)) > 256.0) return 0;
+    if (std::max(std::fabs(lo), std::fabs(hi)) > 2048.0) return 0;  // exact in FP16
     double nm = bits_to_float(st.normmax_bits);
     if (nm * nm >= 8388608.0) return 0;
   }
@@ -430,7 +461,14 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   const int dpad = round_up(d, dtype == CNG_F32 ? 32 : 64);
   const int kpad = round_up(d, 64);
   Prepared pr;
-  cng_status st = prepare(pool, pts, dtype, n, d, dpad, screen, kpad, &pr, s);
+  float scale = 1.f;
+  if (screen == CNG_SCREEN_TC) {
+    const void* pl[1] = {pts};
+    const int64_t nl[1] = {n};
+    cng_status ss = operand_scale(pl, nl, 1, dtype, d, &scale, s);
+    if (ss != CNG_OK) return ss;
+  }
+  cng_status st = prepare(pool, pts, dtype, n, d, dpad, screen, kpad, &pr, s, 1, scale);
   if (st != CNG_OK) return st;
   if (P.metric == CNG_IP_AS_L2 && bits_to_float(pr.st.unitdev_bits) > 1e-3f)
     return fail(CNG_E_INVAL, "CNG_IP_AS_L2 requires unit-norm rows (| ||x|| - 1 | <= 1e-3)");
@@ -475,6 +513,8 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   ki.tc_rows = pr.tc;
   ki.tc_cols = pr.tc;
   ki.kpad = kpad;
+  ki.tc_fp16 = 1;
+  ki.scale2 = scale * scale;
   ki.nb_rows = pr.nb;
   ki.nb_cols = pr.nb;
   ki.rb_rows = pr.rb;
@@ -873,10 +913,17 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
   DevPool pool;
   const int dpad = round_up(d, 32), kpad = round_up(d, 64);
   Prepared pb, prw;
-  cng_status st = prepare(pool, base, CNG_F32, n, d, dpad, screen, kpad, &pb, s);
+  float scale = 1.f;
+  if (screen == CNG_SCREEN_TC) {  // one scale for rows and columns
+    const void* pl[2] = {base, rows};
+    const int64_t nl[2] = {n, self ? 0 : m};
+    cng_status ss = operand_scale(pl, nl, 2, CNG_F32, d, &scale, s);
+    if (ss != CNG_OK) return ss;
+  }
+  cng_status st = prepare(pool, base, CNG_F32, n, d, dpad, screen, kpad, &pb, s, 1, scale);
   if (st != CNG_OK) return st;
   if (!self) {
-    st = prepare(pool, rows, CNG_F32, m, d, dpad, screen, kpad, &prw, s);
+    st = prepare(pool, rows, CNG_F32, m, d, dpad, screen, kpad, &prw, s, 1, scale);
     if (st != CNG_OK) return st;
   }
   Prepared& pr = self ? pb : prw;
@@ -909,6 +956,8 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
   ki.tc_rows = pr.tc;
   ki.tc_cols = pb.tc;
   ki.kpad = kpad;
+  ki.tc_fp16 = 1;
+  ki.scale2 = scale * scale;
   ki.nb_rows = pr.nb;
   ki.nb_cols = pb.nb;
   ki.rb_rows = pr.rb;
@@ -940,18 +989,20 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
   return CNG_OK;
 }
 
-extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* cols, int64_t n,
-                                     int32_t d, float* scores, void* stream) {
+static cng_status tc_scores(const float* rows, int64_t m, const float* cols, int64_t n, int32_t d,
+                            int fp16, float scale, float* scores, void* stream) {
   if (!rows || !cols || !scores) return fail(CNG_E_INVAL, "pointers must be non-NULL");
   if (m < 1 || n < 1 || d < 1 || !tc_screen_supported(d, false))
     return fail(CNG_E_INVAL, "need m, n >= 1 and 1 <= d <= 192");
+  if (!(scale > 0.f) || std::ilogb(scale) != std::log2(scale))
+    return fail(CNG_E_INVAL, "scale must be a power of two");
   cudaStream_t s = (cudaStream_t)stream;
   DevPool pool;
   const int dpad = round_up(d, 32), kpad = round_up(d, 64);
   Prepared pr, pc;
-  cng_status st = prepare(pool, rows, CNG_F32, m, d, dpad, CNG_SCREEN_TC, kpad, &pr, s);
+  cng_status st = prepare(pool, rows, CNG_F32, m, d, dpad, CNG_SCREEN_TC, kpad, &pr, s, fp16, scale);
   if (st != CNG_OK) return st;
-  st = prepare(pool, cols, CNG_F32, n, d, dpad, CNG_SCREEN_TC, kpad, &pc, s);
+  st = prepare(pool, cols, CNG_F32, n, d, dpad, CNG_SCREEN_TC, kpad, &pc, s, fp16, scale);
   if (st != CNG_OK) return st;
   uint32_t* status;
   CK(pool.alloc(&status, 1));
@@ -962,7 +1013,7 @@ extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* 
   ta.m = m;
   ta.n = n;
   ta.kpad = kpad;
-  ta.fp16 = 0;
+  ta.fp16 = fp16;
   ta.nb = pc.nb;
   ta.Lp = 32;
   ta.self_excl = 0;
@@ -976,6 +1027,16 @@ extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* 
   CK(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return check_status(hs);
+}
+
+extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* cols, int64_t n,
+                                     int32_t d, float* scores, void* stream) {
+  return tc_scores(rows, m, cols, n, d, 0, 1.f, scores, stream);
+}
+
+extern "C" cng_status cngx_tc_scores_f16(const float* rows, int64_t m, const float* cols, int64_t n,
+                                         int32_t d, float scale, float* scores, void* stream) {
+  return tc_scores(rows, m, cols, n, d, 1, scale, scores, stream);
 }
 
 

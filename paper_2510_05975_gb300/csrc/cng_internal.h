@@ -52,11 +52,17 @@ struct ScreenModel {
   float rbmax;       // kind 1: max rb
   float acc_err;     // kind 1: absolute accumulation error bound per unit of (||x||+||y||)^2
   float normmax;     // kind 1: max ||x_b||
+  float scale2;      // kind 1: the operands are x_b ~ s x; scores are in units of s^2 (a power of 4)
 };
 
 // Launchers (each returns cudaError_t of the launch).
+// out[0] = bits of max |x|, out[1] != 0 if some coordinate is not an integer (out pre-zeroed).
+cudaError_t launch_absmax(const void* pts, int dtype, int64_t n, int d, uint32_t* out,
+                          cudaStream_t s);
+// xb_* receive round(scale * x) (scale a power of two); nb, rb are in those units.
 cudaError_t launch_prep(const void* pts, int dtype, int64_t n, int d, int dpad, void* xs,
                         __nv_bfloat16* xb_bf, __half* xb_h, int kpad, float* nb, float* rb,
+                        float scale,
                         PrepStats* st, cudaStream_t s);
 cudaError_t launch_entry(const void* xs, int dtype, int64_t n, int d, int dpad, double* part,
                          double* cen, unsigned long long* best, int32_t* entry, cudaStream_t s);

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const Tin* __restrict__ P, in
                                                    __nv_bfloat16* __restrict__ xb_bf,
                                                    __half* __restrict__ xb_h, int kpad,
                                                    float* __restrict__ nb, float* __restrict__ rb,
-                                                   PrepStats* st) {
+                                                   float scale, PrepStats* st) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -40,17 +40,18 @@ __global__ void __launch_bounds__(256) prep_kernel(const Tin* __restrict__ P, in
       if (c < dpad) xs[row * dpad + c] = (Tst)v;
       if (screen && c < kpad) {
         float fb;
+        const float vs = v * scale;  // exact: scale is a power of two
         if (xb_bf) {
-          __nv_bfloat16 b = __float2bfloat16_rn(v);
+          __nv_bfloat16 b = __float2bfloat16_rn(vs);
           xb_bf[row * kpad + c] = b;
           fb = __bfloat162float(b);
         } else {
-          __half h = __float2half_rn(v);
+          __half h = __float2half_rn(vs);
           xb_h[row * kpad + c] = h;
           fb = __half2float(h);
         }
         snb = fmaf(fb, fb, snb);
-        float e = fb - v;
+        float e = fb - vs;
         srb = fmaf(e, e, srb);
       }
       if (c < d) {
@@ -95,17 +96,51 @@ __global__ void __launch_bounds__(256) prep_kernel(const Tin* __restrict__ P, in
 
 cudaError_t launch_prep(const void* pts, int dtype, int64_t n, int d, int dpad, void* xs,
                         __nv_bfloat16* xb_bf, __half* xb_h, int kpad, float* nb, float* rb,
-                        PrepStats* st, cudaStream_t s) {
+                        float scale, PrepStats* st, cudaStream_t s) {
   int64_t warps = (n + 3) / 4;
   int grid = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
   if (grid < 1) grid = 1;
   count_launch();
   if (dtype == CNG_F32)
     prep_kernel<float, float><<<grid, 256, 0, s>>>((const float*)pts, n, d, dpad, (float*)xs,
-                                                   xb_bf, xb_h, kpad, nb, rb, st);
+                                                   xb_bf, xb_h, kpad, nb, rb, scale, st);
   else
     prep_kernel<__half, __half><<<grid, 256, 0, s>>>((const __half*)pts, n, d, dpad,
-                                                     (__half*)xs, xb_bf, xb_h, kpad, nb, rb, st);
+                                                     (__half*)xs, xb_bf, xb_h, kpad, nb, rb, scale,
+                                                     st);
+  return cudaGetLastError();
+}
+
+// max |x| (float bits) and whether some coordinate is not an integer, over an unpadded n x d
+// matrix: out[0], out[1] (out zeroed by the caller).
+template <typename T>
+__global__ void absmax_kernel(const T* __restrict__ P, int64_t total, uint32_t* out) {
+  float m = 0.f;
+  bool nonint = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = to_f(P[e]);
+    m = fmaxf(m, fabsf(v));
+    nonint |= v != rintf(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+  const unsigned ni = __ballot_sync(FULL, nonint);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], __float_as_uint(m));
+    if (ni) atomicOr(&out[1], 1u);
+  }
+}
+
+cudaError_t launch_absmax(const void* pts, int dtype, int64_t n, int d, uint32_t* out,
+                          cudaStream_t s) {
+  const int64_t total = n * (int64_t)d;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 8));
+  count_launch();
+  if (dtype == CNG_F32)
+    absmax_kernel<float><<<grid, 256, 0, s>>>((const float*)pts, total, out);
+  else
+    absmax_kernel<__half><<<grid, 256, 0, s>>>((const __half*)pts, total, out);
   return cudaGetLastError();
 }
 
@@ -496,14 +531,17 @@ rerank_kernel(const T* __restrict__ Xr, const T* __restrict__ Xc, int64_t m, int
         float lb = sc * (1.f - sm.rel_err);
         ok = exact ? (sc > dL) : (lb > dL * (1.f + 2.f * band));
       } else {
+        // scores are in units of scale^2 (operands scale * x, scale a power of two): compare
+        // with dL scaled exactly
         const float nx = sm.nb[row];
+        const float dLs = dL * sm.scale2;
         if (exact) {
-          ok = (sc + nx) > dL;
+          ok = (sc + nx) > dLs;
         } else {
           float nrm = sqrtf(fmaxf(nx, 0.f));
           float eacc = sm.acc_err * (nrm + sm.normmax) * (nrm + sm.normmax);
           float db = sqrtf(fmaxf(sc + nx - eacc, 0.f)) - (sm.rb[row] + sm.rbmax);
-          ok = db > 0.f && db * db > dL * (1.f + 2.f * band);
+          ok = db > 0.f && db * db > dLs * (1.f + 2.f * band);
         }
       }
     }

@@ -57,3 +57,37 @@ def test_tc_scores_exact_on_integers():
     got = _scores(cng, R, C)
     ref = (C.astype(np.float64) ** 2).sum(1)[None, :] - 2.0 * R.astype(np.float64) @ C.astype(np.float64).T
     assert np.array_equal(got, ref)
+
+
+def _scores_f16(cng, R, C, scale):
+    L = cng.lib()
+    L.cngx_tc_scores_f16.restype = ctypes.c_int
+    L.cngx_tc_scores_f16.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_int32, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+    rd, cd = tensor(R), tensor(C)
+    out = torch.full((R.shape[0], C.shape[0]), float("nan"), device="cuda")
+    rc = L.cngx_tc_scores_f16(rd.data_ptr(), R.shape[0], cd.data_ptr(), C.shape[0], R.shape[1], scale,
+                              out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, cng.cng_last_error()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("kind,m,n,d,scale", [("deep", 300, 517, 96, 8192.0), ("gauss", 257, 129, 192, 2048.0),
+                                              ("gist", 200, 300, 160, 1024.0)])
+def test_tc_scores_fp16_scaled(kind, m, n, d, scale):
+    """FP16 operands fp16(scale x) as the build uses them for float data: scores equal the FP64
+    arithmetic on the same rounded operands within the FP32 accumulation bound."""
+    need_gpu()
+    cng = lib()
+    R = synth.generate(kind, m, d, seed=1)
+    C = synth.generate(kind, n, d, seed=2)
+    got = _scores_f16(cng, R, C, scale)
+    rh = (R.astype(np.float32) * np.float32(scale)).astype(np.float16).astype(np.float64)
+    ch = (C.astype(np.float32) * np.float32(scale)).astype(np.float16).astype(np.float64)
+    ref = (ch * ch).sum(1)[None, :] - 2.0 * rh @ ch.T
+    bound = (d + 16) * 2.0 ** -22 * ((np.abs(rh) @ np.abs(ch).T) * 2 + (ch * ch).sum(1)[None, :])
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= bound + 1e-6)
+    # the scaled FP16 operands are 8x closer to the data than BF16 ones
+    rb = _bf16(R) * scale
+    assert np.abs(rh - R * scale).max() < np.abs(rb - R * scale).max()
