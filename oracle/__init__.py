@@ -68,6 +68,9 @@ def _load():
             lib.or_build.restype = ctypes.c_int
             lib.or_build.argtypes = [vp, i64, ctypes.c_int, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                      vp, vp, vp, vp, vp, vp]
+            lib.or_build_ex.restype = ctypes.c_int
+            lib.or_build_ex.argtypes = [vp, i64, ctypes.c_int, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, dbl, dbl, dbl, vp, vp, vp, vp, vp, vp]
             lib.or_search.restype = ctypes.c_int
             lib.or_search.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, vp, i64,
                                       ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
@@ -207,7 +210,9 @@ def connect(X, adj3, deg3, entry_id: int, slots: int = REPAIR_SLOTS, Lc: int = C
 
 
 def build_graph(X, alpha: float, tau: float, R: int, L: int, connect_L: int = CONNECT_L,
-                repair_slots: int = REPAIR_SLOTS) -> Graph:
+                repair_slots: int = REPAIR_SLOTS, adaptive=None) -> Graph:
+    """Alg. 3 with exact candidates.  adaptive = (alpha0, alpha_max, dalpha) prunes with Alg. 4
+    in phases 2 and 3 (alpha is then unused); None prunes with the fixed alpha."""
     X = _f32(X)
     n, d = X.shape
     e = ctypes.c_int32(-1)
@@ -216,8 +221,10 @@ def build_graph(X, alpha: float, tau: float, R: int, L: int, connect_L: int = CO
     fdeg = np.empty(n, np.int32)
     adj = np.empty((n, R), np.int32)
     deg = np.empty(n, np.int32)
-    rc = _load().or_build(_p(X), n, d, float(alpha), float(tau), int(R), int(L), ctypes.byref(e),
-                          _p(cand), _p(fwd), _p(fdeg), _p(adj), _p(deg))
+    a0, am, da = adaptive if adaptive is not None else (0.0, 0.0, 0.0)
+    rc = _load().or_build_ex(_p(X), n, d, float(alpha), float(tau), int(R), int(L),
+                             int(adaptive is not None), float(a0), float(am), float(da),
+                             ctypes.byref(e), _p(cand), _p(fwd), _p(fdeg), _p(adj), _p(deg))
     if rc != 0:
         raise ValueError(f"or_build failed ({rc})")
     G = Graph(int(e.value), cand, fwd, fdeg, adj, deg)

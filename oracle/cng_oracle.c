@@ -213,14 +213,10 @@ int or_prune(const float *X, int64_t n, int d, int64_t p, const int32_t *V, int 
  * imax = round((alpha_max - alpha0) / dalpha); stop at the first S_i with |S_i| >= R/2
  * (real division); return the R closest points of the last S_i computed.
  */
-int or_prune_adaptive(const float *X, int64_t n, int d, int64_t p, const int32_t *V, int nv,
-                      double alpha0, double alpha_max, double dalpha, double tau, int R,
-                      int32_t *S, double *alpha_used) {
-    (void)n;
-    if (nv < 0 || R <= 0 || dalpha <= 0.0) return OR_E_INVAL;
-    or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * (nv > 0 ? nv : 1));
-    if (!pv) return OR_E_NOMEM;
-    sort_by_distance(X, d, p, V, nv, pv);
+/* Alg. 4 on candidates already sorted by (D(p,.), id). */
+static int prune_adaptive_sorted(const float *X, int d, const or_pair *pv, int nv, double alpha0,
+                                 double alpha_max, double dalpha, double tau, int R, int32_t *S,
+                                 double *alpha_used) {
     int imax = (int)floor((alpha_max - alpha0) / dalpha + 0.5);
     int ns = 0;
     double a = alpha0;
@@ -231,11 +227,40 @@ int or_prune_adaptive(const float *X, int64_t n, int d, int64_t p, const int32_t
         if ((double)ns >= (double)R / 2.0) break;
     }
     if (alpha_used) *alpha_used = a;
+    return ns;
+}
+
+int or_prune_adaptive(const float *X, int64_t n, int d, int64_t p, const int32_t *V, int nv,
+                      double alpha0, double alpha_max, double dalpha, double tau, int R,
+                      int32_t *S, double *alpha_used) {
+    (void)n;
+    if (nv < 0 || R <= 0 || dalpha <= 0.0) return OR_E_INVAL;
+    or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * (nv > 0 ? nv : 1));
+    if (!pv) return OR_E_NOMEM;
+    sort_by_distance(X, d, p, V, nv, pv);
+    int ns = prune_adaptive_sorted(X, d, pv, nv, alpha0, alpha_max, dalpha, tau, R, S, alpha_used);
     free(pv);
     return ns;
 }
 
-/* ---- construction (Alg. 3 phases 1-3, exact candidates, fixed alpha) --------------- */
+/* ---- construction (Alg. 3 phases 1-3, exact candidates) ------------------------------ */
+
+/* Pruning used by the build: fixed alpha (Alg. 2) or, with adaptive != 0, Alg. 4 over
+ * alpha0, alpha0 + dalpha, ..., alpha_max -- in phase 2 and in phase 3's re-prune alike (Alg. 3
+ * calls adaptive-pruning in both places). */
+typedef struct {
+    double alpha, tau;
+    int adaptive;
+    double alpha0, alpha_max, dalpha;
+} or_rule;
+
+static int build_prune(const float *X, int d, const or_pair *pv, int nv, const or_rule *r, int R,
+                       int32_t *S) {
+    if (r->adaptive)
+        return prune_adaptive_sorted(X, d, pv, nv, r->alpha0, r->alpha_max, r->dalpha, r->tau, R,
+                                     S, NULL);
+    return prune_sorted(X, d, pv, nv, r->alpha, r->tau, R, S);
+}
 
 /*
  * entry            navigating node
@@ -246,10 +271,12 @@ int or_prune_adaptive(const float *X, int64_t n, int d, int64_t p, const int32_t
  * deg   [n]
  * Returns 0, or a negative error.
  */
-int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
-             int32_t *entry, int32_t *cand, int32_t *fwd, int32_t *fdeg, int32_t *adj,
-             int32_t *deg) {
+int or_build_ex(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
+                int adaptive, double alpha0, double alpha_max, double dalpha, int32_t *entry,
+                int32_t *cand, int32_t *fwd, int32_t *fdeg, int32_t *adj, int32_t *deg) {
     if (n < 2 || d <= 0 || R <= 0 || L <= 0 || L >= n) return OR_E_INVAL;
+    if (adaptive && !(dalpha > 0.0)) return OR_E_INVAL;
+    const or_rule rule = {alpha, tau, adaptive, alpha0, alpha_max, dalpha};
     int32_t *cl = cand ? cand : (int32_t *)malloc(sizeof(int32_t) * n * L);
     double *cd = (double *)malloc(sizeof(double) * n * L);
     if (!cl || !cd) return OR_E_NOMEM;
@@ -267,7 +294,7 @@ int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, 
                 pv[i].D = cd[p * L + i];
             }
             int32_t *S = fwd + p * R;
-            int ns = prune_sorted(X, d, pv, L, alpha, tau, R, S);
+            int ns = build_prune(X, d, pv, L, &rule, R, S);
             for (int i = ns; i < R; ++i) S[i] = -1;
             fdeg[p] = ns;
         }
@@ -317,7 +344,7 @@ int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, 
                 for (int i = 0; i < nv; ++i) A[i] = pv[i].id;
                 na = nv;
             } else {
-                na = prune_sorted(X, d, pv, nv, alpha, tau, R, A);
+                na = build_prune(X, d, pv, nv, &rule, R, A);
             }
             for (int i = na; i < R; ++i) A[i] = -1;
             deg[p] = na;
@@ -329,6 +356,13 @@ int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, 
     free(cur);
     free(off);
     return OR_OK;
+}
+
+int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
+             int32_t *entry, int32_t *cand, int32_t *fwd, int32_t *fdeg, int32_t *adj,
+             int32_t *deg) {
+    return or_build_ex(X, n, d, alpha, tau, R, L, 0, 0.0, 0.0, 0.0, entry, cand, fwd, fdeg, adj,
+                       deg);
 }
 
 /* ---- beam search (Alg. 1) ----------------------------------------------------------- */

@@ -193,3 +193,59 @@ def test_connectivity_repair_on_clusters():
     for r, p in first.items():
         assert int(r) in reach0
         assert G.adj[r, G.deg3[r]] == p
+
+
+ADAPT = (0.9, 1.6, 0.05)  # the paper's setting (Sec. 5.1): alpha0, alpha_max, dalpha
+
+
+def _alphas(a0, am, da):
+    return [a0 + i * da for i in range(int(math.floor((am - a0) / da + 0.5)) + 1)]
+
+
+def _first_alpha_set(X, p, V, R, tau=0.0):
+    """Alg. 4 restated through the fixed-alpha prune: the first alpha_i whose set reaches R/2,
+    else the last one tried."""
+    for a in _alphas(*ADAPT):
+        S = oracle.prune(X, p, V, a, tau, R)
+        if 2 * len(S) >= R:
+            return S
+    return S
+
+
+def test_adaptive_build_reduces_to_fixed():
+    """alpha0 = alpha_max = alpha: Alg. 4 tries exactly one alpha, so the build equals the
+    fixed-alpha build in every phase."""
+    X = synth.generate("gauss", 400, 8, seed=11)
+    G = oracle.build_graph(X, 1.2, 0.0, 8, 24, connect_L=0)
+    H = oracle.build_graph(X, 0.0, 0.0, 8, 24, connect_L=0, adaptive=(1.2, 1.2, 0.05))
+    assert np.array_equal(G.cand, H.cand) and np.array_equal(G.fwd, H.fwd)
+    assert np.array_equal(G.adj, H.adj) and np.array_equal(G.deg, H.deg)
+
+
+@pytest.mark.parametrize("kind,n,d,R,L", [("gauss", 500, 8, 10, 30), ("sift", 600, 16, 12, 40)])
+def test_adaptive_build_phase2_and_phase3(kind, n, d, R, L):
+    """Phase 2 (Alg. 3): every list is Alg. 4 on the candidate list -- the fixed-alpha prune at
+    the first alpha_i reaching R/2.  Phase 3: every merged set above R is pruned the same way;
+    smaller ones are kept whole in (D, id) order."""
+    X = synth.generate(kind, n, d, seed=12)
+    G = oracle.build_graph(X, 0.0, 0.0, R, L, connect_L=0, adaptive=ADAPT)
+    used = set()
+    for p in range(n):
+        S = _first_alpha_set(X, p, G.cand[p], R)
+        assert list(G.fwd[p][:G.fdeg[p]]) == list(S)
+        assert np.all(G.fwd[p][G.fdeg[p]:] == -1)
+    inl = [[] for _ in range(n)]
+    for u in range(n):
+        for v in G.fwd[u][:G.fdeg[u]]:
+            inl[v].append(u)
+    for p in range(n):
+        f = list(G.fwd[p][:G.fdeg[p]])
+        V = f + [u for u in inl[p] if u not in f]
+        got = list(G.adj[p][:G.deg[p]])
+        if len(V) <= R:
+            D = ((X[V].astype(np.float64) - X[p]) ** 2).sum(1)
+            assert got == [V[i] for i in np.lexsort((V, D))]
+        else:
+            assert got == list(_first_alpha_set(X, p, np.array(V, np.int32), R))
+            used.add(p)
+    assert used  # the re-prune branch was exercised
