@@ -405,9 +405,11 @@ def main():
     t_screen = float(np.mean(screen_ms)) / 1e3
     flops = 2.0 * w.n * w.n * w.d
     if screen == cng.CNG_SCREEN_TC and last_stats is not None and last_stats.get("screen_used", 1):
+        # FP16 operands (kind::f16): the same nominal dense rate as BF16, so the measured BF16
+        # sustained figure applies with ratio 1
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                "peak_source": f"{src} bf16 sustained"}
+                "peak_source": f"{src} bf16 sustained x 1 (fp16 operands, same nominal rate)"}
     else:
         # FP32 CUDA cores, direct differences: 2 instructions (FADD + FFMA) per element pair
         # = 2 GEMM-equivalent flops per 2 lane-instructions; 152 SMs x 128 lanes x max clock
