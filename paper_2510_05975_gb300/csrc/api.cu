@@ -222,7 +222,7 @@ static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist
     ta.ids = sids;
     ta.thr = sthr;
     ta.status = &ctr->status;
-    ta.rowbuf_words = screen_tc_rowbuf_words(in.m, in.Lp);
+    ta.rowbuf_words = screen_tc_rowbuf_words(in.m, in.n, in.Lp);
     ta.perm = in.perm;
     ta.wave_start = in.wave_start;
     CK(pool.alloc(&ta.rowbuf, ta.rowbuf_words));
@@ -1018,7 +1018,7 @@ static cng_status tc_scores(const float* rows, int64_t m, const float* cols, int
   ta.Lp = 32;
   ta.self_excl = 0;
   ta.status = status;
-  ta.rowbuf_words = screen_tc_rowbuf_words(m, 32);
+  ta.rowbuf_words = screen_tc_rowbuf_words(m, n, 32);
   CK(pool.alloc(&ta.rowbuf, ta.rowbuf_words));
   std::string msg;
   cudaError_t e = launch_screen_tc_dump(ta, scores, s, &msg);

@@ -52,7 +52,39 @@ struct TcParams {
   uint32_t* status;
   const int32_t* perm;  // rows and columns are positions of a locality order: perm[pos] = id
   int wave_start;       // 1: each wave of row blocks starts its column sweep at its own rows
+  uint32_t* sync;       // zeroed checkpoint counters (producers of a wave stay close), or null
 };
+
+// Producers meet at checkpoints every TC_SYNC_K tiles of their own sequence; a producer at
+// checkpoint c waits until every CTA that reaches checkpoint c - TC_SYNC_D has reached it, so
+// the CTAs of a wave stay within TC_SYNC_D * TC_SYNC_K B tiles of each other and share the tiles
+// through L2 instead of each streaming them from DRAM.  The wait only serves the cache: it is
+// bounded (about 2 ms) and the producer proceeds when it expires.
+constexpr int TC_SYNC_K = 256;
+constexpr int TC_SYNC_D = 8;
+constexpr uint32_t TC_SYNC_SPIN = 8192;
+
+CNG_DEV uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+CNG_DEV void wave_checkpoint(const TcParams& P, int64_t it, int64_t nrb, int ntiles) {
+  if (!P.sync || it == 0 || it % TC_SYNC_K != 0) return;
+  const int64_t c = it / TC_SYNC_K;
+  atomicAdd(&P.sync[c], 1u);
+  if (c <= TC_SYNC_D) return;
+  const int64_t cw = c - TC_SYNC_D;
+  // CTAs reaching tile index cw * K: those with a row block in wave (cw * K) / ntiles
+  const int64_t w = (cw * TC_SYNC_K) / ntiles;
+  const int64_t left = nrb - w * (int64_t)gridDim.x;
+  const uint32_t expect = (uint32_t)(left < 0 ? 0 : (left > gridDim.x ? gridDim.x : left));
+  for (uint32_t i = 0; i < TC_SYNC_SPIN; ++i) {
+    if (ld_acquire_u32(&P.sync[cw]) >= expect) return;
+    __nanosleep(200);
+  }
+}
 
 // First column tile of row block rb's sweep.  A wave is the gridDim.x consecutive row blocks
 // processed together; all its CTAs share the start, so B tiles stay shared through L2.
@@ -407,6 +439,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
           const int s = (int)(it % P.nst);
           const uint32_t ph = (uint32_t)((it / P.nst) & 1);
+          wave_checkpoint(P, it, nrb, ntiles);
           ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
           if (!ok) break;
           mbar_expect_tx(&b_full[s], (uint32_t)(b_bytes + TC_BN * 4));
@@ -600,6 +633,16 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kpad,
   return true;
 }
 
+// 64-bit words for the checkpoint counters (one u32 per checkpoint of the longest producer
+// sequence: waves x column tiles).
+static size_t sync_counter_words(int64_t m, int64_t n, int grid) {
+  const int64_t nrb = (m + TC_BM - 1) / TC_BM;
+  const int64_t waves = (nrb + grid - 1) / grid;
+  const int64_t ntiles = (n + TC_BN - 1) / TC_BN;
+  const int64_t checkpoints = waves * ntiles / TC_SYNC_K + 2;
+  return (size_t)((checkpoints + 1) / 2);
+}
+
 static uint32_t make_idesc(bool fp16) {
   uint32_t d = 0;
   d |= 1u << 4;                      // D format: F32
@@ -617,8 +660,25 @@ static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const 
   cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel<CPL, DUMP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // cooperative when the producers wait for one another (boundedly): every CTA resident at once
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = p.sync ? 1 : 0;
   count_launch();
-  screen_tc_kernel<CPL, DUMP><<<grid, TC_THREADS, smem, s>>>(ma, mb, p, dump);
+  e = cudaLaunchKernelEx(&cfg, screen_tc_kernel<CPL, DUMP>, ma, mb, p, dump);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {  // not all resident: plain launch (waits bounded)
+    (void)cudaGetLastError();
+    cfg.numAttrs = 0;
+    e = cudaLaunchKernelEx(&cfg, screen_tc_kernel<CPL, DUMP>, ma, mb, p, dump);
+  }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -665,11 +725,19 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
   size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * (b_bytes + TC_BN * 4) + 256 + 8 * 256 * 4;
   smem = std::max<size_t>(smem, 116 * 1024);
-  if (!a.rowbuf || a.rowbuf_words < (size_t)grid * TC_BM * p.cap) {
+  const size_t buf_words = (size_t)grid * TC_BM * p.cap;
+  const size_t sync_words = sync_counter_words(a.m, a.n, grid);
+  if (!a.rowbuf || a.rowbuf_words < buf_words + (dump ? 0 : sync_words)) {
     if (msg) *msg = "row buffer missing or too small; ";
     return cudaErrorInvalidValue;
   }
   p.rowbuf = a.rowbuf;
+  p.sync = nullptr;
+  if (!dump) {  // checkpoint counters after the row buffers, zeroed on the stream
+    p.sync = reinterpret_cast<uint32_t*>(a.rowbuf + buf_words);
+    cudaError_t ze = cudaMemsetAsync(p.sync, 0, sync_words * 8, s);
+    if (ze != cudaSuccess) return ze;
+  }
   cudaError_t e;
 #define CNG_TC(C)                                                                             \
   case C:                                                                                     \
@@ -688,11 +756,11 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   return e;
 }
 
-size_t screen_tc_rowbuf_words(int64_t m, int Lp) {
+size_t screen_tc_rowbuf_words(int64_t m, int64_t n, int Lp) {
   const int cpl = 24;  // the largest capacity launch_impl may choose
   const int64_t nrb = (m + TC_BM - 1) / TC_BM;
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
-  return (size_t)grid * TC_BM * cpl * 32;
+  return (size_t)grid * TC_BM * cpl * 32 + sync_counter_words(m, n, grid);
 }
 
 cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg) {

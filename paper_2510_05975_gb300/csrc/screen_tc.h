@@ -21,7 +21,7 @@ struct TcScreenArgs {
   int32_t* ids;       // [m][Lp] screened ids (unordered), -1 padded
   uint32_t* thr;      // [m] ordered key of the largest kept score (0xffffffff: all kept)
   uint32_t* status;
-  uint64_t* rowbuf;     // scratch: screen_tc_rowbuf_words(m, Lp) words
+  uint64_t* rowbuf;     // scratch: screen_tc_rowbuf_words(m, n, Lp) words
   size_t rowbuf_words;
   // Locality order (optional): A and B hold the points at positions of an order, perm[pos]
   // the point id; ids and thr are then written for the point ids (row perm[pos], column
@@ -31,7 +31,8 @@ struct TcScreenArgs {
 };
 
 bool tc_screen_supported(int d, bool fp16);
-size_t screen_tc_rowbuf_words(int64_t m, int Lp);
+// Scratch words for m rows against n columns: row buffers plus checkpoint counters.
+size_t screen_tc_rowbuf_words(int64_t m, int64_t n, int Lp);
 cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg);
 // Test aid: writes every screened score s(x, y) to dump[m][n] instead of selecting.
 cudaError_t launch_screen_tc_dump(const TcScreenArgs& a, float* dump, cudaStream_t s,
