@@ -189,6 +189,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) of one screen launch at full size, from the one-pass ncu capture of
+# the current kernel (profiles/screen_tc_sift1m_dram.md); re-measure when the kernel changes.
+SCREEN_DRAM_BYTES = {"sift1m": 45.22e9 + 23.16e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,8 +422,12 @@ def main():
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
                 "peak_source": "FP32 lanes x max SM clock (derived)"}
     achieved = flops / t_screen / 1e12
+    traffic = None
+    if roof["bound"] == "tensor" and args.workload in SCREEN_DRAM_BYTES:
+        traffic = SCREEN_DRAM_BYTES[args.workload]
     roof.update({"kernel": "candidate screen", "achieved": achieved, "frac": achieved / roof["peak"],
-                 "traffic": None, "algorithmic": "2*n*n*d flops per launch"})
+                 "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                 "algorithmic": "2*n*n*d flops per launch"})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
