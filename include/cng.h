@@ -61,6 +61,13 @@ typedef enum {
  *   input_order      0 (default): the tensor-core screen sweeps the points in a k-d locality
  *                    order, which makes it faster; 1: in input order.  The results are the
  *                    same either way (an engineering option, not in the paper).
+ *   adaptive         1: adaptive-pruning (Alg. 4, Sec. 4.2) in phases 2 and 3 instead of the
+ *                    fixed alpha: alpha_i = alpha0 + i * dalpha for i = 0, 1, ..,
+ *                    round((alpha_max - alpha0) / dalpha); each point keeps the first R points
+ *                    of the first S_i with |S_i| >= R / 2 (else of the last S_i).  alpha is then
+ *                    unused.  The paper's setting (Sec. 4.3): alpha0 0.9, dalpha 0.05,
+ *                    alpha_max 1.6.
+ *   alpha0, alpha_max, dalpha   [alpha_0, alpha_max, Delta alpha] of Alg. 4 (adaptive only)
  */
 typedef struct {
   double alpha;
@@ -74,6 +81,10 @@ typedef struct {
   int32_t keep_lists;
   int32_t connect_L;
   int32_t input_order;
+  int32_t adaptive;
+  double alpha0;
+  double alpha_max;
+  double dalpha;
 } cng_build_params;
 
 /* Per-phase times (device events, milliseconds) and near-tie / certification counts. */
@@ -92,6 +103,7 @@ typedef struct {
   int32_t exact_int;          /* 1 when every FP32 squared distance is an exact integer */
   double screen_err_max;      /* largest |screened - rerank| seen on kept candidates */
   double ms_order;            /* locality order of the screen's operands (part of ms_total) */
+  double alpha_mean;          /* mean alpha of the phase-2 lists (alpha when not adaptive) */
 } cng_build_stats;
 
 typedef struct cng_index cng_index;

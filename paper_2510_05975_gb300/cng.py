@@ -41,7 +41,9 @@ class BuildParams(ctypes.Structure):
                 ("L", ctypes.c_int32), ("metric", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("tie_band", ctypes.c_double), ("margin", ctypes.c_int32),
                 ("keep_lists", ctypes.c_int32), ("connect_L", ctypes.c_int32),
-                ("input_order", ctypes.c_int32)]
+                ("input_order", ctypes.c_int32), ("adaptive", ctypes.c_int32),
+                ("alpha0", ctypes.c_double), ("alpha_max", ctypes.c_double),
+                ("dalpha", ctypes.c_double)]
 
 
 class BuildStats(ctypes.Structure):
@@ -53,7 +55,8 @@ class BuildStats(ctypes.Structure):
                  "merge_max_list", "repair_edges")] + \
                [("repair_rounds", ctypes.c_int32), ("screen_used", ctypes.c_int32),
                 ("entry", ctypes.c_int32), ("exact_int", ctypes.c_int32),
-                ("screen_err_max", ctypes.c_double), ("ms_order", ctypes.c_double)]
+                ("screen_err_max", ctypes.c_double), ("ms_order", ctypes.c_double),
+                ("alpha_mean", ctypes.c_double)]
 
 
 class SearchParams(ctypes.Structure):
@@ -195,7 +198,7 @@ class Index:
 def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: int = CNG_L2,
               screen: int = CNG_SCREEN_TC, tie_band: float = 1e-5, margin: int = 32,
               keep_lists: bool = False, connect_L: int = 0, input_order: bool = False,
-              stream=None):
+              adaptive=None, stream=None):
     """cng_build of include/cng.h.  points: CUDA tensor or host (numpy / CPU tensor), float32
     or float16, shape [n, d].  Returns (Index, stats dict)."""
     if isinstance(points, torch.Tensor):
@@ -205,8 +208,9 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
         import numpy as np
         dt = {np.dtype("float32"): CNG_F32, np.dtype("float16"): CNG_F16}[points.dtype]
         n, d = points.shape
+    a0, am, da = adaptive if adaptive is not None else (0.0, 0.0, 0.0)
     p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists), connect_L,
-                    int(input_order))
+                    int(input_order), int(adaptive is not None), a0, am, da)
     st = BuildStats()
     h = ctypes.c_void_p()
     _check(lib().cng_build(_ptr(points), dt, n, d, ctypes.byref(p), _stream(stream),

@@ -433,6 +433,13 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
   if (!(p->tie_band >= 5e-6) || p->tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
   if (p->margin < 0 || p->margin > 256) return fail(CNG_E_INVAL, "margin must be in [0, 256]");
   if (p->connect_L > 256) return fail(CNG_E_INVAL, "connect_L must be <= 256");
+  if (p->adaptive) {
+    if (!(p->alpha0 > 0.0) || !std::isfinite(p->alpha0) || !std::isfinite(p->alpha_max) ||
+        !(p->alpha_max >= p->alpha0) || !(p->dalpha > 0.0) ||
+        (p->alpha_max - p->alpha0) / p->dalpha > 1000.0)
+      return fail(CNG_E_INVAL,
+                  "adaptive pruning needs 0 < alpha0 <= alpha_max, dalpha > 0 and at most 1001 steps");
+  }
   return CNG_OK;
 }
 
@@ -543,7 +550,13 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   int32_t *fwd, *fdeg;
   CK(pool.alloc(&fwd, (size_t)n * R));
   CK(pool.alloc(&fdeg, (size_t)n));
-  CK(launch_prune_fwd(pr.xs, dtype, n, d, dpad, cand, cdist, L, P.alpha, P.tau, R, band, fwd, fdeg,
+  AlphaGrid ag{0.0, 0.0, -1};
+  if (P.adaptive) {  // Alg. 4: i = 0 .. round((alpha_max - alpha0) / dalpha)
+    ag.alpha0 = P.alpha0;
+    ag.dalpha = P.dalpha;
+    ag.imax = (int)std::floor((P.alpha_max - P.alpha0) / P.dalpha + 0.5);
+  }
+  CK(launch_prune_fwd(pr.xs, dtype, n, d, dpad, cand, cdist, L, P.alpha, P.tau, ag, R, band, fwd, fdeg,
                       ctr, u8, u8w, s));
   tm.mark();  // 4
   // phase 3: reverse edges + lazy pruning
@@ -560,7 +573,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   int32_t* big_list;
   CK(pool.alloc(&big_list, 2 * (size_t)n));  // big list + the 8-bit merge's middle list
   CK(launch_reverse(fwd, fdeg, n, R, indeg, off, cursor, inl, bsum, ctr, s));
-  CK(launch_merge(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band, exact, adj,
+  CK(launch_merge(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, ag, R, band, exact, adj,
                   deg, Rs, ctr, big_list, u8, u8w, s));
   {
     Counters hc0;
@@ -572,7 +585,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       int grid = std::min(hc0.nbig, num_sms() * 2);
       unsigned char* scratch;
       CK(pool.alloc(&scratch, (size_t)grid * cap * 17));
-      CK(launch_merge_big(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, R, band,
+      CK(launch_merge_big(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, ag, R, band,
                           exact, adj, deg, Rs, ctr, big_list, hc0.nbig, scratch, cap, grid, s));
     }
   }
@@ -723,6 +736,8 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     stats->entry = h_entry;
     stats->exact_int = exact;
     stats->screen_err_max = bits_to_float(hc.screen_err_bits);
+    stats->alpha_mean = P.adaptive ? P.alpha0 + P.dalpha * (double)hc.alpha_steps / (double)n
+                                   : P.alpha;
     stats->ms_order = ms_order;
   }
   *out = ix;

@@ -40,6 +40,14 @@ struct Counters {
   int nbig;        // nodes whose merged set exceeds the shared-memory capacity
   int max_indeg;
   int nmid;        // 8-bit merge: nodes deferred from the 128-entry to the 256-entry pass
+  unsigned long long alpha_steps;  // adaptive pruning: sum over phase-2 points of the alpha step
+};
+
+// Alg. 4 grid of adaptive pruning: alpha_i = alpha0 + i * dalpha, i = 0 .. imax (imax < 0:
+// the fixed alpha of Alg. 2 everywhere).
+struct AlphaGrid {
+  double alpha0, dalpha;
+  int imax;
 };
 
 // How the screened score relates to the squared distance (for certification).
@@ -81,7 +89,8 @@ cudaError_t launch_rescan(const void* xr, const void* xc, int dtype, int64_t m, 
                           float* out_dist, cudaStream_t s);
 cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* cand, const float* cdist, int L, double alpha,
-                             double tau, int R, float band, int32_t* fwd, int32_t* fdeg,
+                             double tau, const AlphaGrid& ag, int R, float band, int32_t* fwd,
+                             int32_t* fdeg,
                              Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s);
 // 8-bit rows (integer data spanning <= 255): words per row for d (0: unsupported), conversion.
 int u8_words(int d);
@@ -95,16 +104,17 @@ cudaError_t launch_reverse(const int32_t* fwd, const int32_t* fdeg, int64_t n, i
 // (the second half is the 8-bit path's list between its two passes).
 cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
-                         const int32_t* inl, double alpha, double tau, int R, float band,
-                         int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
-                         int32_t* big_list, const uint8_t* u8, int u8_words, cudaStream_t s);
+                         const int32_t* inl, double alpha, double tau, const AlphaGrid& ag,
+                         int R, float band, int exact, int32_t* adj, int32_t* deg, int rs,
+                         Counters* ctr, int32_t* big_list, const uint8_t* u8, int u8_words,
+                         cudaStream_t s);
 // Merge of the listed nodes with per-CTA global scratch of 17 * big_cap bytes (grid CTAs).
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
-                             const int32_t* inl, double alpha, double tau, int R, float band,
-                             int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
-                             int32_t* big_list, int nbig, unsigned char* scratch, int big_cap,
-                             int grid, cudaStream_t s);
+                             const int32_t* inl, double alpha, double tau, const AlphaGrid& ag,
+                             int R, float band, int exact, int32_t* adj, int32_t* deg, int rs,
+                             Counters* ctr, int32_t* big_list, int nbig, unsigned char* scratch,
+                             int big_cap, int grid, cudaStream_t s);
 // Phase 4 (connectivity) pieces, k_connect.cu.  counts_dev / counts_host: int[4].
 cudaError_t launch_bfs(const int32_t* adj, const int32_t* deg, int Rs, int64_t n, int32_t s,
                        int32_t* reached, int32_t* fa, int32_t* fb, int* counts_dev,

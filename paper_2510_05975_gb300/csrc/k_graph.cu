@@ -30,7 +30,50 @@ struct RuleArgs {
   double alpha64, t64;
   int R;   // out-degree bound
   int rs;  // row stride of the final adjacency (R + connectivity slots)
+  // adaptive pruning (Alg. 4): alpha_i = alpha0 + i * dalpha for i = 0 .. imax; imax < 0: fixed
+  double alpha0, dalpha, tau64;
+  int imax;
 };
+
+// The rule at step i of Alg. 4, in the oracle's operation order (no contraction).
+CNG_DEV RuleArgs rule_step(const RuleArgs& ra, int i) {
+  RuleArgs r = ra;
+  r.alpha64 = __dadd_rn(ra.alpha0, __dmul_rn((double)i, ra.dalpha));
+  r.t64 = __dmul_rn(__dadd_rn(r.alpha64, 1.0), ra.tau64);
+  r.alpha32 = (float)r.alpha64;
+  r.t32 = (float)r.t64;
+  return r;
+}
+
+// Alg. 2 with the fixed alpha, or Alg. 4: sweeps with alpha_0, alpha_1, ... until the kept set
+// holds at least R/2 points (its first R are kept) or alpha_max was tried.  `sweep(rule)` runs
+// one Alg. 2 pass and returns |S| (uniform over the CTA).  *steps receives the last i.
+template <typename F>
+CNG_DEV int prune_with_rule(const RuleArgs& ra, F&& sweep, int* steps) {
+  int ns = 0, i = 0;
+  for (;; ++i) {
+    ns = sweep(ra.imax >= 0 ? rule_step(ra, i) : ra);
+    if (ra.imax < 0 || 2 * ns >= ra.R || i >= ra.imax) break;
+  }
+  *steps = ra.imax >= 0 ? i : 0;
+  return ns;
+}
+
+static RuleArgs rule_args(double alpha, double tau, int R, float band, int rs, const AlphaGrid& g) {
+  RuleArgs ra;
+  ra.rs = rs;
+  ra.alpha64 = alpha;
+  ra.t64 = (alpha + 1.0) * tau;
+  ra.alpha32 = (float)alpha;
+  ra.t32 = (float)ra.t64;
+  ra.band = band;
+  ra.R = R;
+  ra.alpha0 = g.alpha0;
+  ra.dalpha = g.dalpha;
+  ra.tau64 = tau;
+  ra.imax = g.imax;
+  return ra;
+}
 
 CNG_DEV float part_sqdist_ss(const float* __restrict__ a, const float* __restrict__ b, int dpad,
                              int g) {
@@ -380,7 +423,7 @@ prune_fwd_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
   sm.flags = reinterpret_cast<uint8_t*>(ptr); ptr += ((L + 15) / 16) * 16;
   const int nstage = (L * dpad * 4 <= PR_STAGE_BYTES) ? L : 0;
   sm.stage = nstage ? reinterpret_cast<float*>(ptr) : nullptr;
-  unsigned long long ties = 0, edges = 0;
+  unsigned long long ties = 0, edges = 0, asteps = 0;
   for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
     for (int i = threadIdx.x; i < L; i += PR_THREADS) {
       sm.ids[i] = cand[p * L + i];
@@ -389,7 +432,11 @@ prune_fwd_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
     __syncthreads();
     if (nstage) stage_vectors(Xs, dpad, sm.ids, nstage, sm.stage);
     __syncthreads();
-    int ns = prune_sweep(Xs, d, dpad, p, sm, L, nstage, ra, ties);
+    int steps;
+    int ns = prune_with_rule(
+        ra, [&](const RuleArgs& r) { return prune_sweep(Xs, d, dpad, p, sm, L, nstage, r, ties); },
+        &steps);
+    asteps += steps;
     for (int i = threadIdx.x; i < ra.R; i += PR_THREADS) fwd[p * ra.R + i] = i < ns ? sm.S[i] : -1;
     if (threadIdx.x == 0) fdeg[p] = ns;
     edges += ns;
@@ -399,6 +446,7 @@ prune_fwd_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
   if ((threadIdx.x & 31) == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+  if (threadIdx.x == 0 && asteps) atomicAdd(&ctr->alpha_steps, asteps);
   (void)edges;
 }
 
@@ -413,15 +461,19 @@ prune_fwd_reg_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
   __shared__ uint8_t s_flags[NSLOT * PR_GROUPS];
   __shared__ int32_t s_S[64];
   __shared__ __align__(16) float s_vq[DL4 * 32 * 4];
-  unsigned long long ties = 0;
+  unsigned long long ties = 0, asteps = 0;
   for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
     for (int i = threadIdx.x; i < L; i += PR_THREADS) {
       s_ids[i] = cand[p * L + i];
       s_dist[i] = cdist[p * L + i];
     }
     __syncthreads();
-    const int ns = prune_sweep_reg<T, NSLOT, DL4>(Xs, d, dpad, p, s_ids, s_dist, s_flags, s_S, s_vq,
-                                                  L, ra, ties);
+    int steps;
+    const int ns = prune_with_rule(ra, [&](const RuleArgs& r) {
+      return prune_sweep_reg<T, NSLOT, DL4>(Xs, d, dpad, p, s_ids, s_dist, s_flags, s_S, s_vq, L, r,
+                                            ties);
+    }, &steps);
+    asteps += steps;
     for (int i = threadIdx.x; i < ra.R; i += PR_THREADS) fwd[p * ra.R + i] = i < ns ? s_S[i] : -1;
     if (threadIdx.x == 0) fdeg[p] = ns;
     __syncthreads();
@@ -429,6 +481,7 @@ prune_fwd_reg_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
   if ((threadIdx.x & 31) == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+  if (threadIdx.x == 0 && asteps) atomicAdd(&ctr->alpha_steps, asteps);
 }
 
 template <typename T, int DW>
@@ -442,15 +495,19 @@ prune_fwd_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int
   __shared__ int32_t s_S[64];
   __shared__ U8Slot<DW> s_slots[2 * 8];
   __shared__ unsigned s_masks[2 * 8];
-  unsigned long long ties = 0;
+  unsigned long long ties = 0, asteps = 0;
   for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
       s_ids[i] = cand[p * L + i];
       s_dist[i] = cdist[p * L + i];
     }
     __syncthreads();
-    const int ns = prune_sweep_u8<T, DW>(U, Xs, d, dpad, p, s_ids, s_dist, s_S, s_slots, s_masks, L,
-                                         ra, ties);
+    int steps;
+    const int ns = prune_with_rule(ra, [&](const RuleArgs& r) {
+      return prune_sweep_u8<T, DW>(U, Xs, d, dpad, p, s_ids, s_dist, s_S, s_slots, s_masks, L, r,
+                                   ties);
+    }, &steps);
+    asteps += steps;
     for (int i = threadIdx.x; i < ra.R; i += blockDim.x) fwd[p * ra.R + i] = i < ns ? s_S[i] : -1;
     if (threadIdx.x == 0) fdeg[p] = ns;
     __syncthreads();
@@ -458,6 +515,7 @@ prune_fwd_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
   if ((threadIdx.x & 31) == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+  if (threadIdx.x == 0 && asteps) atomicAdd(&ctr->alpha_steps, asteps);
 }
 
 template <typename T>
@@ -519,16 +577,9 @@ static bool launch_prune_reg(const T* xs, int64_t n, int d, int dpad, const int3
 
 cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* cand, const float* cdist, int L, double alpha,
-                             double tau, int R, float band, int32_t* fwd, int32_t* fdeg,
+                             double tau, const AlphaGrid& ag, int R, float band, int32_t* fwd, int32_t* fdeg,
                              Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s) {
-  RuleArgs ra;
-  ra.alpha64 = alpha;
-  ra.t64 = (alpha + 1.0) * tau;
-  ra.alpha32 = (float)alpha;
-  ra.t32 = (float)ra.t64;
-  ra.band = band;
-  ra.R = R;
-  ra.rs = R;
+  RuleArgs ra = rule_args(alpha, tau, R, band, R, ag);
   if (dtype == CNG_F32 ? launch_prune_u8(u8, u8_words, (const float*)xs, n, d, dpad, cand, cdist, L,
                                          ra, fwd, fdeg, ctr, s)
                        : launch_prune_u8(u8, u8_words, (const __half*)xs, n, d, dpad, cand, cdist,
@@ -829,14 +880,20 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
     for (int i = tid; i < nv; i += PR_THREADS) sm.S[i] = ar.ids[i];
     __syncthreads();
   } else if (NS > 0 && nv <= NS * PR_GROUPS) {
-    na = prune_sweep_reg<T, (NS > 0 ? NS : 1), (DL > 0 ? DL : 1)>(Xs, d, dpad, p, ar.ids, ar.dist,
-                                                                  ar.flags, sm.S, sm.vq, nv, ra, ties);
+    int steps;
+    na = prune_with_rule(ra, [&](const RuleArgs& r) {
+      return prune_sweep_reg<T, (NS > 0 ? NS : 1), (DL > 0 ? DL : 1)>(
+          Xs, d, dpad, p, ar.ids, ar.dist, ar.flags, sm.S, sm.vq, nv, r, ties);
+    }, &steps);
     ++repruned;
   } else {
     const int nstage = min(nv, stage_cap);
     stage_vectors(Xs, dpad, ar.ids, nstage, sm.stage);
     __syncthreads();
-    na = prune_sweep(Xs, d, dpad, p, sm, nv, nstage, ra, ties);
+    int steps;
+    na = prune_with_rule(
+        ra, [&](const RuleArgs& r) { return prune_sweep(Xs, d, dpad, p, sm, nv, nstage, r, ties); },
+        &steps);
     ++repruned;
   }
   for (int i = tid; i < ra.rs; i += PR_THREADS) adj_row[i] = i < na ? sm.S[i] : -1;
@@ -994,8 +1051,11 @@ merge_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int64_t
       if (tid < nv) s_S[tid] = s_ids[tid];
       __syncthreads();
     } else {
-      na = prune_sweep_u8<T, DW>(U, Xs, d, dpad, p, s_ids, s_dist, s_S, s_slots, s_masks, nv, ra,
-                                 ties);
+      int steps;
+      na = prune_with_rule(ra, [&](const RuleArgs& r) {
+        return prune_sweep_u8<T, DW>(U, Xs, d, dpad, p, s_ids, s_dist, s_S, s_slots, s_masks, nv, r,
+                                     ties);
+      }, &steps);
       ++repruned;
     }
     int32_t* row = adj + p * ra.rs;
@@ -1081,24 +1141,14 @@ static cudaError_t merge_t(const uint8_t* U, int dw, const void* xs, int64_t n, 
                                 big_list, big_scratch, big_cap, grid, s);
 }
 
-static RuleArgs rule_args(double alpha, double tau, int R, float band, int rs) {
-  RuleArgs ra;
-  ra.rs = rs;
-  ra.alpha64 = alpha;
-  ra.t64 = (alpha + 1.0) * tau;
-  ra.alpha32 = (float)alpha;
-  ra.t32 = (float)ra.t64;
-  ra.band = band;
-  ra.R = R;
-  return ra;
-}
 
 cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
-                         const int32_t* inl, double alpha, double tau, int R, float band,
-                         int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
-                         int32_t* big_list, const uint8_t* u8, int u8_words, cudaStream_t s) {
-  RuleArgs ra = rule_args(alpha, tau, R, band, rs);
+                         const int32_t* inl, double alpha, double tau, const AlphaGrid& ag,
+                         int R, float band, int exact, int32_t* adj, int32_t* deg, int rs,
+                         Counters* ctr, int32_t* big_list, const uint8_t* u8, int u8_words,
+                         cudaStream_t s) {
+  RuleArgs ra = rule_args(alpha, tau, R, band, rs, ag);
   int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
   return dtype == CNG_F32
              ? merge_t<float, false>(u8, u8_words, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
@@ -1109,11 +1159,11 @@ cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
 
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
-                             const int32_t* inl, double alpha, double tau, int R, float band,
-                             int exact, int32_t* adj, int32_t* deg, int rs, Counters* ctr,
-                             int32_t* big_list, int nbig, unsigned char* scratch, int big_cap,
-                             int grid, cudaStream_t s) {
-  RuleArgs ra = rule_args(alpha, tau, R, band, rs);
+                             const int32_t* inl, double alpha, double tau, const AlphaGrid& ag,
+                             int R, float band, int exact, int32_t* adj, int32_t* deg, int rs,
+                             Counters* ctr, int32_t* big_list, int nbig, unsigned char* scratch,
+                             int big_cap, int grid, cudaStream_t s) {
+  RuleArgs ra = rule_args(alpha, tau, R, band, rs, ag);
   (void)nbig;
   return dtype == CNG_F32
              ? merge_t<float, true>(nullptr, 0, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj,

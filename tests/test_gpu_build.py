@@ -129,3 +129,24 @@ def test_locality_order_same_lists(kind, n, d, R, L):
         cng.cng_free(idx)
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kind,n,d,R,L,screen", [
+    ("gauss", 3000, 32, 16, 64, 1),    # FP32 register-resident sweep
+    ("sift", 3001, 128, 32, 128, 1),   # 8-bit integer sweep
+    ("deep", 2500, 96, 24, 80, 1),     # FP32 register-resident sweep, d = 96
+    ("gist", 1500, 200, 16, 48, 0),    # staged sweep (rows too wide for registers)
+])
+def test_adaptive_build_matches_oracle(kind, n, d, R, L, screen):
+    """Adaptive pruning (Alg. 4 with the paper's alpha0 0.9, dalpha 0.05, alpha_max 1.6) in
+    phases 2 and 3: lists and graph identical to the oracle's adaptive build."""
+    need_gpu()
+    cng = lib()
+    grid = (0.9, 1.6, 0.05)
+    X = synth.generate(kind, n, d, seed=7)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=R, L=L, screen=screen, keep_lists=True,
+                            adaptive=grid)
+    G = oracle.build_graph(X, 1.2, 0.0, R, L, adaptive=grid)
+    _check_graph(X, G, idx, cng, R, L)
+    assert 0.9 <= st["alpha_mean"] <= 1.6
+    cng.cng_free(idx)
