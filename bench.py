@@ -201,7 +201,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sift1m")
-    ap.add_argument("--screen", default="tc", choices=["tc", "fp32"])
+    ap.add_argument("--screen", default="tc", choices=["tc", "tc-bf16", "fp32"],
+                    help="tensor-core screen with FP16 (tc) or BF16 (tc-bf16) operands, or FP32 "
+                         "CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--knn-n", type=int, default=0,
                     help="only run the exact k-NN path (screen + rerank) on the first N points "
@@ -232,7 +234,8 @@ def main():
         dist.barrier()
     cng.lib()
     w = synth.WORKLOADS[args.workload]
-    screen = cng.CNG_SCREEN_TC if args.screen == "tc" else cng.CNG_SCREEN_FP32
+    screen = {"tc": cng.CNG_SCREEN_TC, "tc-bf16": cng.CNG_SCREEN_TC_BF16,
+              "fp32": cng.CNG_SCREEN_FP32}[args.screen]
     if args.knn_n:
         Xs = torch.from_numpy(w.base(args.knn_n).astype(np.float32)).cuda()
         cng.cng_knn(Xs, w.L, screen=screen)  # warm-up
@@ -409,12 +412,14 @@ def main():
     pk, src = peaks()
     t_screen = float(np.mean(screen_ms)) / 1e3
     flops = 2.0 * w.n * w.n * w.d
-    if screen == cng.CNG_SCREEN_TC and last_stats is not None and last_stats.get("screen_used", 1):
-        # FP16 operands (kind::f16): the same nominal dense rate as BF16, so the measured BF16
-        # sustained figure applies with ratio 1
+    if screen in (cng.CNG_SCREEN_TC, cng.CNG_SCREEN_TC_BF16) and last_stats is not None and \
+            last_stats.get("screen_used", 1) in (cng.CNG_SCREEN_TC, cng.CNG_SCREEN_TC_BF16):
+        # FP16 operands (kind::f16) have the same nominal dense rate as BF16, so the measured
+        # BF16 sustained figure applies with ratio 1
         peak = pk["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                "peak_source": f"{src} bf16 sustained x 1 (fp16 operands, same nominal rate)"}
+        how = "bf16 sustained" if screen == cng.CNG_SCREEN_TC_BF16 else \
+            "bf16 sustained x 1 (fp16 operands, same nominal rate)"
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_source": f"{src} {how}"}
     else:
         # FP32 CUDA cores, direct differences: 2 instructions (FADD + FFMA) per element pair
         # = 2 GEMM-equivalent flops per 2 lane-instructions; 152 SMs x 128 lanes x max clock
@@ -423,7 +428,7 @@ def main():
                 "peak_source": "FP32 lanes x max SM clock (derived)"}
     achieved = flops / t_screen / 1e12
     traffic = None
-    if roof["bound"] == "tensor" and args.workload in SCREEN_DRAM_BYTES:
+    if roof["bound"] == "tensor" and screen == cng.CNG_SCREEN_TC and args.workload in SCREEN_DRAM_BYTES:
         traffic = SCREEN_DRAM_BYTES[args.workload]
     roof.update({"kernel": "candidate screen", "achieved": achieved, "frac": achieved / roof["peak"],
                  "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",

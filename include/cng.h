@@ -42,7 +42,10 @@ typedef enum { CNG_L2 = 0, CNG_IP_AS_L2 = 1 } cng_metric;
 typedef enum { CNG_F32 = 0, CNG_F16 = 1 } cng_dtype;
 typedef enum {
   CNG_SCREEN_FP32 = 0,  /* FP32 CUDA-core candidate screen (direct differences) */
-  CNG_SCREEN_TC = 1     /* tensor-core screen: BF16 (FP16 for f16 data) operands, FP32 accumulate */
+  CNG_SCREEN_TC = 1,    /* tensor-core screen: FP16 operands fp16(s x), s a power of two (1 for
+                           integer data up to 2048 and for f16 input), FP32 accumulate */
+  CNG_SCREEN_TC_BF16 = 2 /* tensor-core screen with BF16 operands bf16(x) (f32 input; f16 input
+                            stays FP16), FP32 accumulate: 8x coarser rounding, same rate */
 } cng_screen;
 
 /*

@@ -21,7 +21,7 @@ CNG_OK, CNG_E_INVAL, CNG_E_NOMEM, CNG_E_CUDA, CNG_E_TIMEOUT, CNG_E_UNSUPPORTED, 
     0, -1, -2, -3, -4, -5, -6)
 CNG_L2, CNG_IP_AS_L2 = 0, 1
 CNG_F32, CNG_F16 = 0, 1
-CNG_SCREEN_FP32, CNG_SCREEN_TC = 0, 1
+CNG_SCREEN_FP32, CNG_SCREEN_TC, CNG_SCREEN_TC_BF16 = 0, 1, 2
 CNG_SEARCH_FIXED, CNG_SEARCH_LEARNED = 0, 1
 
 EXPORTS = ("cng_build", "cng_free", "cng_last_error", "cng_graph", "cng_lists", "cng_search",

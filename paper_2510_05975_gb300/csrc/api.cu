@@ -403,13 +403,14 @@ static bool u8_rows_ok(const PrepStats& st, int d) {
 // Squared distances are exact FP32 integers when every coordinate is an integer and
 // d * span^2 < 2^24 (span = max - min coordinate); the tensor-core screen additionally needs
 // |coordinate| <= 256 (exact in bf16) and ||x||^2 < 2^24.
-static int exact_int(const PrepStats& st, int d, int screen) {
+static int exact_int(const PrepStats& st, int d, int screen, int bf16ops = 0) {
   if (st.nonint) return 0;
   double lo = key_to_float(st.vmin_key), hi = key_to_float(st.vmax_key);
   double span = hi - lo;
   if ((double)d * span * span >= 16777216.0) return 0;
   if (screen == CNG_SCREEN_TC) {
-    if (std::max(std::fabs(lo), std::fabs(hi)) > 2048.0) return 0;  // exact in FP16
+    // integers are exact up to 2048 in FP16, up to 256 in BF16
+    if (std::max(std::fabs(lo), std::fabs(hi)) > (bf16ops ? 256.0 : 2048.0)) return 0;
     double nm = bits_to_float(st.normmax_bits);
     if (nm * nm >= 8388608.0) return 0;
   }
@@ -429,7 +430,8 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
   if (!(p->alpha > 0.0) || !std::isfinite(p->alpha)) return fail(CNG_E_INVAL, "alpha must be a positive finite number");
   if (!(p->tau >= 0.0) || !std::isfinite(p->tau)) return fail(CNG_E_INVAL, "tau must be finite and >= 0");
   if (p->metric != CNG_L2 && p->metric != CNG_IP_AS_L2) return fail(CNG_E_INVAL, "unknown metric");
-  if (p->screen != CNG_SCREEN_FP32 && p->screen != CNG_SCREEN_TC) return fail(CNG_E_INVAL, "unknown screen");
+  if (p->screen != CNG_SCREEN_FP32 && p->screen != CNG_SCREEN_TC && p->screen != CNG_SCREEN_TC_BF16)
+    return fail(CNG_E_INVAL, "unknown screen");
   if (!(p->tie_band >= 5e-6) || p->tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
   if (p->margin < 0 || p->margin > 256) return fail(CNG_E_INVAL, "margin must be in [0, 256]");
   if (p->connect_L > 256) return fail(CNG_E_INVAL, "connect_L must be <= 256");
@@ -452,7 +454,9 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   if (vs != CNG_OK) return vs;
   cudaStream_t s = (cudaStream_t)stream;
   const cng_build_params& P = *params;
-  int screen = P.screen;
+  // BF16 operands (unscaled) for f32 data on request; FP16 input is screened in FP16 as stored
+  const int bf16ops = P.screen == CNG_SCREEN_TC_BF16 && dtype == CNG_F32;
+  int screen = P.screen == CNG_SCREEN_TC_BF16 ? CNG_SCREEN_TC : P.screen;
   if (screen == CNG_SCREEN_TC && !tc_screen_supported(d, dtype == CNG_F16)) screen = CNG_SCREEN_FP32;
   DevPool pool;
   Timer tm(s);
@@ -469,17 +473,17 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   const int kpad = round_up(d, 64);
   Prepared pr;
   float scale = 1.f;
-  if (screen == CNG_SCREEN_TC) {
+  if (screen == CNG_SCREEN_TC && !bf16ops) {
     const void* pl[1] = {pts};
     const int64_t nl[1] = {n};
     cng_status ss = operand_scale(pl, nl, 1, dtype, d, &scale, s);
     if (ss != CNG_OK) return ss;
   }
-  cng_status st = prepare(pool, pts, dtype, n, d, dpad, screen, kpad, &pr, s, 1, scale);
+  cng_status st = prepare(pool, pts, dtype, n, d, dpad, screen, kpad, &pr, s, !bf16ops, scale);
   if (st != CNG_OK) return st;
   if (P.metric == CNG_IP_AS_L2 && bits_to_float(pr.st.unitdev_bits) > 1e-3f)
     return fail(CNG_E_INVAL, "CNG_IP_AS_L2 requires unit-norm rows (| ||x|| - 1 | <= 1e-3)");
-  const int exact = exact_int(pr.st, d, screen);
+  const int exact = exact_int(pr.st, d, screen, bf16ops);
   const float band = (float)P.tie_band;
   tm.mark();  // 1
   // phase 1: navigating node
@@ -520,7 +524,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   ki.tc_rows = pr.tc;
   ki.tc_cols = pr.tc;
   ki.kpad = kpad;
-  ki.tc_fp16 = 1;
+  ki.tc_fp16 = !bf16ops;
   ki.scale2 = scale * scale;
   ki.nb_rows = pr.nb;
   ki.nb_cols = pr.nb;
@@ -727,7 +731,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     stats->n_edges = (int64_t)hc.edges + repair_edges;
     stats->repair_edges = repair_edges;
     stats->repair_rounds = repair_rounds;
-    stats->screen_used = screen;
+    stats->screen_used = screen == CNG_SCREEN_TC && bf16ops ? CNG_SCREEN_TC_BF16 : screen;
     stats->cert_fail_rows = hc.nfail;
     stats->order_ties = (int64_t)hc.order_ties;
     stats->rule_ties = (int64_t)hc.rule_ties;
@@ -918,7 +922,10 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
   if (self) m = n;
   if (n < 1 || m < 0 || k < 1 || k > 256 || k > n || (self && k >= n))
     return fail(CNG_E_INVAL, "need 1 <= k <= 256, k <= n (k < n without rows)");
-  if (screen != CNG_SCREEN_FP32 && screen != CNG_SCREEN_TC) return fail(CNG_E_INVAL, "unknown screen");
+  if (screen != CNG_SCREEN_FP32 && screen != CNG_SCREEN_TC && screen != CNG_SCREEN_TC_BF16)
+    return fail(CNG_E_INVAL, "unknown screen");
+  const int bf16ops = screen == CNG_SCREEN_TC_BF16;
+  if (bf16ops) screen = CNG_SCREEN_TC;
   if (!(tie_band >= 5e-6) || tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
   if (!is_device_ptr(base) || (!self && !is_device_ptr(rows)) || !is_device_ptr(ids) || !is_device_ptr(dists))
     return fail(CNG_E_INVAL, "cng_knn takes device pointers");
@@ -929,16 +936,16 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
   const int dpad = round_up(d, 32), kpad = round_up(d, 64);
   Prepared pb, prw;
   float scale = 1.f;
-  if (screen == CNG_SCREEN_TC) {  // one scale for rows and columns
+  if (screen == CNG_SCREEN_TC && !bf16ops) {  // one scale for rows and columns
     const void* pl[2] = {base, rows};
     const int64_t nl[2] = {n, self ? 0 : m};
     cng_status ss = operand_scale(pl, nl, 2, CNG_F32, d, &scale, s);
     if (ss != CNG_OK) return ss;
   }
-  cng_status st = prepare(pool, base, CNG_F32, n, d, dpad, screen, kpad, &pb, s, 1, scale);
+  cng_status st = prepare(pool, base, CNG_F32, n, d, dpad, screen, kpad, &pb, s, !bf16ops, scale);
   if (st != CNG_OK) return st;
   if (!self) {
-    st = prepare(pool, rows, CNG_F32, m, d, dpad, screen, kpad, &prw, s, 1, scale);
+    st = prepare(pool, rows, CNG_F32, m, d, dpad, screen, kpad, &prw, s, !bf16ops, scale);
     if (st != CNG_OK) return st;
   }
   Prepared& pr = self ? pb : prw;
@@ -967,11 +974,11 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
   ki.Lp = (int)std::min<int64_t>((int64_t)k + 32, self ? n - 1 : n);
   ki.screen = screen;
   ki.band = (float)tie_band;
-  ki.exact = exact_int(both, d, screen);
+  ki.exact = exact_int(both, d, screen, bf16ops);
   ki.tc_rows = pr.tc;
   ki.tc_cols = pb.tc;
   ki.kpad = kpad;
-  ki.tc_fp16 = 1;
+  ki.tc_fp16 = !bf16ops;
   ki.scale2 = scale * scale;
   ki.nb_rows = pr.nb;
   ki.nb_cols = pb.nb;

@@ -36,6 +36,8 @@ def _check_graph(X, G, idx, cng, R, L):
     ("deep", 2500, 96, 1.3, 0.0, 24, 80, 0),
     ("gauss", 3000, 32, 1.2, 0.0, 16, 64, 1),
     ("sift", 3001, 128, 1.2, 0.0, 32, 128, 1),
+    ("gauss", 3000, 32, 1.2, 0.0, 16, 64, 2),   # BF16 operands
+    ("sift", 3001, 128, 1.2, 0.0, 32, 128, 2),
 ])
 def test_build_matches_oracle(kind, n, d, alpha, tau, R, L, screen):
     need_gpu()
@@ -46,6 +48,7 @@ def test_build_matches_oracle(kind, n, d, alpha, tau, R, L, screen):
     _check_graph(X, G, idx, cng, R, L)
     if kind == "sift":
         assert st["exact_int"] == 1
+    assert st["screen_used"] == screen
     cng.cng_free(idx)
 
 
