@@ -189,6 +189,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def hbm_kernels(w, X, st, ndc_sum, hops_sum, search_ms, peak, src):
+    """Achieved bandwidth of the gather-bound kernels: algorithmic bytes per launch (the model
+    in each entry) over the launch's CUDA-event time, against the measured HBM copy peak."""
+    if not st:
+        return None
+    n, d, L, R = w.n, w.d, w.L, w.R
+    dpad = (d + 31) // 32 * 32
+    f32row = 4 * dpad
+    integer = bool(np.all(X == np.rint(X)))
+    u8 = integer and float(X.max() - X.min()) <= 255.0 and d <= 128
+    prow = (d + 15) // 16 * 16 if u8 else f32row
+    Lp = L + 32
+    out = {}
+
+    def put(name, nbytes, ms, model):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"bytes": nbytes, "ms": ms, "achieved_gbs": gbs, "frac": gbs / peak,
+                     "model": model}
+
+    put("rerank", n * (Lp * f32row + Lp * 4 + L * 8), st["ms_rerank"],
+        "n (L' rows of 4 dpad B + L' ids) + n L (id, dist) written")
+    put("prune", n * (L * prow + L * 8 + R * 4), st["ms_prune"],
+        ("n L rows of d bytes (8-bit rows)" if u8 else "n L rows of 4 dpad B") +
+        " + n L (id, dist) + n R ids written")
+    put("merge", n * (2 * R * prow * 2 + 2 * R * 4 + (R + 8) * 4), st["ms_merge"],
+        "each phase-2 edge's row read from both ends, twice (order, sweep) + lists")
+    put("search_fixed", ndc_sum * f32row + hops_sum * (R + 8) * 4 + w.nq * (d * 4 + w.k * 8),
+        search_ms, "sum NDC rows of 4 dpad B + sum hops adjacency rows + queries + results")
+    out["peak_gbs"] = peak
+    out["peak_source"] = f"{src} HBM copy"
+    return out
+
+
 # DRAM bytes (read + write) of one screen launch at full size, from the one-pass ncu capture of
 # the current kernel (profiles/screen_tc_sift1m_dram.md); re-measure when the kernel changes.
 SCREEN_DRAM_BYTES = {"sift1m": 45.22e9 + 23.16e9}
@@ -370,6 +403,8 @@ def main():
     rec_l = recall_at_k(res_l["ids"].cpu().numpy(), gt)
     hops_f = float(res_f["hops"].float().mean())
     hops_l = float(res_l["hops"].float().mean())
+    ndc_sum_f = float(res_f["ndc"].double().sum())
+    hops_sum_f = float(res_f["hops"].double().sum())
     cng.cng_free(idx)
 
     def allmax(v):
@@ -434,6 +469,8 @@ def main():
                  "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
                  "algorithmic": "2*n*n*d flops per launch"})
 
+    hbm = hbm_kernels(w, X, last_stats, ndc_sum_f, hops_sum_f, f_ms, pk["hbm_gbs"], src)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_baseline(X.astype(np.float32), Q[:4096].astype(np.float32), adj_h, deg_h, entry,
@@ -463,7 +500,8 @@ def main():
                                  ("n_edges", "cert_fail_rows", "order_ties", "rule_ties",
                                   "merge_repruned", "merge_max_list", "repair_edges", "repair_rounds",
                                   "exact_int", "screen_used")} if last_stats else None,
-                "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "hbm_kernels": hbm,
+                "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if ws > 1:
