@@ -244,6 +244,9 @@ def main():
     ap.add_argument("--build-n", type=int, default=0,
                     help="only run one graph build on the first N points of the workload (after a "
                          "warm-up build) and print its phase timings (small case for profiling)")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="with --build-n: adaptive pruning (Alg. 4, alpha0 0.9, dalpha 0.05, "
+                         "alpha_max 1.6) instead of the workload's fixed alpha")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -285,12 +288,14 @@ def main():
     if args.build_n:
         Xs = torch.from_numpy(w.base(args.build_n).astype(np.float32)).cuda()
         for it in range(2):  # warm-up, then the reported build
-            idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+            idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
+                                    adaptive=(0.9, 1.6, 0.05) if args.adaptive else None)
             torch.cuda.synchronize()
             cng.cng_free(idx)
         print(json.dumps({"build_n": args.build_n, "d": w.d, "L": w.L, "R": w.R,
                           **{k: st[k] for k in ("ms_total", "ms_order", "ms_screen", "ms_rerank",
                                                 "ms_prune", "ms_merge", "ms_connect", "rule_ties", "cert_fail_rows", "order_ties",
+                                                "alpha_mean",
                                                 "merge_repruned", "n_edges")}}), flush=True)
         return
     X = w.base()
