@@ -188,7 +188,11 @@ typedef enum { CNG_SEARCH_FIXED = 0, CNG_SEARCH_LEARNED = 1 } cng_search_mode;
  * model        required for CNG_SEARCH_LEARNED, ignored otherwise
  * max_hops     0 = unbounded; otherwise queries stop after this many hop vertices (flagged)
  * use_graph    1: launch through a cached CUDA graph for this (nq, k, L, mode) shape
- * warps_per_block  0 = autotuned
+ * warps_per_block  queries per CTA (one warp each, <= 8); 0 = autotuned: the first search
+ *              of an (L, mode) shape on an index of a given shape (device, dtype, padded d,
+ *              adjacency row stride) times every launch shape (1, 2, 4, 8 warps per block x
+ *              visited filters of 512, 1024, 2048 slots) on up to 4,096 of its queries and
+ *              keeps the fastest for the rest of the process; results do not depend on it
  */
 typedef struct {
   int32_t mode;
@@ -207,6 +211,7 @@ typedef struct {
   int64_t fp64_decisions;   /* queue-order near-ties re-decided in FP64 */
   int64_t stopped_early;    /* queries stopped by the learned rule */
   int32_t warps_per_block;  /* launch shape used */
+  int32_t hash_slots;       /* visited-filter slots per query used */
 } cng_search_stats;
 
 /*

@@ -68,7 +68,8 @@ class SearchParams(ctypes.Structure):
 class SearchStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("ndc_total", ctypes.c_int64),
                 ("hops_total", ctypes.c_int64), ("fp64_decisions", ctypes.c_int64),
-                ("stopped_early", ctypes.c_int64), ("warps_per_block", ctypes.c_int32)]
+                ("stopped_early", ctypes.c_int64), ("warps_per_block", ctypes.c_int32),
+                ("hash_slots", ctypes.c_int32)]
 
 
 class TrainParams(ctypes.Structure):

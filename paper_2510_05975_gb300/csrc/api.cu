@@ -116,6 +116,14 @@ struct cng_index {
   std::vector<GraphEntry> graphs;
 };
 
+// Autotuned search launch shapes, shared by every index of the same shape in the process.
+struct TunedShape {
+  int dev, dtype, dpad, rs, L, mode;  // key
+  int wpb, hash;                      // warps per block, visited-filter slots
+};
+static std::mutex g_tune_mu;
+static std::vector<TunedShape> g_tuned;
+
 struct cng_stop_model {
   float* P = nullptr;     // FP32 master parameters
   float* mu = nullptr;    // [16]
@@ -826,8 +834,6 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   a.nq = nq;
   a.k = k;
   a.L = L;
-  a.hash_slots = L <= 64 ? 1024 : 2048;
-  a.warp_smem = search_warp_smem(ix->dpad, L, a.hash_slots);
   a.band = ix->band;
   a.exact = ix->exact;
   a.max_hops = P.max_hops;
@@ -844,16 +850,79 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     a.zthr = std::log(P.threshold / (1.f - P.threshold));
     a.check_every = P.check_every;
   }
-  int wpb = P.warps_per_block > 0 ? P.warps_per_block : 4;
-  if (wpb > 8) wpb = 8;
-  while (wpb > 1 && (size_t)wpb * a.warp_smem > 200 * 1024) wpb >>= 1;
-  int bps = search_blocks_per_sm(ix->dtype, wpb, (size_t)wpb * a.warp_smem + (a.model ? STOP_BLOCK_BYTES : 0));
+  const size_t model_bytes = a.model ? STOP_BLOCK_BYTES : 0;
+  // blocks per SM of a launch shape (0: does not fit)
+  auto shape_bps = [&](int w, int h) {
+    const size_t ws = search_warp_smem(ix->dpad, L, h);
+    if ((size_t)w * ws + model_bytes > 200 * 1024) return 0;
+    return search_blocks_per_sm(ix->dtype, w, (size_t)w * ws + model_bytes);
+  };
+  std::lock_guard<std::mutex> lock(ix->mu);
+  int wpb, hash;
+  if (P.warps_per_block > 0) {  // caller's queries per CTA, default visited-filter size
+    wpb = std::min(P.warps_per_block, 8);
+    hash = L <= 64 ? 1024 : 2048;
+    while (wpb > 1 && shape_bps(wpb, hash) < 1) wpb >>= 1;
+  } else {
+    // autotune once per (L, mode): queries per CTA (warps per block) and visited-filter size,
+    // each candidate timed on up to 4,096 of these queries; the results do not depend on it
+    // (ids and hops are exact; only NDC varies with the lossy filter)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> tl(g_tune_mu);
+    auto it = std::find_if(g_tuned.begin(), g_tuned.end(), [&](const TunedShape& t) {
+      return t.dev == dev && t.dtype == ix->dtype && t.dpad == ix->dpad && t.rs == ix->rs &&
+             t.L == L && t.mode == P.mode;
+    });
+    if (it != g_tuned.end()) {
+      wpb = it->wpb;
+      hash = it->hash;
+    } else {
+      SearchArgs t = a;
+      t.nq = std::min<int64_t>(nq, 4096);
+      float best = 1e30f;
+      wpb = 0;
+      hash = 0;
+      cudaEvent_t t0, t1;
+      cudaEventCreate(&t0);
+      cudaEventCreate(&t1);
+      for (int h : {512, 1024, 2048}) {
+        if (h < 2 * L) continue;
+        for (int w : {1, 2, 4, 8}) {
+          const int b = shape_bps(w, h);
+          if (b < 1) continue;
+          t.hash_slots = h;
+          t.warp_smem = search_warp_smem(ix->dpad, L, h);
+          float ms = 0.f;
+          for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
+            CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
+            cudaEventRecord(t0, s);
+            CK(launch_search(t, w, num_sms() * b, s));
+            cudaEventRecord(t1, s);
+            CK(cudaEventSynchronize(t1));
+            cudaEventElapsedTime(&ms, t0, t1);
+          }
+          if (ms < best) {
+            best = ms;
+            wpb = w;
+            hash = h;
+          }
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      if (!wpb) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
+      g_tuned.push_back({dev, ix->dtype, ix->dpad, ix->rs, L, P.mode, wpb, hash});
+    }
+  }
+  a.hash_slots = hash;
+  a.warp_smem = search_warp_smem(ix->dpad, L, hash);
+  int bps = shape_bps(wpb, hash);
   if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
   int grid = num_sms() * bps;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  std::lock_guard<std::mutex> lock(ix->mu);
   CK(cudaMemsetAsync(ix->tot, 0, 4 * sizeof(unsigned long long), s));
   cudaEventRecord(e0, s);
   if (P.use_graph) {
@@ -905,6 +974,7 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
       stats->fp64_decisions = (int64_t)tot[2];
       stats->stopped_early = (int64_t)tot[3];
       stats->warps_per_block = wpb;
+      stats->hash_slots = hash;
     }
   }
   cudaEventDestroy(e0);

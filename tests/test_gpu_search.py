@@ -74,3 +74,23 @@ def test_search_host_buffers_and_edges():
     with pytest.raises(cng.CngError):
         cng.cng_search(idx, tensor(Q), k=9, L=8)
     cng.cng_free(idx)
+
+
+def test_search_launch_shapes_and_autotune():
+    """Queries per CTA (1 or 8 warps per block) and the autotuned shape give the oracle's ids
+    and hops; the autotuned shape is reported and reused."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate("sift", 5000, 128, seed=6)
+    Q = synth.generate("sift", 700, 128, seed=1006)
+    idx, _ = cng.cng_build(tensor(X), alpha=1.2, R=16, L=64)
+    for wpb in (1, 8):
+        r = _search_check(X, Q, idx, cng, 10, 40, warps_per_block=wpb, with_stats=True)
+        assert r["stats"]["warps_per_block"] == wpb
+    a = _search_check(X, Q, idx, cng, 10, 40, warps_per_block=0, with_stats=True)
+    b = _search_check(X, Q, idx, cng, 10, 40, warps_per_block=0, with_stats=True)
+    assert a["stats"]["warps_per_block"] in (1, 2, 4, 8)
+    assert a["stats"]["hash_slots"] in (512, 1024, 2048)
+    assert (a["stats"]["warps_per_block"], a["stats"]["hash_slots"]) == \
+        (b["stats"]["warps_per_block"], b["stats"]["hash_slots"])
+    cng.cng_free(idx)
