@@ -101,6 +101,11 @@ struct cng_index {
   float* cdist = nullptr;
   int32_t* fwd = nullptr;   // [n][R] (keep_lists)
   int32_t* fdeg = nullptr;
+  float vmin = 0.f, vmax = 0.f;  // data value range (exact integer data)
+  uint8_t* u8 = nullptr;         // 8-bit rows x - vmin [n][4 u8w] (integer data spanning <= 255)
+  int u8w = 0;
+  uint8_t* qbuf = nullptr;       // per-search query flags + 8-bit query rows (grown on demand)
+  size_t qbuf_cap = 0;
   // search scratch
   int* counter = nullptr;
   unsigned long long* tot = nullptr;
@@ -152,6 +157,8 @@ extern "C" void cng_free(cng_index* ix) {
   cudaFree(ix->cdist);
   cudaFree(ix->fwd);
   cudaFree(ix->fdeg);
+  cudaFree(ix->u8);
+  cudaFree(ix->qbuf);
   cudaFree(ix->counter);
   cudaFree(ix->tot);
   cudaFree(ix->status);
@@ -660,6 +667,10 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       sa.warp_smem = search_warp_smem(dpad, Lc, sa.hash_slots);
       sa.band = band;
       sa.exact = exact;
+      if (u8 && exact) {  // stored points as queries: exact 8-bit rows
+        sa.U = u8;
+        sa.u8w = u8w;
+      }
       sa.max_hops = 0;
       sa.counter = sc_counter;
       sa.ids = rid;
@@ -667,7 +678,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       sa.tot = sc_tot;
       sa.status = sc_status;
       const int wpb = 4;
-      int bps = search_blocks_per_sm(dtype, wpb, (size_t)wpb * sa.warp_smem);
+      int bps = search_blocks_per_sm(dtype, sa.U ? sa.u8w : 0, wpb, (size_t)wpb * sa.warp_smem);
       if (bps < 1) return fail(CNG_E_UNSUPPORTED, "connectivity search shape does not fit");
       CK(cudaMemsetAsync(sc_counter, 0, sizeof(int), s));
       CK(launch_search(sa, wpb, num_sms() * bps, s));
@@ -704,6 +715,13 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   ix->band = band;
   ix->xs = pr.xs;
   pool.release(pr.xs);
+  ix->vmin = key_to_float(pr.st.vmin_key);
+  ix->vmax = key_to_float(pr.st.vmax_key);
+  if (u8) {
+    ix->u8 = u8;
+    ix->u8w = u8w;
+    pool.release(u8);
+  }
   ix->adj = adj;
   pool.release(adj);
   ix->deg = deg;
@@ -777,6 +795,32 @@ extern "C" cng_status cng_lists(const cng_index* ix, const int32_t** cand, const
   if (fwd) *fwd = ix->fwd;
   if (fdeg) *fdeg = ix->fdeg;
   if (R) *R = ix->R;
+  return CNG_OK;
+}
+
+// Exact data: per-query exactness flags and, with 8-bit rows, the queries as 8-bit rows
+// (a buffer of the index, grown on demand; searches on one index run one at a time).
+static cng_status search_queries(cng_index* ix, const float* qd, int64_t nq, SearchArgs* a,
+                                 cudaStream_t s) {
+  if (!ix->exact || ix->dtype != CNG_F32 || nq == 0) return CNG_OK;
+  const size_t row = ix->u8 ? (size_t)ix->u8w * 4 : 0;
+  const size_t need = ((size_t)nq + 15) / 16 * 16 + (size_t)nq * row;
+  if (need > ix->qbuf_cap) {
+    cudaFree(ix->qbuf);
+    ix->qbuf = nullptr;
+    ix->qbuf_cap = 0;
+    CK(cudaMalloc(&ix->qbuf, need));
+    ix->qbuf_cap = need;
+  }
+  uint8_t* flag = ix->qbuf;
+  uint8_t* rows = ix->u8 ? ix->qbuf + ((size_t)nq + 15) / 16 * 16 : nullptr;
+  CK(launch_query_check(qd, nq, ix->d, ix->vmin, ix->vmax, ix->u8w, rows, flag, s));
+  a->qflag = flag;
+  if (ix->u8) {
+    a->U = ix->u8;
+    a->QU = rows;
+    a->u8w = ix->u8w;
+  }
   return CNG_OK;
 }
 
@@ -855,9 +899,13 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   auto shape_bps = [&](int w, int h) {
     const size_t ws = search_warp_smem(ix->dpad, L, h);
     if ((size_t)w * ws + model_bytes > 200 * 1024) return 0;
-    return search_blocks_per_sm(ix->dtype, w, (size_t)w * ws + model_bytes);
+    return search_blocks_per_sm(ix->dtype, a.U ? a.u8w : 0, w, (size_t)w * ws + model_bytes);
   };
   std::lock_guard<std::mutex> lock(ix->mu);
+  {
+    cng_status qs = search_queries(ix, qd, nq, &a, s);
+    if (qs != CNG_OK) return qs;
+  }
   int wpb, hash;
   if (P.warps_per_block > 0) {  // caller's queries per CTA, default visited-filter size
     wpb = std::min(P.warps_per_block, 8);
@@ -1186,8 +1234,10 @@ static cng_status run_trace(cng_index* ix, const float* qd, int64_t nq, int k, i
   a.trace_feats = feats;
   a.max_trace = T;
   a.check_every = 1;
+  cng_status qs = search_queries(ix, qd, nq, &a, s);  // callers hold ix->mu
+  if (qs != CNG_OK) return qs;
   const int wpb = 4;
-  int bps = search_blocks_per_sm(ix->dtype, wpb, (size_t)wpb * a.warp_smem);
+  int bps = search_blocks_per_sm(ix->dtype, a.U ? a.u8w : 0, wpb, (size_t)wpb * a.warp_smem);
   if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
   CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
   CK(launch_search(a, wpb, num_sms() * bps, s));

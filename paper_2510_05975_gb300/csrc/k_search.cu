@@ -130,8 +130,37 @@ CNG_DEV float mlp_logit(const StopSmem& m, float f, int lane) {
   return z + m.b3[0];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
+// Squared distance of the query to row v by an 8-lane group, every lane of the group gets it.
+// DW == 0: FP32 direct differences over the stored row; DW > 0: exact integer arithmetic on
+// 8-bit rows, |q|^2 + |v|^2 - 2 <q, v> (every term below 2^24, so the FP32 value is exact).
+template <typename T, int DW>
+CNG_DEV float group_sqdist(const float* qv, const uint4* qu, uint32_t qn, const SearchArgs& a,
+                           const T* X, int64_t v, int g) {
+  if constexpr (DW == 0) {
+    float s = part_sqdist<SQ_G>(qv, X + v * a.dpad, a.dpad, g);
+    return group_reduce<SQ_G>(s);
+  } else {
+    uint32_t dot = 0, nv = 0;
+    const uint4* r = reinterpret_cast<const uint4*>(a.U + v * (DW * 4));
+#pragma unroll
+    for (int w = g; w < DW / 4; w += SQ_G) {
+      const uint4 x = __ldg(r + w), y = qu[w];
+      dot = __dp4a(x.x, y.x, dot); dot = __dp4a(x.y, y.y, dot);
+      dot = __dp4a(x.z, y.z, dot); dot = __dp4a(x.w, y.w, dot);
+      nv = __dp4a(x.x, x.x, nv); nv = __dp4a(x.y, x.y, nv);
+      nv = __dp4a(x.z, x.z, nv); nv = __dp4a(x.w, x.w, nv);
+    }
+#pragma unroll
+    for (int o = SQ_G / 2; o > 0; o >>= 1) {
+      dot += __shfl_xor_sync(FULL, dot, o);
+      nv += __shfl_xor_sync(FULL, nv, o);
+    }
+    return (float)(qn + nv - 2u * dot);
+  }
+}
+
+template <typename T, int DW>
+__global__ void __launch_bounds__(256, 2)
 search_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -170,19 +199,38 @@ search_kernel(SearchArgs a) {
     if (lane == 0) qi = atomicAdd(a.counter, 1);
     qi = __shfl_sync(FULL, qi, 0);
     if (qi >= a.nq) break;
-    if (a.qids) {  // the query is a stored point (phase-4 searches)
+    // exact queries: the data's FP32 squared distances are exact integers and this query is an
+    // integer vector inside the data's range (stored points always are); others resolve
+    // near-ties in FP64
+    const int qexact = a.exact && (a.qids != nullptr || (a.qflag && a.qflag[qi] == 0));
+    const bool use8 = DW > 0 && qexact;
+    uint32_t qn = 0;
+    if (use8) {  // the query as an 8-bit row in shared memory, and |q|^2
+      uint4* qu = reinterpret_cast<uint4*>(qv);
+      const uint8_t* src = a.qids ? a.U + (int64_t)a.qids[qi] * (DW * 4) : a.QU + (int64_t)qi * (DW * 4);
+      if (lane < DW / 4) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(src) + lane);
+        qu[lane] = x;
+        qn = __dp4a(x.x, x.x, qn); qn = __dp4a(x.y, x.y, qn);
+        qn = __dp4a(x.z, x.z, qn); qn = __dp4a(x.w, x.w, qn);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) qn += __shfl_xor_sync(FULL, qn, o);
+    } else if (a.qids) {  // the query is a stored point (phase-4 searches)
       load_row(qv, X + (int64_t)a.qids[qi] * dpad, dpad, lane, 32);
     } else {
       const float* qg = a.Q + (int64_t)qi * a.d;
       for (int c = lane; c < dpad; c += 32) qv[c] = c < a.d ? qg[c] : 0.f;
     }
+    const uint4* qu = reinterpret_cast<const uint4*>(qv);
     for (int c = lane; c < a.hash_slots; c += 32) H[c] = -1;
     __syncwarp();
     QEnt cur{Ak, Ax, Ae}, nxt{Bk, Bx, Be};
     // entry point
     {
-      float s = part_sqdist<SQ_G>(qv, X + (int64_t)a.entry * dpad, dpad, g);
-      s = group_reduce<SQ_G>(s);
+      __syncwarp();
+      const float s = use8 ? group_sqdist<T, DW>(qv, qu, qn, a, X, a.entry, g)
+                           : group_sqdist<T, 0>(qv, qu, qn, a, X, a.entry, g);
       if (lane == 0) {
         cur.k[0] = pack_key(s, a.entry);
         cur.x[0] = __longlong_as_double(0x7ff8000000000000ll);
@@ -237,10 +285,9 @@ search_kernel(SearchArgs a) {
       // FP32 distances, 4 per round
       for (int b0 = 0; b0 < nb; b0 += 32 / SQ_G) {
         int b = b0 + grp;
-        float s = 0.f;
         int32_t v = b < nb ? Nv[b] : 0;
-        if (b < nb) s = part_sqdist<SQ_G>(qv, X + (int64_t)v * dpad, dpad, g);
-        s = group_reduce<SQ_G>(s);
+        const float s = use8 ? group_sqdist<T, DW>(qv, qu, qn, a, X, v, g)
+                             : group_sqdist<T, 0>(qv, qu, qn, a, X, v, g);
         if (b < nb && g == 0) {
           Nk[b] = pack_key(s, v);
           Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
@@ -276,7 +323,7 @@ search_kernel(SearchArgs a) {
         }
         // Q is in exact order, FP32 keys are near-sorted: scan the neighbourhood for equality
         bool dup = false;
-        if (a.exact) {
+        if (qexact) {
           dup = lo < len && cur.k[lo] == kb;
         } else {
           // Q is in exact order, its FP32 keys sorted up to near-ties: scan the window of
@@ -322,7 +369,7 @@ search_kernel(SearchArgs a) {
       if (nbv == 0) break;
       // near-ties: mark batch entries close to a neighbour in the batch or to a Q entry, and
       // the Q entries concerned; give every marked entry its canonical FP64 distance
-      if (!a.exact) {
+      if (!qexact) {
         bool any = false;
         for (int b = lane; b < nbv; b += 32) {
           const float db = key_dist(Nk[b]);
@@ -375,7 +422,7 @@ search_kernel(SearchArgs a) {
         int lo = 0, hi = nbv;  // # batch entries before Q[i]
         while (lo < hi) {
           int mid = (lo + hi) >> 1;
-          if (before(Nk[mid], Nx[mid], ki, xi, a.band, a.exact)) lo = mid + 1; else hi = mid;
+          if (before(Nk[mid], Nx[mid], ki, xi, a.band, qexact)) lo = mid + 1; else hi = mid;
         }
         int pos = i + lo;
         if (pos < nlen) { nxt.k[pos] = ki; nxt.x[pos] = xi; nxt.e[pos] = cur.e[i]; }
@@ -389,7 +436,7 @@ search_kernel(SearchArgs a) {
         int lo = 0, hi = len;  // # Q entries before batch[b]
         while (lo < hi) {
           int mid = (lo + hi) >> 1;
-          if (before(cur.k[mid], cur.x[mid], kb, xb, a.band, a.exact)) lo = mid + 1; else hi = mid;
+          if (before(cur.k[mid], cur.x[mid], kb, xb, a.band, qexact)) lo = mid + 1; else hi = mid;
         }
         int pos = b + lo;
         if (pos < nlen) {
@@ -480,28 +527,75 @@ size_t search_warp_smem(int dpad, int L, int hash_slots) {
   return (b + 15) / 16 * 16;
 }
 
-// The kernel's shared-memory attribute is set by search_blocks_per_sm, which callers run
-// first (outside any stream capture).
-cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s) {
-  size_t sh = (size_t)warps_per_block * a.warp_smem + (a.model ? STOP_BLOCK_BYTES : 0);
+template <typename T, int DW>
+static cudaError_t launch_search_t(const SearchArgs& a, int warps_per_block, int grid,
+                                   cudaStream_t s) {
+  const size_t sh = (size_t)warps_per_block * a.warp_smem + (a.model ? STOP_BLOCK_BYTES : 0);
   count_launch();
-  if (a.dtype == CNG_F32)
-    search_kernel<float><<<grid, warps_per_block * 32, sh, s>>>(a);
-  else
-    search_kernel<__half><<<grid, warps_per_block * 32, sh, s>>>(a);
+  search_kernel<T, DW><<<grid, warps_per_block * 32, sh, s>>>(a);
   return cudaGetLastError();
 }
 
-int search_blocks_per_sm(int dtype, int warps_per_block, size_t smem) {
-  int nb = 0;
-  if (dtype == CNG_F32) {
-    cudaFuncSetAttribute(search_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<float>, warps_per_block * 32, smem);
-  } else {
-    cudaFuncSetAttribute(search_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<__half>, warps_per_block * 32, smem);
+// The kernel's shared-memory attribute is set by search_blocks_per_sm (same dtype and u8w),
+// which callers run first, outside any stream capture.
+cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s) {
+  if (a.dtype != CNG_F32) return launch_search_t<__half, 0>(a, warps_per_block, grid, s);
+  switch (a.U ? a.u8w : 0) {
+    case 8: return launch_search_t<float, 8>(a, warps_per_block, grid, s);
+    case 16: return launch_search_t<float, 16>(a, warps_per_block, grid, s);
+    case 24: return launch_search_t<float, 24>(a, warps_per_block, grid, s);
+    case 32: return launch_search_t<float, 32>(a, warps_per_block, grid, s);
+    default: return launch_search_t<float, 0>(a, warps_per_block, grid, s);
   }
+}
+
+template <typename T, int DW>
+static int bps_t(int warps_per_block, size_t smem) {
+  int nb = 0;
+  cudaFuncSetAttribute(search_kernel<T, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<T, DW>, warps_per_block * 32, smem);
   return nb;
+}
+
+int search_blocks_per_sm(int dtype, int u8w, int warps_per_block, size_t smem) {
+  if (dtype != CNG_F32) return bps_t<__half, 0>(warps_per_block, smem);
+  switch (u8w) {
+    case 8: return bps_t<float, 8>(warps_per_block, smem);
+    case 16: return bps_t<float, 16>(warps_per_block, smem);
+    case 24: return bps_t<float, 24>(warps_per_block, smem);
+    case 32: return bps_t<float, 32>(warps_per_block, smem);
+    default: return bps_t<float, 0>(warps_per_block, smem);
+  }
+}
+
+// One warp per query: flag[q] = 0 if every coordinate is an integer in [vmin, vmax], else 1;
+// with out != null also the 8-bit row out[q][c] = x[q][c] - vmin (0 in the padding).
+__global__ void query_check_kernel(const float* __restrict__ Q, int64_t nq, int d, float vmin,
+                                   float vmax, int u8w, uint8_t* __restrict__ out,
+                                   uint8_t* __restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = w0; q < nq; q += nw) {
+    bool bad = false;
+    for (int c = lane; c < d; c += 32) {
+      const float x = Q[q * d + c];
+      bad |= !(x == rintf(x)) || !(x >= vmin && x <= vmax);
+      if (out) out[q * (u8w * 4) + c] = (uint8_t)(int)fminf(fmaxf(x - vmin, 0.f), 255.f);
+    }
+    if (out)
+      for (int c = d + lane; c < u8w * 4; c += 32) out[q * (u8w * 4) + c] = 0;
+    const unsigned b = __ballot_sync(FULL, bad);
+    if (lane == 0) flag[q] = b ? 1 : 0;
+  }
+}
+
+cudaError_t launch_query_check(const float* Q, int64_t nq, int d, float vmin, float vmax, int u8w,
+                               uint8_t* out, uint8_t* flag, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nq * 32 + 255) / 256, (int64_t)num_sms() * 8));
+  count_launch();
+  query_check_kernel<<<grid, 256, 0, s>>>(Q, nq, d, vmin, vmax, u8w, out, flag);
+  return cudaGetLastError();
 }
 
 }  // namespace cng

@@ -94,3 +94,20 @@ def test_search_launch_shapes_and_autotune():
     assert (a["stats"]["warps_per_block"], a["stats"]["hash_slots"]) == \
         (b["stats"]["warps_per_block"], b["stats"]["hash_slots"])
     cng.cng_free(idx)
+
+
+def test_search_mixed_query_exactness():
+    """Integer data: integer queries inside the data's range take the exact integer path
+    (8-bit rows); non-integer or out-of-range queries take the FP32 path with FP64 near-tie
+    decisions.  A batch mixing both gives the oracle's ids and hops for every query."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate("sift", 4000, 128, seed=8)
+    Q = synth.generate("sift", 300, 128, seed=1008)
+    Q[100:200] += 0.37                      # not integers
+    Q[200:250, 0] = float(X.max()) + 3.0    # outside the data's range
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=16, L=64)
+    assert st["exact_int"] == 1
+    _search_check(X, Q, idx, cng, 10, 32)
+    _search_check(X, Q, idx, cng, 10, 32, use_graph=True)
+    cng.cng_free(idx)
