@@ -159,6 +159,40 @@ CNG_DEV float group_sqdist(const float* qv, const uint4* qu, uint32_t qn, const 
   }
 }
 
+// One lane's exact squared distance to 8-bit row v: the whole row in DW / 4 independent 16-byte
+// loads, then |q|^2 + |v|^2 - 2 <q, v> in integers.
+template <int DW>
+CNG_DEV float u8_lane_sqdist(const uint4* qu, uint32_t qn, const uint8_t* __restrict__ U, int64_t v) {
+  const uint4* r = reinterpret_cast<const uint4*>(U + v * (DW * 4));
+  uint4 x[DW / 4];
+#pragma unroll
+  for (int q = 0; q < DW / 4; ++q) x[q] = __ldg(r + q);
+  uint32_t dot = 0, nv = 0;
+#pragma unroll
+  for (int q = 0; q < DW / 4; ++q) {
+    const uint4 y = qu[q];
+    dot = __dp4a(x[q].x, y.x, dot); dot = __dp4a(x[q].y, y.y, dot);
+    dot = __dp4a(x[q].z, y.z, dot); dot = __dp4a(x[q].w, y.w, dot);
+    nv = __dp4a(x[q].x, x[q].x, nv); nv = __dp4a(x[q].y, x[q].y, nv);
+    nv = __dp4a(x[q].z, x[q].z, nv); nv = __dp4a(x[q].w, x[q].w, nv);
+  }
+  return (float)(qn + nv - 2u * dot);
+}
+
+// Ascending bitonic sort of one 64-bit key per lane across the warp (lane i ends with the
+// i-th smallest).
+CNG_DEV uint64_t warp_sort32(uint64_t key, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(FULL, key, j);
+      const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+      key = take_min ? (o < key ? o : key) : (o > key ? o : key);
+    }
+  return key;
+}
+
 template <typename T, int DW>
 __global__ void __launch_bounds__(256, 2)
 search_kernel(SearchArgs a) {
@@ -265,12 +299,11 @@ search_kernel(SearchArgs a) {
       __syncwarp();
       if (lane == 0) cur.e[idx] = 1;
       ++hops;
-      const int du = a.deg[u];
-      // fresh neighbours -> Nv[0..nb)
+      // fresh neighbours -> Nv[0..nb); rows hold -1 past the degree, so the row alone is read
       int nb = 0;
       for (int r = 0; r < a.R; r += 32) {
         int j = r + lane;
-        int32_t v = j < du ? a.adj[(int64_t)u * a.R + j] : -1;
+        int32_t v = j < a.R ? a.adj[(int64_t)u * a.R + j] : -1;
         bool fresh = v >= 0 && visit(H, hmask, v);
         unsigned bal = __ballot_sync(FULL, fresh);
         if (fresh) Nv[nb + __popc(bal & ((1u << lane) - 1))] = v;
@@ -282,6 +315,24 @@ search_kernel(SearchArgs a) {
       bool chg = false;     // the first min(k, |Q|) ids changed
       do {                  // merge of the hop's new points (skipped when there are none)
       if (nb == 0) break;
+      int P2;
+      bool sorted = false;
+      if constexpr (DW > 0) {
+        if (use8 && nb <= 32) {  // one lane per neighbour, keys sorted in registers
+          uint64_t key = ~0ull;
+          if (lane < nb) {
+            const int32_t v = Nv[lane];
+            key = pack_key(u8_lane_sqdist<DW>(qu, qn, a.U, v), v);
+          }
+          key = warp_sort32(key, lane);
+          Nk[lane] = key;
+          Nx[lane] = __longlong_as_double(0x7ff8000000000000ll);
+          P2 = 32;
+          sorted = true;
+          __syncwarp();
+        }
+      }
+      if (!sorted) {
       // FP32 distances, 4 per round
       for (int b0 = 0; b0 < nb; b0 += 32 / SQ_G) {
         int b = b0 + grp;
@@ -293,7 +344,7 @@ search_kernel(SearchArgs a) {
           Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
         }
       }
-      int P2 = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
+      P2 = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
       for (int b = nb + lane; b < P2; b += 32) {
         Nk[b] = ~0ull;
         Nx[b] = __longlong_as_double(0x7ff8000000000000ll);
@@ -312,6 +363,7 @@ search_kernel(SearchArgs a) {
           }
           __syncwarp();
         }
+      }  // !sorted
       // drop batch entries already in Q (exact key match; only when the filter lost them)
       int nbv = nb;
       for (int b = lane; b < nb; b += 32) {
