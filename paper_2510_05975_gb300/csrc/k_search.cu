@@ -27,6 +27,7 @@ namespace cng {
 
 constexpr int SQ_G = 8;
 constexpr int SQ_MAXB = 128;  // batch capacity (row stride <= 128)
+constexpr int SQ_ROWSLOTS = 3;  // 32-lane slices of an adjacency row (row stride R + 8 <= 96)
 
 struct QEnt {
   uint64_t* k;   // keys
@@ -194,7 +195,7 @@ CNG_DEV uint64_t warp_sort32(uint64_t key, int lane) {
 }
 
 template <typename T, int DW>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 4)
 search_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -280,6 +281,10 @@ search_kernel(SearchArgs a) {
     // every point is explored at most once, so n hops bound a correct search; the cap keeps a
     // corrupted queue from looping
     const int hop_cap = a.max_hops > 0 ? a.max_hops : (int)min(a.n, (int64_t)0x3fffffff);
+    // adjacency row of the predicted next hop vertex, loaded during the previous hop's merge
+    // (used only if the prediction holds; rows have at most SQ_ROWSLOTS * 32 slots)
+    int32_t pf_u = -1;
+    int32_t pf[SQ_ROWSLOTS];
     for (;;) {
       // first unexplored
       int idx = -1;
@@ -300,10 +305,17 @@ search_kernel(SearchArgs a) {
       if (lane == 0) cur.e[idx] = 1;
       ++hops;
       // fresh neighbours -> Nv[0..nb); rows hold -1 past the degree, so the row alone is read
+      int32_t row[SQ_ROWSLOTS];
+      const bool hit = u == pf_u;
+#pragma unroll
+      for (int r = 0; r < SQ_ROWSLOTS; ++r) {
+        const int j = r * 32 + lane;
+        row[r] = hit ? pf[r] : (j < a.R ? a.adj[(int64_t)u * a.R + j] : -1);
+      }
       int nb = 0;
-      for (int r = 0; r < a.R; r += 32) {
-        int j = r + lane;
-        int32_t v = j < a.R ? a.adj[(int64_t)u * a.R + j] : -1;
+#pragma unroll
+      for (int r = 0; r < SQ_ROWSLOTS; ++r) {
+        const int32_t v = row[r];
         bool fresh = v >= 0 && visit(H, hmask, v);
         unsigned bal = __ballot_sync(FULL, fresh);
         if (fresh) Nv[nb + __popc(bal & ((1u << lane) - 1))] = v;
@@ -364,6 +376,25 @@ search_kernel(SearchArgs a) {
           __syncwarp();
         }
       }  // !sorted
+      {  // predict the next hop vertex (old queue's next unexplored vs the batch's minimum) and
+         // start loading its adjacency row
+        int nidx = -1;
+        for (int b = 0; b < len && nidx < 0; b += 32) {
+          const int t = b + lane;
+          const unsigned bal = __ballot_sync(FULL, t < len && !cur.e[t]);
+          if (bal) nidx = b + __ffs(bal) - 1;
+        }
+        uint64_t kn = nidx >= 0 ? cur.k[nidx] : ~0ull;
+        if (Nk[0] < kn) kn = Nk[0];
+        pf_u = kn == ~0ull ? -1 : key_id(kn);
+        if (pf_u >= 0) {
+#pragma unroll
+          for (int r = 0; r < SQ_ROWSLOTS; ++r) {
+            const int j = r * 32 + lane;
+            pf[r] = j < a.R ? a.adj[(int64_t)pf_u * a.R + j] : -1;
+          }
+        }
+      }
       // drop batch entries already in Q (exact key match; only when the filter lost them)
       int nbv = nb;
       for (int b = lane; b < nb; b += 32) {
