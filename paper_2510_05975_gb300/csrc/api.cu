@@ -107,14 +107,16 @@ struct cng_index {
   uint8_t* qbuf = nullptr;       // per-search query flags + 8-bit query rows (grown on demand)
   size_t qbuf_cap = 0;
   // search scratch
-  int* counter = nullptr;
+  int* counter = nullptr;        // SEARCH_COUNTER_INTS
+  int32_t* defer = nullptr;      // queries left to the general search kernel (grown on demand)
+  int64_t defer_cap = 0;
   unsigned long long* tot = nullptr;
   uint32_t* status = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream for CUDA-graph capture
   std::mutex mu;
   struct GraphEntry {
     SearchArgs args;
-    int wpb, grid;
+    SearchPlan plan;
     cudaStream_t stream;
     cudaGraphExec_t exec;
   };
@@ -123,7 +125,7 @@ struct cng_index {
 
 // Autotuned search launch shapes, shared by every index of the same shape in the process.
 struct TunedShape {
-  int dev, dtype, dpad, rs, L, mode;  // key
+  int dev, dtype, dpad, rs, u8w, L, mode;  // key
   int wpb, hash;                      // warps per block, visited-filter slots
 };
 static std::mutex g_tune_mu;
@@ -160,6 +162,7 @@ extern "C" void cng_free(cng_index* ix) {
   cudaFree(ix->u8);
   cudaFree(ix->qbuf);
   cudaFree(ix->counter);
+  cudaFree(ix->defer);
   cudaFree(ix->tot);
   cudaFree(ix->status);
   if (ix->cap_stream) cudaStreamDestroy(ix->cap_stream);
@@ -632,7 +635,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     CK(pool.alloc(&rdist, (size_t)n * kc));
     CK(pool.alloc(&best, (size_t)n));
     CK(pool.alloc(&counts, 4));
-    CK(pool.alloc(&sc_counter, 1));
+    CK(pool.alloc(&sc_counter, SEARCH_COUNTER_INTS));
     CK(pool.alloc(&sc_tot, 4));
     CK(pool.alloc(&sc_status, 1));
     CK(cudaMemsetAsync(sc_status, 0, 4, s));
@@ -663,8 +666,6 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       sa.nq = nu;
       sa.k = kc;
       sa.L = Lc;
-      sa.hash_slots = 1024;
-      sa.warp_smem = search_warp_smem(dpad, Lc, sa.hash_slots);
       sa.band = band;
       sa.exact = exact;
       if (u8 && exact) {  // stored points as queries: exact 8-bit rows
@@ -677,11 +678,11 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       sa.dists = rdist;
       sa.tot = sc_tot;
       sa.status = sc_status;
-      const int wpb = 4;
-      int bps = search_blocks_per_sm(dtype, sa.U ? sa.u8w : 0, wpb, (size_t)wpb * sa.warp_smem);
-      if (bps < 1) return fail(CNG_E_UNSUPPORTED, "connectivity search shape does not fit");
-      CK(cudaMemsetAsync(sc_counter, 0, sizeof(int), s));
-      CK(launch_search(sa, wpb, num_sms() * bps, s));
+      SearchPlan plan;  // stored points are exact queries: nothing is deferred
+      if (!search_plan(sa, 4, 1024, &plan))
+        return fail(CNG_E_UNSUPPORTED, "connectivity search shape does not fit");
+      CK(cudaMemsetAsync(sc_counter, 0, SEARCH_COUNTER_INTS * sizeof(int), s));
+      CK(launch_search(sa, plan, s));
       CK(launch_pick_add(U, rid, nu, kc, best, n, adj, deg, Rs, counts + 3, s));
       CK(cudaMemcpyAsync(&hc_counts[3], counts + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -736,7 +737,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     ix->fdeg = fdeg;
     pool.release(fdeg);
   }
-  if (cudaMalloc(&ix->counter, sizeof(int)) != cudaSuccess ||
+  if (cudaMalloc(&ix->counter, SEARCH_COUNTER_INTS * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ix->tot, 4 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&ix->status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ix->status, 0, sizeof(uint32_t)) != cudaSuccess ||
@@ -800,6 +801,17 @@ extern "C" cng_status cng_lists(const cng_index* ix, const int32_t** cand, const
 
 // Exact data: per-query exactness flags and, with 8-bit rows, the queries as 8-bit rows
 // (a buffer of the index, grown on demand; searches on one index run one at a time).
+// Grows the deferred-query list of ix to at least nq entries (callers hold ix->mu).
+static cudaError_t ensure_defer(cng_index* ix, int64_t nq) {
+  if (ix->defer_cap >= nq) return cudaSuccess;
+  cudaFree(ix->defer);
+  ix->defer = nullptr;
+  ix->defer_cap = 0;
+  const cudaError_t e = cudaMalloc(&ix->defer, (size_t)nq * sizeof(int32_t));
+  if (e == cudaSuccess) ix->defer_cap = nq;
+  return e;
+}
+
 static cng_status search_queries(cng_index* ix, const float* qd, int64_t nq, SearchArgs* a,
                                  cudaStream_t s) {
   if (!ix->exact || ix->dtype != CNG_F32 || nq == 0) return CNG_OK;
@@ -894,23 +906,19 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     a.zthr = std::log(P.threshold / (1.f - P.threshold));
     a.check_every = P.check_every;
   }
-  const size_t model_bytes = a.model ? STOP_BLOCK_BYTES : 0;
-  // blocks per SM of a launch shape (0: does not fit)
-  auto shape_bps = [&](int w, int h) {
-    const size_t ws = search_warp_smem(ix->dpad, L, h);
-    if ((size_t)w * ws + model_bytes > 200 * 1024) return 0;
-    return search_blocks_per_sm(ix->dtype, a.U ? a.u8w : 0, w, (size_t)w * ws + model_bytes);
-  };
   std::lock_guard<std::mutex> lock(ix->mu);
   {
     cng_status qs = search_queries(ix, qd, nq, &a, s);
     if (qs != CNG_OK) return qs;
   }
+  CK(ensure_defer(ix, nq));
+  a.defer = ix->defer;
+  SearchPlan plan;
   int wpb, hash;
   if (P.warps_per_block > 0) {  // caller's queries per CTA, default visited-filter size
     wpb = std::min(P.warps_per_block, 8);
     hash = L <= 64 ? 1024 : 2048;
-    while (wpb > 1 && shape_bps(wpb, hash) < 1) wpb >>= 1;
+    while (wpb > 1 && !search_plan(a, wpb, hash, &plan)) wpb >>= 1;
   } else {
     // autotune once per (L, mode): queries per CTA (warps per block) and visited-filter size,
     // each candidate timed on up to 4,096 of these queries; the results do not depend on it
@@ -920,7 +928,7 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     std::lock_guard<std::mutex> tl(g_tune_mu);
     auto it = std::find_if(g_tuned.begin(), g_tuned.end(), [&](const TunedShape& t) {
       return t.dev == dev && t.dtype == ix->dtype && t.dpad == ix->dpad && t.rs == ix->rs &&
-             t.L == L && t.mode == P.mode;
+             t.u8w == (a.U ? a.u8w : 0) && t.L == L && t.mode == P.mode;
     });
     if (it != g_tuned.end()) {
       wpb = it->wpb;
@@ -937,15 +945,13 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
       for (int h : {512, 1024, 2048}) {
         if (h < 2 * L) continue;
         for (int w : {1, 2, 4, 8}) {
-          const int b = shape_bps(w, h);
-          if (b < 1) continue;
-          t.hash_slots = h;
-          t.warp_smem = search_warp_smem(ix->dpad, L, h);
+          SearchPlan tp;
+          if (!search_plan(t, w, h, &tp)) continue;
           float ms = 0.f;
           for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
-            CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
+            CK(cudaMemsetAsync(ix->counter, 0, SEARCH_COUNTER_INTS * sizeof(int), s));
             cudaEventRecord(t0, s);
-            CK(launch_search(t, w, num_sms() * b, s));
+            CK(launch_search(t, tp, s));
             cudaEventRecord(t1, s);
             CK(cudaEventSynchronize(t1));
             cudaEventElapsedTime(&ms, t0, t1);
@@ -960,14 +966,11 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
       cudaEventDestroy(t0);
       cudaEventDestroy(t1);
       if (!wpb) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
-      g_tuned.push_back({dev, ix->dtype, ix->dpad, ix->rs, L, P.mode, wpb, hash});
+      g_tuned.push_back({dev, ix->dtype, ix->dpad, ix->rs, a.U ? a.u8w : 0, L, P.mode, wpb, hash});
     }
   }
-  a.hash_slots = hash;
-  a.warp_smem = search_warp_smem(ix->dpad, L, hash);
-  int bps = shape_bps(wpb, hash);
-  if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
-  int grid = num_sms() * bps;
+  if (!search_plan(a, wpb, hash, &plan))
+    return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -976,24 +979,25 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   if (P.use_graph) {
     cudaGraphExec_t exec = nullptr;
     for (auto& g : ix->graphs)
-      if (g.stream == s && g.wpb == wpb && g.grid == grid && !memcmp(&g.args, &a, sizeof(a))) exec = g.exec;
+      if (g.stream == s && !memcmp(&g.plan, &plan, sizeof(plan)) && !memcmp(&g.args, &a, sizeof(a)))
+        exec = g.exec;
     if (!exec) {
       // capture on the index's private stream (the legacy default stream cannot be captured);
       // the instantiated graph is then launched on the caller's stream
       cudaGraph_t graph;
       cudaStream_t cs = ix->cap_stream;
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      cudaMemsetAsync(ix->counter, 0, sizeof(int), cs);
-      launch_search(a, wpb, grid, cs);
+      cudaMemsetAsync(ix->counter, 0, SEARCH_COUNTER_INTS * sizeof(int), cs);
+      launch_search(a, plan, cs);
       CK(cudaStreamEndCapture(cs, &graph));
       CK(cudaGraphInstantiate(&exec, graph, 0));
       cudaGraphDestroy(graph);
-      ix->graphs.push_back({a, wpb, grid, s, exec});
+      ix->graphs.push_back({a, plan, s, exec});
     }
     CK(cudaGraphLaunch(exec, s));
   } else {
-    CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
-    CK(launch_search(a, wpb, grid, s));
+    CK(cudaMemsetAsync(ix->counter, 0, SEARCH_COUNTER_INTS * sizeof(int), s));
+    CK(launch_search(a, plan, s));
   }
   cudaEventRecord(e1, s);
   if (host_out) {
@@ -1220,8 +1224,6 @@ static cng_status run_trace(cng_index* ix, const float* qd, int64_t nq, int k, i
   a.nq = nq;
   a.k = k;
   a.L = L;
-  a.hash_slots = L <= 64 ? 1024 : 2048;
-  a.warp_smem = search_warp_smem(ix->dpad, L, a.hash_slots);
   a.band = ix->band;
   a.exact = ix->exact;
   a.counter = ix->counter;
@@ -1236,11 +1238,13 @@ static cng_status run_trace(cng_index* ix, const float* qd, int64_t nq, int k, i
   a.check_every = 1;
   cng_status qs = search_queries(ix, qd, nq, &a, s);  // callers hold ix->mu
   if (qs != CNG_OK) return qs;
-  const int wpb = 4;
-  int bps = search_blocks_per_sm(ix->dtype, a.U ? a.u8w : 0, wpb, (size_t)wpb * a.warp_smem);
-  if (bps < 1) return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
-  CK(cudaMemsetAsync(ix->counter, 0, sizeof(int), s));
-  CK(launch_search(a, wpb, num_sms() * bps, s));
+  CK(ensure_defer(ix, nq));
+  a.defer = ix->defer;
+  SearchPlan plan;
+  if (!search_plan(a, 4, L <= 64 ? 1024 : 2048, &plan))
+    return fail(CNG_E_UNSUPPORTED, "search shape does not fit in shared memory");
+  CK(cudaMemsetAsync(ix->counter, 0, SEARCH_COUNTER_INTS * sizeof(int), s));
+  CK(launch_search(a, plan, s));
   return CNG_OK;
 }
 

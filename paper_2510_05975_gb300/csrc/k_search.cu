@@ -22,12 +22,12 @@
 #include "cng_internal.h"
 #include "device_common.cuh"
 #include "search_internal.h"
+#include "search_device.cuh"
 
 namespace cng {
 
 constexpr int SQ_G = 8;
 constexpr int SQ_MAXB = 128;  // batch capacity (row stride <= 128)
-constexpr int SQ_ROWSLOTS = 3;  // 32-lane slices of an adjacency row (row stride R + 8 <= 96)
 
 struct QEnt {
   uint64_t* k;   // keys
@@ -47,88 +47,9 @@ CNG_DEV bool before(uint64_t ka, double xa, uint64_t kb, double xb, float band, 
   return ka < kb;
 }
 
-CNG_DEV uint32_t hash32(uint32_t x) {
-  x ^= x >> 16;
-  x *= 0x7feb352dU;
-  x ^= x >> 15;
-  x *= 0x846ca68bU;
-  x ^= x >> 16;
-  return x;
-}
-
-// Returns true if v was not known to be visited (then it is recorded if there is room).
-CNG_DEV bool visit(int32_t* H, int hmask, int32_t v) {
-  uint32_t h = hash32((uint32_t)v) & hmask;
-  for (int p = 0; p < 8; ++p) {
-    int32_t* slot = H + ((h + p) & hmask);
-    int32_t cur = *slot;
-    if (cur == v) return false;
-    if (cur == -1) {
-      int32_t old = atomicCAS(slot, -1, v);
-      if (old == -1) return true;
-      if (old == v) return false;
-    }
-  }
-  return true;
-}
-
 template <typename T>
 CNG_DEV double canon_q(const float* __restrict__ q, const T* __restrict__ x, int d) {
   return canon_dist(q, x, d);
-}
-
-CNG_DEV float lgf(float x) { return logf(fmaxf(x, 1e-30f)); }
-
-// The stop model in shared memory: BF16 weights (inputs-major, so lane o reads W[i][o]
-// conflict-free), FP32 biases and input normalisation.
-struct StopSmem {
-  const __nv_bfloat16* W1T;  // [16][64]
-  const __nv_bfloat16* W2T;  // [64][64]
-  const float *b1, *b2, *w3, *b3, *mu, *sg;
-};
-CNG_DEV StopSmem stop_smem(const unsigned char* mb) {
-  StopSmem m;
-  m.W1T = reinterpret_cast<const __nv_bfloat16*>(mb);
-  m.W2T = m.W1T + 16 * 64;
-  const float* f = reinterpret_cast<const float*>(m.W2T + 64 * 64);
-  m.b1 = f;
-  m.b2 = f + 64;
-  m.w3 = f + 128;
-  m.b3 = f + 192;
-  m.mu = f + 196;
-  m.sg = f + 212;
-  return m;
-}
-
-// Logit of the 16-64-64-1 ReLU network for the features held by lanes 0..15 (FP32 math on
-// BF16 weights); every lane returns the same value.
-CNG_DEV float mlp_logit(const StopSmem& m, float f, int lane) {
-  const float xh = lane < 16 ? (f - m.mu[lane]) / m.sg[lane] : 0.f;
-  float a0 = m.b1[lane], a1 = m.b1[lane + 32];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const float xi = __shfl_sync(FULL, xh, i);
-    a0 = fmaf(__bfloat162float(m.W1T[i * 64 + lane]), xi, a0);
-    a1 = fmaf(__bfloat162float(m.W1T[i * 64 + lane + 32]), xi, a1);
-  }
-  const float h0 = fmaxf(a0, 0.f), h1 = fmaxf(a1, 0.f);
-  float c0 = m.b2[lane], c1 = m.b2[lane + 32];
-#pragma unroll 8
-  for (int i = 0; i < 32; ++i) {
-    const float hi = __shfl_sync(FULL, h0, i);
-    c0 = fmaf(__bfloat162float(m.W2T[i * 64 + lane]), hi, c0);
-    c1 = fmaf(__bfloat162float(m.W2T[i * 64 + lane + 32]), hi, c1);
-  }
-#pragma unroll 8
-  for (int i = 0; i < 32; ++i) {
-    const float hi = __shfl_sync(FULL, h1, i);
-    c0 = fmaf(__bfloat162float(m.W2T[(i + 32) * 64 + lane]), hi, c0);
-    c1 = fmaf(__bfloat162float(m.W2T[(i + 32) * 64 + lane + 32]), hi, c1);
-  }
-  float z = m.w3[lane] * fmaxf(c0, 0.f) + m.w3[lane + 32] * fmaxf(c1, 0.f);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(FULL, z, o);
-  return z + m.b3[0];
 }
 
 // Squared distance of the query to row v by an 8-lane group, every lane of the group gets it.
@@ -158,40 +79,6 @@ CNG_DEV float group_sqdist(const float* qv, const uint4* qu, uint32_t qn, const 
     }
     return (float)(qn + nv - 2u * dot);
   }
-}
-
-// One lane's exact squared distance to 8-bit row v: the whole row in DW / 4 independent 16-byte
-// loads, then |q|^2 + |v|^2 - 2 <q, v> in integers.
-template <int DW>
-CNG_DEV float u8_lane_sqdist(const uint4* qu, uint32_t qn, const uint8_t* __restrict__ U, int64_t v) {
-  const uint4* r = reinterpret_cast<const uint4*>(U + v * (DW * 4));
-  uint4 x[DW / 4];
-#pragma unroll
-  for (int q = 0; q < DW / 4; ++q) x[q] = __ldg(r + q);
-  uint32_t dot = 0, nv = 0;
-#pragma unroll
-  for (int q = 0; q < DW / 4; ++q) {
-    const uint4 y = qu[q];
-    dot = __dp4a(x[q].x, y.x, dot); dot = __dp4a(x[q].y, y.y, dot);
-    dot = __dp4a(x[q].z, y.z, dot); dot = __dp4a(x[q].w, y.w, dot);
-    nv = __dp4a(x[q].x, x[q].x, nv); nv = __dp4a(x[q].y, x[q].y, nv);
-    nv = __dp4a(x[q].z, x[q].z, nv); nv = __dp4a(x[q].w, x[q].w, nv);
-  }
-  return (float)(qn + nv - 2u * dot);
-}
-
-// Ascending bitonic sort of one 64-bit key per lane across the warp (lane i ends with the
-// i-th smallest).
-CNG_DEV uint64_t warp_sort32(uint64_t key, int lane) {
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1)
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const uint64_t o = __shfl_xor_sync(FULL, key, j);
-      const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
-      key = take_min ? (o < key ? o : key) : (o > key ? o : key);
-    }
-  return key;
 }
 
 template <typename T, int DW>
@@ -229,11 +116,15 @@ search_kernel(SearchArgs a) {
   const int g = lane % SQ_G, grp = lane / SQ_G;
   unsigned long long t_ndc = 0, t_hops = 0, t_f64 = 0, t_stop = 0;
 
+  // work list: all queries, or the ones the register-queue kernel deferred
+  const int64_t nwork = a.qlist ? (int64_t)*a.nq_dev : a.nq;
+  int* const head = a.qlist ? a.counter + 2 : a.counter;
   for (;;) {
     int qi = 0;
-    if (lane == 0) qi = atomicAdd(a.counter, 1);
+    if (lane == 0) qi = atomicAdd(head, 1);
     qi = __shfl_sync(FULL, qi, 0);
-    if (qi >= a.nq) break;
+    if (qi >= nwork) break;
+    if (a.qlist) qi = a.qlist[qi];
     // exact queries: the data's FP32 squared distances are exact integers and this query is an
     // integer vector inside the data's range (stored points always are); others resolve
     // near-ties in FP64
@@ -595,9 +486,7 @@ search_kernel(SearchArgs a) {
     atomicAdd(&a.tot[0], t_ndc);
     atomicAdd(&a.tot[1], t_hops);
   }
-  // t_f64 is per lane
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t_f64 += __shfl_xor_sync(FULL, t_f64, o);
+  // t_f64 counts the same warp-wide ballots in every lane
   if (lane == 0) {
     if (t_f64) atomicAdd(&a.tot[2], t_f64);
     if (t_stop) atomicAdd(&a.tot[3], t_stop);
@@ -611,7 +500,7 @@ size_t search_warp_smem(int dpad, int L, int hash_slots) {
 }
 
 template <typename T, int DW>
-static cudaError_t launch_search_t(const SearchArgs& a, int warps_per_block, int grid,
+static cudaError_t launch_general_t(const SearchArgs& a, int warps_per_block, int grid,
                                    cudaStream_t s) {
   const size_t sh = (size_t)warps_per_block * a.warp_smem + (a.model ? STOP_BLOCK_BYTES : 0);
   count_launch();
@@ -621,15 +510,63 @@ static cudaError_t launch_search_t(const SearchArgs& a, int warps_per_block, int
 
 // The kernel's shared-memory attribute is set by search_blocks_per_sm (same dtype and u8w),
 // which callers run first, outside any stream capture.
-cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s) {
-  if (a.dtype != CNG_F32) return launch_search_t<__half, 0>(a, warps_per_block, grid, s);
+cudaError_t launch_search_general(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s) {
+  if (a.dtype != CNG_F32) return launch_general_t<__half, 0>(a, warps_per_block, grid, s);
   switch (a.U ? a.u8w : 0) {
-    case 8: return launch_search_t<float, 8>(a, warps_per_block, grid, s);
-    case 16: return launch_search_t<float, 16>(a, warps_per_block, grid, s);
-    case 24: return launch_search_t<float, 24>(a, warps_per_block, grid, s);
-    case 32: return launch_search_t<float, 32>(a, warps_per_block, grid, s);
-    default: return launch_search_t<float, 0>(a, warps_per_block, grid, s);
+    case 8: return launch_general_t<float, 8>(a, warps_per_block, grid, s);
+    case 16: return launch_general_t<float, 16>(a, warps_per_block, grid, s);
+    case 24: return launch_general_t<float, 24>(a, warps_per_block, grid, s);
+    case 32: return launch_general_t<float, 32>(a, warps_per_block, grid, s);
+    default: return launch_general_t<float, 0>(a, warps_per_block, grid, s);
   }
+}
+
+bool search_plan(SearchArgs& a, int wpb, int hash_slots, SearchPlan* p) {
+  constexpr size_t kMaxBlockSmem = 200 * 1024;
+  const size_t extra_smem = a.model ? STOP_BLOCK_BYTES : 0;
+  *p = SearchPlan{};
+  a.hash_slots = hash_slots;
+  a.warp_smem = search_warp_smem(a.dpad, a.L, hash_slots);
+  a.warp_smem_fast = 0;
+  // the register-queue kernel: exact data with 8-bit rows, L <= 256, and row stride <= 96
+  int qs = 0;
+  if (a.U && a.exact && a.dtype == CNG_F32 && a.R <= SQ_ROWSLOTS * 32 && a.k <= a.L)
+    qs = a.L <= 32 ? 1 : a.L <= 64 ? 2 : a.L <= 128 ? 4 : a.L <= 256 ? 8 : 0;
+  if (qs) {
+    a.warp_smem_fast = search_fast_warp_smem(a.u8w, hash_slots);
+    const size_t sh = (size_t)wpb * a.warp_smem_fast + extra_smem;
+    const int b = sh <= kMaxBlockSmem ? search_fast_blocks_per_sm(a.u8w, qs, wpb, sh) : 0;
+    if (b < 1) return false;
+    p->grid = num_sms() * b;
+    p->fast_qs = qs;
+  }
+  // the general kernel: every query, or the deferred ones (same warps per block when it fits)
+  int w = wpb;
+  int b = 0;
+  for (; w >= 1; w >>= 1) {
+    const size_t sh = (size_t)w * a.warp_smem + extra_smem;
+    b = sh <= kMaxBlockSmem ? search_blocks_per_sm(a.dtype, a.U ? a.u8w : 0, w, sh) : 0;
+    if (b >= 1 || qs == 0) break;
+  }
+  if (b < 1) return false;
+  if (qs) {
+    p->grid_defer = num_sms() * b;
+    p->wpb_defer = w;
+  } else {
+    p->grid = num_sms() * b;
+  }
+  p->wpb = wpb;
+  return true;
+}
+
+cudaError_t launch_search(const SearchArgs& a, const SearchPlan& p, cudaStream_t s) {
+  if (p.fast_qs == 0) return launch_search_general(a, p.wpb, p.grid, s);
+  cudaError_t e = launch_search_fast(a, p.fast_qs, p.wpb, p.grid, s);
+  if (e != cudaSuccess) return e;
+  SearchArgs g = a;
+  g.qlist = a.defer;
+  g.nq_dev = a.counter + 1;
+  return launch_search_general(g, p.wpb_defer, p.grid_defer, s);
 }
 
 template <typename T, int DW>

@@ -1,0 +1,397 @@
+// k_search_fast.cu -- batched beam search of Alg. 1 with each warp's queue in registers, sm_103a.
+//
+// Data stored as exact 8-bit rows (integer coordinates spanning <= 255, d <= 128) gives every
+// squared distance as an exact integer below 2^24, so the queue order of Alg. 1 -- by distance,
+// then id -- is decided by integer keys alone.  This kernel keeps a warp's queue Q of up to
+// 32 * QS entries in registers, entry 32 s + lane in q[s] of that lane, as 64-bit keys
+//   key = D^2 << 32 | id << 1 | explored
+// whose unsigned order is the (D^2, id) order (ids are below 2^31); KINF pads the tail.
+//
+// One hop: the first unexplored entry u* of Q (one ballot per slot); its out-list (prefetched
+// during the previous hop when the prediction holds); the visited filter; the exact distance of
+// each new point by its own lane; a 32-key bitonic sort of the batch; then the merge of the
+// batch into Q as a single bitonic merge network -- the batch, reversed, is folded into the last
+// slot (the half-cleaner of the bitonic sequence [Q ascending | batch descending]) and
+// log2(32 QS) compare-exchange levels restore the order; entries past L are dropped (Alg. 1's
+// truncation to the L closest).  A hop with more than 32 new points merges them 32 at a time,
+// which gives the same queue because truncation keeps the L smallest of the union either way.
+//
+// The visited filter is lossy only in one direction: a point whose probe slots are all taken is
+// reported as possibly seen.  Such a point may already be in Q, so it is looked up there (binary
+// search over the registers) and dropped when present; a seen point absent from Q lies beyond
+// Q's L-th entry, which never grows, and is cut again by the truncation.
+//
+// Queries that are not exact (non-integer coordinates, or outside the data's range) are
+// appended to a list that the general kernel serves afterwards.
+#include "launch_count.h"
+#include "cng_internal.h"
+#include "device_common.cuh"
+#include "search_internal.h"
+#include "search_device.cuh"
+
+namespace cng {
+namespace {
+
+constexpr uint64_t KINF = ~0ull;
+
+CNG_DEV uint64_t rkey(uint32_t d2, int32_t id) {
+  return ((uint64_t)d2 << 32) | ((uint64_t)(uint32_t)id << 1);
+}
+CNG_DEV int32_t rkey_id(uint64_t k) { return (int32_t)((uint32_t)k >> 1); }
+CNG_DEV float rkey_d2(uint64_t k) { return (float)(uint32_t)(k >> 32); }
+CNG_DEV bool unexplored(uint64_t k) { return k != KINF && !(k & 1); }
+
+// Q entry i (i the same in every lane).
+template <int QS>
+CNG_DEV uint64_t qget(const uint64_t (&q)[QS], int i) {
+  uint64_t v = q[0];
+#pragma unroll
+  for (int s = 1; s < QS; ++s)
+    if ((i >> 5) == s) v = q[s];
+  return __shfl_sync(FULL, v, i & 31);
+}
+
+// Q entry i (i per lane).
+template <int QS>
+CNG_DEV uint64_t qget_lane(const uint64_t (&q)[QS], int i) {
+  uint64_t r = 0;
+#pragma unroll
+  for (int s = 0; s < QS; ++s) {
+    const uint64_t t = __shfl_sync(FULL, q[s], i & 31);
+    if ((i >> 5) == s) r = t;
+  }
+  return r;
+}
+
+// Whether the point of key kb is in Q (binary search on (D^2, id)).
+template <int QS>
+CNG_DEV bool qcontains(const uint64_t (&q)[QS], uint64_t kb) {
+  const uint64_t x = kb >> 1;
+  int pos = 0;
+#pragma unroll
+  for (int step = 16 * QS; step >= 1; step >>= 1)
+    if ((qget_lane<QS>(q, pos + step - 1) >> 1) < x) pos += step;
+  return (qget_lane<QS>(q, pos) >> 1) == x;
+}
+
+// First unexplored entry of Q, or -1 (same in every lane).
+template <int QS>
+CNG_DEV int first_unexplored(const uint64_t (&q)[QS]) {
+  int idx = -1;
+#pragma unroll
+  for (int s = 0; s < QS; ++s) {
+    const unsigned bal = __ballot_sync(FULL, unexplored(q[s]));
+    if (idx < 0 && bal) idx = s * 32 + __ffs(bal) - 1;
+  }
+  return idx;
+}
+
+// Q <- the 32 QS smallest of Q and the batch, sorted; kdesc: the batch sorted descending across
+// the lanes.  [Q ascending | KINF ... KINF, batch descending] is bitonic; its half-cleaner leaves
+// Q unchanged except min(q[QS-1], kdesc), and a bitonic merge of the lower half sorts it.
+template <int QS>
+CNG_DEV void qmerge(uint64_t (&q)[QS], uint64_t kdesc, int lane) {
+  q[QS - 1] = kdesc < q[QS - 1] ? kdesc : q[QS - 1];
+#pragma unroll
+  for (int st = QS / 2; st >= 1; st >>= 1)
+#pragma unroll
+    for (int s = 0; s < QS; ++s)
+      if (!(s & st)) {
+        const uint64_t x = q[s], y = q[s + st];
+        q[s] = x < y ? x : y;
+        q[s + st] = x < y ? y : x;
+      }
+#pragma unroll
+  for (int j = 16; j >= 1; j >>= 1)
+#pragma unroll
+    for (int s = 0; s < QS; ++s) {
+      const uint64_t o = __shfl_xor_sync(FULL, q[s], j);
+      q[s] = (lane & j) ? (o > q[s] ? o : q[s]) : (o < q[s] ? o : q[s]);
+    }
+}
+
+template <int DW, int QS>
+__global__ void __launch_bounds__(256, 4) search_fast_kernel(SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* base = smem + (size_t)warp * a.warp_smem_fast;
+  uint4* qu = reinterpret_cast<uint4*>(base);                     // query as an 8-bit row
+  int32_t* Nv = reinterpret_cast<int32_t*>(base + 128);           // new points of a hop
+  float* hist = reinterpret_cast<float*>(Nv + SQ_ROWSLOTS * 32);  // Dk after the last 64 hops
+  int32_t* H = reinterpret_cast<int32_t*>(hist + 64);             // visited filter
+  StopSmem ms;
+  if (a.model) {
+    unsigned char* mb = smem + (size_t)(blockDim.x >> 5) * a.warp_smem_fast;
+    const int4* src = reinterpret_cast<const int4*>(a.model);
+    int4* dst = reinterpret_cast<int4*>(mb);
+    for (int i = threadIdx.x; i < STOP_BLOCK_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    ms = stop_smem(mb);
+    __syncthreads();
+  }
+  const int hmask = a.hash_slots - 1, L = a.L;
+  unsigned long long t_ndc = 0, t_hops = 0, t_stop = 0;
+
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(a.counter, 1);
+    qi = __shfl_sync(FULL, qi, 0);
+    if (qi >= a.nq) break;
+    if (!a.qids && !(a.qflag && a.qflag[qi] == 0)) {  // not exact: left to the general kernel
+      if (lane == 0) a.defer[atomicAdd(a.counter + 1, 1)] = qi;
+      continue;
+    }
+    const uint8_t* src = a.qids ? a.U + (int64_t)a.qids[qi] * (DW * 4) : a.QU + (int64_t)qi * (DW * 4);
+    uint32_t qn = 0;
+    if (lane < DW / 4) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(src) + lane);
+      qu[lane] = x;
+      qn = __dp4a(x.x, x.x, qn); qn = __dp4a(x.y, x.y, qn);
+      qn = __dp4a(x.z, x.z, qn); qn = __dp4a(x.w, x.w, qn);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qn += __shfl_xor_sync(FULL, qn, o);
+    for (int c = lane; c < a.hash_slots; c += 32) H[c] = -1;
+    __syncwarp();
+    // entry point
+    const uint32_t d0 = u8_lane_d2<DW>(qu, qn, a.U, a.entry);
+    uint64_t q[QS];
+#pragma unroll
+    for (int s = 0; s < QS; ++s) q[s] = KINF;
+    if (lane == 0) {
+      q[0] = rkey(d0, a.entry);
+      H[hash32((uint32_t)a.entry) & hmask] = a.entry;
+    }
+    int len = 1, ndc = 1, hops = 0, flags = 0, tlc = 0;
+    const float D0 = sqrtf((float)d0);
+    if (lane == 0) hist[0] = D0;
+    __syncwarp();
+    // every point is explored at most once, so n hops bound a correct search
+    const int hop_cap = a.max_hops > 0 ? a.max_hops : (int)min(a.n, (int64_t)0x3fffffff);
+    int32_t pf_u = -1;  // predicted next hop vertex and its out-list
+    int32_t pf[SQ_ROWSLOTS];
+    for (;;) {
+      const int idx = first_unexplored<QS>(q);
+      if (idx < 0) break;
+      if (hops >= hop_cap) {
+        flags |= 2;
+        if (a.max_hops == 0 && lane == 0) atomicOr(a.status, ST_BOUNDS);
+        break;
+      }
+      const uint64_t ku = qget<QS>(q, idx);
+#pragma unroll
+      for (int s = 0; s < QS; ++s)
+        if (s == (idx >> 5) && lane == (idx & 31)) q[s] |= 1;
+      const int32_t u = rkey_id(ku);
+      const float Du = sqrtf(rkey_d2(ku));
+      ++hops;
+      // out-list of u (rows hold -1 past the degree)
+      int32_t row[SQ_ROWSLOTS];
+      const bool hit = u == pf_u;
+#pragma unroll
+      for (int r = 0; r < SQ_ROWSLOTS; ++r) {
+        const int j = r * 32 + lane;
+        row[r] = hit ? pf[r] : (j < a.R ? a.adj[(int64_t)u * a.R + j] : -1);
+      }
+      // visited filter -> Nv[0 .. nb); bit 31 marks points whose filter slots were full
+      int nb = 0;
+#pragma unroll
+      for (int r = 0; r < SQ_ROWSLOTS; ++r) {
+        if (r * 32 >= a.R) break;
+        const int32_t v = row[r];
+        const int st = v >= 0 ? visit3(H, hmask, v) : 0;
+        const unsigned bal = __ballot_sync(FULL, st != 0);
+        if (st) Nv[nb + __popc(bal & ((1u << lane) - 1))] = st == 2 ? (int32_t)((uint32_t)v | 0x80000000u) : v;
+        nb += __popc(bal);
+      }
+      __syncwarp();
+      ndc += nb;
+      bool chg = false;  // the first min(k, |Q|) ids changed
+      uint64_t kbs[SQ_ROWSLOTS];
+#pragma unroll
+      for (int ci = 0; ci < SQ_ROWSLOTS; ++ci) {
+        kbs[ci] = KINF;
+        if (ci * 32 >= nb) continue;
+        const int nbc = min(32, nb - ci * 32);
+        const bool has = lane < nbc;
+        const int32_t raw = has ? Nv[ci * 32 + lane] : 0;
+        const int32_t v = raw & 0x7fffffff;
+        uint64_t kb = has ? rkey(u8_lane_d2<DW>(qu, qn, a.U, v), v) : KINF;
+        const bool unsure = has && raw < 0;
+        if (__ballot_sync(FULL, unsure)) {  // possibly seen: drop if in Q (or twice in the batch)
+          const bool in_q = qcontains<QS>(q, kb);
+          const unsigned same = __match_any_sync(FULL, unsure ? v : -1 - lane);
+          if (unsure && (in_q || (same & ((1u << lane) - 1)))) kb = KINF;
+        }
+        kb = warp_sort32(kb, lane);
+        kbs[ci] = kb;
+        if (ci == 0) {  // predict the next hop vertex and start loading its out-list
+          const int nidx = first_unexplored<QS>(q);
+          uint64_t kn = KINF;
+          if (nidx >= 0) kn = qget<QS>(q, nidx);
+          const uint64_t k0 = __shfl_sync(FULL, kb, 0);
+          if (k0 < kn) kn = k0;
+          pf_u = kn == KINF ? -1 : rkey_id(kn);
+          if (pf_u >= 0) {
+#pragma unroll
+            for (int r = 0; r < SQ_ROWSLOTS; ++r) {
+              const int j = r * 32 + lane;
+              pf[r] = j < a.R ? a.adj[(int64_t)pf_u * a.R + j] : -1;
+            }
+          }
+        }
+        const int nv = __popc(__ballot_sync(FULL, kb != KINF));
+        if (nv == 0) continue;
+        const int old_len = len;
+        const uint64_t old_kth = old_len >= a.k ? qget<QS>(q, a.k - 1) : 0;
+        qmerge<QS>(q, __shfl_sync(FULL, kb, 31 - lane), lane);
+        len = min(len + nv, L);
+#pragma unroll
+        for (int s = 0; s < QS; ++s)
+          if (s * 32 + lane >= L) q[s] = KINF;
+        // a new point lands in the first k: when |Q| < k its smallest does; otherwise the old
+        // k-th entry moves down
+        if (old_len < a.k) chg = true;
+        else chg |= (qget<QS>(q, a.k - 1) >> 1) != (old_kth >> 1);
+      }
+      // points of this hop still in Q: those not beyond its last entry
+      int ins = 0;
+      {
+        const uint64_t last = qget<QS>(q, len - 1);
+#pragma unroll
+        for (int ci = 0; ci < SQ_ROWSLOTS; ++ci)
+          ins += __popc(__ballot_sync(FULL, kbs[ci] != KINF && kbs[ci] <= last));
+      }
+      // ---- search state after this hop (learned early stop) ----
+      if (a.trace_feats || a.model) {
+        const int kk = min(a.k, len);
+        const float Dk = sqrtf(rkey_d2(qget<QS>(q, kk - 1)));
+        if (chg) tlc = hops;
+        const bool want_trace = a.trace_feats && hops <= a.max_trace;
+        const bool want_check = a.model && (hops % a.check_every) == 0;
+        float f = 0.f;
+        if (want_trace || want_check) {
+          int U = 0;
+#pragma unroll
+          for (int s = 0; s < QS; ++s) U += __popc(__ballot_sync(FULL, unexplored(q[s])));
+          const float D1 = sqrtf(rkey_d2(qget<QS>(q, 0)));
+          const float DL = sqrtf(rkey_d2(qget<QS>(q, len - 1)));
+          const float lD0 = lgf(D0), lDk = lgf(Dk);
+          if (lane == 0) f = lD0;
+          else if (lane == 1) f = logf(1.f + (float)hops);
+          else if (lane == 2) f = lgf(D1) - lD0;
+          else if (lane == 3) f = lDk - lD0;
+          else if (lane == 4) f = lgf(DL) - lD0;
+          else if (lane == 5) f = lgf(Du) - lDk;
+          else if (lane < 12) {
+            const int h = max(hops - (1 << (lane - 6)), 0);
+            f = lgf(hist[h & 63]) - lDk;
+          } else if (lane == 12) f = logf(1.f + (float)(hops - tlc));
+          else if (lane == 13) f = (float)U / (float)a.L;
+          else if (lane == 14) f = (float)len / (float)a.L;
+          else if (lane == 15) f = (float)ins / (float)a.R;
+          if (want_trace && lane < 16)
+            a.trace_feats[((int64_t)qi * a.max_trace + (hops - 1)) * 16 + lane] = f;
+        }
+        __syncwarp();
+        if (lane == 0) hist[hops & 63] = Dk;
+        __syncwarp();
+        if (want_check && mlp_logit(ms, f, lane) >= a.zthr) {
+          flags |= 4;
+          ++t_stop;
+          break;
+        }
+      }
+    }
+    // results
+#pragma unroll
+    for (int s = 0; s < QS; ++s) {
+      const int t = s * 32 + lane;
+      if (t < a.k) {
+        const bool ok = t < len;
+        a.ids[(int64_t)qi * a.k + t] = ok ? rkey_id(q[s]) : -1;
+        a.dists[(int64_t)qi * a.k + t] = ok ? sqrtf(rkey_d2(q[s])) : INFINITY;
+      }
+    }
+    if (lane == 0) {
+      if (a.ndc) a.ndc[qi] = ndc;
+      if (a.hops) a.hops[qi] = hops;
+      if (a.flags) a.flags[qi] = flags;
+      if (a.tlc) a.tlc[qi] = tlc;
+    }
+    t_ndc += ndc;
+    t_hops += hops;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&a.tot[0], t_ndc);
+    atomicAdd(&a.tot[1], t_hops);
+    if (t_stop) atomicAdd(&a.tot[3], t_stop);
+  }
+}
+
+template <int DW, int QS>
+cudaError_t launch_fast_t(const SearchArgs& a, int wpb, int grid, cudaStream_t s) {
+  const size_t sh = (size_t)wpb * a.warp_smem_fast + (a.model ? STOP_BLOCK_BYTES : 0);
+  count_launch();
+  search_fast_kernel<DW, QS><<<grid, wpb * 32, sh, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DW>
+cudaError_t launch_fast_dw(const SearchArgs& a, int qs, int wpb, int grid, cudaStream_t s) {
+  switch (qs) {
+    case 1: return launch_fast_t<DW, 1>(a, wpb, grid, s);
+    case 2: return launch_fast_t<DW, 2>(a, wpb, grid, s);
+    case 4: return launch_fast_t<DW, 4>(a, wpb, grid, s);
+    case 8: return launch_fast_t<DW, 8>(a, wpb, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int DW, int QS>
+int bps_fast_t(int wpb, size_t smem) {
+  int nb = 0;
+  cudaFuncSetAttribute(search_fast_kernel<DW, QS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_fast_kernel<DW, QS>, wpb * 32, smem);
+  return nb;
+}
+
+template <int DW>
+int bps_fast_dw(int qs, int wpb, size_t smem) {
+  switch (qs) {
+    case 1: return bps_fast_t<DW, 1>(wpb, smem);
+    case 2: return bps_fast_t<DW, 2>(wpb, smem);
+    case 4: return bps_fast_t<DW, 4>(wpb, smem);
+    case 8: return bps_fast_t<DW, 8>(wpb, smem);
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+size_t search_fast_warp_smem(int u8w, int hash_slots) {
+  (void)u8w;  // the query row takes 128 bytes for every width
+  return 128 + SQ_ROWSLOTS * 32 * 4 + 64 * 4 + (size_t)hash_slots * 4;
+}
+
+cudaError_t launch_search_fast(const SearchArgs& a, int qs, int wpb, int grid, cudaStream_t s) {
+  switch (a.u8w) {
+    case 8: return launch_fast_dw<8>(a, qs, wpb, grid, s);
+    case 16: return launch_fast_dw<16>(a, qs, wpb, grid, s);
+    case 24: return launch_fast_dw<24>(a, qs, wpb, grid, s);
+    case 32: return launch_fast_dw<32>(a, qs, wpb, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int search_fast_blocks_per_sm(int u8w, int qs, int wpb, size_t smem) {
+  switch (u8w) {
+    case 8: return bps_fast_dw<8>(qs, wpb, smem);
+    case 16: return bps_fast_dw<16>(qs, wpb, smem);
+    case 24: return bps_fast_dw<24>(qs, wpb, smem);
+    case 32: return bps_fast_dw<32>(qs, wpb, smem);
+    default: return 0;
+  }
+}
+
+}  // namespace cng

@@ -26,7 +26,7 @@ struct SearchArgs {
   float band;
   int exact;
   int max_hops;
-  int* counter;         // work queue head (zeroed before launch)
+  int* counter;         // SEARCH_COUNTER_INTS work-queue words, zeroed before launch
   int32_t* ids;
   float* dists;
   int32_t* ndc;
@@ -49,6 +49,27 @@ struct SearchArgs {
   const uint8_t* U;         // [n][4 u8w]
   const uint8_t* QU;        // queries in the same form [nq][4 u8w] (unused with qids)
   int u8w;                  // 8, 16, 24 or 32
+  // two-kernel launch (SearchPlan::fast_qs > 0): the register-queue kernel serves every exact
+  // query and appends the others to defer[] (>= nq entries, counter[1] counts them); the general
+  // kernel then serves the list qlist[0 .. *nq_dev) with counter[2] as its queue head
+  int32_t* defer;
+  const int32_t* qlist;
+  const int* nq_dev;
+  size_t warp_smem_fast;    // bytes of shared memory per warp of the register-queue kernel
+};
+
+constexpr int SEARCH_COUNTER_INTS = 4;
+
+// Launch shape of one batched search.  fast_qs > 0: the register-queue kernel (queue of up to
+// 32 * fast_qs entries in registers; data with 8-bit rows) runs first on `grid` blocks, then the
+// general kernel on `grid_defer` blocks for the deferred queries; fast_qs == 0: the general
+// kernel alone on `grid` blocks.
+struct SearchPlan {
+  int wpb = 0;
+  int grid = 0;
+  int fast_qs = 0;
+  int grid_defer = 0;
+  int wpb_defer = 0;
 };
 
 // Packed stop model for inference: W1T bf16 [16][64], W2T bf16 [64][64], then floats
@@ -56,13 +77,22 @@ struct SearchArgs {
 constexpr int STOP_BLOCK_BYTES = 16 * 64 * 2 + 64 * 64 * 2 + (64 * 3 + 4 + 32) * 4;
 
 size_t search_warp_smem(int dpad, int L, int hash_slots);
-cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s);
+// Plans a search of `a` (its L, U/u8w, exact, model set) with wpb warps per block and a visited
+// filter of hash_slots entries: fills a.hash_slots, a.warp_smem, a.warp_smem_fast and *p and sets
+// the kernels' shared-memory attributes, so call it outside any stream capture.  Returns false
+// if the shape does not fit.
+bool search_plan(SearchArgs& a, int wpb, int hash_slots, SearchPlan* p);
+cudaError_t launch_search(const SearchArgs& a, const SearchPlan& p, cudaStream_t s);
 // Per-query exactness flags (0: integer query inside [vmin, vmax]) and, with out != null, the
 // queries as 8-bit rows out[q][c] = x[q][c] - vmin.
 cudaError_t launch_query_check(const float* Q, int64_t nq, int d, float vmin, float vmax, int u8w,
                                uint8_t* out, uint8_t* flag, cudaStream_t s);
-// Blocks per SM of the search variant for (dtype, u8w: 0 = FP32 path); also sets its
-// shared-memory attribute, so call it before launching (outside any stream capture).
+// Blocks per SM of the general search kernel for (dtype, u8w: 0 = FP32 path), and of the
+// register-queue kernel for (u8w, qs); both also set the kernel's shared-memory attribute.
 int search_blocks_per_sm(int dtype, int u8w, int warps_per_block, size_t smem);
+int search_fast_blocks_per_sm(int u8w, int qs, int warps_per_block, size_t smem);
+size_t search_fast_warp_smem(int u8w, int hash_slots);
+cudaError_t launch_search_general(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s);
+cudaError_t launch_search_fast(const SearchArgs& a, int qs, int warps_per_block, int grid, cudaStream_t s);
 
 }  // namespace cng

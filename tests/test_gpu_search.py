@@ -111,3 +111,30 @@ def test_search_mixed_query_exactness():
     _search_check(X, Q, idx, cng, 10, 32)
     _search_check(X, Q, idx, cng, 10, 32, use_graph=True)
     cng.cng_free(idx)
+
+
+@pytest.fixture(scope="module")
+def sift_r32():
+    need_gpu()
+    cng = lib()
+    X = synth.generate("sift", 6000, 128, seed=21)
+    Q = synth.generate("sift", 400, 128, seed=1021)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=32, L=128)
+    assert st["exact_int"] == 1
+    yield cng, X, Q, idx
+    cng.cng_free(idx)
+
+
+@pytest.mark.parametrize("L", [12, 40, 100, 256])
+def test_search_register_queue(sift_r32, L):
+    """Exact 8-bit data runs on the register-queue kernel (queues of 32, 64, 128 and 256
+    entries): the oracle's ids and hops for every query, through hops with more than 32 new
+    points (row stride 40, merged 32 at a time) and, at L = 256, visited filters that overflow
+    (their points are looked up in the queue, so NDC exceeds the oracle's)."""
+    cng, X, Q, idx = sift_r32
+    r = _search_check(X, Q, idx, cng, 10, L, warps_per_block=4, with_stats=True)
+    _search_check(X, Q, idx, cng, 10, L, use_graph=True)
+    if L == 256:
+        adj, deg, R, entry = cng.cng_graph(idx)
+        _, _, ndc, _ = oracle.search(X, host(adj), host(deg), entry, Q, 10, L)
+        assert (host(r["ndc"]) > ndc).any()
