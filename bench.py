@@ -248,6 +248,10 @@ def main():
     ap.add_argument("--adaptive", action="store_true",
                     help="with --build-n: adaptive pruning (Alg. 4, alpha0 0.9, dalpha 0.05, "
                          "alpha_max 1.6) instead of the workload's fixed alpha")
+    ap.add_argument("--search-L", type=int, default=0,
+                    help="only build the workload's index and run its queries at this fixed beam "
+                         "width with 4 queries per CTA (no autotuning): a warm-up search, then the "
+                         "reported one (for profiling the search kernel)")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -298,6 +302,22 @@ def main():
                                                 "ms_prune", "ms_merge", "ms_connect", "rule_ties", "cert_fail_rows", "order_ties",
                                                 "alpha_mean",
                                                 "merge_repruned", "n_edges")}}), flush=True)
+        return
+    if args.search_L:
+        xs = torch.from_numpy(w.base()).cuda()
+        qs = torch.from_numpy(w.queries().astype(np.float32)).cuda()
+        idx, _ = cng.cng_build(xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+        for it in range(2):
+            r = cng.cng_search(idx, qs, k=w.k, L=args.search_L, warps_per_block=4,
+                               with_stats=True)
+            torch.cuda.synchronize()
+        st = r["stats"]
+        print(json.dumps({"search_L": args.search_L, "nq": len(qs), "ms": st["ms"],
+                          "hops_per_query": st["hops_total"] / len(qs),
+                          "ndc_per_query": st["ndc_total"] / len(qs),
+                          "warps_per_block": st["warps_per_block"],
+                          "hash_slots": st["hash_slots"]}), flush=True)
+        cng.cng_free(idx)
         return
     X = w.base()
     Q = w.queries()

@@ -215,14 +215,23 @@ __global__ void __launch_bounds__(256, 4) search_fast_kernel(SearchArgs a) {
         const bool has = lane < nbc;
         const int32_t raw = has ? Nv[ci * 32 + lane] : 0;
         const int32_t v = raw & 0x7fffffff;
-        uint64_t kb = has ? rkey(u8_lane_d2<DW>(qu, qn, a.U, v), v) : KINF;
+        const uint32_t d2 = has ? u8_lane_d2<DW>(qu, qn, a.U, v) : 0u;
+        bool keep = has;
         const bool unsure = has && raw < 0;
         if (__ballot_sync(FULL, unsure)) {  // possibly seen: drop if in Q (or twice in the batch)
-          const bool in_q = qcontains<QS>(q, kb);
+          const bool in_q = qcontains<QS>(q, rkey(d2, v));
           const unsigned same = __match_any_sync(FULL, unsure ? v : -1 - lane);
-          if (unsure && (in_q || (same & ((1u << lane) - 1)))) kb = KINF;
+          if (unsure && (in_q || (same & ((1u << lane) - 1)))) keep = false;
         }
-        kb = warp_sort32(kb, lane);
+        // sort on 32-bit keys D^2 << 5 | lane (D^2 < 2^23 for d <= 128 and a span <= 255), then
+        // by id among equal distances
+        uint32_t k32 = keep ? (d2 << 5) | (uint32_t)lane : 0xffffffffu;
+        k32 = warp_sort32(k32, lane);
+        const int32_t vs = __shfl_sync(FULL, v, k32 & 31);
+        uint64_t kb = k32 == 0xffffffffu ? KINF : rkey(k32 >> 5, vs);
+        const uint32_t prev = __shfl_up_sync(FULL, k32, 1);
+        if (__ballot_sync(FULL, lane > 0 && k32 != 0xffffffffu && (prev >> 5) == (k32 >> 5)))
+          kb = warp_sort32(kb, lane);
         kbs[ci] = kb;
         if (ci == 0) {  // predict the next hop vertex and start loading its out-list
           const int nidx = first_unexplored<QS>(q);

@@ -24,16 +24,11 @@ CNG_DEV uint32_t hash32(uint32_t x) {
 // may or may not have been seen (slots never empty, so a recorded point is always found before
 // a free slot, and a point once refused is refused again).
 CNG_DEV int visit3(int32_t* H, int hmask, int32_t v) {
-  uint32_t h = hash32((uint32_t)v) & hmask;
-  for (int p = 0; p < 8; ++p) {
-    int32_t* slot = H + ((h + p) & hmask);
-    int32_t cur = *slot;
-    if (cur == v) return 0;
-    if (cur == -1) {
-      int32_t old = atomicCAS(slot, -1, v);
-      if (old == -1) return 1;
-      if (old == v) return 0;
-    }
+  const uint32_t h = hash32((uint32_t)v) & hmask;
+  for (int p = 0; p < 8; ++p) {  // one compare-and-swap per probe: claims a free slot or reads it
+    const int32_t old = atomicCAS(H + ((h + p) & hmask), -1, v);
+    if (old == -1) return 1;
+    if (old == v) return 0;
   }
   return 2;
 }
@@ -120,14 +115,15 @@ CNG_DEV float u8_lane_sqdist(const uint4* qu, uint32_t qn, const uint8_t* __rest
   return (float)u8_lane_d2<DW>(qu, qn, U, v);
 }
 
-// Ascending bitonic sort of one 64-bit key per lane across the warp (lane i ends with the
-// i-th smallest).
-CNG_DEV uint64_t warp_sort32(uint64_t key, int lane) {
+// Ascending bitonic sort of one key per lane across the warp (lane i ends with the i-th
+// smallest).
+template <typename K>
+CNG_DEV K warp_sort32(K key, int lane) {
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1)
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      const uint64_t o = __shfl_xor_sync(FULL, key, j);
+      const K o = __shfl_xor_sync(FULL, key, j);
       const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
       key = take_min ? (o < key ? o : key) : (o > key ? o : key);
     }
