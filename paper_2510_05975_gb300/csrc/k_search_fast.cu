@@ -110,8 +110,51 @@ CNG_DEV void qmerge(uint64_t (&q)[QS], uint64_t kdesc, int lane) {
     }
 }
 
+// Exact squared distances of up to 32 batch rows (row b named by lane b's v, present when
+// b < nb), returned in lane b.  G lanes read one row, 16 bytes each, so a warp load covers 32 / G
+// whole rows (coalesced) instead of one 16-byte piece of 32 rows; round r of G reads rows
+// r * 32 / G + (lane / G).  The G partial sums per lane are reduced across each group by a
+// transposed butterfly: after log2(G) exchange levels, lane g of a group holds round g's totals.
+// qy: this lane's 16 bytes of the query row; qn = |q|^2.
+template <int DW>
+CNG_DEV uint32_t batch_d2(uint4 qy, uint32_t qn, const uint8_t* __restrict__ U, int32_t v, int nb,
+                          int lane) {
+  constexpr int G = DW <= 8 ? 2 : DW <= 16 ? 4 : 8;  // lanes per row
+  constexpr int RPR = 32 / G;                         // rows per round
+  const int grp = lane / G, g = lane % G;
+  uint4 x[G];
+#pragma unroll
+  for (int r = 0; r < G; ++r) {
+    const int b = r * RPR + grp;
+    const int32_t vb = __shfl_sync(FULL, v, b);
+    x[r] = make_uint4(0u, 0u, 0u, 0u);
+    if (b < nb && g * 4 < DW) x[r] = __ldg(reinterpret_cast<const uint4*>(U + (int64_t)vb * (DW * 4)) + g);
+  }
+  uint32_t pd[G], pn[G];
+#pragma unroll
+  for (int r = 0; r < G; ++r) {
+    pd[r] = __dp4a(x[r].x, qy.x, 0u); pd[r] = __dp4a(x[r].y, qy.y, pd[r]);
+    pd[r] = __dp4a(x[r].z, qy.z, pd[r]); pd[r] = __dp4a(x[r].w, qy.w, pd[r]);
+    pn[r] = __dp4a(x[r].x, x[r].x, 0u); pn[r] = __dp4a(x[r].y, x[r].y, pn[r]);
+    pn[r] = __dp4a(x[r].z, x[r].z, pn[r]); pn[r] = __dp4a(x[r].w, x[r].w, pn[r]);
+  }
+#pragma unroll
+  for (int s = G / 2; s >= 1; s >>= 1) {  // list length 2 s -> s
+    const bool up = g & s;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const uint32_t rd = __shfl_xor_sync(FULL, up ? pd[i] : pd[i + s], s);
+      const uint32_t rn = __shfl_xor_sync(FULL, up ? pn[i] : pn[i + s], s);
+      pd[i] = (up ? pd[i + s] : pd[i]) + rd;
+      pn[i] = (up ? pn[i + s] : pn[i]) + rn;
+    }
+  }
+  const uint32_t d2 = qn + pn[0] - 2u * pd[0];  // row g * RPR + grp
+  return __shfl_sync(FULL, d2, (lane % RPR) * G + lane / RPR);
+}
+
 template <int DW, int QS>
-__global__ void __launch_bounds__(256, 4) search_fast_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* base = smem + (size_t)warp * a.warp_smem_fast;
@@ -152,6 +195,8 @@ __global__ void __launch_bounds__(256, 4) search_fast_kernel(SearchArgs a) {
     for (int o = 16; o > 0; o >>= 1) qn += __shfl_xor_sync(FULL, qn, o);
     for (int c = lane; c < a.hash_slots; c += 32) H[c] = -1;
     __syncwarp();
+    constexpr int G = DW <= 8 ? 2 : DW <= 16 ? 4 : 8;  // lanes per row in batch_d2
+    const uint4 qy = (lane % G) * 4 < DW ? qu[lane % G] : make_uint4(0u, 0u, 0u, 0u);
     // entry point
     const uint32_t d0 = u8_lane_d2<DW>(qu, qn, a.U, a.entry);
     uint64_t q[QS];
@@ -215,7 +260,7 @@ __global__ void __launch_bounds__(256, 4) search_fast_kernel(SearchArgs a) {
         const bool has = lane < nbc;
         const int32_t raw = has ? Nv[ci * 32 + lane] : 0;
         const int32_t v = raw & 0x7fffffff;
-        const uint32_t d2 = has ? u8_lane_d2<DW>(qu, qn, a.U, v) : 0u;
+        const uint32_t d2 = batch_d2<DW>(qy, qn, a.U, v, nbc, lane);
         bool keep = has;
         const bool unsure = has && raw < 0;
         if (__ballot_sync(FULL, unsure)) {  // possibly seen: drop if in Q (or twice in the batch)
