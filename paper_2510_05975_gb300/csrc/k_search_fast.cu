@@ -115,10 +115,9 @@ CNG_DEV void qmerge(uint64_t (&q)[QS], uint64_t kdesc, int lane) {
 // whole rows (coalesced) instead of one 16-byte piece of 32 rows; round r of G reads rows
 // r * 32 / G + (lane / G).  The G partial sums per lane are reduced across each group by a
 // transposed butterfly: after log2(G) exchange levels, lane g of a group holds round g's totals.
-// qy: this lane's 16 bytes of the query row; qn = |q|^2.
+// qy: this lane's 16 bytes of the query row (zero past the row, as the stored rows are).
 template <int DW>
-CNG_DEV uint32_t batch_d2(uint4 qy, uint32_t qn, const uint8_t* __restrict__ U, int32_t v, int nb,
-                          int lane) {
+CNG_DEV uint32_t batch_d2(uint4 qy, const uint8_t* __restrict__ U, int32_t v, int nb, int lane) {
   constexpr int G = DW <= 8 ? 2 : DW <= 16 ? 4 : 8;  // lanes per row
   constexpr int RPR = 32 / G;                         // rows per round
   const int grp = lane / G, g = lane % G;
@@ -130,26 +129,29 @@ CNG_DEV uint32_t batch_d2(uint4 qy, uint32_t qn, const uint8_t* __restrict__ U, 
     x[r] = make_uint4(0u, 0u, 0u, 0u);
     if (b < nb && g * 4 < DW) x[r] = __ldg(reinterpret_cast<const uint4*>(U + (int64_t)vb * (DW * 4)) + g);
   }
-  uint32_t pd[G], pn[G];
+  // per byte |x - q| (exact in 8 bits), squared and summed by dp4a
+  uint32_t p[G];
 #pragma unroll
   for (int r = 0; r < G; ++r) {
-    pd[r] = __dp4a(x[r].x, qy.x, 0u); pd[r] = __dp4a(x[r].y, qy.y, pd[r]);
-    pd[r] = __dp4a(x[r].z, qy.z, pd[r]); pd[r] = __dp4a(x[r].w, qy.w, pd[r]);
-    pn[r] = __dp4a(x[r].x, x[r].x, 0u); pn[r] = __dp4a(x[r].y, x[r].y, pn[r]);
-    pn[r] = __dp4a(x[r].z, x[r].z, pn[r]); pn[r] = __dp4a(x[r].w, x[r].w, pn[r]);
+    uint32_t t = __vabsdiffu4(x[r].x, qy.x);
+    p[r] = __dp4a(t, t, 0u);
+    t = __vabsdiffu4(x[r].y, qy.y);
+    p[r] = __dp4a(t, t, p[r]);
+    t = __vabsdiffu4(x[r].z, qy.z);
+    p[r] = __dp4a(t, t, p[r]);
+    t = __vabsdiffu4(x[r].w, qy.w);
+    p[r] = __dp4a(t, t, p[r]);
   }
 #pragma unroll
   for (int s = G / 2; s >= 1; s >>= 1) {  // list length 2 s -> s
     const bool up = g & s;
 #pragma unroll
     for (int i = 0; i < s; ++i) {
-      const uint32_t rd = __shfl_xor_sync(FULL, up ? pd[i] : pd[i + s], s);
-      const uint32_t rn = __shfl_xor_sync(FULL, up ? pn[i] : pn[i + s], s);
-      pd[i] = (up ? pd[i + s] : pd[i]) + rd;
-      pn[i] = (up ? pn[i + s] : pn[i]) + rn;
+      const uint32_t rv = __shfl_xor_sync(FULL, up ? p[i] : p[i + s], s);
+      p[i] = (up ? p[i + s] : p[i]) + rv;
     }
   }
-  const uint32_t d2 = qn + pn[0] - 2u * pd[0];  // row g * RPR + grp
+  const uint32_t d2 = p[0];  // row g * RPR + grp
   return __shfl_sync(FULL, d2, (lane % RPR) * G + lane / RPR);
 }
 
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
         const bool has = lane < nbc;
         const int32_t raw = has ? Nv[ci * 32 + lane] : 0;
         const int32_t v = raw & 0x7fffffff;
-        const uint32_t d2 = batch_d2<DW>(qy, qn, a.U, v, nbc, lane);
+        const uint32_t d2 = batch_d2<DW>(qy, a.U, v, nbc, lane);
         bool keep = has;
         const bool unsure = has && raw < 0;
         if (__ballot_sync(FULL, unsure)) {  // possibly seen: drop if in Q (or twice in the batch)
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
       }
       // points of this hop still in Q: those not beyond its last entry
       int ins = 0;
-      {
+      if (a.trace_feats || a.model) {
         const uint64_t last = qget<QS>(q, len - 1);
 #pragma unroll
         for (int ci = 0; ci < SQ_ROWSLOTS; ++ci)
