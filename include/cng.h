@@ -185,6 +185,9 @@ typedef enum { CNG_SEARCH_FIXED = 0, CNG_SEARCH_LEARNED = 1 } cng_search_mode;
  * mode         CNG_SEARCH_FIXED: Alg. 1 exactly (stop when every queue entry is explored);
  *              CNG_SEARCH_LEARNED: additionally stop when the stop model's probability reaches
  *              `threshold` at a check (every `check_every` hops); Alg. 1's own rule remains.
+ * min_stable   learned mode: a check consults the model only when the first min(k, |Q|) ids
+ *              have not changed for at least this many hops (0 = at every check); the gate is
+ *              free, so the network runs only where a stop is plausible
  * model        required for CNG_SEARCH_LEARNED, ignored otherwise
  * max_hops     0 = unbounded; otherwise queries stop after this many hop vertices (flagged)
  * use_graph    1: launch through a cached CUDA graph for this (nq, k, L, mode) shape
@@ -202,6 +205,7 @@ typedef struct {
   int32_t max_hops;
   int32_t use_graph;
   int32_t warps_per_block;
+  int32_t min_stable;
 } cng_search_params;
 
 typedef struct {
@@ -243,7 +247,10 @@ cng_status cng_search(const cng_index *index, const float *queries, int64_t nq, 
  * Training samples: every hop t <= max_trace of the plain search of each training query, label
  * 1 iff t >= that query's final tlc.  Parameters (flat FP32, CNG_STOP_NPARAMS):
  *   W1[64][16] b1[64] W2[64][64] b2[64] w3[64] b3[1];  inputs standardised by mu[16], sigma[16].
- * Inference uses BF16-rounded weights with FP32 arithmetic.
+ * Inference runs on the tensor cores with BF16-rounded weights: each activation (standardised
+ * input, hidden layer 1) enters as a pair of BF16 values hi + lo (about 16 significant bits),
+ * products are exact and sums are FP32, so the logit is the FP64 network's on the rounded
+ * weights to within ~1e-5 relative.
  * ------------------------------------------------------------------------------------- */
 
 #define CNG_STOP_NPARAMS 5313

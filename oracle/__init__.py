@@ -82,7 +82,7 @@ def _load():
             lib.or_search_ex.restype = ctypes.c_int
             lib.or_search_ex.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, vp, i64,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, dbl,
-                                         ctypes.c_int, vp, vp, vp, vp, vp]
+                                         ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
             lib.or_num_threads.restype = ctypes.c_int
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -256,9 +256,11 @@ NF = 16
 
 
 def search_ex(X, adj, deg, entry_id: int, Q, k: int, L: int, max_trace: int = 0, model=None,
-              zthr: float = 0.0, check_every: int = 1):
+              zthr: float = 0.0, check_every: int = 1, min_stable: int = 0):
     """Alg. 1 with per-hop search-state features (learned early stop) and, if ``model`` (the
-    parameter vector followed by mu[16], sigma[16]) is given, the learned stop rule.
+    parameter vector followed by mu[16], sigma[16]) is given, the learned stop rule: the model
+    is consulted after hops t with t % check_every == 0 whose top-k ids have not changed for
+    min_stable hops.
     Returns dict(ids, dists, ndc, hops, tlc, stopped, feats [nq, max_trace, 16] or None)."""
     X, Q = _f32(X), _f32(Q)
     adj = np.ascontiguousarray(adj, dtype=np.int32)
@@ -273,7 +275,7 @@ def search_ex(X, adj, deg, entry_id: int, Q, k: int, L: int, max_trace: int = 0,
     rc = _load().or_search_ex(_p(X), n, d, _p(adj), _p(deg), adj.shape[1], int(entry_id), _p(Q), nq,
                               int(k), int(L), int(max_trace),
                               _p(out["feats"]) if max_trace else None, _p(out["tlc"]),
-                              None if mdl is None else _p(mdl), float(zthr), int(check_every),
+                              None if mdl is None else _p(mdl), float(zthr), int(check_every), int(min_stable),
                               _p(out["ids"]), _p(out["dists"]), _p(out["ndc"]), _p(out["hops"]),
                               _p(out["stopped"]))
     if rc != 0:

@@ -580,15 +580,17 @@ double or_mlp_logit(const double *model, const double *f) {
 /*
  * Alg. 1 as or_search, plus: per-hop features into feats[qi][t-1][16] for t <= max_trace
  * (when feats != NULL), the final tlc per query, and -- when model != NULL -- the learned stop:
- * after every hop t with t % check_every == 0 the search ends if or_mlp_logit >= zthr
- * (stopped[qi] = 1).  Ids, distances, ndc and hops as or_search.
+ * after every hop t with t % check_every == 0 and t - tlc >= min_stable (the top-k ids unchanged
+ * for min_stable hops) the search ends if or_mlp_logit >= zthr (stopped[qi] = 1).  Ids,
+ * distances, ndc and hops as or_search.
  */
 int or_search_ex(const float *X, int64_t n, int d, const int32_t *adj, const int32_t *deg, int R,
                  int32_t s, const float *Qv, int64_t nq, int k, int L, int max_trace, double *feats,
                  int32_t *tlc_out, const double *model, double zthr, int check_every,
-                 int32_t *out_ids, double *out_d, int32_t *ndc_out, int32_t *hops_out,
+                 int min_stable, int32_t *out_ids, double *out_d, int32_t *ndc_out, int32_t *hops_out,
                  int32_t *stopped) {
-    if (n <= 0 || k <= 0 || L < k || s < 0 || s >= n || check_every < 1) return OR_E_INVAL;
+    if (n <= 0 || k <= 0 || L < k || s < 0 || s >= n || check_every < 1 || min_stable < 0)
+        return OR_E_INVAL;
 #pragma omp parallel
     {
         unsigned char *vis = (unsigned char *)calloc((size_t)n, 1);
@@ -661,7 +663,8 @@ int or_search_ex(const float *X, int64_t n, int d, const int32_t *adj, const int
                     hist = (double *)realloc(hist, sizeof(double) * hcap);
                 }
                 hist[hops] = Dk;
-                if ((feats && hops <= max_trace) || (model && hops % check_every == 0)) {
+                const int check = model && hops % check_every == 0 && hops - tlc >= min_stable;
+                if ((feats && hops <= max_trace) || check) {
                     int U = 0, ins = 0;
                     for (int t = 0; t < len; ++t) {
                         U += !Q[t].explored;
@@ -686,7 +689,7 @@ int or_search_ex(const float *X, int64_t n, int d, const int32_t *adj, const int
                     if (feats && hops <= max_trace)
                         for (int j = 0; j < OR_NF; ++j)
                             feats[(qi * (int64_t)max_trace + (hops - 1)) * OR_NF + j] = f[j];
-                    if (model && hops % check_every == 0 && or_mlp_logit(model, f) >= zthr) {
+                    if (check && or_mlp_logit(model, f) >= zthr) {
                         stop = 1;
                         break;
                     }

@@ -62,7 +62,8 @@ class BuildStats(ctypes.Structure):
 class SearchParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("model", ctypes.c_void_p), ("threshold", ctypes.c_float),
                 ("check_every", ctypes.c_int32), ("max_hops", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("warps_per_block", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("min_stable", ctypes.c_int32)]
 
 
 class SearchStats(ctypes.Structure):
@@ -247,7 +248,7 @@ def cng_lists(index: Index):
 def cng_search(index: Index, queries, k: int, L: int, mode: int = CNG_SEARCH_FIXED, model=None,
                threshold: float = 0.5, check_every: int = 1, max_hops: int = 0,
                use_graph: bool = False, warps_per_block: int = 0, out=None, stream=None,
-               with_stats: bool = True):
+               with_stats: bool = True, min_stable: int = 0):
     """cng_search of include/cng.h.  queries: CUDA tensor [nq, d] float32 (or host array, then
     outputs are host arrays).  Returns dict(ids, dists, ndc, hops, flags, stats)."""
     nq = queries.shape[0]
@@ -266,7 +267,7 @@ def cng_search(index: Index, queries, k: int, L: int, mode: int = CNG_SEARCH_FIX
                        ndc=np.empty(nq, np.int32), hops=np.empty(nq, np.int32),
                        flags=np.empty(nq, np.int32))
     p = SearchParams(mode, None if model is None else model.handle, threshold, check_every, max_hops,
-                     int(use_graph), warps_per_block)
+                     int(use_graph), warps_per_block, int(min_stable))
     st = SearchStats()
     _check(lib().cng_search(index.handle, _ptr(queries), nq, k, L, ctypes.byref(p), _ptr(out["ids"]),
                             _ptr(out["dists"]), _ptr(out.get("ndc")), _ptr(out.get("hops")),

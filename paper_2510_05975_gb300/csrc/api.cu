@@ -852,6 +852,7 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   if (P.mode == CNG_SEARCH_LEARNED && (!P.model || !(P.threshold > 0.f && P.threshold < 1.f) || P.check_every < 1))
     return fail(CNG_E_INVAL, "learned mode needs a model, 0 < threshold < 1 and check_every >= 1");
   if (P.max_hops < 0) return fail(CNG_E_INVAL, "max_hops must be >= 0");
+  if (P.min_stable < 0) return fail(CNG_E_INVAL, "min_stable must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   if (nq == 0) {
     if (stats) memset(stats, 0, sizeof(*stats));
@@ -905,6 +906,7 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     a.model = P.model->blk;
     a.zthr = std::log(P.threshold / (1.f - P.threshold));
     a.check_every = P.check_every;
+    a.min_stable = P.min_stable;
   }
   std::lock_guard<std::mutex> lock(ix->mu);
   {

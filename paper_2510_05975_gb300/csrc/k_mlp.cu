@@ -285,22 +285,23 @@ __global__ void mlp_init_kernel(float* __restrict__ P, uint64_t seed) {
 // FP32 master parameters + normalisation -> packed inference block (BF16 weights).
 __global__ void pack_model_kernel(const float* __restrict__ P, const float* __restrict__ mu,
                                   const float* __restrict__ sg, unsigned char* __restrict__ blk) {
-  __nv_bfloat16* W1T = reinterpret_cast<__nv_bfloat16*>(blk);
-  __nv_bfloat16* W2T = W1T + 16 * 64;
-  float* f = reinterpret_cast<float*>(W2T + 64 * 64);
+  // output-major rows padded to 24 and 72 elements (the pads are zero)
+  __nv_bfloat16* W1b = reinterpret_cast<__nv_bfloat16*>(blk);
+  __nv_bfloat16* W2b = W1b + 64 * 24;
+  float* f = reinterpret_cast<float*>(W2b + 64 * 72);
   const float* W1 = P;
   const float* b1 = W1 + 64 * 16;
   const float* W2 = b1 + 64;
   const float* b2 = W2 + 64 * 64;
   const float* w3 = b2 + 64;
   const float* b3 = w3 + 64;
-  for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
-    int i = e >> 6, o = e & 63;
-    W1T[e] = __float2bfloat16_rn(W1[o * 16 + i]);
+  for (int e = threadIdx.x; e < 64 * 24; e += blockDim.x) {
+    const int o = e / 24, i = e % 24;
+    W1b[e] = __float2bfloat16_rn(i < 16 ? W1[o * 16 + i] : 0.f);
   }
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    int i = e >> 6, o = e & 63;
-    W2T[e] = __float2bfloat16_rn(W2[o * 64 + i]);
+  for (int e = threadIdx.x; e < 64 * 72; e += blockDim.x) {
+    const int o = e / 72, i = e % 72;
+    W2b[e] = __float2bfloat16_rn(i < 64 ? W2[o * 64 + i] : 0.f);
   }
   for (int e = threadIdx.x; e < 64; e += blockDim.x) {
     f[e] = b1[e];

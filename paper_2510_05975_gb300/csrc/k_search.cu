@@ -433,26 +433,16 @@ search_kernel(SearchArgs a) {
         const float Dk = sqrtf(key_dist(cur.k[kk - 1]));
         if (chg) tlc = hops;
         const bool want_trace = a.trace_feats && hops <= a.max_trace;
-        const bool want_check = a.model && (hops % a.check_every) == 0;
+        const bool want_check =
+            a.model && (hops % a.check_every) == 0 && hops - tlc >= a.min_stable;
         float f = 0.f;
         if (want_trace || want_check) {
           int U = 0;
           for (int b = 0; b < len; b += 32)
             U += __popc(__ballot_sync(FULL, b + lane < len && !cur.e[b + lane]));
-          const float lD0 = lgf(D0), lDk = lgf(Dk);
-          if (lane == 0) f = lD0;
-          else if (lane == 1) f = logf(1.f + (float)hops);
-          else if (lane == 2) f = lgf(sqrtf(key_dist(cur.k[0]))) - lD0;
-          else if (lane == 3) f = lDk - lD0;
-          else if (lane == 4) f = lgf(sqrtf(key_dist(cur.k[len - 1]))) - lD0;
-          else if (lane == 5) f = lgf(Du) - lDk;
-          else if (lane < 12) {
-            const int h = max(hops - (1 << (lane - 6)), 0);
-            f = lgf(hist[h & 63]) - lDk;
-          } else if (lane == 12) f = logf(1.f + (float)(hops - tlc));
-          else if (lane == 13) f = (float)U / (float)a.L;
-          else if (lane == 14) f = (float)len / (float)a.L;
-          else if (lane == 15) f = (float)ins / (float)a.R;
+          f = stop_feature(lane, D0, sqrtf(key_dist(cur.k[0])), Dk,
+                           sqrtf(key_dist(cur.k[len - 1])), Du, hist, hops, tlc, U, len, ins,
+                           a.L, a.R);
           if (want_trace && lane < 16)
             a.trace_feats[((int64_t)qi * a.max_trace + (hops - 1)) * 16 + lane] = f;
         }
@@ -535,7 +525,7 @@ bool search_plan(SearchArgs& a, int wpb, int hash_slots, SearchPlan* p) {
   if (qs) {
     a.warp_smem_fast = search_fast_warp_smem(a.u8w, hash_slots);
     const size_t sh = (size_t)wpb * a.warp_smem_fast + extra_smem;
-    const int b = sh <= kMaxBlockSmem ? search_fast_blocks_per_sm(a.u8w, qs, wpb, sh) : 0;
+    const int b = sh <= kMaxBlockSmem ? search_fast_blocks_per_sm(a.u8w, qs, a.model || a.trace_feats, wpb, sh) : 0;
     if (b < 1) return false;
     p->grid = num_sms() * b;
     p->fast_qs = qs;

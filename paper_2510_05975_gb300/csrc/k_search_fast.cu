@@ -155,7 +155,9 @@ CNG_DEV uint32_t batch_d2(uint4 qy, const uint8_t* __restrict__ U, int32_t v, in
   return __shfl_sync(FULL, d2, (lane % RPR) * G + lane / RPR);
 }
 
-template <int DW, int QS>
+// LEARN: the variant that records stop features and runs the stop model (traces and the
+// learned mode); the other variant carries none of that state.
+template <int DW, int QS, bool LEARN>
 __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
   float* hist = reinterpret_cast<float*>(Nv + SQ_ROWSLOTS * 32);  // Dk after the last 64 hops
   int32_t* H = reinterpret_cast<int32_t*>(hist + 64);             // visited filter
   StopSmem ms;
-  if (a.model) {
+  if (LEARN && a.model) {
     unsigned char* mb = smem + (size_t)(blockDim.x >> 5) * a.warp_smem_fast;
     const int4* src = reinterpret_cast<const int4*>(a.model);
     int4* dst = reinterpret_cast<int4*>(mb);
@@ -253,10 +255,10 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
       __syncwarp();
       ndc += nb;
       bool chg = false;  // the first min(k, |Q|) ids changed
-      uint64_t kbs[SQ_ROWSLOTS];
+      uint64_t kbs[LEARN ? SQ_ROWSLOTS : 1];  // this hop's sorted batches (stop features)
 #pragma unroll
       for (int ci = 0; ci < SQ_ROWSLOTS; ++ci) {
-        kbs[ci] = KINF;
+        if constexpr (LEARN) kbs[ci] = KINF;
         if (ci * 32 >= nb) continue;
         const int nbc = min(32, nb - ci * 32);
         const bool has = lane < nbc;
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
         const uint32_t prev = __shfl_up_sync(FULL, k32, 1);
         if (__ballot_sync(FULL, lane > 0 && k32 != 0xffffffffu && (prev >> 5) == (k32 >> 5)))
           kb = warp_sort32(kb, lane);
-        kbs[ci] = kb;
+        if constexpr (LEARN) kbs[ci] = kb;
         if (ci == 0) {  // predict the next hop vertex and start loading its out-list
           const int nidx = first_unexplored<QS>(q);
           uint64_t kn = KINF;
@@ -309,42 +311,28 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
         if (old_len < a.k) chg = true;
         else chg |= (qget<QS>(q, a.k - 1) >> 1) != (old_kth >> 1);
       }
-      // points of this hop still in Q: those not beyond its last entry
-      int ins = 0;
-      if (a.trace_feats || a.model) {
-        const uint64_t last = qget<QS>(q, len - 1);
-#pragma unroll
-        for (int ci = 0; ci < SQ_ROWSLOTS; ++ci)
-          ins += __popc(__ballot_sync(FULL, kbs[ci] != KINF && kbs[ci] <= last));
-      }
       // ---- search state after this hop (learned early stop) ----
-      if (a.trace_feats || a.model) {
+      if constexpr (LEARN) {
         const int kk = min(a.k, len);
         const float Dk = sqrtf(rkey_d2(qget<QS>(q, kk - 1)));
         if (chg) tlc = hops;
         const bool want_trace = a.trace_feats && hops <= a.max_trace;
-        const bool want_check = a.model && (hops % a.check_every) == 0;
+        const bool want_check =
+            a.model && (hops % a.check_every) == 0 && hops - tlc >= a.min_stable;
         float f = 0.f;
         if (want_trace || want_check) {
+          // points of this hop still in Q: those not beyond its last entry
+          int ins = 0;
+          const uint64_t last = qget<QS>(q, len - 1);
+#pragma unroll
+          for (int ci = 0; ci < SQ_ROWSLOTS; ++ci)
+            ins += __popc(__ballot_sync(FULL, kbs[ci] != KINF && kbs[ci] <= last));
           int U = 0;
 #pragma unroll
           for (int s = 0; s < QS; ++s) U += __popc(__ballot_sync(FULL, unexplored(q[s])));
           const float D1 = sqrtf(rkey_d2(qget<QS>(q, 0)));
           const float DL = sqrtf(rkey_d2(qget<QS>(q, len - 1)));
-          const float lD0 = lgf(D0), lDk = lgf(Dk);
-          if (lane == 0) f = lD0;
-          else if (lane == 1) f = logf(1.f + (float)hops);
-          else if (lane == 2) f = lgf(D1) - lD0;
-          else if (lane == 3) f = lDk - lD0;
-          else if (lane == 4) f = lgf(DL) - lD0;
-          else if (lane == 5) f = lgf(Du) - lDk;
-          else if (lane < 12) {
-            const int h = max(hops - (1 << (lane - 6)), 0);
-            f = lgf(hist[h & 63]) - lDk;
-          } else if (lane == 12) f = logf(1.f + (float)(hops - tlc));
-          else if (lane == 13) f = (float)U / (float)a.L;
-          else if (lane == 14) f = (float)len / (float)a.L;
-          else if (lane == 15) f = (float)ins / (float)a.R;
+          f = stop_feature(lane, D0, D1, Dk, DL, Du, hist, hops, tlc, U, len, ins, a.L, a.R);
           if (want_trace && lane < 16)
             a.trace_feats[((int64_t)qi * a.max_trace + (hops - 1)) * 16 + lane] = f;
         }
@@ -389,7 +377,10 @@ template <int DW, int QS>
 cudaError_t launch_fast_t(const SearchArgs& a, int wpb, int grid, cudaStream_t s) {
   const size_t sh = (size_t)wpb * a.warp_smem_fast + (a.model ? STOP_BLOCK_BYTES : 0);
   count_launch();
-  search_fast_kernel<DW, QS><<<grid, wpb * 32, sh, s>>>(a);
+  if (a.model || a.trace_feats)
+    search_fast_kernel<DW, QS, true><<<grid, wpb * 32, sh, s>>>(a);
+  else
+    search_fast_kernel<DW, QS, false><<<grid, wpb * 32, sh, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -404,23 +395,29 @@ cudaError_t launch_fast_dw(const SearchArgs& a, int qs, int wpb, int grid, cudaS
   }
 }
 
-template <int DW, int QS>
+template <int DW, int QS, bool LEARN>
 int bps_fast_t(int wpb, size_t smem) {
   int nb = 0;
-  cudaFuncSetAttribute(search_fast_kernel<DW, QS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_fast_kernel<DW, QS>, wpb * 32, smem);
+  cudaFuncSetAttribute(search_fast_kernel<DW, QS, LEARN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_fast_kernel<DW, QS, LEARN>, wpb * 32, smem);
   return nb;
 }
 
-template <int DW>
+template <int DW, bool LEARN>
 int bps_fast_dw(int qs, int wpb, size_t smem) {
   switch (qs) {
-    case 1: return bps_fast_t<DW, 1>(wpb, smem);
-    case 2: return bps_fast_t<DW, 2>(wpb, smem);
-    case 4: return bps_fast_t<DW, 4>(wpb, smem);
-    case 8: return bps_fast_t<DW, 8>(wpb, smem);
+    case 1: return bps_fast_t<DW, 1, LEARN>(wpb, smem);
+    case 2: return bps_fast_t<DW, 2, LEARN>(wpb, smem);
+    case 4: return bps_fast_t<DW, 4, LEARN>(wpb, smem);
+    case 8: return bps_fast_t<DW, 8, LEARN>(wpb, smem);
     default: return 0;
   }
+}
+
+template <int DW>
+int bps_fast_dw(int qs, bool learn, int wpb, size_t smem) {
+  return learn ? bps_fast_dw<DW, true>(qs, wpb, smem) : bps_fast_dw<DW, false>(qs, wpb, smem);
 }
 
 }  // namespace
@@ -440,12 +437,12 @@ cudaError_t launch_search_fast(const SearchArgs& a, int qs, int wpb, int grid, c
   }
 }
 
-int search_fast_blocks_per_sm(int u8w, int qs, int wpb, size_t smem) {
+int search_fast_blocks_per_sm(int u8w, int qs, bool learn, int wpb, size_t smem) {
   switch (u8w) {
-    case 8: return bps_fast_dw<8>(qs, wpb, smem);
-    case 16: return bps_fast_dw<16>(qs, wpb, smem);
-    case 24: return bps_fast_dw<24>(qs, wpb, smem);
-    case 32: return bps_fast_dw<32>(qs, wpb, smem);
+    case 8: return bps_fast_dw<8>(qs, learn, wpb, smem);
+    case 16: return bps_fast_dw<16>(qs, learn, wpb, smem);
+    case 24: return bps_fast_dw<24>(qs, learn, wpb, smem);
+    case 32: return bps_fast_dw<32>(qs, learn, wpb, smem);
     default: return 0;
   }
 }

@@ -41,6 +41,7 @@ struct SearchArgs {
   const void* model;        // packed stop model (STOP_BLOCK_BYTES), or null
   float zthr;               // stop when the logit >= zthr
   int check_every;
+  int min_stable;           // the model is consulted only when hops - tlc >= min_stable
   // per-query exactness when the data is exact (exact != 0): qflag[q] == 0 marks an integer
   // query inside the data's range; other queries resolve near-ties in FP64 (unused with qids)
   const uint8_t* qflag;
@@ -72,9 +73,10 @@ struct SearchPlan {
   int wpb_defer = 0;
 };
 
-// Packed stop model for inference: W1T bf16 [16][64], W2T bf16 [64][64], then floats
-// b1[64] b2[64] w3[64] b3[1] pad[3] mu[16] sigma[16].
-constexpr int STOP_BLOCK_BYTES = 16 * 64 * 2 + 64 * 64 * 2 + (64 * 3 + 4 + 32) * 4;
+// Packed stop model for inference: W1 bf16 [64][24] (row o = W1[o][0..15], then 8 pad), W2
+// bf16 [64][72] (row o = W2[o][0..63], then 8 pad), then floats b1[64] b2[64] w3[64] b3[1]
+// pad[3] mu[16] sigma[16].
+constexpr int STOP_BLOCK_BYTES = 64 * 24 * 2 + 64 * 72 * 2 + (64 * 3 + 4 + 32) * 4;
 
 size_t search_warp_smem(int dpad, int L, int hash_slots);
 // Plans a search of `a` (its L, U/u8w, exact, model set) with wpb warps per block and a visited
@@ -88,9 +90,10 @@ cudaError_t launch_search(const SearchArgs& a, const SearchPlan& p, cudaStream_t
 cudaError_t launch_query_check(const float* Q, int64_t nq, int d, float vmin, float vmax, int u8w,
                                uint8_t* out, uint8_t* flag, cudaStream_t s);
 // Blocks per SM of the general search kernel for (dtype, u8w: 0 = FP32 path), and of the
-// register-queue kernel for (u8w, qs); both also set the kernel's shared-memory attribute.
+// register-queue kernel for (u8w, qs, learn: the variant with stop features); both also set
+// the kernel's shared-memory attribute.
 int search_blocks_per_sm(int dtype, int u8w, int warps_per_block, size_t smem);
-int search_fast_blocks_per_sm(int u8w, int qs, int warps_per_block, size_t smem);
+int search_fast_blocks_per_sm(int u8w, int qs, bool learn, int warps_per_block, size_t smem);
 size_t search_fast_warp_smem(int u8w, int hash_slots);
 cudaError_t launch_search_general(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t s);
 cudaError_t launch_search_fast(const SearchArgs& a, int qs, int warps_per_block, int grid, cudaStream_t s);

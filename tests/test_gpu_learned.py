@@ -73,7 +73,8 @@ def test_trace_features_match_oracle(small_index):
         assert np.allclose(F[q, :h], ref["feats"][q, :h], rtol=1e-4, atol=2e-5), q
 
 
-def test_learned_stop_matches_oracle_rule(small_index):
+@pytest.mark.parametrize("every,gate", [(2, 0), (1, 3)])
+def test_learned_stop_matches_oracle_rule(small_index, every, gate):
     cng, X, Q, idx, A, D, entry = small_index
     rng = np.random.default_rng(5)
     P = mlp.init(9).astype(np.float32)
@@ -84,11 +85,12 @@ def test_learned_stop_matches_oracle_rule(small_index):
     model = cng.cng_stop_import(P, mu, sg)
     _, _, _, Pb = cng.cng_stop_export(model)
     omodel = np.concatenate([Pb.astype(np.float64), mu.astype(np.float64), sg.astype(np.float64)])
-    thr, every = 0.6, 2
+    thr = 0.6
     zthr = math.log(thr / (1 - thr))
     res = cng.cng_search(idx, tensor(Q), k=10, L=24, mode=cng.CNG_SEARCH_LEARNED, model=model,
-                         threshold=thr, check_every=every)
-    orc = oracle.search_ex(X, A, D, entry, Q, 10, 24, model=omodel, zthr=zthr, check_every=every)
+                         threshold=thr, check_every=every, min_stable=gate)
+    orc = oracle.search_ex(X, A, D, entry, Q, 10, 24, model=omodel, zthr=zthr, check_every=every,
+                           min_stable=gate)
     checked = 0
     for q in range(len(Q)):
         # skip queries whose decision is within 1e-3 of the threshold at some check up to the stop

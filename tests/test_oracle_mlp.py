@@ -83,3 +83,29 @@ def test_learned_stop_rule_in_oracle():
     assert np.all(r["stopped"] == 1) and np.all(r["hops"] == 3)
     r2 = oracle.search_ex(X, G.adj, G.deg, G.entry, Q, 5, 20, model=model, zthr=1.5, check_every=3)
     assert np.all(r2["stopped"] == 0)
+
+
+def test_learned_stop_gate_in_oracle():
+    """min_stable: with a constant stop logit, each query stops at its first check hop t whose
+    top-k ids have been unchanged for min_stable hops (t - tlc_t >= min_stable, with tlc_t from
+    the plain search's features); a gate longer than any search never stops one."""
+    X = synth.generate("gauss", 800, 8, seed=1)
+    Q = synth.generate("gauss", 30, 8, seed=3)
+    G = oracle.build_graph(X, 1.2, 0.0, 10, 24)
+    model = np.concatenate([np.zeros(mlp.N_PARAMS), np.zeros(16), np.ones(16)])
+    model[mlp.N_PARAMS - 1] = 1.0  # constant logit 1
+    plain = oracle.search_ex(X, G.adj, G.deg, G.entry, Q, 5, 20, max_trace=400)
+    for g, ce in ((2, 1), (3, 2)):
+        r = oracle.search_ex(X, G.adj, G.deg, G.entry, Q, 5, 20, model=model, zthr=0.5,
+                             check_every=ce, min_stable=g)
+        for qi in range(len(Q)):
+            h = plain["hops"][qi]
+            since = np.rint(np.exp(plain["feats"][qi, :h, 12]) - 1).astype(int)  # t - tlc_t
+            ok = [t for t in range(1, h + 1) if t % ce == 0 and since[t - 1] >= g]
+            if ok:
+                assert r["stopped"][qi] == 1 and r["hops"][qi] == ok[0], qi
+            else:
+                assert r["stopped"][qi] == 0 and r["hops"][qi] == h, qi
+    r = oracle.search_ex(X, G.adj, G.deg, G.entry, Q, 5, 20, model=model, zthr=0.5,
+                         check_every=1, min_stable=10 ** 6)
+    assert np.all(r["stopped"] == 0) and np.array_equal(r["hops"], plain["hops"])
