@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(256, 4)
 search_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nwork = a.qlist ? (int64_t)*a.nq_dev : a.nq;
+  if (nwork == 0) return;  // nothing deferred (uniform over the grid)
   const int L = a.L, dpad = a.dpad;
   unsigned char* base = smem + (size_t)warp * a.warp_smem;
   float* qv = reinterpret_cast<float*>(base);
@@ -116,14 +118,18 @@ search_kernel(SearchArgs a) {
   const int g = lane % SQ_G, grp = lane / SQ_G;
   unsigned long long t_ndc = 0, t_hops = 0, t_f64 = 0, t_stop = 0;
 
-  // work list: all queries, or the ones the register-queue kernel deferred
-  const int64_t nwork = a.qlist ? (int64_t)*a.nq_dev : a.nq;
+  // work list: all queries, or the ones the register-queue kernel deferred; each warp takes
+  // item (its index) first, then items nw + (queue head) as it finishes them
   int* const head = a.qlist ? a.counter + 2 : a.counter;
-  for (;;) {
-    int qi = 0;
-    if (lane == 0) qi = atomicAdd(head, 1);
-    qi = __shfl_sync(FULL, qi, 0);
-    if (qi >= nwork) break;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  auto next_item = [&]() -> int64_t {
+    int x = 0;
+    if (lane == 0) x = atomicAdd(head, 1);
+    return nw + __shfl_sync(FULL, x, 0);
+  };
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;; it = next_item()) {
+    if (it >= nwork) break;
+    int qi = (int)it;
     if (a.qlist) qi = a.qlist[qi];
     // exact queries: the data's FP32 squared distances are exact integers and this query is an
     // integer vector inside the data's range (stored points always are); others resolve

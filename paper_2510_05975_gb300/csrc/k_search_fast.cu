@@ -178,11 +178,16 @@ __global__ void __launch_bounds__(256, 3) search_fast_kernel(SearchArgs a) {
   const int hmask = a.hash_slots - 1, L = a.L;
   unsigned long long t_ndc = 0, t_hops = 0, t_stop = 0;
 
-  for (;;) {
-    int qi = 0;
-    if (lane == 0) qi = atomicAdd(a.counter, 1);
-    qi = __shfl_sync(FULL, qi, 0);
-    if (qi >= a.nq) break;
+  // each warp takes query (its index) first, then queries nw + (queue head) as it finishes them
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  auto next_item = [&]() -> int64_t {
+    int x = 0;
+    if (lane == 0) x = atomicAdd(a.counter, 1);
+    return nw + __shfl_sync(FULL, x, 0);
+  };
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;; it = next_item()) {
+    if (it >= a.nq) break;
+    const int qi = (int)it;
     if (!a.qids && !(a.qflag && a.qflag[qi] == 0)) {  // not exact: left to the general kernel
       if (lane == 0) a.defer[atomicAdd(a.counter + 1, 1)] = qi;
       continue;
