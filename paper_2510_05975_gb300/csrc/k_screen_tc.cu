@@ -229,6 +229,7 @@ CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uin
   __syncwarp();
   uint32_t prefix = 0;
   int need = Lp;
+  const uint32_t hist_s = smem_u32(hist);
 #pragma unroll 1
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 24 - 8 * pass;
@@ -239,7 +240,8 @@ CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uin
     for (int i = 0; i < CAP_PER_LANE; ++i) {
       const bool valid = i * 32 + lane < cnt;
       const bool match = pass == 0 || ((k[i] ^ prefix) >> (shift + 8)) == 0;
-      if (valid && match) atomicAdd(&hist[(k[i] >> shift) & 255u], 1u);
+      if (valid && match)
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(hist_s + 4u * ((k[i] >> shift) & 255u)) : "memory");
     }
     __syncwarp();
     uint32_t h[8], tot = 0;
@@ -311,14 +313,21 @@ CNG_DEV void fma2(uint32_t& d0, uint32_t& d1, uint32_t a0, uint32_t a1, float b,
 // One row's 32 accumulator columns [cb, cb + 32): screened scores, masking of out-of-range
 // and self columns, minimum against the row threshold, appends below the threshold.  The
 // minimum is taken per group of 4 columns first, so appends visit only groups that hold one.
+CNG_DEV float4 lds_f4(uint32_t saddr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(saddr));
+  return v;
+}
+
 template <bool DUMP>
 CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_t row,
-                           const TcParams& P, const float* nbs, float thr, int& cnt,
+                           const TcParams& P, uint32_t nbs, float thr, int& cnt,
                            uint64_t* rbuf, float* dump) {
-  const float4* nb4 = reinterpret_cast<const float4*>(nbs);
-  float4 y[8];
+  float4 y[8];  // the 32 column norms (shared memory, same address in every lane)
 #pragma unroll
-  for (int q = 0; q < 8; ++q) y[q] = nb4[q];
+  for (int q = 0; q < 8; ++q) y[q] = lds_f4(nbs + 16 * q);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     fma2(r[4 * q + 0], r[4 * q + 1], r[4 * q + 0], r[4 * q + 1], -2.f, y[q].x, y[q].y);
@@ -345,14 +354,17 @@ CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_
                         __uint_as_float(r[4 * g + 2])),
                   __uint_as_float(r[4 * g + 3]));
   const float mall = min3f(min3f(gm[0], gm[1], gm[2]), min3f(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-  if (live && mall < thr) {
+  // appends, under warp-uniform branches (all lanes of the warp are converged here)
+  const bool want = live && mall < thr;
+  if (__any_sync(FULL, want)) {
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
-      if (gm[g] < thr) {
+      const bool wg = want && gm[g] < thr;
+      if (__any_sync(FULL, wg)) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float vj = __uint_as_float(r[4 * g + k]);
-          if (vj < thr) {
+          if (wg && vj < thr) {
             if (cnt < P.cap)
               rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + 4 * g + k);
             else
@@ -536,7 +548,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&t_empty[b]);
           }
-          process_chunk<DUMP>(r, c0 + ch * 32, edge, live, row, P, sNB + stage * TC_BN + ch * 32, thr, cnt, rbuf, dump);
+          process_chunk<DUMP>(r, c0 + ch * 32, edge, live, row, P,
+                              smem_u32(sNB + stage * TC_BN + ch * 32), thr, cnt, rbuf, dump);
         }
         // norms of this stage no longer needed: release the stage (with the MMA's commit)
         __syncwarp();
