@@ -194,8 +194,9 @@ typedef enum { CNG_SEARCH_FIXED = 0, CNG_SEARCH_LEARNED = 1 } cng_search_mode;
  * warps_per_block  queries per CTA (one warp each, <= 8); 0 = autotuned: the first search
  *              of an (L, mode) shape on an index of a given shape (device, dtype, padded d,
  *              adjacency row stride) times every launch shape (1, 2, 4, 8 warps per block x
- *              visited filters of 512, 1024, 2048 slots) on up to 4,096 of its queries and
- *              keeps the fastest for the rest of the process; results do not depend on it
+ *              visited filters of 512, 1024, 2048 slots) on up to 16,384 of its queries
+ *              (best of two runs) and keeps the fastest for the rest of the process; results
+ *              do not depend on it
  */
 typedef struct {
   int32_t mode;
