@@ -439,6 +439,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
       int64_t it = 0;
       int j = 0;
+      int s = 0;        // B stage of tile `it` (it % nst, advanced without dividing)
+      uint32_t ph = 0;  // its phase ((it / nst) & 1)
       bool ok = true;
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
         ok = mbar_wait(a_empty, (j & 1) ^ 1, abort_flag, P.status);
@@ -449,8 +451,6 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           tma_load_2d(sA + kc * (TC_BM * 128), &mapA, kc * TC_KC, (int)(rb * TC_BM), a_full);
         for (int ti = 0; ti < ntiles; ++ti, ++it) {
           const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
-          const int s = (int)(it % P.nst);
-          const uint32_t ph = (uint32_t)((it / P.nst) & 1);
           wave_checkpoint(P, it, nrb, ntiles);
           ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
           if (!ok) break;
@@ -459,6 +459,10 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           for (int kc = 0; kc < P.nkc; ++kc)
             tma_load_2d(dst + kc * (TC_BN * 128), &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
           bulk_load(sNB + s * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &b_full[s]);
+          if (++s == P.nst) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
       }
       if (!ok) {
@@ -471,18 +475,19 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     }
   } else if (warp == TC_MMA) {
     if (lane == 0) {
-      int64_t it = 0, tt = 0;
+      int64_t tt = 0;
       int j = 0;
+      int s = 0;         // B stage of the tile (advanced without dividing)
+      uint32_t sph = 0;  // its phase
       bool ok = true;
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
         ok = mbar_wait(a_full, j & 1, abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA);
-        for (int t = 0; t < ntiles; ++t, ++it, ++tt) {
-          const int s = (int)(it % P.nst);
+        for (int t = 0; t < ntiles; ++t, ++tt) {
           const int b = (int)(tt & 1);
-          ok = mbar_wait(&b_full[s], (uint32_t)((it / P.nst) & 1), abort_flag, P.status);
+          ok = mbar_wait(&b_full[s], sph, abort_flag, P.status);
           if (!ok) break;
           ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> 1) & 1) ^ 1), abort_flag, P.status);
           if (!ok) break;
@@ -501,6 +506,10 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           }
           mma_commit(&b_empty[s]);
           mma_commit(&t_full[b]);
+          if (++s == P.nst) {
+            s = 0;
+            sph ^= 1u;
+          }
         }
         if (!ok) break;
         mma_commit(a_empty);
@@ -517,6 +526,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     uint64_t* rbuf = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rloc) * P.cap;
     uint32_t* hist = hist_all + warp * 256;
     int64_t tt = 0;
+    int stage = 0;     // the B stage (and its norms) of tile tt, advanced without dividing
+    uint32_t sph = 0;  // its phase
     bool ok = true;
     for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
       const int64_t row = rb * TC_BM + rloc;
@@ -531,10 +542,9 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         if (!ok) break;
         tc_fence_after();
         const int64_t c0 = (int64_t)t * TC_BN;
-        const int stage = (int)(tt % P.nst);  // the B stage (and its norms) of this tile
         // observe the stage's TMA completion too (already complete; the stage cannot be refilled
         // before this warp releases it), so the norms written by the copy engine are visible
-        ok = mbar_wait_warp(&b_full[stage], (uint32_t)((tt / P.nst) & 1), abort_flag, P.status);
+        ok = mbar_wait_warp(&b_full[stage], sph, abort_flag, P.status);
         if (!ok) break;
         const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
         const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + accsel * 128);
@@ -554,6 +564,10 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         // norms of this stage no longer needed: release the stage (with the MMA's commit)
         __syncwarp();
         if (lane == 0) mbar_arrive(&b_empty[stage]);
+        if (++stage == P.nst) {
+          stage = 0;
+          sph ^= 1u;
+        }
         if (DUMP) continue;
         // compact every row whose buffer could overflow on the next tile
         unsigned needc = __ballot_sync(FULL, cnt > P.cap - TC_BN);
