@@ -36,8 +36,9 @@ constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
 constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
 constexpr int TC_PRODUCER = 8;
 constexpr int TC_MMA = 9;
-constexpr uint32_t TC_SPIN = 1u << 17;     // wait iterations before declaring a timeout
-constexpr uint32_t TC_SUSPEND_NS = 20000;  // try_wait suspend-time hint (wakes on completion)
+// wait iterations before declaring a timeout (each try_wait may suspend the thread for a
+// system-dependent time; no suspend-time hint, so a completed phase is seen at once)
+constexpr uint32_t TC_SPIN = 1u << 19;
 
 struct TcParams {
   int64_t m, n;
@@ -111,9 +112,9 @@ CNG_DEV void mbar_arrive(uint64_t* b) {
 CNG_DEV bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity), "r"(TC_SUSPEND_NS)
+      : "r"(smem_u32(b)), "r"(parity)
       : "memory");
   return ok != 0;
 }
