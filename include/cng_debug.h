@@ -34,6 +34,15 @@ cng_status cngx_tc_scores_f16(const float *rows_dev, int64_t m, const float *col
  * site counts once per launch). */
 long long cngx_launches(void);
 
+/*
+ * cngx_wait_probe -- failure-path check of the tensor-core screen's bounded waits: one warp
+ * waits on an mbarrier nothing arrives on and polls a device word nothing sets, each with the
+ * screen's own bounded wait; both must run out.  *status_out receives the device status word:
+ * bit 0 (timeout) set and bit 3 clear when the waits expired as designed.  Synchronises the
+ * device; the context stays usable.
+ */
+cng_status cngx_wait_probe(uint32_t *status_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -135,10 +135,19 @@ def lib():
             L.cng_entry_noalloc.argtypes = [vp, i32, i64, i32, vp, vp]
             L.cngx_launches.restype = ctypes.c_longlong
             L.cngx_launches.argtypes = []
+            L.cngx_wait_probe.restype = ctypes.c_int
+            L.cngx_wait_probe.argtypes = [vp]
             L.cng_mlp_adam.restype = ctypes.c_int
             L.cng_mlp_adam.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, vp]
             _lib = L
     return _lib
+
+
+def cngx_wait_probe() -> int:
+    """Device status word after the screen's bounded waits were made to run out (include/cng_debug.h)."""
+    st = ctypes.c_uint32(0)
+    _check(lib().cngx_wait_probe(ctypes.byref(st)))
+    return st.value
 
 
 def cng_last_error() -> str:

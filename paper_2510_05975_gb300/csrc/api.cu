@@ -1182,6 +1182,19 @@ extern "C" cng_status cngx_tc_scores(const float* rows, int64_t m, const float* 
   return tc_scores(rows, m, cols, n, d, 0, 1.f, scores, stream);
 }
 
+extern "C" cng_status cngx_wait_probe(uint32_t* status_out) {
+  if (!status_out) return fail(CNG_E_INVAL, "status_out must be non-NULL");
+  uint32_t* dev = nullptr;
+  CK(cudaMalloc(&dev, 2 * sizeof(uint32_t)));
+  cudaError_t e = cudaMemset(dev, 0, 2 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = launch_wait_probe(dev, dev + 1, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status_out, dev, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  cudaFree(dev);
+  CK(e);
+  return CNG_OK;
+}
+
 extern "C" cng_status cngx_tc_scores_f16(const float* rows, int64_t m, const float* cols, int64_t n,
                                          int32_t d, float scale, float* scores, void* stream) {
   return tc_scores(rows, m, cols, n, d, 1, scale, scores, stream);

@@ -131,8 +131,9 @@ CNG_DEV bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, u
 
 // Warp-uniform bounded wait: every lane polls, the warp proceeds only when all lanes saw the
 // phase complete, so the whole warp leaves together (needed before .sync.aligned TMEM loads).
-CNG_DEV bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
-  for (uint32_t i = 0; i < TC_SPIN; ++i) {
+CNG_DEV bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t* status,
+                            uint32_t spin = TC_SPIN) {
+  for (uint32_t i = 0; i < spin; ++i) {
     if (__all_sync(FULL, mbar_try(b, parity))) return true;
     if ((i & 15u) == 15u && __any_sync(FULL, *abort_flag != 0)) return false;
   }
@@ -621,6 +622,37 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
+}
+
+// Failure-path probe: one warp waits, with the screen's own bounded wait, on an mbarrier that
+// nothing arrives on (and, with spin_flag, on a global flag nothing sets), so both waits run
+// out and record ST_TIMEOUT in *status without faulting or hanging the context.
+__global__ void wait_probe_kernel(uint32_t* status, const uint32_t* never_set) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_warp(&bar, 0, &abort_flag, status, 4096);
+  // the checkpoint spin of the producer: a bounded poll of a counter that never reaches 1
+  bool seen = false;
+  for (uint32_t i = 0; i < TC_SYNC_SPIN && !seen; ++i) {
+    seen = ld_acquire_u32(never_set) >= 1u;
+    __nanosleep(200);
+  }
+  if (threadIdx.x == 0) {
+    if (ok) atomicOr(status, ST_BOUNDS);        // a wait that should not have completed did
+    if (!seen) atomicOr(status, ST_TIMEOUT);
+  }
+}
+
+cudaError_t launch_wait_probe(uint32_t* status, const uint32_t* never_set, cudaStream_t s) {
+  count_launch();
+  wait_probe_kernel<<<1, 32, 0, s>>>(status, never_set);
+  return cudaGetLastError();
 }
 
 // ---- host side ---------------------------------------------------------------------------------

@@ -35,6 +35,9 @@ bool tc_screen_supported(int d, bool fp16);
 size_t screen_tc_rowbuf_words(int64_t m, int64_t n, int Lp);
 cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg);
 // Test aid: writes every screened score s(x, y) to dump[m][n] instead of selecting.
+// One warp runs the screen's bounded waits on a barrier and a flag that never complete; they
+// must run out and leave ST_TIMEOUT in *status (never_set: a zeroed device word).
+cudaError_t launch_wait_probe(uint32_t* status, const uint32_t* never_set, cudaStream_t s);
 cudaError_t launch_screen_tc_dump(const TcScreenArgs& a, float* dump, cudaStream_t s,
                                   std::string* msg);
 

@@ -91,3 +91,17 @@ def test_tc_scores_fp16_scaled(kind, m, n, d, scale):
     # the scaled FP16 operands are 8x closer to the data than BF16 ones
     rb = _bf16(R) * scale
     assert np.abs(rh - R * scale).max() < np.abs(rb - R * scale).max()
+
+
+def test_bounded_waits_expire_without_fault():
+    """The screen's bounded waits (an mbarrier nothing arrives on, a flag nothing sets) run out,
+    record the timeout bit and return; the context stays usable for a screen afterwards."""
+    need_gpu()
+    cng = lib()
+    st = cng.cngx_wait_probe()
+    assert st & 1 and not st & 8
+    import oracle
+    A = synth.generate("sift", 600, 64, seed=31)
+    ids, _, _ = cng.cng_knn(tensor(A), 5)
+    gt, _ = oracle.knn(A, 5)
+    assert np.array_equal(ids.cpu().numpy(), gt)
