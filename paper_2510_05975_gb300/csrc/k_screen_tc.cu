@@ -32,6 +32,11 @@ namespace cng {
 
 constexpr int TC_BM = 256;          // rows per CTA block (two M=128 accumulators)
 constexpr int TC_BN = 128;          // columns per B tile
+constexpr int TC_NBUF = 512 / (2 * TC_BN);  // accumulator buffers in the 512 TMEM columns
+constexpr int TC_NBUF_LOG = TC_NBUF == 4 ? 2 : 1;
+constexpr int TC_MAXST = TC_BN == 64 ? 8 : 4;  // B stages at most
+static_assert((2 * TC_MAXST + 2 * TC_NBUF + 3) * 8 + 16 <= 256, "barrier block exceeds its 256 bytes");
+static_assert(TC_NBUF == 2 || TC_NBUF == 4, "two or four accumulator buffers");
 constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
 constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
 constexpr int TC_PRODUCER = 8;
@@ -61,7 +66,7 @@ struct TcParams {
 // the CTAs of a wave stay within TC_SYNC_D * TC_SYNC_K B tiles of each other and share the tiles
 // through L2 instead of each streaming them from DRAM.  The wait only serves the cache: it is
 // bounded (about 2 ms) and the producer proceeds when it expires.
-constexpr int TC_SYNC_K = 256;
+constexpr int TC_SYNC_K = 256 * 128 / TC_BN;  // tiles per checkpoint window (32,768 columns)
 constexpr int TC_SYNC_D = 8;
 constexpr uint32_t TC_SYNC_SPIN = 8192;
 
@@ -396,9 +401,9 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   uint64_t* bars = reinterpret_cast<uint64_t*>(sNB + P.nst * TC_BN);
   uint64_t* b_full = bars;               // [nst]
   uint64_t* b_empty = bars + P.nst;      // [nst]
-  uint64_t* t_full = bars + 2 * P.nst;   // [2]
-  uint64_t* t_empty = t_full + 2;        // [2]
-  uint64_t* a_full = t_empty + 2;        // [1]
+  uint64_t* t_full = bars + 2 * P.nst;   // [TC_NBUF]
+  uint64_t* t_empty = t_full + TC_NBUF;  // [TC_NBUF]
+  uint64_t* a_full = t_empty + TC_NBUF;  // [1]
   uint64_t* a_empty = a_full + 1;        // [1]
   uint64_t* fin = a_empty + 1;           // [1] MMA drain at exit
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
@@ -414,7 +419,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       mbar_init(&b_full[i], 1);
       mbar_init(&b_empty[i], 1 + 8);  // MMA commit + the 8 epilogue warps (norms read)
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < TC_NBUF; ++i) {
       mbar_init(&t_full[i], 1);
       mbar_init(&t_empty[i], 8);
     }
@@ -488,10 +493,10 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         tc_fence_after();
         const uint32_t a_base = smem_u32(sA);
         for (int t = 0; t < ntiles; ++t, ++tt) {
-          const int b = (int)(tt & 1);
+          const int b = (int)(tt & (TC_NBUF - 1));
           ok = mbar_wait(&b_full[s], sph, abort_flag, P.status);
           if (!ok) break;
-          ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> 1) & 1) ^ 1), abort_flag, P.status);
+          ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> TC_NBUF_LOG) & 1) ^ 1), abort_flag, P.status);
           if (!ok) break;
           tc_fence_after();
           const uint32_t b_base = smem_u32(sB + s * b_bytes);
@@ -502,7 +507,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 #pragma unroll
               for (int acc = 0; acc < 2; ++acc) {
                 const uint64_t ad = desc_sw128(a_base + kc * (TC_BM * 128) + acc * (128 * 128) + k16 * 32);
-                mma_f16(tmem + (uint32_t)(b * 256 + acc * 128), ad, bd, P.idesc, (kc | k16) != 0);
+                mma_f16(tmem + (uint32_t)(b * (2 * TC_BN) + acc * TC_BN), ad, bd, P.idesc, (kc | k16) != 0);
               }
             }
           }
@@ -539,8 +544,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       const int t0 = sweep_start(P, rb, ntiles);
       for (int ti = 0; ti < ntiles; ++ti, ++tt) {
         const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
-        const int b = (int)(tt & 1);
-        ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> 1) & 1), abort_flag, P.status);
+        const int b = (int)(tt & (TC_NBUF - 1));
+        ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> TC_NBUF_LOG) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
         const int64_t c0 = (int64_t)t * TC_BN;
@@ -549,7 +554,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         ok = mbar_wait_warp(&b_full[stage], sph, abort_flag, P.status);
         if (!ok) break;
         const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
-        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + accsel * 128);
+        const uint32_t ta =
+            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * (2 * TC_BN) + accsel * TC_BN);
 #pragma unroll 1
         for (int ch = 0; ch < TC_BN / 32; ++ch) {
           uint32_t r[32];
@@ -755,7 +761,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   p.nkc = kpad / 64;
   const int a_bytes = TC_BM * kpad * 2, b_bytes = TC_BN * kpad * 2;
   const int budget = 220 * 1024 - a_bytes - 1024 - 256 - 8 * 256 * 4;
-  p.nst = std::min(4, budget / (b_bytes + TC_BN * 4));
+  p.nst = std::min(TC_MAXST, budget / (b_bytes + TC_BN * 4));
   if (p.nst < 2) {
     if (msg) *msg = "shared memory too small for two B stages; ";
     return cudaErrorInvalidValue;
