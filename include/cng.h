@@ -38,7 +38,7 @@ typedef enum {
   CNG_E_INTERNAL = -6     /* a device-side consistency check failed */
 } cng_status;
 
-typedef enum { CNG_L2 = 0, CNG_IP_AS_L2 = 1 } cng_metric;
+typedef enum { CNG_L2 = 0, CNG_IP_AS_L2 = 1, CNG_IP = 2 } cng_metric;
 typedef enum { CNG_F32 = 0, CNG_F16 = 1 } cng_dtype;
 typedef enum {
   CNG_SCREEN_FP32 = 0,  /* FP32 CUDA-core candidate screen (direct differences) */
@@ -54,7 +54,15 @@ typedef enum {
  *   tau     [tau]    pruning parameter of Def. 2 / Eq. 1, >= 0, raw distance units
  *   R       [M]      out-degree bound, 1 <= R <= L, R <= 64
  *   L       [C]      candidate-list size: the exact L nearest points of P \ {p}, L < n, L <= 256
- *   metric           CNG_IP_AS_L2 requires unit-norm rows (|‖x‖ - 1| <= 1e-3) and then uses L2
+ *   metric           CNG_IP_AS_L2 requires unit-norm rows (|‖x‖ - 1| <= 1e-3) and then uses L2.
+ *                    CNG_IP: maximum inner product for rows of any norm, by building the L2
+ *                    graph of the augmented rows x' = [x, sqrt(M^2 - |x|^2)] (M^2 = max |x|^2,
+ *                    each |x|^2 summed in FP64 in coordinate order, the extra coordinate the
+ *                    correctly rounded FP64 root rounded to FP32; d <= 4095).  Searches (and
+ *                    traces, stop training) take d-dimensional queries and use q' = [q, 0], so
+ *                    |q' - x'|^2 = |q|^2 + M^2 - 2 <q, x>: ids come in decreasing <q, x> and the
+ *                    returned distances are |q' - x'|.  The Euclidean graph is the paper's
+ *                    (Sec. 2.1); the augmentation is this library's addition.
  *   screen           cng_screen
  *   tie_band         relative band for FP64 re-decision, >= 5e-6 (default 1e-5)
  *   margin           screened list size is L + margin (default 32; clipped to n - 1)

@@ -296,3 +296,23 @@ def recall(found_ids, true_ids) -> float:
     k = true_ids.shape[1]
     hit = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(found_ids, true_ids))
     return hit / (k * true_ids.shape[0])
+
+
+def mips_augment(X):
+    """Rows for maximum-inner-product search as Euclidean search (the library's CNG_IP metric;
+    the paper builds its graph over a metric space, Sec. 2.1, and has no inner-product variant):
+    x' = [x, sqrt(M^2 - |x|^2)] with |x|^2 summed in FP64 over the coordinates in order (each
+    square is exact), M^2 = max |x|^2, and the correctly rounded FP64 root rounded to FP32.
+    Returns (X' float32 [n, d + 1], M^2)."""
+    X = _f32(X)
+    sq = X.astype(np.float64) ** 2
+    nrm2 = np.cumsum(sq, axis=1)[:, -1]  # sequential left-to-right sums
+    M2 = float(nrm2.max())
+    extra = np.sqrt(M2 - nrm2).astype(np.float32)
+    return np.concatenate([X, extra[:, None]], axis=1), M2
+
+
+def mips_queries(Q):
+    """Queries for an augmented index: q' = [q, 0], so |q' - x'|^2 = |q|^2 + M^2 - 2 <q, x>."""
+    Q = _f32(Q)
+    return np.concatenate([Q, np.zeros((Q.shape[0], 1), np.float32)], axis=1)

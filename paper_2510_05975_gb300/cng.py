@@ -19,7 +19,7 @@ _lib = None
 
 CNG_OK, CNG_E_INVAL, CNG_E_NOMEM, CNG_E_CUDA, CNG_E_TIMEOUT, CNG_E_UNSUPPORTED, CNG_E_INTERNAL = (
     0, -1, -2, -3, -4, -5, -6)
-CNG_L2, CNG_IP_AS_L2 = 0, 1
+CNG_L2, CNG_IP_AS_L2, CNG_IP = 0, 1, 2
 CNG_F32, CNG_F16 = 0, 1
 CNG_SCREEN_FP32, CNG_SCREEN_TC, CNG_SCREEN_TC_BF16 = 0, 1, 2
 CNG_SEARCH_FIXED, CNG_SEARCH_LEARNED = 0, 1

@@ -18,6 +18,7 @@
 #include "mlp_internal.h"
 #include "order_internal.h"
 #include "screen_tc.h"
+#include "mips_internal.h"
 
 namespace cng {
 
@@ -90,6 +91,8 @@ using namespace cng;
 struct cng_index {
   int64_t n = 0;
   int d = 0, dpad = 0, dtype = 0, R = 0, L = 0;
+  int metric = CNG_L2;      // CNG_IP: rows (and queries) are augmented by one coordinate
+  double mips_M2 = 0.0;     // CNG_IP: the largest squared row norm
   int rs = 0;               // adjacency row stride (R + REPAIR_SLOTS)
   int32_t entry = -1;
   int exact = 0;
@@ -443,11 +446,13 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
   if (dtype != CNG_F32 && dtype != CNG_F16) return fail(CNG_E_INVAL, "dtype must be CNG_F32 or CNG_F16");
   if (n < 2 || n > 0x7fffffffLL) return fail(CNG_E_INVAL, "n must be in [2, 2^31 - 1]");
   if (d < 1 || d > 4096) return fail(CNG_E_INVAL, "d must be in [1, 4096]");
+  if (p->metric == CNG_IP && d > 4095) return fail(CNG_E_INVAL, "CNG_IP needs d <= 4095");
   if (p->L < 1 || p->L > 256 || p->L >= n) return fail(CNG_E_INVAL, "L must satisfy 1 <= L <= 256 and L < n");
   if (p->R < 1 || p->R > p->L || p->R > 64) return fail(CNG_E_INVAL, "R must satisfy 1 <= R <= min(L, 64)");
   if (!(p->alpha > 0.0) || !std::isfinite(p->alpha)) return fail(CNG_E_INVAL, "alpha must be a positive finite number");
   if (!(p->tau >= 0.0) || !std::isfinite(p->tau)) return fail(CNG_E_INVAL, "tau must be finite and >= 0");
-  if (p->metric != CNG_L2 && p->metric != CNG_IP_AS_L2) return fail(CNG_E_INVAL, "unknown metric");
+  if (p->metric != CNG_L2 && p->metric != CNG_IP_AS_L2 && p->metric != CNG_IP)
+    return fail(CNG_E_INVAL, "unknown metric");
   if (p->screen != CNG_SCREEN_FP32 && p->screen != CNG_SCREEN_TC && p->screen != CNG_SCREEN_TC_BF16)
     return fail(CNG_E_INVAL, "unknown screen");
   if (!(p->tie_band >= 5e-6) || p->tie_band > 0.01) return fail(CNG_E_INVAL, "tie_band must be in [5e-6, 0.01]");
@@ -472,6 +477,36 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   if (vs != CNG_OK) return vs;
   cudaStream_t s = (cudaStream_t)stream;
   const cng_build_params& P = *params;
+  if (P.metric == CNG_IP) {
+    // maximum inner product: the L2 index of the augmented rows [x, sqrt(M^2 - |x|^2)]
+    DevPool apool;
+    const size_t el = dtype == CNG_F32 ? 4 : 2;
+    const void* src = points;
+    if (!is_device_ptr(points)) {
+      char* tmp;
+      CK(apool.alloc(&tmp, (size_t)n * d * el));
+      CK(cudaMemcpyAsync(tmp, points, (size_t)n * d * el, cudaMemcpyHostToDevice, s));
+      src = tmp;
+    }
+    double* nrm2;
+    unsigned long long* mbits;
+    float* aug;
+    CK(apool.alloc(&nrm2, (size_t)n));
+    CK(apool.alloc(&mbits, 1));
+    CK(apool.alloc(&aug, (size_t)n * (d + 1)));
+    CK(launch_mips_augment(src, dtype, n, d, nrm2, mbits, aug, s));
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, mbits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cng_build_params q = P;
+    q.metric = CNG_L2;
+    cng_status st = cng_build(aug, CNG_F32, n, d + 1, &q, stream, out, stats);
+    if (st == CNG_OK) {
+      (*out)->metric = CNG_IP;
+      memcpy(&(*out)->mips_M2, &hb, sizeof(double));
+    }
+    return st;
+  }
   // BF16 operands (unscaled) for f32 data on request; FP16 input is screened in FP16 as stored
   const int bf16ops = P.screen == CNG_SCREEN_TC_BF16 && dtype == CNG_F32;
   int screen = P.screen == CNG_SCREEN_TC_BF16 ? CNG_SCREEN_TC : P.screen;
@@ -801,6 +836,29 @@ extern "C" cng_status cng_lists(const cng_index* ix, const int32_t** cand, const
 
 // Exact data: per-query exactness flags and, with 8-bit rows, the queries as 8-bit rows
 // (a buffer of the index, grown on demand; searches on one index run one at a time).
+// The queries as the index searches them: device memory with the index's dimensions (host
+// queries are copied; an inner-product index appends the zero coordinate).  Allocations are
+// owned by `pool`.
+static cng_status index_queries(const cng_index* ix, const float* queries, int64_t nq, DevPool& pool,
+                                cudaStream_t s, const float** out) {
+  const int din = ix->metric == CNG_IP ? ix->d - 1 : ix->d;
+  const float* qd = queries;
+  if (!is_device_ptr(queries)) {
+    float* t;
+    CK(pool.alloc(&t, (size_t)nq * din));
+    CK(cudaMemcpyAsync(t, queries, (size_t)nq * din * 4, cudaMemcpyHostToDevice, s));
+    qd = t;
+  }
+  if (ix->metric == CNG_IP) {
+    float* a;
+    CK(pool.alloc(&a, (size_t)nq * ix->d));
+    CK(launch_append_zero(qd, nq, din, a, s));
+    qd = a;
+  }
+  *out = qd;
+  return CNG_OK;
+}
+
 // Grows the deferred-query list of ix to at least nq entries (callers hold ix->mu).
 static cudaError_t ensure_defer(cng_index* ix, int64_t nq) {
   if (ix->defer_cap >= nq) return cudaSuccess;
@@ -859,13 +917,11 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     return CNG_OK;
   }
   DevPool pool;
-  const float* qd = queries;
   const bool host_q = !is_device_ptr(queries);
-  if (host_q) {
-    float* t;
-    CK(pool.alloc(&t, (size_t)nq * ix->d));
-    CK(cudaMemcpyAsync(t, queries, (size_t)nq * ix->d * 4, cudaMemcpyHostToDevice, s));
-    qd = t;
+  const float* qd = nullptr;
+  {
+    cng_status qs = index_queries(ix, queries, nq, pool, s, &qd);
+    if (qs != CNG_OK) return qs;
   }
   int32_t *o_ids = ids, *o_ndc = ndc, *o_hops = hops, *o_flags = flags;
   float* o_d = dists;
@@ -1275,8 +1331,13 @@ extern "C" cng_status cng_trace(const cng_index* cix, const float* queries, int6
   DevPool pool;
   float* dists;
   CK(pool.alloc(&dists, (size_t)nq * k));
+  const float* qd = nullptr;
+  {
+    cng_status qs = index_queries(ix, queries, nq, pool, s, &qd);
+    if (qs != CNG_OK) return qs;
+  }
   std::lock_guard<std::mutex> lock(ix->mu);
-  cng_status st = run_trace(ix, queries, nq, k, L, max_trace, feats, hops, tlc, ids, dists, s);
+  cng_status st = run_trace(ix, qd, nq, k, L, max_trace, feats, hops, tlc, ids, dists, s);
   if (st != CNG_OK) return st;
   CK(cudaStreamSynchronize(s));
   return CNG_OK;
@@ -1297,12 +1358,10 @@ extern "C" cng_status cng_stop_train(const cng_index* cix, const float* train_q,
     return fail(CNG_E_INVAL, "need nq >= 1, 1 <= k <= L <= 256, max_trace <= 4096, batch <= 2^20");
   cudaStream_t s = (cudaStream_t)stream;
   DevPool pool;
-  const float* qd = train_q;
-  if (!is_device_ptr(train_q)) {
-    float* t;
-    CK(pool.alloc(&t, (size_t)nq * ix->d));
-    CK(cudaMemcpyAsync(t, train_q, (size_t)nq * ix->d * 4, cudaMemcpyHostToDevice, s));
-    qd = t;
+  const float* qd = nullptr;
+  {
+    cng_status qs = index_queries(ix, train_q, nq, pool, s, &qd);
+    if (qs != CNG_OK) return qs;
   }
   Timer tm(s);
   tm.mark();

@@ -153,3 +153,28 @@ def test_adaptive_build_matches_oracle(kind, n, d, R, L, screen):
     _check_graph(X, G, idx, cng, R, L)
     assert 0.9 <= st["alpha_mean"] <= 1.6
     cng.cng_free(idx)
+
+
+@pytest.mark.parametrize("screen", [0, 1])
+def test_mips_metric_matches_oracle(screen):
+    """CNG_IP: the graph equals the oracle's graph of the augmented rows, searches with plain
+    d-dimensional queries equal the oracle's Alg. 1 on the augmented queries, and the results
+    are the largest inner products."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(7)
+    X = (synth.generate("gauss", 2500, 24, seed=7) * rng.uniform(0.3, 2.5, (2500, 1))).astype(np.float32)
+    Q = synth.generate("gauss", 200, 24, seed=1007)
+    Xa, M2 = oracle.mips_augment(X)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=16, L=64, screen=screen, keep_lists=True,
+                            metric=cng.CNG_IP)
+    G = oracle.build_graph(Xa, 1.2, 0.0, 16, 64)
+    _check_graph(Xa, G, idx, cng, 16, 64)
+    adj, deg, _, entry = cng.cng_graph(idx)
+    res = cng.cng_search(idx, tensor(Q), k=10, L=64)
+    ids, ds, _, hops = oracle.search(Xa, host(adj), host(deg), entry, oracle.mips_queries(Q), 10, 64)
+    assert np.array_equal(host(res["ids"]), ids)
+    assert np.array_equal(host(res["hops"]), hops)
+    top = np.argsort(-(Q.astype(np.float64) @ X.astype(np.float64).T), axis=1, kind="stable")[:, :10]
+    assert oracle.recall(host(res["ids"]), top) > 0.9
+    cng.cng_free(idx)
