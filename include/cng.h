@@ -242,6 +242,32 @@ cng_status cng_search(const cng_index *index, const float *queries, int64_t nq, 
                       cng_search_stats *stats);
 
 /* ---------------------------------------------------------------------------------------
+ * Grid search of tau on held-out queries (Sec. 5, parameter configuration: tau = 0 against
+ * the coarse values 10, 1, 0.1, 0.01, 0.001, then a finer search around the best).  Every
+ * trial builds the graph of `points` with `params` (its tau replaced) and scores it on the
+ * nq queries: the smallest beam width L in search_Ls[0 .. n_Ls) (ascending, each >= k) whose
+ * mean Recall@k against gt_ids [nq][k] (host, the exact k nearest ids, e.g. from cng_knn)
+ * reaches `target`, and the mean number of hop vertices at that width -- a device-independent
+ * cost (the paper compares query speed; hops count the search work and do not depend on the
+ * machine).  Fine step: with the best coarse value t > 0, t / 2 and 2 t; with t = 0, 0.0005.
+ * The best trial has the fewest mean hops among those reaching the target (ties: smaller
+ * tau); *best_tau = 0 when none reaches it.  trials [max_trials] receives each trial in the
+ * order run (up to 8), *n_trials their count.  Synchronises; the indexes are freed.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  double tau;
+  int32_t L;         /* smallest width reaching the target, 0 if none */
+  double recall;     /* mean Recall@k at L (at the largest width if none reaches the target) */
+  double hops_mean;  /* mean hop vertices per query at that width */
+} cng_tau_trial;
+
+cng_status cng_tune_tau(const void *points, int32_t dtype, int64_t n, int32_t d,
+                        const cng_build_params *params, const float *queries, int64_t nq,
+                        int32_t k, const int32_t *gt_ids, const int32_t *search_Ls, int32_t n_Ls,
+                        double target, void *stream, double *best_tau, cng_tau_trial *trials,
+                        int32_t max_trials, int32_t *n_trials);
+
+/* ---------------------------------------------------------------------------------------
  * Learned early stop.  Not part of the paper (its search stops only by Alg. 1's rule): a
  * 16 -> 64 -> 64 -> 1 ReLU network reads the state of a search after a hop and predicts whether
  * the top-k result list is already final; the learned search mode stops when the predicted

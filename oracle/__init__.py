@@ -316,3 +316,42 @@ def mips_queries(Q):
     """Queries for an augmented index: q' = [q, 0], so |q' - x'|^2 = |q|^2 + M^2 - 2 <q, x>."""
     Q = _f32(Q)
     return np.concatenate([Q, np.zeros((Q.shape[0], 1), np.float32)], axis=1)
+
+
+def tune_tau(X, alpha: float, R: int, L: int, Q, k: int, gt_ids, search_Ls, target: float):
+    """The grid search of tau on held-out queries (Sec. 5 parameter configuration): tau = 0, then
+    the coarse values 10, 1, 0.1, 0.01, 0.001, then t / 2 and 2 t around the best coarse value t
+    (0.0005 when t = 0).  A trial's score is the smallest width in search_Ls whose mean
+    Recall@k reaches `target` and the mean hops there (the recall summed query by query in
+    order).  Best: reaches the target, then fewest mean hops, then smaller tau.
+    Returns (best_tau, trials as dicts in the order run)."""
+    gt = [set(int(v) for v in row) for row in np.asarray(gt_ids)]
+    done = []
+
+    def run(tau):
+        if any(t["tau"] == tau for t in done):
+            return
+        G = build_graph(X, alpha, tau, R, L)
+        tr = dict(tau=tau, L=0, recall=0.0, hops_mean=0.0)
+        for Ls in search_Ls:
+            ids, _, _, hops = search(X, G.adj, G.deg, G.entry, Q, k, int(Ls))
+            rec = 0.0
+            for q in range(len(Q)):
+                rec += sum(1 for v in ids[q] if int(v) in gt[q]) / k
+            tr["recall"] = rec / len(Q)
+            tr["hops_mean"] = float(int(hops.astype(np.int64).sum())) / len(Q)
+            if tr["recall"] >= target:
+                tr["L"] = int(Ls)
+                break
+        done.append(tr)
+
+    def key(t):
+        return (0 if t["L"] > 0 else 1, t["hops_mean"] if t["L"] > 0 else 0.0, t["tau"])
+
+    for tau in (0.0, 10.0, 1.0, 0.1, 0.01, 0.001):
+        run(tau)
+    best = min(done, key=key)
+    for tau in ((best["tau"] / 2, best["tau"] * 2) if best["tau"] > 0 else (0.0005, 0.0005)):
+        run(tau)
+    best = min(done, key=key)
+    return (best["tau"] if best["L"] > 0 else 0.0), done

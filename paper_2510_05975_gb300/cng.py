@@ -66,6 +66,11 @@ class SearchParams(ctypes.Structure):
                 ("min_stable", ctypes.c_int32)]
 
 
+class TauTrial(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("L", ctypes.c_int32), ("recall", ctypes.c_double),
+                ("hops_mean", ctypes.c_double)]
+
+
 class SearchStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("ndc_total", ctypes.c_int64),
                 ("hops_total", ctypes.c_int64), ("fp64_decisions", ctypes.c_int64),
@@ -135,6 +140,11 @@ def lib():
             L.cng_entry_noalloc.argtypes = [vp, i32, i64, i32, vp, vp]
             L.cngx_launches.restype = ctypes.c_longlong
             L.cngx_launches.argtypes = []
+            L.cng_tune_tau.restype = ctypes.c_int
+            L.cng_tune_tau.argtypes = [vp, i32, i64, i32, ctypes.POINTER(BuildParams), vp, i64, i32,
+                                       vp, vp, i32, ctypes.c_double, vp,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(TauTrial),
+                                       i32, ctypes.POINTER(ctypes.c_int32)]
             L.cngx_wait_probe.restype = ctypes.c_int
             L.cngx_wait_probe.argtypes = [vp]
             L.cng_mlp_adam.restype = ctypes.c_int
@@ -227,6 +237,29 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
     _check(lib().cng_build(_ptr(points), dt, n, d, ctypes.byref(p), _stream(stream),
                            ctypes.byref(h), ctypes.byref(st)))
     return Index(h.value, n, d), _as_dict(st)
+
+
+def cng_tune_tau(points, alpha: float, R: int, L: int, queries, k: int, gt_ids, search_Ls,
+                 target: float, metric: int = CNG_L2, screen: int = CNG_SCREEN_TC, stream=None):
+    """cng_tune_tau of include/cng.h.  points / queries as cng_build / cng_search; gt_ids: host
+    int32 [nq, k].  Returns (best_tau, [dict(tau, L, recall, hops_mean), ...])."""
+    import numpy as np
+    if isinstance(points, torch.Tensor):
+        dt = {torch.float32: CNG_F32, torch.float16: CNG_F16}[points.dtype]
+    else:
+        dt = {np.dtype("float32"): CNG_F32, np.dtype("float16"): CNG_F16}[points.dtype]
+    n, d = points.shape
+    p = BuildParams(alpha, 0.0, R, L, metric, screen, 1e-5, 32, 0, 0, 0, 0, 0.0, 0.0, 0.0)
+    gt = np.ascontiguousarray(gt_ids, dtype=np.int32)
+    Ls = np.ascontiguousarray(search_Ls, dtype=np.int32)
+    best = ctypes.c_double()
+    trials = (TauTrial * 8)()
+    nt = ctypes.c_int32()
+    _check(lib().cng_tune_tau(_ptr(points), dt, n, d, ctypes.byref(p), _ptr(queries), queries.shape[0],
+                              k, gt.ctypes.data, Ls.ctypes.data, len(Ls), float(target), _stream(stream),
+                              ctypes.byref(best), trials, 8, ctypes.byref(nt)))
+    return best.value, [dict(tau=t.tau, L=t.L, recall=t.recall, hops_mean=t.hops_mean)
+                        for t in trials[:nt.value]]
 
 
 def cng_free(index: Index):

@@ -1095,6 +1095,100 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
   return CNG_OK;
 }
 
+extern "C" cng_status cng_tune_tau(const void* points, int32_t dtype, int64_t n, int32_t d,
+                                   const cng_build_params* params, const float* queries,
+                                   int64_t nq, int32_t k, const int32_t* gt_ids,
+                                   const int32_t* search_Ls, int32_t n_Ls, double target,
+                                   void* stream, double* best_tau, cng_tau_trial* trials,
+                                   int32_t max_trials, int32_t* n_trials) {
+  if (!points || !params || !queries || !gt_ids || !search_Ls || !best_tau || !n_trials)
+    return fail(CNG_E_INVAL, "pointers must be non-NULL");
+  if (nq < 1 || k < 1 || n_Ls < 1 || !(target > 0.0 && target <= 1.0) || max_trials < 0 ||
+      (max_trials > 0 && !trials))
+    return fail(CNG_E_INVAL, "need nq >= 1, k >= 1, n_Ls >= 1, 0 < target <= 1");
+  for (int i = 0; i < n_Ls; ++i)
+    if (search_Ls[i] < k || search_Ls[i] > 256 || (i > 0 && search_Ls[i] <= search_Ls[i - 1]))
+      return fail(CNG_E_INVAL, "search_Ls must ascend with k <= L <= 256");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevPool pool;
+  int32_t *ids_d, *hops_d;
+  float* dists_d;
+  CK(pool.alloc(&ids_d, (size_t)nq * k));
+  CK(pool.alloc(&dists_d, (size_t)nq * k));
+  CK(pool.alloc(&hops_d, (size_t)nq));
+  std::vector<int32_t> ids((size_t)nq * k), hops((size_t)nq);
+  std::vector<std::vector<int32_t>> gt((size_t)nq);
+  for (int64_t q = 0; q < nq; ++q) {
+    gt[q].assign(gt_ids + q * k, gt_ids + (q + 1) * k);
+    std::sort(gt[q].begin(), gt[q].end());
+  }
+  std::vector<cng_tau_trial> done;
+  auto run = [&](double tau) -> cng_status {
+    for (const auto& t : done)
+      if (t.tau == tau) return CNG_OK;
+    cng_build_params bp = *params;
+    bp.tau = tau;
+    cng_index* ix = nullptr;
+    cng_status st = cng_build(points, dtype, n, d, &bp, stream, &ix, nullptr);
+    if (st != CNG_OK) return st;
+    cng_tau_trial tr{tau, 0, 0.0, 0.0};
+    for (int li = 0; li < n_Ls; ++li) {
+      cng_search_params sp{};
+      st = cng_search(ix, queries, nq, k, search_Ls[li], &sp, ids_d, dists_d, nullptr, hops_d,
+                      nullptr, stream, nullptr);
+      if (st != CNG_OK) break;
+      if (cudaMemcpyAsync(ids.data(), ids_d, ids.size() * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemcpyAsync(hops.data(), hops_d, hops.size() * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        st = fail(CNG_E_CUDA, "tau search: copy of the results failed");
+        break;
+      }
+      double rec = 0.0, h = 0.0;
+      for (int64_t q = 0; q < nq; ++q) {
+        int hit = 0;
+        for (int j = 0; j < k; ++j)
+          hit += std::binary_search(gt[q].begin(), gt[q].end(), ids[q * k + j]) ? 1 : 0;
+        rec += (double)hit / k;
+        h += hops[q];
+      }
+      tr.recall = rec / (double)nq;
+      tr.hops_mean = h / (double)nq;
+      if (tr.recall >= target) {
+        tr.L = search_Ls[li];
+        break;
+      }
+    }
+    cng_free(ix);
+    if (st != CNG_OK) return st;
+    done.push_back(tr);
+    return CNG_OK;
+  };
+  // the better of two trials: reaches the target, then fewer hops, then smaller tau
+  auto better = [](const cng_tau_trial& a, const cng_tau_trial& b) {
+    if ((a.L > 0) != (b.L > 0)) return a.L > 0;
+    if (a.L > 0 && a.hops_mean != b.hops_mean) return a.hops_mean < b.hops_mean;
+    return a.tau < b.tau;
+  };
+  for (double tau : {0.0, 10.0, 1.0, 0.1, 0.01, 0.001}) {
+    cng_status st = run(tau);
+    if (st != CNG_OK) return st;
+  }
+  cng_tau_trial best = done[0];
+  for (const auto& t : done)
+    if (better(t, best)) best = t;
+  const double fine[2] = {best.tau > 0.0 ? best.tau / 2 : 0.0005, best.tau > 0.0 ? best.tau * 2 : 0.0005};
+  for (double tau : fine) {
+    cng_status st = run(tau);
+    if (st != CNG_OK) return st;
+  }
+  for (const auto& t : done)
+    if (better(t, best)) best = t;
+  *best_tau = best.L > 0 ? best.tau : 0.0;
+  *n_trials = (int32_t)std::min<size_t>(done.size(), (size_t)max_trials);
+  for (int i = 0; i < *n_trials; ++i) trials[i] = done[i];
+  return CNG_OK;
+}
+
 extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, int64_t m, int32_t d,
                               int32_t k, int32_t screen, double tie_band, int32_t* ids, float* dists,
                               void* stream, cng_build_stats* stats) {

@@ -178,3 +178,19 @@ def test_mips_metric_matches_oracle(screen):
     top = np.argsort(-(Q.astype(np.float64) @ X.astype(np.float64).T), axis=1, kind="stable")[:, :10]
     assert oracle.recall(host(res["ids"]), top) > 0.9
     cng.cng_free(idx)
+
+
+def test_tau_grid_search_matches_oracle():
+    """cng_tune_tau runs the same trials as the oracle's grid search (graphs, widths, recalls
+    and hop counts are exact) and picks the same tau."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate("gauss", 1500, 16, seed=12)
+    Q = synth.generate("gauss", 120, 16, seed=1012)
+    gt, _ = oracle.knn(X, 10, rows=Q)
+    Ls = [10, 12, 16, 24, 32, 48]
+    best, trials = cng.cng_tune_tau(tensor(X), 1.2, 16, 48, tensor(Q), 10, gt, Ls, 0.95)
+    obest, otrials = oracle.tune_tau(X, 1.2, 16, 48, Q, 10, gt, Ls, 0.95)
+    key = lambda ts: [(t["tau"], t["L"], t["recall"], t["hops_mean"]) for t in ts]
+    assert key(trials) == key(otrials)
+    assert best == obest

@@ -249,3 +249,29 @@ def test_adaptive_build_phase2_and_phase3(kind, n, d, R, L):
             assert got == list(_first_alpha_set(X, p, np.array(V, np.int32), R))
             used.add(p)
     assert used  # the re-prune branch was exercised
+
+
+def test_tau_grid_search_in_oracle():
+    """The tau grid search runs tau = 0, the coarse values 10, 1, 0.1, 0.01, 0.001, then halves
+    and doubles the best; a target no graph reaches picks tau = 0 with every width exhausted;
+    an easy target is reached at the first width by every graph and the fewest hops win."""
+    X = synth.generate("gauss", 600, 8, seed=4)
+    Q = synth.generate("gauss", 40, 8, seed=1004)
+    gt, _ = oracle.knn(X, 5, rows=Q)
+    Ls = [5, 8, 16]
+    best, trials = oracle.tune_tau(X, 1.2, 10, 24, Q, 5, gt, Ls, 0.5)
+    taus = [t["tau"] for t in trials]
+    assert taus[:6] == [0.0, 10.0, 1.0, 0.1, 0.01, 0.001]
+    reached = [t for t in trials if t["L"] > 0]
+    assert all(t["L"] == 5 for t in reached)
+    b = min(reached, key=lambda t: (t["hops_mean"], t["tau"]))
+    assert best == b["tau"]
+    bc = min([t for t in trials[:6] if t["L"] > 0], key=lambda t: (t["hops_mean"], t["tau"]))
+    fine = set(taus[6:])
+    assert fine <= ({bc["tau"] / 2, bc["tau"] * 2} if bc["tau"] > 0 else {0.0005})
+    best2, trials2 = oracle.tune_tau(X, 1.2, 10, 24, Q, 5, gt, Ls, 1.01)
+    assert best2 == 0.0 and all(t["L"] == 0 for t in trials2)
+    # a graph's hop count at a width is Alg. 1's own: recompute one trial directly
+    G = oracle.build_graph(X, 1.2, trials[2]["tau"], 10, 24)
+    _, _, _, hops = oracle.search(X, G.adj, G.deg, G.entry, Q, 5, 5)
+    assert trials[2]["hops_mean"] == hops.sum() / len(Q)
