@@ -113,6 +113,8 @@ struct cng_index {
   int* counter = nullptr;        // SEARCH_COUNTER_INTS
   int32_t* defer = nullptr;      // queries left to the general search kernel (grown on demand)
   int64_t defer_cap = 0;
+  char* stage = nullptr;         // device staging of host queries and results (grown on demand)
+  size_t stage_cap = 0;
   unsigned long long* tot = nullptr;
   uint32_t* status = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream for CUDA-graph capture
@@ -166,6 +168,7 @@ extern "C" void cng_free(cng_index* ix) {
   cudaFree(ix->qbuf);
   cudaFree(ix->counter);
   cudaFree(ix->defer);
+  cudaFree(ix->stage);
   cudaFree(ix->tot);
   cudaFree(ix->status);
   if (ix->cap_stream) cudaStreamDestroy(ix->cap_stream);
@@ -859,6 +862,17 @@ static cng_status index_queries(const cng_index* ix, const float* queries, int64
   return CNG_OK;
 }
 
+// Grows the staging area of ix to at least `bytes` (callers hold ix->mu).
+static cudaError_t ensure_stage(cng_index* ix, size_t bytes) {
+  if (ix->stage_cap >= bytes) return cudaSuccess;
+  cudaFree(ix->stage);
+  ix->stage = nullptr;
+  ix->stage_cap = 0;
+  const cudaError_t e = cudaMalloc(&ix->stage, bytes);
+  if (e == cudaSuccess) ix->stage_cap = bytes;
+  return e;
+}
+
 // Grows the deferred-query list of ix to at least nq entries (callers hold ix->mu).
 static cudaError_t ensure_defer(cng_index* ix, int64_t nq) {
   if (ix->defer_cap >= nq) return cudaSuccess;
@@ -916,22 +930,45 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     if (stats) memset(stats, 0, sizeof(*stats));
     return CNG_OK;
   }
-  DevPool pool;
+  std::lock_guard<std::mutex> lock(ix->mu);
+  // host queries / results and the inner-product queries go through the index's staging area,
+  // so repeated host calls allocate nothing and keep their graph arguments
   const bool host_q = !is_device_ptr(queries);
-  const float* qd = nullptr;
-  {
-    cng_status qs = index_queries(ix, queries, nq, pool, s, &qd);
-    if (qs != CNG_OK) return qs;
+  const bool host_out = !is_device_ptr(ids);
+  const int din = ix->metric == CNG_IP ? ix->d - 1 : ix->d;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t need = 0;
+  if (host_q) need += al((size_t)nq * din * 4);
+  if (ix->metric == CNG_IP) need += al((size_t)nq * ix->d * 4);
+  if (host_out)
+    need += 2 * al((size_t)nq * k * 4) + (ndc ? al((size_t)nq * 4) : 0) +
+            (hops ? al((size_t)nq * 4) : 0) + (flags ? al((size_t)nq * 4) : 0);
+  CK(ensure_stage(ix, need));
+  char* sp = ix->stage;
+  auto carve = [&](size_t b) {
+    char* r = sp;
+    sp += al(b);
+    return r;
+  };
+  const float* qd = queries;
+  if (host_q) {
+    float* t = reinterpret_cast<float*>(carve((size_t)nq * din * 4));
+    CK(cudaMemcpyAsync(t, queries, (size_t)nq * din * 4, cudaMemcpyHostToDevice, s));
+    qd = t;
+  }
+  if (ix->metric == CNG_IP) {
+    float* t = reinterpret_cast<float*>(carve((size_t)nq * ix->d * 4));
+    CK(launch_append_zero(qd, nq, din, t, s));
+    qd = t;
   }
   int32_t *o_ids = ids, *o_ndc = ndc, *o_hops = hops, *o_flags = flags;
   float* o_d = dists;
-  const bool host_out = !is_device_ptr(ids);
   if (host_out) {
-    CK(pool.alloc(&o_ids, (size_t)nq * k));
-    CK(pool.alloc(&o_d, (size_t)nq * k));
-    if (ndc) CK(pool.alloc(&o_ndc, (size_t)nq));
-    if (hops) CK(pool.alloc(&o_hops, (size_t)nq));
-    if (flags) CK(pool.alloc(&o_flags, (size_t)nq));
+    o_ids = reinterpret_cast<int32_t*>(carve((size_t)nq * k * 4));
+    o_d = reinterpret_cast<float*>(carve((size_t)nq * k * 4));
+    if (ndc) o_ndc = reinterpret_cast<int32_t*>(carve((size_t)nq * 4));
+    if (hops) o_hops = reinterpret_cast<int32_t*>(carve((size_t)nq * 4));
+    if (flags) o_flags = reinterpret_cast<int32_t*>(carve((size_t)nq * 4));
   }
   SearchArgs a{};
   a.X = ix->xs;
@@ -964,7 +1001,6 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     a.check_every = P.check_every;
     a.min_stable = P.min_stable;
   }
-  std::lock_guard<std::mutex> lock(ix->mu);
   {
     cng_status qs = search_queries(ix, qd, nq, &a, s);
     if (qs != CNG_OK) return qs;
