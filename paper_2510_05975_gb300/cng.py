@@ -26,7 +26,8 @@ CNG_SEARCH_FIXED, CNG_SEARCH_LEARNED = 0, 1
 
 EXPORTS = ("cng_build", "cng_free", "cng_last_error", "cng_graph", "cng_lists", "cng_search",
            "cng_knn", "cng_stop_train", "cng_stop_free", "cng_stop_export", "cng_stop_import",
-           "cng_trace", "cng_mlp_grad", "cng_mlp_adam", "cng_entry_noalloc")
+           "cng_trace", "cng_mlp_grad", "cng_mlp_adam", "cng_entry_noalloc", "cng_tune_tau",
+           "cngx_wait_probe")
 CNG_STOP_NPARAMS = 5313
 
 
