@@ -969,7 +969,7 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
 // Pass 1 (CAP 128) takes every node and defers larger sets to mid_list; pass 2 (CAP 256) takes
 // mid_list and defers larger sets to big_list for the global-scratch pass.
 template <typename T, int DW, int CAP>
-__global__ void __launch_bounds__(CAP)
+__global__ void __launch_bounds__(CAP, 1024 / CAP)  // 64 registers: 32 warps per SM
 merge_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int64_t n, int d, int dpad,
                 const int32_t* __restrict__ fwd, const int32_t* __restrict__ fdeg,
                 const int64_t* __restrict__ off, const int32_t* __restrict__ inl, RuleArgs ra,
