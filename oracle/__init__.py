@@ -83,6 +83,13 @@ def _load():
             lib.or_search_ex.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32, vp, i64,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, dbl,
                                          ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
+            lib.or_beam_candidates.restype = ctypes.c_int
+            lib.or_beam_candidates.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, i32,
+                                               ctypes.c_int, ctypes.c_int, vp, vp, vp]
+            lib.or_build_beam.restype = ctypes.c_int
+            lib.or_build_beam.argtypes = [vp, i64, ctypes.c_int, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                          dbl, dbl, dbl, vp, ctypes.c_int, i32, ctypes.c_int,
+                                          ctypes.c_int, vp, vp, vp, vp, vp]
             lib.or_num_threads.restype = ctypes.c_int
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -228,6 +235,55 @@ def build_graph(X, alpha: float, tau: float, R: int, L: int, connect_L: int = CO
     if rc != 0:
         raise ValueError(f"or_build failed ({rc})")
     G = Graph(int(e.value), cand, fwd, fdeg, adj, deg)
+    if connect_L > 0:
+        G.adj, G.deg, G.repair_edges, G.repair_rounds = connect(X, adj, deg, G.entry, repair_slots,
+                                                                connect_L)
+    return G
+
+
+def beam_candidates(X, adj, deg, entry_id: int, L: int, C: int):
+    """Alg. 3 phase 2 candidates (Sec. 4.3): for each point p, Alg. 1 on the graph (adj, deg)
+    from entry_id with queue size L and x_p as the query; of every point whose distance was
+    computed, the C closest by (D, id) with p excluded.  Returns (ids [n, C] padded with -1,
+    dists [n, C] float64 padded with inf, counts [n])."""
+    X = _f32(X)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    deg = np.ascontiguousarray(deg, dtype=np.int32)
+    n, d = X.shape
+    ids = np.empty((n, C), np.int32)
+    ds = np.empty((n, C), np.float64)
+    cnt = np.empty(n, np.int32)
+    rc = _load().or_beam_candidates(_p(X), n, d, _p(adj), _p(deg), adj.shape[1], int(entry_id),
+                                    int(L), int(C), _p(ids), _p(ds), _p(cnt))
+    if rc != 0:
+        raise ValueError(f"or_beam_candidates failed ({rc})")
+    return ids, ds, cnt
+
+
+def build_graph_beam(X, alpha: float, tau: float, R: int, C: int, K: int, Lb: int,
+                     connect_L: int = CONNECT_L, repair_slots: int = REPAIR_SLOTS,
+                     adaptive=None, knn_graph=None) -> Graph:
+    """Alg. 3 with the paper's candidate route: G0 = a K-NN graph (knn_graph [n, K], default the
+    exact one), the navigating node of the exact route (the point nearest the centroid; the
+    paper finds it by a beam search on G0), candidates = beam_candidates(G0, queue Lb, C), then
+    phases 2-4 as build_graph.  Graph.cand holds the [n, C] candidate lists."""
+    X = _f32(X)
+    n, d = X.shape
+    G0 = knn(X, K)[0] if knn_graph is None else np.ascontiguousarray(knn_graph, np.int32)
+    e = entry(X)
+    cand = np.empty((n, C), np.int32)
+    fwd = np.empty((n, R), np.int32)
+    fdeg = np.empty(n, np.int32)
+    adj = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    a0, am, da = adaptive if adaptive is not None else (0.0, 0.0, 0.0)
+    rc = _load().or_build_beam(_p(X), n, d, float(alpha), float(tau), int(R),
+                               int(adaptive is not None), float(a0), float(am), float(da),
+                               _p(G0), int(G0.shape[1]), int(e), int(Lb), int(C), _p(cand),
+                               _p(fwd), _p(fdeg), _p(adj), _p(deg))
+    if rc != 0:
+        raise ValueError(f"or_build_beam failed ({rc})")
+    G = Graph(int(e), cand, fwd, fdeg, adj, deg)
     if connect_L > 0:
         G.adj, G.deg, G.repair_edges, G.repair_rounds = connect(X, adj, deg, G.entry, repair_slots,
                                                                 connect_L)

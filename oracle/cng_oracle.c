@@ -263,45 +263,32 @@ static int build_prune(const float *X, int d, const or_pair *pv, int nv, const o
 }
 
 /*
- * entry            navigating node
- * cand  [n][L]     exact candidate lists (may be NULL)
- * fwd   [n][R]     phase-2 out-lists (pruned candidates), padded with -1
- * fdeg  [n]
- * adj   [n][R]     final out-lists after reverse merge + lazy pruning, padded with -1
- * deg   [n]
- * Returns 0, or a negative error.
+ * Phases 2 and 3 of Alg. 3 from candidate lists cl [n][C] sorted by (D, id) with their canonical
+ * distances cd, each row ending at its first -1 (at most C entries).
  */
-int or_build_ex(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
-                int adaptive, double alpha0, double alpha_max, double dalpha, int32_t *entry,
-                int32_t *cand, int32_t *fwd, int32_t *fdeg, int32_t *adj, int32_t *deg) {
-    if (n < 2 || d <= 0 || R <= 0 || L <= 0 || L >= n) return OR_E_INVAL;
-    if (adaptive && !(dalpha > 0.0)) return OR_E_INVAL;
-    const or_rule rule = {alpha, tau, adaptive, alpha0, alpha_max, dalpha};
-    int32_t *cl = cand ? cand : (int32_t *)malloc(sizeof(int32_t) * n * L);
-    double *cd = (double *)malloc(sizeof(double) * n * L);
-    if (!cl || !cd) return OR_E_NOMEM;
-    *entry = or_entry(X, n, d);
-    or_knn(X, n, X, n, d, L, 1, cl, cd);
-
+static int build_from_lists(const float *X, int64_t n, int d, const or_rule *rp, int R, int C,
+                            const int32_t *cl, const double *cd, int32_t *fwd, int32_t *fdeg,
+                            int32_t *adj, int32_t *deg) {
+    const or_rule rule = *rp;
     /* phase 2: prune every candidate list (already sorted by (D, id)) */
 #pragma omp parallel
     {
-        or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * L);
+        or_pair *pv = (or_pair *)malloc(sizeof(or_pair) * C);
 #pragma omp for schedule(dynamic, 16)
         for (int64_t p = 0; p < n; ++p) {
-            for (int i = 0; i < L; ++i) {
-                pv[i].id = cl[p * L + i];
-                pv[i].D = cd[p * L + i];
+            int nv = 0;
+            while (nv < C && cl[p * C + nv] >= 0) {
+                pv[nv].id = cl[p * C + nv];
+                pv[nv].D = cd[p * C + nv];
+                ++nv;
             }
             int32_t *S = fwd + p * R;
-            int ns = build_prune(X, d, pv, L, &rule, R, S);
+            int ns = build_prune(X, d, pv, nv, &rule, R, S);
             for (int i = ns; i < R; ++i) S[i] = -1;
             fdeg[p] = ns;
         }
         free(pv);
     }
-    free(cd);
-    if (!cand) free(cl);
 
     /* phase 3: reverse edges from the phase-2 snapshot, then lazy pruning */
     int64_t *off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -356,6 +343,33 @@ int or_build_ex(const float *X, int64_t n, int d, double alpha, double tau, int 
     free(cur);
     free(off);
     return OR_OK;
+}
+
+/*
+ * Alg. 3 phases 1-3 with exact candidates:
+ * entry            navigating node
+ * cand  [n][L]     exact candidate lists (may be NULL)
+ * fwd   [n][R]     phase-2 out-lists (pruned candidates), padded with -1
+ * fdeg  [n]
+ * adj   [n][R]     final out-lists after reverse merge + lazy pruning, padded with -1
+ * deg   [n]
+ * Returns 0, or a negative error.
+ */
+int or_build_ex(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
+                int adaptive, double alpha0, double alpha_max, double dalpha, int32_t *entry,
+                int32_t *cand, int32_t *fwd, int32_t *fdeg, int32_t *adj, int32_t *deg) {
+    if (n < 2 || d <= 0 || R <= 0 || L <= 0 || L >= n) return OR_E_INVAL;
+    if (adaptive && !(dalpha > 0.0)) return OR_E_INVAL;
+    const or_rule rule = {alpha, tau, adaptive, alpha0, alpha_max, dalpha};
+    int32_t *cl = cand ? cand : (int32_t *)malloc(sizeof(int32_t) * n * L);
+    double *cd = (double *)malloc(sizeof(double) * n * L);
+    if (!cl || !cd) return OR_E_NOMEM;
+    *entry = or_entry(X, n, d);
+    or_knn(X, n, X, n, d, L, 1, cl, cd);
+    int rc = build_from_lists(X, n, d, &rule, R, L, cl, cd, fwd, fdeg, adj, deg);
+    free(cd);
+    if (!cand) free(cl);
+    return rc;
 }
 
 int or_build(const float *X, int64_t n, int d, double alpha, double tau, int R, int L,
@@ -451,6 +465,124 @@ int or_search(const float *X, int64_t n, int d, const int32_t *adj, const int32_
         free(Q);
     }
     return err;
+}
+
+/* ---- beam-search candidates (Alg. 3 phase 2, Sec. 4.3) ------------------------------- */
+
+/*
+ * For every point p: beam search (Alg. 1, queue size L) on the graph (adj [n][R], deg) from s
+ * with x_p as the query; every point whose distance is computed is collected, and the C closest
+ * by (D, id), p itself excluded by id, form p's candidate list out_ids [n][C] with canonical
+ * distances out_d (rows padded with -1 / +inf); out_cnt [n] = entries in the row.
+ */
+int or_beam_candidates(const float *X, int64_t n, int d, const int32_t *adj, const int32_t *deg,
+                       int R, int32_t s, int L, int C, int32_t *out_ids, double *out_d,
+                       int32_t *out_cnt) {
+    if (n <= 0 || L < 1 || C < 1 || s < 0 || s >= n) return OR_E_INVAL;
+#pragma omp parallel
+    {
+        unsigned char *vis = (unsigned char *)calloc((size_t)n, 1);
+        or_pair *seen = NULL;
+        int64_t scap = 0;
+        or_qent *Q = (or_qent *)malloc(sizeof(or_qent) * (L + 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < n; ++p) {
+            const float *q = X + p * (int64_t)d;
+            int64_t ns = 0;
+            if (scap == 0) {
+                scap = 4096;
+                seen = (or_pair *)malloc(sizeof(or_pair) * scap);
+            }
+            int len = 1;
+            Q[0].D = or_dist(q, X + (int64_t)s * d, d);
+            Q[0].id = s;
+            Q[0].explored = 0;
+            vis[s] = 1;
+            seen[ns].D = Q[0].D;
+            seen[ns++].id = s;
+            for (;;) {
+                int i = 0;
+                while (i < len && Q[i].explored) ++i;
+                if (i == len) break;
+                Q[i].explored = 1;
+                int32_t u = Q[i].id;
+                for (int j = 0; j < deg[u]; ++j) {
+                    int32_t v = adj[(int64_t)u * R + j];
+                    if (vis[v]) continue;
+                    vis[v] = 1;
+                    double D = or_dist(q, X + (int64_t)v * d, d);
+                    if (ns >= scap) {
+                        scap *= 2;
+                        seen = (or_pair *)realloc(seen, sizeof(or_pair) * scap);
+                    }
+                    seen[ns].D = D;
+                    seen[ns++].id = v;
+                    if (len < L || key_less(D, v, Q[len - 1].D, Q[len - 1].id)) {
+                        int pos = (len < L) ? len : L - 1;
+                        while (pos > 0 && key_less(D, v, Q[pos - 1].D, Q[pos - 1].id)) {
+                            Q[pos] = Q[pos - 1];
+                            --pos;
+                        }
+                        Q[pos].D = D;
+                        Q[pos].id = v;
+                        Q[pos].explored = 0;
+                        if (len < L) ++len;
+                    }
+                }
+            }
+            for (int64_t t = 0; t < ns; ++t) vis[seen[t].id] = 0;
+            qsort(seen, (size_t)ns, sizeof(or_pair), pair_cmp);
+            int c = 0;
+            for (int64_t t = 0; t < ns && c < C; ++t) {
+                if (seen[t].id == (int32_t)p) continue;
+                out_ids[p * C + c] = seen[t].id;
+                out_d[p * C + c] = seen[t].D;
+                ++c;
+            }
+            out_cnt[p] = c;
+            for (int t = c; t < C; ++t) {
+                out_ids[p * C + t] = -1;
+                out_d[p * C + t] = INFINITY;
+            }
+        }
+        free(vis);
+        free(seen);
+        free(Q);
+    }
+    return OR_OK;
+}
+
+/*
+ * Alg. 3 phases 1-3 with the paper's candidate route: G0 = the K-NN graph given as knn [n][K]
+ * (an approximate one in the paper; any K-NN graph here), s = the navigating node given,
+ * candidates = or_beam_candidates on G0 (queue Lb, C entries), then phases 2 and 3 as for exact
+ * candidates.  cand [n][C] receives the candidate lists (may be NULL).
+ */
+int or_build_beam(const float *X, int64_t n, int d, double alpha, double tau, int R,
+                  int adaptive, double alpha0, double alpha_max, double dalpha,
+                  const int32_t *knn, int K, int32_t s, int Lb, int C, int32_t *cand,
+                  int32_t *fwd, int32_t *fdeg, int32_t *adj, int32_t *deg) {
+    if (n < 2 || d <= 0 || R <= 0 || K <= 0 || C <= 0 || Lb <= 0 || s < 0 || s >= n)
+        return OR_E_INVAL;
+    if (adaptive && !(dalpha > 0.0)) return OR_E_INVAL;
+    const or_rule rule = {alpha, tau, adaptive, alpha0, alpha_max, dalpha};
+    int32_t *g0deg = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *cl = cand ? cand : (int32_t *)malloc(sizeof(int32_t) * n * C);
+    double *cd = (double *)malloc(sizeof(double) * n * C);
+    int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * n);
+    if (!g0deg || !cl || !cd || !cnt) return OR_E_NOMEM;
+    for (int64_t p = 0; p < n; ++p) {
+        int k = 0;
+        while (k < K && knn[p * K + k] >= 0) ++k;
+        g0deg[p] = k;
+    }
+    int rc = or_beam_candidates(X, n, d, knn, g0deg, K, s, Lb, C, cl, cd, cnt);
+    if (rc == OR_OK) rc = build_from_lists(X, n, d, &rule, R, C, cl, cd, fwd, fdeg, adj, deg);
+    free(g0deg);
+    free(cd);
+    free(cnt);
+    if (!cand) free(cl);
+    return rc;
 }
 
 /* ---- connectivity (Alg. 3 phase 4) ------------------------------------------------------ */
