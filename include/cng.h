@@ -76,7 +76,7 @@ typedef enum {
  *                    fixed alpha: alpha_i = alpha0 + i * dalpha for i = 0, 1, ..,
  *                    round((alpha_max - alpha0) / dalpha); each point keeps the first R points
  *                    of the first S_i with |S_i| >= R / 2 (else of the last S_i).  alpha is then
- *                    unused.  The paper's setting (Sec. 4.3): alpha0 0.9, dalpha 0.05,
+ *                    unused.  The paper's setting (Sec. 4.4): alpha0 0.9, dalpha 0.05,
  *                    alpha_max 1.6.
  *   alpha0, alpha_max, dalpha   [alpha_0, alpha_max, Delta alpha] of Alg. 4 (adaptive only)
  */
@@ -242,7 +242,7 @@ cng_status cng_search(const cng_index *index, const float *queries, int64_t nq, 
                       cng_search_stats *stats);
 
 /* ---------------------------------------------------------------------------------------
- * Grid search of tau on held-out queries (Sec. 5, parameter configuration: tau = 0 against
+ * Grid search of tau on held-out queries (Sec. 4.4, parameter configuration: tau = 0 against
  * the coarse values 10, 1, 0.1, 0.01, 0.001, then a finer search around the best).  Every
  * trial builds the graph of `points` with `params` (its tau replaced) and scores it on the
  * nq queries: the smallest beam width L in search_Ls[0 .. n_Ls) (ascending, each >= k) whose

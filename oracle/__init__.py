@@ -242,7 +242,7 @@ def build_graph(X, alpha: float, tau: float, R: int, L: int, connect_L: int = CO
 
 
 def beam_candidates(X, adj, deg, entry_id: int, L: int, C: int):
-    """Alg. 3 phase 2 candidates (Sec. 4.3): for each point p, Alg. 1 on the graph (adj, deg)
+    """Alg. 3 phase 2 candidates (Sec. 4.1): for each point p, Alg. 1 on the graph (adj, deg)
     from entry_id with queue size L and x_p as the query; of every point whose distance was
     computed, the C closest by (D, id) with p excluded.  Returns (ids [n, C] padded with -1,
     dists [n, C] float64 padded with inf, counts [n])."""
@@ -375,7 +375,7 @@ def mips_queries(Q):
 
 
 def tune_tau(X, alpha: float, R: int, L: int, Q, k: int, gt_ids, search_Ls, target: float):
-    """The grid search of tau on held-out queries (Sec. 5 parameter configuration): tau = 0, then
+    """The grid search of tau on held-out queries (Sec. 4.4, parameter configuration): tau = 0, then
     the coarse values 10, 1, 0.1, 0.01, 0.001, then t / 2 and 2 t around the best coarse value t
     (0.0005 when t = 0).  A trial's score is the smallest width in search_Ls whose mean
     Recall@k reaches `target` and the mean hops there (the recall summed query by query in

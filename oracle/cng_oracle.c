@@ -467,7 +467,7 @@ int or_search(const float *X, int64_t n, int d, const int32_t *adj, const int32_
     return err;
 }
 
-/* ---- beam-search candidates (Alg. 3 phase 2, Sec. 4.3) ------------------------------- */
+/* ---- beam-search candidates (Alg. 3 phase 2, Sec. 4.1) ------------------------------- */
 
 /*
  * For every point p: beam search (Alg. 1, queue size L) on the graph (adj [n][R], deg) from s

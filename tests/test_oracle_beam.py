@@ -1,4 +1,4 @@
-"""Pins of the oracle's beam-search candidate route (Alg. 3 phases 1-2, Sec. 4.3) against what
+"""Pins of the oracle's beam-search candidate route (Alg. 3 phases 1-2, Sec. 4.1) against what
 fixes it independently: on a complete graph with a queue longer than n the search computes
 every distance, so the candidates are the exact C nearest and the beam-candidate build equals
 the exact-candidate build; on a sparse K-NN graph the lists are (D, id)-sorted, distinct,

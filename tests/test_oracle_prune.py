@@ -195,7 +195,7 @@ def test_connectivity_repair_on_clusters():
         assert G.adj[r, G.deg3[r]] == p
 
 
-ADAPT = (0.9, 1.6, 0.05)  # the paper's setting (Sec. 5.1): alpha0, alpha_max, dalpha
+ADAPT = (0.9, 1.6, 0.05)  # the paper's setting (Sec. 4.4): alpha0, alpha_max, dalpha
 
 
 def _alphas(a0, am, da):
