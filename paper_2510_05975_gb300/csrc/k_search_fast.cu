@@ -8,12 +8,14 @@
 // whose unsigned order is the (D^2, id) order (ids are below 2^31); KINF pads the tail.
 //
 // One hop: the first unexplored entry u* of Q (one ballot per slot); its out-list (prefetched
-// during the previous hop when the prediction holds); the visited filter; the exact distance of
-// each new point by its own lane; a 32-key bitonic sort of the batch; then the merge of the
-// batch into Q as a single bitonic merge network -- the batch, reversed, is folded into the last
-// slot (the half-cleaner of the bitonic sequence [Q ascending | batch descending]) and
-// log2(32 QS) compare-exchange levels restore the order; entries past L are dropped (Alg. 1's
-// truncation to the L closest).  A hop with more than 32 new points merges them 32 at a time,
+// during the previous hop when the prediction holds); the visited filter (one compare-and-swap
+// per probe); the exact distances of the new points, 8 lanes reading each 128-byte row
+// (coalesced) and a transposed butterfly handing each distance to its point's lane; a bitonic
+// sort of the batch on 32-bit keys D^2 << 5 | lane (64-bit (D^2, id) keys when two distances
+// tie); then the merge of the batch into Q as a single bitonic merge network -- the batch,
+// reversed, is folded into the last slot (the half-cleaner of the bitonic sequence
+// [Q ascending | batch descending]) and log2(32 QS) compare-exchange levels restore the order;
+// entries past L are dropped (Alg. 1's truncation to the L closest).  A hop with more than 32 new points merges them 32 at a time,
 // which gives the same queue because truncation keeps the L smallest of the union either way.
 //
 // The visited filter is lossy only in one direction: a point whose probe slots are all taken is
