@@ -1,7 +1,9 @@
-// k_search.cu -- batched beam search of Alg. 1 (K7), sm_103a.
+// k_search.cu -- batched beam search of Alg. 1 (K7), general kernel, sm_103a.
 //
-// One persistent launch serves all queries: each warp takes the next query from an atomic
-// counter and runs Alg. 1 to completion; queries of any length share the launch.
+// One persistent launch serves the batch: each warp takes the next query from an atomic
+// counter and runs Alg. 1 to completion; queries of any length share the launch.  On data with
+// exact 8-bit rows the register-queue kernel (k_search_fast.cu) runs first and this kernel only
+// serves the queries it deferred (non-integer or out-of-range coordinates).
 //
 // Per warp (shared memory):
 //   Q   sorted queue of <= L entries: key = (FP32 squared distance, id), an explored flag,
