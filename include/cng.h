@@ -141,9 +141,12 @@ cng_status cng_build(const void *points, int32_t dtype, int64_t n, int32_t d,
 /*
  * cng_entry_noalloc -- the navigating node of cng_build (the point nearest the centroid, ties
  * to the smaller id) without allocating any memory, for callers that cannot allocate device
- * memory when they need it: code running while a stream is captured into a CUDA graph,
- * processes whose device memory belongs to another allocator, latency-bound loops.  The paper
- * has no counterpart to this call; it is an engineering addition.
+ * memory when they need it: processes whose device memory is owned by another allocator (a
+ * framework's caching allocator, a fixed arena) or budgeted at start-up, and latency-bound
+ * loops that cannot afford an allocation's implicit synchronisation.  The paper has no
+ * counterpart to this call; it is an engineering addition.  The id equals cng_build's entry
+ * for CNG_L2 and CNG_IP_AS_L2 builds of the same points; a CNG_IP build takes its entry on the
+ * augmented rows [x, sqrt(M^2 - |x|^2)], which this call does not form.
  * points_dev: device, n x d of `dtype`, row-major without padding; entry_dev: device int32
  * receiving the id.  Asynchronous on `stream`; calls no allocator.  Scratch is a fixed 4 MiB
  * device array held by every GPU that loads the library until exit: a call needs
@@ -198,7 +201,10 @@ typedef enum { CNG_SEARCH_FIXED = 0, CNG_SEARCH_LEARNED = 1 } cng_search_mode;
  *              free, so the network runs only where a stop is plausible
  * model        required for CNG_SEARCH_LEARNED, ignored otherwise
  * max_hops     0 = unbounded; otherwise queries stop after this many hop vertices (flagged)
- * use_graph    1: launch through a cached CUDA graph for this (nq, k, L, mode) shape
+ * use_graph    1: launch through a CUDA graph cached per index for this exact call: the
+ *              query and output pointers, nq, k, L, mode, launch shape and stream all form
+ *              its key, so repeated calls on the same buffers replay one graph; at most 16
+ *              are kept per index (the oldest is destroyed first)
  * warps_per_block  queries per CTA (one warp each, <= 8); 0 = autotuned: the first search
  *              of an (L, mode) shape on an index of a given shape (device, dtype, padded d,
  *              adjacency row stride) times every launch shape (1, 2, 4, 8 warps per block x
@@ -235,6 +241,9 @@ typedef struct {
  *   bit 2: stopped by the learned rule).
  * Requires 1 <= k <= L <= 256.  Ties in the queue order by (D, id).  Returns identical ids to the
  * FP64 definition for fixed-L mode.  stats may be NULL; when given, `stream` is synchronised.
+ * The outputs must all be host memory or all device memory (CNG_E_INVAL otherwise).  Calls on
+ * one index share its search scratch, so the library orders them on the GPU: a call on a
+ * stream other than the previous call's first waits (cudaStreamWaitEvent) for that call.
  */
 cng_status cng_search(const cng_index *index, const float *queries, int64_t nq, int32_t k,
                       int32_t L, const cng_search_params *params, int32_t *ids, float *dists,

@@ -90,6 +90,8 @@ def _load():
             lib.or_build_beam.argtypes = [vp, i64, ctypes.c_int, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                           dbl, dbl, dbl, vp, ctypes.c_int, i32, ctypes.c_int,
                                           ctypes.c_int, vp, vp, vp, vp, vp]
+            lib.or_check_rule.restype = i64
+            lib.or_check_rule.argtypes = [vp, i64, ctypes.c_int, vp, vp, ctypes.c_int, dbl, dbl, vp]
             lib.or_num_threads.restype = ctypes.c_int
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -180,6 +182,25 @@ def prune_adaptive(X, p: int, V, alpha0: float, alpha_max: float, dalpha: float,
     if ns < 0:
         raise ValueError(f"or_prune_adaptive failed ({ns})")
     return S[:ns].copy(), a.value
+
+
+def check_rule(X, lists, cnt, alpha: float, tau: float):
+    """Def. 2 / Alg. 2 soundness of every kept list: lists [n, stride] (row p's first cnt[p]
+    entries) must be distinct valid ids != p in (D(p, .), id) order, with no member pruned by
+    an earlier one.  Returns (number of unsound rows, per-row code: 0 sound, 1 bad id or
+    duplicate, 2 order, 3 a pair the rule prunes)."""
+    X = _f32(X)
+    lists = np.ascontiguousarray(lists, np.int32)
+    cnt = np.ascontiguousarray(cnt, np.int32)
+    n, d = X.shape
+    if lists.shape[0] != n or cnt.shape[0] != n:
+        raise ValueError("lists and cnt need one row per point")
+    bad = np.empty(n, np.int32)
+    nb = _load().or_check_rule(_p(X), n, d, _p(lists), _p(cnt), lists.shape[1], float(alpha),
+                               float(tau), _p(bad))
+    if nb < 0:
+        raise ValueError(f"or_check_rule failed ({nb})")
+    return int(nb), bad
 
 
 REPAIR_SLOTS = 8  # row slots beyond R for phase-4 connectivity edges

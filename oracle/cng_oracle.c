@@ -15,7 +15,8 @@
  *                           L nearest points of P \ {p} ordered by (D, id).
  *   navigating node         Alg. 3, phase 1: nearest point to the centroid of P (exact
  *                           form: argmin over all points of (D(c, x), id)).
- *   pruning                 Def. 2 (Eq. 1) and Alg. 2, fixed alpha, stop at R kept.
+ *   pruning                 Def. 2 (Eq. 1) and Alg. 2, fixed alpha, stop at R kept; the
+ *                           soundness check of whole kept lists follows the same rule.
  *   adaptive pruning        Alg. 4 with alpha_i = alpha0 + i * dalpha.
  *   reverse merge           Alg. 3, phase 3 and the lazy-pruning paragraph of Sec. 4.3.
  *   beam search             Alg. 1 (with a visited set; identical returned ids).
@@ -75,7 +76,7 @@ int or_knn(const float *base, int64_t n, const float *rows, int64_t m, int d, in
            int exclude_self, int32_t *out_ids, double *out_d) {
     if (n < 0 || m < 0 || d <= 0 || L <= 0) return OR_E_INVAL;
     int err = 0;
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < m; ++i) {
         int32_t *ids = out_ids + i * L;
         double *ds = out_d + i * L;
@@ -241,6 +242,56 @@ int or_prune_adaptive(const float *X, int64_t n, int d, int64_t p, const int32_t
     int ns = prune_adaptive_sorted(X, d, pv, nv, alpha0, alpha_max, dalpha, tau, R, S, alpha_used);
     free(pv);
     return ns;
+}
+
+/*
+ * Soundness of kept lists under Def. 2 (Eq. 1) and Alg. 2: for every point p, its list
+ * S = lists[p][0 .. cnt[p]) (row stride `stride`) must hold distinct valid ids other than p, in
+ * ascending (D(p, .), id) order, and no member S[j] may be pruned by an earlier member S[i]
+ * (i < j): D(p, S[j]) > alpha * D(S[j], S[i]) + (alpha + 1) * tau must be false for every such
+ * pair, because Alg. 2 tests each candidate against every point kept before it.  bad[p] (if not
+ * NULL) receives 0 for a sound row, 1 for a bad id or duplicate, 2 for an order violation, 3 for
+ * a pair that the rule prunes.  Returns the number of unsound rows.
+ */
+int64_t or_check_rule(const float *X, int64_t n, int d, const int32_t *lists, const int32_t *cnt,
+                      int stride, double alpha, double tau, int32_t *bad) {
+    if (n <= 0 || stride <= 0) return OR_E_INVAL;
+    const double t = (alpha + 1.0) * tau;
+    int64_t nbad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : nbad)
+    for (int64_t p = 0; p < n; ++p) {
+        const int32_t *S = lists + p * stride;
+        const int c = cnt[p];
+        const float *xp = X + p * (int64_t)d;
+        int why = c < 0 || c > stride;
+        double prevD = -1.0;
+        for (int j = 0; j < c && !why; ++j) {
+            const int32_t u = S[j];
+            if (u < 0 || u >= n || u == p) {
+                why = 1;
+                break;
+            }
+            for (int i = 0; i < j; ++i)
+                if (S[i] == u) why = 1;
+            if (why) break;
+            const double Dpu = or_dist(xp, X + (int64_t)u * d, d);
+            if (j > 0 && !(Dpu > prevD || (Dpu == prevD && u > S[j - 1]))) {
+                why = 2;
+                break;
+            }
+            prevD = Dpu;
+            for (int i = 0; i < j; ++i) {
+                const double Duv = or_dist(X + (int64_t)u * d, X + (int64_t)S[i] * d, d);
+                if (rule_prunes(Dpu, Duv, alpha, t)) {
+                    why = 3;
+                    break;
+                }
+            }
+        }
+        if (bad) bad[p] = why;
+        nbad += why != 0;
+    }
+    return nbad;
 }
 
 /* ---- construction (Alg. 3 phases 1-3, exact candidates) ------------------------------ */

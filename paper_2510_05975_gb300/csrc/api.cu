@@ -118,6 +118,11 @@ struct cng_index {
   unsigned long long* tot = nullptr;
   uint32_t* status = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream for CUDA-graph capture
+  // Calls that use the scratch above are ordered on the GPU: each records `done` on its stream
+  // and the next call, if on another stream, waits for it first.
+  cudaEvent_t done = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool has_last = false;
   std::mutex mu;
   struct GraphEntry {
     SearchArgs args;
@@ -172,6 +177,7 @@ extern "C" void cng_free(cng_index* ix) {
   cudaFree(ix->tot);
   cudaFree(ix->status);
   if (ix->cap_stream) cudaStreamDestroy(ix->cap_stream);
+  if (ix->done) cudaEventDestroy(ix->done);
   delete ix;
 }
 
@@ -779,7 +785,8 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       cudaMalloc(&ix->tot, 4 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&ix->status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ix->status, 0, sizeof(uint32_t)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ix->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&ix->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ix->done, cudaEventDisableTiming) != cudaSuccess) {
     cng_free(ix);
     return fail(CNG_E_NOMEM, "index scratch allocation failed");
   }
@@ -884,6 +891,24 @@ static cudaError_t ensure_defer(cng_index* ix, int64_t nq) {
   return e;
 }
 
+// Orders this call after the index's previous one when they run on different streams (the
+// per-index scratch -- queue counter, totals, status, query flags, deferred list, staging -- is
+// shared by every call).  Callers hold ix->mu.
+static cng_status order_after_last(cng_index* ix, cudaStream_t s) {
+  if (ix->has_last && ix->last_stream != s) CK(cudaStreamWaitEvent(s, ix->done, 0));
+  return CNG_OK;
+}
+
+static cng_status mark_done(cng_index* ix, cudaStream_t s) {
+  CK(cudaEventRecord(ix->done, s));
+  ix->last_stream = s;
+  ix->has_last = true;
+  return CNG_OK;
+}
+
+// Graphs cached per index (oldest evicted beyond this).
+constexpr size_t MAX_GRAPHS = 16;
+
 static cng_status search_queries(cng_index* ix, const float* qd, int64_t nq, SearchArgs* a,
                                  cudaStream_t s) {
   if (!ix->exact || ix->dtype != CNG_F32 || nq == 0) return CNG_OK;
@@ -930,11 +955,23 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     if (stats) memset(stats, 0, sizeof(*stats));
     return CNG_OK;
   }
-  std::lock_guard<std::mutex> lock(ix->mu);
   // host queries / results and the inner-product queries go through the index's staging area,
   // so repeated host calls allocate nothing and keep their graph arguments
   const bool host_q = !is_device_ptr(queries);
   const bool host_out = !is_device_ptr(ids);
+  {
+    const void* outs[4] = {dists, ndc, hops, flags};
+    const char* names[4] = {"dists", "ndc", "hops", "flags"};
+    for (int i = 0; i < 4; ++i)
+      if (outs[i] && is_device_ptr(outs[i]) == host_out)
+        return fail(CNG_E_INVAL, std::string("outputs must all be host or all be device memory (ids is ") +
+                                     (host_out ? "host" : "device") + ", " + names[i] + " is not)");
+  }
+  std::lock_guard<std::mutex> lock(ix->mu);
+  {
+    cng_status os = order_after_last(ix, s);
+    if (os != CNG_OK) return os;
+  }
   const int din = ix->metric == CNG_IP ? ix->d - 1 : ix->d;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t need = 0;
@@ -1088,6 +1125,10 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
       CK(cudaStreamEndCapture(cs, &graph));
       CK(cudaGraphInstantiate(&exec, graph, 0));
       cudaGraphDestroy(graph);
+      if (ix->graphs.size() >= MAX_GRAPHS) {  // evict the oldest (earlier launches are queued)
+        cudaGraphExecDestroy(ix->graphs.front().exec);
+        ix->graphs.erase(ix->graphs.begin());
+      }
       ix->graphs.push_back({a, plan, s, exec});
     }
     CK(cudaGraphLaunch(exec, s));
@@ -1096,6 +1137,10 @@ extern "C" cng_status cng_search(const cng_index* cix, const float* queries, int
     CK(launch_search(a, plan, s));
   }
   cudaEventRecord(e1, s);
+  {
+    cng_status ds = mark_done(ix, s);
+    if (ds != CNG_OK) return ds;
+  }
   if (host_out) {
     CK(cudaMemcpyAsync(ids, o_ids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(dists, o_d, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s));
@@ -1467,7 +1512,9 @@ extern "C" cng_status cng_trace(const cng_index* cix, const float* queries, int6
     if (qs != CNG_OK) return qs;
   }
   std::lock_guard<std::mutex> lock(ix->mu);
-  cng_status st = run_trace(ix, qd, nq, k, L, max_trace, feats, hops, tlc, ids, dists, s);
+  cng_status st = order_after_last(ix, s);
+  if (st == CNG_OK) st = run_trace(ix, qd, nq, k, L, max_trace, feats, hops, tlc, ids, dists, s);
+  if (st == CNG_OK) st = mark_done(ix, s);
   if (st != CNG_OK) return st;
   CK(cudaStreamSynchronize(s));
   return CNG_OK;
@@ -1505,7 +1552,9 @@ extern "C" cng_status cng_stop_train(const cng_index* cix, const float* train_q,
   CK(pool.alloc(&ids, (size_t)nq * P.k));
   CK(pool.alloc(&off, (size_t)nq + 1));
   std::lock_guard<std::mutex> lock(ix->mu);
-  cng_status st = run_trace(ix, qd, nq, P.k, P.L, T, feats, hops, tlc, ids, dists, s);
+  cng_status st = order_after_last(ix, s);
+  if (st == CNG_OK) st = run_trace(ix, qd, nq, P.k, P.L, T, feats, hops, tlc, ids, dists, s);
+  if (st == CNG_OK) st = mark_done(ix, s);
   if (st != CNG_OK) return st;
   CK(launch_offsets(hops, nq, T, off, s));
   int64_t N = 0;

@@ -1,11 +1,12 @@
 // k_entry_noalloc.cu -- the navigating node without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they need this result: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc is not capturable),
-// processes whose device memory belongs to another allocator (a framework's caching pool that
-// must see every byte), and latency-bound loops that cannot wait for the allocator.  For them
+// Some callers cannot allocate device memory at the moment they need this result: processes
+// whose device memory belongs to another allocator (a framework's caching pool that must see
+// every byte, or a fixed arena budgeted at start-up), and latency-bound loops that cannot wait
+// for the allocator's implicit synchronisation.  For them
 // cng_entry_noalloc computes the same navigating node as cng_build -- the point nearest the
-// centroid, ties to the smaller id, the centroid summed in blocks of 4,096 rows in FP64 --
+// centroid, ties to the smaller id, the centroid summed in blocks of 4,096 rows in FP64; for
+// CNG_L2 and CNG_IP_AS_L2 builds (a CNG_IP build takes its entry on augmented rows) --
 // using only the caller's input and output plus a file-scope device array.
 //
 // The array holds the block partial sums, the centroid and the two argmin words.  It has a

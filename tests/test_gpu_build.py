@@ -38,6 +38,9 @@ def _check_graph(X, G, idx, cng, R, L):
     ("sift", 3001, 128, 1.2, 0.0, 32, 128, 1),
     ("gauss", 3000, 32, 1.2, 0.0, 16, 64, 2),   # BF16 operands
     ("sift", 3001, 128, 1.2, 0.0, 32, 128, 2),
+    ("gist", 2000, 960, 1.2, 0.0, 32, 128, 0),  # the GIST-like width: staged prune and merge
+    ("gist", 2000, 960, 1.2, 0.0, 32, 128, 1),
+    ("gist", 1003, 960, 1.2, 0.05, 16, 100, 1),  # ragged tiles, tau > 0
 ])
 def test_build_matches_oracle(kind, n, d, alpha, tau, R, L, screen):
     need_gpu()
@@ -139,6 +142,8 @@ def test_locality_order_same_lists(kind, n, d, R, L):
     ("sift", 3001, 128, 32, 128, 1),   # 8-bit integer sweep
     ("deep", 2500, 96, 24, 80, 1),     # FP32 register-resident sweep, d = 96
     ("gist", 1500, 200, 16, 48, 0),    # staged sweep (rows too wide for registers)
+    ("gist", 2000, 960, 32, 128, 0),   # the GIST-like width, FP32 screen
+    ("gist", 2000, 960, 32, 128, 1),   # the GIST-like width, tensor-core screen
 ])
 def test_adaptive_build_matches_oracle(kind, n, d, R, L, screen):
     """Adaptive pruning (Alg. 4 with the paper's alpha0 0.9, dalpha 0.05, alpha_max 1.6) in

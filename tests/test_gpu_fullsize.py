@@ -63,6 +63,31 @@ def test_sampled_merged_lists(built):
         assert len(got) - len(ref) <= 8
 
 
+def test_rule_holds_on_every_list(built):
+    """Def. 2 / Alg. 2 over the whole 1M graph: every phase-2 list is in (D, id) order and no
+    kept point is pruned by one kept before it; the same holds for every node whose merged set
+    exceeded R and was pruned again (phase 3), up to the rows a phase-4 edge was appended to."""
+    X, w, fwd, fdeg = built["X"], built["w"], built["fwd"], built["fdeg"]
+    nb, bad = oracle.check_rule(X, fwd, fdeg, w.alpha, 0.0)
+    assert nb == 0, np.flatnonzero(bad)[:10]
+    n, R = len(X), fwd.shape[1]
+    valid = np.arange(R)[None, :] < fdeg[:, None]
+    src = np.repeat(np.arange(n, dtype=np.int64), R)[valid.ravel()]
+    dst = fwd.ravel()[valid.ravel()].astype(np.int64)
+    fkeys = np.sort(src * n + dst)
+    rev = dst * n + src
+    pos = np.searchsorted(fkeys, rev).clip(max=len(fkeys) - 1)
+    mutual = fkeys[pos] == rev  # u -> p with p -> u too: counted once in V'(p)
+    indeg = np.bincount(dst, minlength=n)
+    vsize = fdeg + indeg - np.bincount(dst[mutual], minlength=n)
+    rep = np.flatnonzero(vsize > R)
+    adj, deg = built["adj"], built["deg"]
+    assert rep.size > 0
+    cnt3 = np.where(vsize > R, np.minimum(deg, R), 0).astype(np.int32)
+    nb3, _ = oracle.check_rule(X, adj[:, :R], cnt3, w.alpha, 0.0)
+    assert nb3 <= built["st"]["repair_edges"], nb3
+
+
 def test_every_point_reachable(built):
     adj, deg, n = built["adj"], built["deg"], len(built["X"])
     seen = np.zeros(n, bool)

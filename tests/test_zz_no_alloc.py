@@ -1,6 +1,6 @@
 """cng_entry_noalloc: the navigating node computed with a fixed device array instead of
-allocations, for callers that cannot allocate device memory (graph capture, memory owned by
-another allocator, latency-bound loops).  Its result must equal the navigating node cng_build
+allocations, for callers that cannot allocate device memory (memory owned by another
+allocator or budgeted at start-up, latency-bound loops).  Its result must equal the navigating node cng_build
 reports for the same points; consecutive calls on different inputs check that no state of an
 earlier call leaks into the next.  Kept in a file collected last."""
 import numpy as np
