@@ -109,7 +109,7 @@ typedef struct {
   int64_t merge_max_list;     /* largest merged candidate set */
   int64_t repair_edges;       /* edges added by phase 4 (connectivity) */
   int32_t repair_rounds;      /* phase-4 rounds */
-  int32_t screen_used;        /* cng_screen actually used (the tensor-core screen needs d <= 192) */
+  int32_t screen_used;        /* cng_screen actually used */
   int32_t entry;              /* navigating node s */
   int32_t exact_int;          /* 1 when every FP32 squared distance is an exact integer */
   double screen_err_max;      /* largest |screened - rerank| seen on kept candidates */

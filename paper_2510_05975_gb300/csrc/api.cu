@@ -1364,6 +1364,7 @@ extern "C" cng_status cng_knn(const float* base, int64_t n, const float* rows, i
     stats->cert_fail_rows = hc.nfail;
     stats->order_ties = (int64_t)hc.order_ties;
     stats->exact_int = ki.exact;
+    stats->screen_used = screen == CNG_SCREEN_TC && bf16ops ? CNG_SCREEN_TC_BF16 : screen;
   }
   return CNG_OK;
 }
@@ -1372,7 +1373,7 @@ static cng_status tc_scores(const float* rows, int64_t m, const float* cols, int
                             int fp16, float scale, float* scores, void* stream) {
   if (!rows || !cols || !scores) return fail(CNG_E_INVAL, "pointers must be non-NULL");
   if (m < 1 || n < 1 || d < 1 || !tc_screen_supported(d, false))
-    return fail(CNG_E_INVAL, "need m, n >= 1 and 1 <= d <= 192");
+    return fail(CNG_E_INVAL, "need m, n >= 1 and 1 <= d <= 4096");
   if (!(scale > 0.f) || std::ilogb(scale) != std::log2(scale))
     return fail(CNG_E_INVAL, "scale must be a power of two");
   cudaStream_t s = (cudaStream_t)stream;

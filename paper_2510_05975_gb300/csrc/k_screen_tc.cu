@@ -7,16 +7,19 @@
 // the list; rows it cannot certify are rescanned exactly.
 //
 // CTA organisation (one CTA per SM, persistent over 256-row blocks):
-//   warp 8      TMA producer: the row block's A tile once, then B tiles of 128 columns
-//               through an NST-stage ring (full / empty mbarriers)
+//   warp 8      TMA producer: for kpad <= 192 the row block's A tile once, then B tiles of 128
+//               columns through an NST-stage ring (full / empty mbarriers); for wider rows A and
+//               B together in 64-wide K chunks through the same ring; plus each tile's 128
+//               column norms into a 4-slot norm ring
 //   warp 9      TMEM owner (512 columns) and MMA issuer: per B tile, two M=128 x N=128
 //               accumulators (rows 0-127 and 128-255), K in steps of 16, into one of two TMEM
-//               buffers; tcgen05.commit frees the B stage and publishes the buffer
+//               buffers; tcgen05.commit frees each operand stage and publishes the buffer
 //   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of accumulator w / 4,
-//               so each thread owns one row; 32 columns per tcgen05.ld; score = fma(-2, acc,
-//               ||y_b||^2); the minimum of 32 scores is compared with the row threshold and
-//               only then are entries appended to the row's buffer; full buffers are compacted
-//               by the warp (radix select) which lowers the threshold
+//               so each thread owns one row; the row's 128 columns are loaded at once and the
+//               TMEM buffer is released before scoring; score = fma(-2, acc, ||y_b||^2); the
+//               minimum of each 32 scores is compared with the row threshold and only then are
+//               entries appended to the row's buffer; full buffers are compacted by the warp
+//               (radix select) which lowers the threshold
 // All CTAs sweep the columns in the same order, so B tiles are shared through L2.
 // Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT, drains its own
 // TMA copies and MMAs (bounded) and frees TMEM before returning.
@@ -34,8 +37,10 @@ constexpr int TC_BM = 256;          // rows per CTA block (two M=128 accumulator
 constexpr int TC_BN = 128;          // columns per B tile
 constexpr int TC_NBUF = 512 / (2 * TC_BN);  // accumulator buffers in the 512 TMEM columns
 constexpr int TC_NBUF_LOG = TC_NBUF == 4 ? 2 : 1;
-constexpr int TC_MAXST = TC_BN == 64 ? 8 : 4;  // B stages at most
-static_assert((2 * TC_MAXST + 2 * TC_NBUF + 3) * 8 + 16 <= 256, "barrier block exceeds its 256 bytes");
+constexpr int TC_MAXST = TC_BN == 64 ? 8 : 4;  // operand stages at most
+constexpr int TC_NR = 4;            // column-norm ring slots (tiles whose norms are in flight)
+static_assert((2 * TC_MAXST + 2 * TC_NBUF + 2 * TC_NR + 3) * 8 + 8 <= 256,
+              "barrier block exceeds its 256 bytes");
 static_assert(TC_NBUF == 2 || TC_NBUF == 4, "two or four accumulator buffers");
 constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
 constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
@@ -317,9 +322,6 @@ CNG_DEV void fma2(uint32_t& d0, uint32_t& d1, uint32_t a0, uint32_t a1, float b,
   asm("mov.b64 {%0, %1}, %2;" : "=r"(d0), "=r"(d1) : "l"(r));
 }
 
-// One row's 32 accumulator columns [cb, cb + 32): screened scores, masking of out-of-range
-// and self columns, minimum against the row threshold, appends below the threshold.  The
-// minimum is taken per group of 4 columns first, so appends visit only groups that hold one.
 CNG_DEV float4 lds_f4(uint32_t saddr) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -328,64 +330,95 @@ CNG_DEV float4 lds_f4(uint32_t saddr) {
   return v;
 }
 
-template <bool DUMP>
-CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_t row,
-                           const TcParams& P, uint32_t nbs, float thr, int& cnt,
-                           uint64_t* rbuf, float* dump) {
-  float4 y[8];  // the 32 column norms (shared memory, same address in every lane)
+CNG_DEV float fu(uint32_t x) { return __uint_as_float(x); }
+
+// Selection for one tile row (scores already in r): minimums per 32-column chunk and per
+// 4-column group against the row threshold; appends visit only chunks and groups that hold one;
+// every branch is warp-uniform.
+CNG_DEV void select_tile(const uint32_t (&r)[TC_BN], int64_t c0, bool live, const TcParams& P,
+                         float thr, int& cnt, uint64_t* rbuf) {
+  float cm[TC_BN / 32];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) y[q] = lds_f4(nbs + 16 * q);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    fma2(r[4 * q + 0], r[4 * q + 1], r[4 * q + 0], r[4 * q + 1], -2.f, y[q].x, y[q].y);
-    fma2(r[4 * q + 2], r[4 * q + 3], r[4 * q + 2], r[4 * q + 3], -2.f, y[q].z, y[q].w);
-  }
-  if (edge) {
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-      const int64_t col = cb + jj;
-      if (col >= P.n || (P.self_excl && col == row)) r[jj] = 0x7f800000u;
-    }
-  }
-  if (DUMP) {
-    if (live)
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj)
-        if (cb + jj < P.n) dump[row * P.n + cb + jj] = __uint_as_float(r[jj]);
-    return;
-  }
-  float gm[8];
-#pragma unroll
-  for (int g = 0; g < 8; ++g)
-    gm[g] = fminf(min3f(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]),
-                        __uint_as_float(r[4 * g + 2])),
-                  __uint_as_float(r[4 * g + 3]));
-  const float mall = min3f(min3f(gm[0], gm[1], gm[2]), min3f(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-  // appends, under warp-uniform branches (all lanes of the warp are converged here)
-  const bool want = live && mall < thr;
-  if (__any_sync(FULL, want)) {
+  for (int ch = 0; ch < TC_BN / 32; ++ch) {
+    float gm[8];
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
-      const bool wg = want && gm[g] < thr;
-      if (__any_sync(FULL, wg)) {
+      const int b0 = 32 * ch + 4 * g;
+      gm[g] = fminf(min3f(fu(r[b0]), fu(r[b0 + 1]), fu(r[b0 + 2])), fu(r[b0 + 3]));
+    }
+    cm[ch] = min3f(min3f(gm[0], gm[1], gm[2]), min3f(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
+  }
+  float tmin = cm[0];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float vj = __uint_as_float(r[4 * g + k]);
-          if (wg && vj < thr) {
-            if (cnt < P.cap)
-              rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + 4 * g + k);
-            else
-              atomicOr(P.status, ST_OVERFLOW);
-            ++cnt;
-          }
+  for (int ch = 1; ch < TC_BN / 32; ++ch) tmin = fminf(tmin, cm[ch]);
+  const bool want = live && tmin < thr;
+  if (!__any_sync(FULL, want)) return;
+#pragma unroll
+  for (int ch = 0; ch < TC_BN / 32; ++ch) {
+    const bool wc = want && cm[ch] < thr;
+    if (!__any_sync(FULL, wc)) continue;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int b0 = 32 * ch + 4 * g;
+      const float gmv = fminf(min3f(fu(r[b0]), fu(r[b0 + 1]), fu(r[b0 + 2])), fu(r[b0 + 3]));
+      const bool wg = wc && gmv < thr;
+      if (!__any_sync(FULL, wg)) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float vj = fu(r[b0 + k]);
+        if (wg && vj < thr) {
+          if (cnt < P.cap)
+            rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(c0 + b0 + k);
+          else
+            atomicOr(P.status, ST_OVERFLOW);
+          ++cnt;
         }
       }
     }
   }
 }
 
+// One row's TC_BN accumulator columns [c0, c0 + TC_BN), already in registers: screened scores
+// fma(-2, acc, ||y_b||^2) (the column norms from the norm ring slot at `nbs`, released once
+// read), masking of out-of-range and self columns, then the selection (or, for the score-dump
+// test aid, the scores written out).
+template <bool DUMP>
+CNG_DEV void process_tile(uint32_t (&r)[TC_BN], int64_t c0, bool edge, bool live, int64_t row,
+                          const TcParams& P, uint32_t nbs, uint64_t* nempty, int lane, float thr,
+                          int& cnt, uint64_t* rbuf, float* dump) {
+#pragma unroll
+  for (int q = 0; q < TC_BN / 4; ++q) {
+    const float4 y = lds_f4(nbs + 16 * q);
+    fma2(r[4 * q + 0], r[4 * q + 1], r[4 * q + 0], r[4 * q + 1], -2.f, y.x, y.y);
+    fma2(r[4 * q + 2], r[4 * q + 3], r[4 * q + 2], r[4 * q + 3], -2.f, y.z, y.w);
+  }
+  // the norms are in registers: release the ring slot to the producer
+  __syncwarp();
+  if (lane == 0) mbar_arrive(nempty);
+  if (edge) {
+#pragma unroll
+    for (int jj = 0; jj < TC_BN; ++jj) {
+      const int64_t col = c0 + jj;
+      if (col >= P.n || (P.self_excl && col == row)) r[jj] = 0x7f800000u;
+    }
+  }
+  if constexpr (DUMP) {
+    if (live)
+#pragma unroll
+      for (int jj = 0; jj < TC_BN; ++jj)
+        if (c0 + jj < P.n) dump[row * P.n + c0 + jj] = fu(r[jj]);
+  } else {
+    select_tile(r, c0, live, P, thr, cnt, rbuf);
+  }
+}
+
 // ---- the kernel --------------------------------------------------------------------------------
-template <int CPL, bool DUMP>
+// KSTREAM = false: the row block's A tile stays resident (kpad <= 192) and each stage holds one
+//   B tile of TC_BN columns x kpad.
+// KSTREAM = true: A and B are streamed together in 64-wide K chunks (any kpad), each stage
+//   holding the row block's A chunk and the column tile's B chunk; the accumulators sum the
+//   chunks of a tile in TMEM.
+template <int CPL, bool DUMP, bool KSTREAM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  TcParams P, float* dump) {
@@ -393,22 +426,24 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   // 1024-byte aligned tile region
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int a_bytes = TC_BM * P.kpad * 2;
-  const int b_bytes = TC_BN * P.kpad * 2;
+  const int a_bytes = KSTREAM ? 0 : TC_BM * P.kpad * 2;
+  const int stage_bytes = KSTREAM ? (TC_BM + TC_BN) * TC_KC * 2 : TC_BN * P.kpad * 2;
   unsigned char* sA = smem;
   unsigned char* sB = smem + a_bytes;
-  float* sNB = reinterpret_cast<float*>(sB + P.nst * b_bytes);  // [nst][TC_BN] column norms
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sNB + P.nst * TC_BN);
+  float* sNB = reinterpret_cast<float*>(sB + P.nst * stage_bytes);  // [TC_NR][TC_BN] column norms
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sNB + TC_NR * TC_BN);
   uint64_t* b_full = bars;               // [nst]
   uint64_t* b_empty = bars + P.nst;      // [nst]
   uint64_t* t_full = bars + 2 * P.nst;   // [TC_NBUF]
   uint64_t* t_empty = t_full + TC_NBUF;  // [TC_NBUF]
-  uint64_t* a_full = t_empty + TC_NBUF;  // [1]
+  uint64_t* n_full = t_empty + TC_NBUF;  // [TC_NR]
+  uint64_t* n_empty = n_full + TC_NR;    // [TC_NR]
+  uint64_t* a_full = n_empty + TC_NR;    // [1]
   uint64_t* a_empty = a_full + 1;        // [1]
   uint64_t* fin = a_empty + 1;           // [1] MMA drain at exit
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  uint32_t* hist_all = reinterpret_cast<uint32_t*>(tmem_slot + 4);  // [8 warps][256]
+  uint32_t* hist_all = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);  // [8][256]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nrb = (P.m + TC_BM - 1) / TC_BM;
@@ -417,11 +452,15 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   if (tid == 0) {
     for (int i = 0; i < P.nst; ++i) {
       mbar_init(&b_full[i], 1);
-      mbar_init(&b_empty[i], 1 + 8);  // MMA commit + the 8 epilogue warps (norms read)
+      mbar_init(&b_empty[i], 1);  // the MMA's commit
     }
     for (int i = 0; i < TC_NBUF; ++i) {
       mbar_init(&t_full[i], 1);
       mbar_init(&t_empty[i], 8);
+    }
+    for (int i = 0; i < TC_NR; ++i) {
+      mbar_init(&n_full[i], 1);
+      mbar_init(&n_empty[i], 8);
     }
     mbar_init(a_full, 1);
     mbar_init(a_empty, 1);
@@ -446,37 +485,69 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
       int64_t it = 0;
       int j = 0;
-      int s = 0;        // B stage of tile `it` (it % nst, advanced without dividing)
-      uint32_t ph = 0;  // its phase ((it / nst) & 1)
+      int s = 0;         // stage of the next copy (advanced without dividing)
+      uint32_t ph = 0;   // its phase
+      int ns = 0;        // norm ring slot of the next tile
+      uint32_t nph = 0;  // its phase
       bool ok = true;
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
-        ok = mbar_wait(a_empty, (j & 1) ^ 1, abort_flag, P.status);
-        if (!ok) break;
+        if (!KSTREAM) {
+          ok = mbar_wait(a_empty, (j & 1) ^ 1, abort_flag, P.status);
+          if (!ok) break;
+          mbar_expect_tx(a_full, (uint32_t)a_bytes);
+          for (int kc = 0; kc < P.nkc; ++kc)
+            tma_load_2d(sA + kc * (TC_BM * 128), &mapA, kc * TC_KC, (int)(rb * TC_BM), a_full);
+        }
         const int t0 = sweep_start(P, rb, ntiles);
-        mbar_expect_tx(a_full, (uint32_t)a_bytes);
-        for (int kc = 0; kc < P.nkc; ++kc)
-          tma_load_2d(sA + kc * (TC_BM * 128), &mapA, kc * TC_KC, (int)(rb * TC_BM), a_full);
         for (int ti = 0; ti < ntiles; ++ti, ++it) {
           const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
           wave_checkpoint(P, it, nrb, ntiles);
-          ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
+          // the tile's column norms into the norm ring
+          ok = mbar_wait(&n_empty[ns], nph ^ 1, abort_flag, P.status);
           if (!ok) break;
-          mbar_expect_tx(&b_full[s], (uint32_t)(b_bytes + TC_BN * 4));
-          unsigned char* dst = sB + s * b_bytes;
-          for (int kc = 0; kc < P.nkc; ++kc)
-            tma_load_2d(dst + kc * (TC_BN * 128), &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
-          bulk_load(sNB + s * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &b_full[s]);
-          if (++s == P.nst) {
-            s = 0;
-            ph ^= 1u;
+          mbar_expect_tx(&n_full[ns], TC_BN * 4);
+          bulk_load(sNB + ns * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &n_full[ns]);
+          if (++ns == TC_NR) {
+            ns = 0;
+            nph ^= 1u;
+          }
+          if (!KSTREAM) {
+            ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
+            if (!ok) break;
+            mbar_expect_tx(&b_full[s], (uint32_t)stage_bytes);
+            unsigned char* dst = sB + s * stage_bytes;
+            for (int kc = 0; kc < P.nkc; ++kc)
+              tma_load_2d(dst + kc * (TC_BN * 128), &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
+            if (++s == P.nst) {
+              s = 0;
+              ph ^= 1u;
+            }
+          } else {
+            for (int kc = 0; kc < P.nkc && ok; ++kc) {
+              ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
+              if (!ok) break;
+              mbar_expect_tx(&b_full[s], (uint32_t)stage_bytes);
+              unsigned char* dst = sB + s * stage_bytes;
+              tma_load_2d(dst, &mapA, kc * TC_KC, (int)(rb * TC_BM), &b_full[s]);
+              tma_load_2d(dst + TC_BM * 128, &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
+              if (++s == P.nst) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!ok) break;
           }
         }
       }
       if (!ok) {
         // drain: wait (bounded) for copies this thread issued into stages not yet consumed
-        for (int s = 0; s < P.nst; ++s) {
-          for (uint32_t i = 0; i < (1u << 20); ++i)
-            if (mbar_try(&b_full[s], 0) || mbar_try(&b_full[s], 1)) break;
+        for (int i = 0; i < P.nst; ++i) {
+          for (uint32_t w = 0; w < (1u << 20); ++w)
+            if (mbar_try(&b_full[i], 0) || mbar_try(&b_full[i], 1)) break;
+        }
+        for (int i = 0; i < TC_NR; ++i) {
+          for (uint32_t w = 0; w < (1u << 20); ++w)
+            if (mbar_try(&n_full[i], 0) || mbar_try(&n_full[i], 1)) break;
         }
       }
     }
@@ -484,42 +555,71 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     if (lane == 0) {
       int64_t tt = 0;
       int j = 0;
-      int s = 0;         // B stage of the tile (advanced without dividing)
+      int s = 0;         // stage (advanced without dividing)
       uint32_t sph = 0;  // its phase
       bool ok = true;
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++j) {
-        ok = mbar_wait(a_full, j & 1, abort_flag, P.status);
-        if (!ok) break;
-        tc_fence_after();
+        if (!KSTREAM) {
+          ok = mbar_wait(a_full, j & 1, abort_flag, P.status);
+          if (!ok) break;
+          tc_fence_after();
+        }
         const uint32_t a_base = smem_u32(sA);
         for (int t = 0; t < ntiles; ++t, ++tt) {
           const int b = (int)(tt & (TC_NBUF - 1));
-          ok = mbar_wait(&b_full[s], sph, abort_flag, P.status);
-          if (!ok) break;
-          ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> TC_NBUF_LOG) & 1) ^ 1), abort_flag, P.status);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t b_base = smem_u32(sB + s * b_bytes);
-          for (int kc = 0; kc < P.nkc; ++kc) {
+          const uint32_t d_base = tmem + (uint32_t)(b * (2 * TC_BN));
+          if (!KSTREAM) {
+            ok = mbar_wait(&b_full[s], sph, abort_flag, P.status);
+            if (!ok) break;
+            ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> TC_NBUF_LOG) & 1) ^ 1), abort_flag, P.status);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t b_base = smem_u32(sB + s * stage_bytes);
+            for (int kc = 0; kc < P.nkc; ++kc) {
 #pragma unroll
-            for (int k16 = 0; k16 < TC_KC / 16; ++k16) {
-              const uint64_t bd = desc_sw128(b_base + kc * (TC_BN * 128) + k16 * 32);
+              for (int k16 = 0; k16 < TC_KC / 16; ++k16) {
+                const uint64_t bd = desc_sw128(b_base + kc * (TC_BN * 128) + k16 * 32);
 #pragma unroll
-              for (int acc = 0; acc < 2; ++acc) {
-                const uint64_t ad = desc_sw128(a_base + kc * (TC_BM * 128) + acc * (128 * 128) + k16 * 32);
-                mma_f16(tmem + (uint32_t)(b * (2 * TC_BN) + acc * TC_BN), ad, bd, P.idesc, (kc | k16) != 0);
+                for (int acc = 0; acc < 2; ++acc) {
+                  const uint64_t ad = desc_sw128(a_base + kc * (TC_BM * 128) + acc * (128 * 128) + k16 * 32);
+                  mma_f16(d_base + (uint32_t)(acc * TC_BN), ad, bd, P.idesc, (kc | k16) != 0);
+                }
               }
             }
+            mma_commit(&b_empty[s]);
+            if (++s == P.nst) {
+              s = 0;
+              sph ^= 1u;
+            }
+          } else {
+            ok = mbar_wait(&t_empty[b], (uint32_t)(((tt >> TC_NBUF_LOG) & 1) ^ 1), abort_flag, P.status);
+            if (!ok) break;
+            for (int kc = 0; kc < P.nkc && ok; ++kc) {
+              ok = mbar_wait(&b_full[s], sph, abort_flag, P.status);
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t st_base = smem_u32(sB + s * stage_bytes);
+#pragma unroll
+              for (int k16 = 0; k16 < TC_KC / 16; ++k16) {
+                const uint64_t bd = desc_sw128(st_base + TC_BM * 128 + k16 * 32);
+#pragma unroll
+                for (int acc = 0; acc < 2; ++acc) {
+                  const uint64_t ad = desc_sw128(st_base + acc * (128 * 128) + k16 * 32);
+                  mma_f16(d_base + (uint32_t)(acc * TC_BN), ad, bd, P.idesc, (kc | k16) != 0);
+                }
+              }
+              mma_commit(&b_empty[s]);
+              if (++s == P.nst) {
+                s = 0;
+                sph ^= 1u;
+              }
+            }
+            if (!ok) break;
           }
-          mma_commit(&b_empty[s]);
           mma_commit(&t_full[b]);
-          if (++s == P.nst) {
-            s = 0;
-            sph ^= 1u;
-          }
         }
         if (!ok) break;
-        mma_commit(a_empty);
+        if (!KSTREAM) mma_commit(a_empty);
       }
       // drain every MMA this thread issued before TMEM is released
       mma_commit(fin);
@@ -533,8 +633,8 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     uint64_t* rbuf = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rloc) * P.cap;
     uint32_t* hist = hist_all + warp * 256;
     int64_t tt = 0;
-    int stage = 0;     // the B stage (and its norms) of tile tt, advanced without dividing
-    uint32_t sph = 0;  // its phase
+    int ns = 0;        // norm ring slot of tile tt (advanced without dividing)
+    uint32_t nph = 0;  // its phase
     bool ok = true;
     for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
       const int64_t row = rb * TC_BM + rloc;
@@ -548,33 +648,26 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> TC_NBUF_LOG) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
-        const int64_t c0 = (int64_t)t * TC_BN;
-        // observe the stage's TMA completion too (already complete; the stage cannot be refilled
-        // before this warp releases it), so the norms written by the copy engine are visible
-        ok = mbar_wait_warp(&b_full[stage], sph, abort_flag, P.status);
-        if (!ok) break;
-        const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
+        // the whole tile row into registers, then the accumulator buffer goes back to the MMA
+        // at once: the MMA of tile tt + 2 overlaps the scoring and selection of this one
         const uint32_t ta =
             tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * (2 * TC_BN) + accsel * TC_BN);
-#pragma unroll 1
-        for (int ch = 0; ch < TC_BN / 32; ++ch) {
-          uint32_t r[32];
-          tmem_ld32_nowait(ta + ch * 32, r);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (ch == TC_BN / 32 - 1) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&t_empty[b]);
-          }
-          process_chunk<DUMP>(r, c0 + ch * 32, edge, live, row, P,
-                              smem_u32(sNB + stage * TC_BN + ch * 32), thr, cnt, rbuf, dump);
-        }
-        // norms of this stage no longer needed: release the stage (with the MMA's commit)
+        uint32_t r[TC_BN];
+#pragma unroll
+        for (int ch = 0; ch < TC_BN / 32; ++ch) tmem_ld32_nowait(ta + ch * 32, r + ch * 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&b_empty[stage]);
-        if (++stage == P.nst) {
-          stage = 0;
-          sph ^= 1u;
+        if (lane == 0) mbar_arrive(&t_empty[b]);
+        ok = mbar_wait_warp(&n_full[ns], nph, abort_flag, P.status);
+        if (!ok) break;
+        const int64_t c0 = (int64_t)t * TC_BN;
+        const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
+        process_tile<DUMP>(r, c0, edge, live, row, P, smem_u32(sNB + ns * TC_BN), &n_empty[ns], lane,
+                           thr, cnt, rbuf, dump);
+        if (++ns == TC_NR) {
+          ns = 0;
+          nph ^= 1u;
         }
         if (DUMP) continue;
         // compact every row whose buffer could overflow on the next tile
@@ -662,7 +755,11 @@ cudaError_t launch_wait_probe(uint32_t* status, const uint32_t* never_set, cudaS
 }
 
 // ---- host side ---------------------------------------------------------------------------------
-bool tc_screen_supported(int d, bool) { return d >= 1 && ((d + 63) / 64) * 64 <= 192; }
+// Rows up to 192 wide keep the A tile resident; wider rows stream A and B in K chunks.
+constexpr int TC_KRES_MAX = 192;
+constexpr int TC_KPAD_MAX = 4096;
+
+bool tc_screen_supported(int d, bool) { return d >= 1 && ((d + 63) / 64) * 64 <= TC_KPAD_MAX; }
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -720,10 +817,10 @@ static uint32_t make_idesc(bool fp16) {
   return d;
 }
 
-template <int CPL, bool DUMP>
+template <int CPL, bool DUMP, bool KSTREAM>
 static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
                            size_t smem, int grid, cudaStream_t s, float* dump) {
-  cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel<CPL, DUMP>,
+  cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel<CPL, DUMP, KSTREAM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // cooperative when the producers wait for one another (boundedly): every CTA resident at once
@@ -738,11 +835,11 @@ static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const 
   cfg.attrs = attr;
   cfg.numAttrs = p.sync ? 1 : 0;
   count_launch();
-  e = cudaLaunchKernelEx(&cfg, screen_tc_kernel<CPL, DUMP>, ma, mb, p, dump);
+  e = cudaLaunchKernelEx(&cfg, screen_tc_kernel<CPL, DUMP, KSTREAM>, ma, mb, p, dump);
   if (e == cudaErrorCooperativeLaunchTooLarge) {  // not all resident: plain launch (waits bounded)
     (void)cudaGetLastError();
     cfg.numAttrs = 0;
-    e = cudaLaunchKernelEx(&cfg, screen_tc_kernel<CPL, DUMP>, ma, mb, p, dump);
+    e = cudaLaunchKernelEx(&cfg, screen_tc_kernel<CPL, DUMP, KSTREAM>, ma, mb, p, dump);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -750,20 +847,23 @@ static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const 
 
 static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::string* msg, float* dump) {
   const int kpad = a.kpad;
-  if (kpad % 64 != 0 || kpad > 192) {
-    if (msg) *msg = "kpad must be a multiple of 64 and <= 192; ";
+  if (kpad % 64 != 0 || kpad < 64 || kpad > TC_KPAD_MAX) {
+    if (msg) *msg = "kpad must be a multiple of 64 in [64, 4096]; ";
     return cudaErrorInvalidValue;
   }
+  const bool kstream = kpad > TC_KRES_MAX;
   TcParams p{};
   p.m = a.m;
   p.n = a.n;
   p.kpad = kpad;
   p.nkc = kpad / 64;
-  const int a_bytes = TC_BM * kpad * 2, b_bytes = TC_BN * kpad * 2;
-  const int budget = 220 * 1024 - a_bytes - 1024 - 256 - 8 * 256 * 4;
-  p.nst = std::min(TC_MAXST, budget / (b_bytes + TC_BN * 4));
+  const int a_bytes = kstream ? 0 : TC_BM * kpad * 2;
+  const int stage_bytes = kstream ? (TC_BM + TC_BN) * TC_KC * 2 : TC_BN * kpad * 2;
+  const int fixed = 1024 + TC_NR * TC_BN * 4 + 256 + 8 * 256 * 4;  // alignment, norms, barriers, hist
+  const int budget = 220 * 1024 - a_bytes - fixed;
+  p.nst = std::min(TC_MAXST, budget / stage_bytes);
   if (p.nst < 2) {
-    if (msg) *msg = "shared memory too small for two B stages; ";
+    if (msg) *msg = "shared memory too small for two operand stages; ";
     return cudaErrorInvalidValue;
   }
   p.Lp = a.Lp;
@@ -789,7 +889,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   const int64_t nrb = (a.m + TC_BM - 1) / TC_BM;
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
   // at least ~116 KB so that a single CTA (and its 512 TMEM columns) fits per SM
-  size_t smem = 1024 + (size_t)a_bytes + (size_t)p.nst * (b_bytes + TC_BN * 4) + 256 + 8 * 256 * 4;
+  size_t smem = (size_t)fixed + (size_t)a_bytes + (size_t)p.nst * stage_bytes;
   smem = std::max<size_t>(smem, 116 * 1024);
   const size_t buf_words = (size_t)grid * TC_BM * p.cap;
   const size_t sync_words = sync_counter_words(a.m, a.n, grid);
@@ -807,8 +907,12 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   cudaError_t e;
 #define CNG_TC(C)                                                                             \
   case C:                                                                                     \
-    e = dump ? launch_t<C, true>(ma, mb, p, smem, grid, s, dump)                              \
-             : launch_t<C, false>(ma, mb, p, smem, grid, s, dump);                            \
+    if (kstream)                                                                              \
+      e = dump ? launch_t<C, true, true>(ma, mb, p, smem, grid, s, dump)                      \
+               : launch_t<C, false, true>(ma, mb, p, smem, grid, s, dump);                    \
+    else                                                                                      \
+      e = dump ? launch_t<C, true, false>(ma, mb, p, smem, grid, s, dump)                     \
+               : launch_t<C, false, false>(ma, mb, p, smem, grid, s, dump);                   \
     break;
   switch (cpl) {
     CNG_TC(12)

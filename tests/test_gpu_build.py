@@ -102,14 +102,16 @@ def test_ip_metric_requires_unit_norm():
     cng.cng_free(idx)
 
 
-@pytest.mark.parametrize("screen", [0, 1])
-def test_knn_rows_vs_oracle(screen):
+@pytest.mark.parametrize("kind,d,screen", [("gauss", 48, 0), ("gauss", 48, 1), ("gist", 960, 1),
+                                           ("gist", 330, 1)])
+def test_knn_rows_vs_oracle(kind, d, screen):
     need_gpu()
     cng = lib()
-    X = synth.generate("gauss", 5003, 48, seed=8)
-    Q = synth.generate("gauss", 300, 48, seed=9)
+    X = synth.generate(kind, 5003, d, seed=8)
+    Q = synth.generate(kind, 300, d, seed=9)
     ids, ds, st = cng.cng_knn(tensor(X), 100, rows=tensor(Q), screen=screen)
     ref, rd = oracle.knn(X, 100, rows=Q)
+    assert st["screen_used"] == screen
     assert np.array_equal(host(ids), ref)
     assert np.allclose(host(ds), rd, rtol=2e-6)
 

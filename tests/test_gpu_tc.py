@@ -34,7 +34,9 @@ def _scores(cng, R, C):
 
 
 @pytest.mark.parametrize("m,n,d", [(256, 128, 64), (300, 517, 100), (513, 1000, 128), (64, 300, 32),
-                                   (257, 129, 192)])
+                                   (257, 129, 192),
+                                   # wider rows: A and B streamed together in 64-wide K chunks
+                                   (300, 517, 200), (257, 389, 960), (40, 1000, 4000)])
 def test_tc_scores_match_reference(m, n, d):
     need_gpu()
     cng = lib()
@@ -73,7 +75,7 @@ def _scores_f16(cng, R, C, scale):
 
 
 @pytest.mark.parametrize("kind,m,n,d,scale", [("deep", 300, 517, 96, 8192.0), ("gauss", 257, 129, 192, 2048.0),
-                                              ("gist", 200, 300, 160, 1024.0)])
+                                              ("gist", 200, 300, 160, 1024.0), ("gist", 300, 700, 960, 1024.0)])
 def test_tc_scores_fp16_scaled(kind, m, n, d, scale):
     """FP16 operands fp16(scale x) as the build uses them for float data: scores equal the FP64
     arithmetic on the same rounded operands within the FP32 accumulation bound."""
