@@ -117,74 +117,160 @@ def recall_at_k(found: np.ndarray, gt: np.ndarray) -> float:
     return hits / (k * gt.shape[0])
 
 
-def oracle_baseline(X: np.ndarray, Q: np.ndarray, adj, deg, entry, w, k: int, L: int,
+def bench_config(w, args, ws: int) -> dict:
+    """The workload and build configuration both arms report (same keys, same values)."""
+    ops = {"tc": "fp16 (power-of-two scaled, FP32 accumulate)", "tc-bf16": "bf16 (FP32 accumulate)",
+           "fp32": "fp32 (CUDA cores)"}[args.screen]
+    return {"workload": args.workload, "n": w.n, "d": w.d, "dtype": w.dtype, "alpha": w.alpha,
+            "tau": 0.0, "R": w.R, "L": w.L, "nq": w.nq, "k": w.k, "screen": args.screen,
+            "screen_operands": ops, "parallelism": "replicas" if ws > 1 else "single",
+            "l2": f"inputs larger than L2 ({w.n * w.d * (2 if w.dtype == 'float16' else 4) >> 20} MB points)"}
+
+
+def gpu_lists(w, X):
+    """Inputs for the oracle's phase-3/4 sample: the GPU build's phase-2 lists and final graph
+    (device kernels, untimed; the oracle legs time only the oracle)."""
+    import torch
+
+    import paper_2510_05975_gb300.cng as cng
+
+    idx, st = cng.cng_build(torch.from_numpy(X).cuda(), alpha=w.alpha, R=w.R, L=w.L, keep_lists=True)
+    _, _, fwd, fdeg = cng.cng_lists(idx)
+    adj, deg, _, entry = cng.cng_graph(idx)
+    out = dict(fwd=fwd.cpu().numpy(), fdeg=fdeg.cpu().numpy(), adj=adj.cpu().numpy(),
+               deg=deg.cpu().numpy(), entry=entry, repair_edges=int(st["repair_edges"]))
+    cng.cng_free(idx)
+    torch.cuda.synchronize()
+    return out
+
+
+def oracle_build_sample(X: np.ndarray, w, G: dict, m: int, seed: int) -> dict:
+    """The FP64 oracle, as it stands, on one bounded sample of the build (Alg. 3):
+    phase 1 (entry point) over all points; phase 2 (exact L-NN + Alg. 2) for m sampled points;
+    phase 3 (reverse edges of all phase-2 lists, then each sampled point's merged set, pruned
+    when it exceeds R) with the GPU's phase-2 lists as input; phase 4 (reachability over the
+    final graph + Alg. 1 searches for as many points as the GPU build repaired).  Sampled parts
+    are extrapolated to n; whole passes are timed as they are.  Returns seconds per part."""
+    import oracle
+
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(n, size=min(m, n), replace=False)
+    t = {}
+    t0 = time.perf_counter()
+    oracle.entry(X)
+    t["entry"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ids, _ = oracle.knn(X, w.L + 1, rows=X[rows], exclude_self=False)
+    for r, row in zip(rows, ids):
+        oracle.prune(X, int(r), row[row != r][: w.L], w.alpha, 0.0, w.R)
+    t["phase2"] = (time.perf_counter() - t0) / len(rows) * n
+    fwd, fdeg = G["fwd"], G["fdeg"]
+    t0 = time.perf_counter()
+    valid = np.arange(fwd.shape[1])[None, :] < fdeg[:, None]
+    src = np.repeat(np.arange(n, dtype=np.int32), fwd.shape[1])[valid.ravel()]
+    dst = fwd.ravel()[valid.ravel()]
+    order = np.argsort(dst, kind="stable")
+    src_s, off = src[order], np.concatenate([[0], np.cumsum(np.bincount(dst, minlength=n))])
+    t_csr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for p in rows:
+        mine = fwd[p, : fdeg[p]]
+        inn = src_s[off[p]: off[p + 1]]
+        V = np.concatenate([mine, inn[~np.isin(inn, mine)]]).astype(np.int32)
+        if len(V) > w.R:
+            oracle.prune(X, int(p), V, w.alpha, 0.0, w.R)
+        else:
+            sorted((oracle.dist(X[p], X[v]), int(v)) for v in V)
+    t["phase3"] = t_csr + (time.perf_counter() - t0) / len(rows) * n
+    adj, deg = G["adj"], G["deg"]
+    t0 = time.perf_counter()
+    seen = np.zeros(n, bool)
+    seen[G["entry"]] = True
+    frontier = np.array([G["entry"]])
+    while frontier.size:
+        nb = adj[frontier]
+        nb = nb[nb >= 0]
+        nb = np.unique(nb[~seen[nb]])
+        seen[nb] = True
+        frontier = nb
+    nrep = max(1, G["repair_edges"])
+    qs = X[rng.choice(n, size=min(nrep, 4096), replace=False)]
+    oracle.search(X, adj, deg, G["entry"], qs, min(8, 32), 32)
+    t["phase4"] = (time.perf_counter() - t0)
+    if nrep > 4096:
+        t["phase4"] *= nrep / 4096
+    t["total"] = t["entry"] + t["phase2"] + t["phase3"] + t["phase4"]
+    return t
+
+
+def oracle_baseline(X: np.ndarray, Q: np.ndarray, G: dict, w, k: int, L: int,
                     budget_s: float = 15.0):
-    """The FP64 oracle, as it stands, on a bounded sample: exact candidate lists + Alg. 2 for
-    sampled points (extrapolated to the full build), Alg. 1 for sampled queries."""
+    """cpu_baseline leg: oracle_build_sample grown until about budget/2 seconds, then Alg. 1
+    for sampled queries on the GPU-built graph."""
     import oracle
 
     threads = oracle.num_threads()
-    rng = np.random.default_rng(0)
-    # build sample: grow until ~budget/2 seconds
-    m, t_build, pts = 8, 0.0, 0
-    while t_build < budget_s / 2 and pts < X.shape[0]:
-        rows = rng.integers(0, X.shape[0], size=m)
+    m, t_used, parts = 64, 0.0, None
+    while True:
         t0 = time.perf_counter()
-        ids, _ = oracle.knn(X, w.L, rows=X[rows], exclude_self=False)
-        for r, row in zip(rows, ids):
-            cand = row[row != r][: w.L]
-            oracle.prune(X, int(r), cand, w.alpha, 0.0, w.R)
-        t_build += time.perf_counter() - t0
-        pts += m
-        m *= 2
-    build_s = t_build / pts * X.shape[0]
-    # search sample
+        parts = oracle_build_sample(X, w, G, m, seed=0)
+        t_used = time.perf_counter() - t0
+        if t_used >= budget_s / 2 or m >= 4096:
+            break
+        m *= 4
     nq, t_s, qs = 64, 0.0, 0
     while t_s < budget_s / 2 and qs < Q.shape[0]:
         sel = Q[qs: qs + nq]
         t0 = time.perf_counter()
-        oracle.search(X, adj, deg, entry, sel, k, L)
+        oracle.search(X, G["adj"], G["deg"], G["entry"], sel, k, L)
         t_s += time.perf_counter() - t0
         qs += sel.shape[0]
         nq *= 2
-    qps = qs / t_s
-    return {"value": build_s, "unit": "s (build, extrapolated)", "cores": threads, "kind": "oracle",
-            "sample": f"{pts} points: exact L-NN over all {X.shape[0]} points in FP64 + Alg. 2, "
-                      f"extrapolated x{X.shape[0] / pts:.0f}; reverse merge not sampled; "
+    return {"value": parts["total"], "unit": "s (build, extrapolated)", "cores": threads,
+            "kind": "oracle", "parts_s": parts,
+            "sample": f"{m} points: phase 1 over all points; exact L-NN over all {X.shape[0]} points "
+                      f"in FP64 + Alg. 2 and the phase-3 merge for the sample, extrapolated "
+                      f"x{X.shape[0] / m:.0f}; reverse edges and phase-4 reachability as whole passes; "
                       f"search {qs} queries at L={L} on the GPU-built graph",
-            "search_qps": qps}
+            "search_qps": qs / t_s}
 
 
 def run_reference(args):
-    ws, rank, _ = dist_env()
+    ws, rank, local = dist_env()
     if rank != 0:
         return
     from paper_2510_05975_gb300 import synth
 
     w = synth.WORKLOADS[args.workload]
-    X = w.base()
-    Q = w.queries()
+    X = w.base().astype(np.float32)
     import oracle
 
     oracle.build()
+    import torch
+
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    G = gpu_lists(w, X)
+    m = 64
     times = []
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        rng = np.random.default_rng(step)
-        rows = rng.integers(0, X.shape[0], size=16)
-        ids, _ = oracle.knn(X, w.L, rows=X[rows], exclude_self=False)
-        for r, row in zip(rows, ids):
-            oracle.prune(X, int(r), row[row != r][: w.L], w.alpha, 0.0, w.R)
-        dt = time.perf_counter() - t0
+        parts = oracle_build_sample(X, w, G, m, seed=step)
         if step >= args.warmup:
-            times.append(dt / 16 * X.shape[0])
+            times.append(parts["total"])
     v = float(np.mean(times))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "n": w.n, "d": w.d},
+            "data": "synthetic", "config": bench_config(w, args, ws),
             "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": v,
-                             "sample": "16 points per step: exact L-NN in FP64 + Alg. 2, extrapolated to n"},
+                             "parts_s": parts,
+                             "sample": f"{m} points per step: phase 1 over all points; exact L-NN in "
+                                       f"FP64 + Alg. 2 and the phase-3 merge for the sample "
+                                       f"(GPU phase-2 lists as input), extrapolated to n; reverse "
+                                       f"edges and phase-4 reachability as whole passes"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -223,9 +309,18 @@ def hbm_kernels(w, X, st, ndc_sum, hops_sum, search_ms, peak, src):
     return out
 
 
-# DRAM bytes (read + write) of one screen launch at full size, from the one-pass ncu capture of
-# the current kernel (profiles/screen_tc_sift1m_dram.md); re-measure when the kernel changes.
-SCREEN_DRAM_BYTES = {"sift1m": 47.16e9 + 23.35e9}
+# DRAM bytes (read + write) of one full-size screen launch from a one-pass ncu capture, keyed by
+# (workload, digest of the screen kernel's source): a changed kernel has no entry, so its
+# traffic is reported as null until it is captured again.
+SCREEN_DRAM_BYTES = {}
+
+
+def screen_digest() -> str:
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_2510_05975_gb300", "csrc", "k_screen_tc.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def main():
@@ -384,8 +479,6 @@ def main():
     if best is None:
         best = (Ls, 0.99, 1, 0, float("inf"))
     Ll, theta, cev, gatev = best[0], best[1], best[2], best[3]
-    adj, deg, _, entry = cng.cng_graph(idx)
-    adj_h, deg_h = adj.cpu().numpy(), deg.cpu().numpy()
     cng.cng_free(idx)
 
     # timed device-resident steps: build, stop-model training, fixed-L search, learned search
@@ -501,28 +594,26 @@ def main():
                 "peak_source": "FP32 lanes x max SM clock (derived)"}
     achieved = flops / t_screen / 1e12
     traffic = None
-    if roof["bound"] == "tensor" and screen == cng.CNG_SCREEN_TC and args.workload in SCREEN_DRAM_BYTES:
-        traffic = SCREEN_DRAM_BYTES[args.workload]
+    if roof["bound"] == "tensor" and screen == cng.CNG_SCREEN_TC:
+        traffic = SCREEN_DRAM_BYTES.get((args.workload, screen_digest()))
     roof.update({"kernel": "candidate screen", "achieved": achieved, "frac": achieved / roof["peak"],
                  "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                 "kernel_digest": screen_digest(),
                  "algorithmic": "2*n*n*d flops per launch"})
 
     hbm = hbm_kernels(w, X, last_stats, ndc_sum_f, hops_sum_f, f_ms, pk["hbm_gbs"], src)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(X.astype(np.float32), Q[:4096].astype(np.float32), adj_h, deg_h, entry,
-                              w, w.k, Ls)
+        X32 = X.astype(np.float32)
+        cpu = oracle_baseline(X32, Q[:4096].astype(np.float32), gpu_lists(w, X32), w, w.k, Ls)
 
     clocks = sampler.summary()
     if rank == 0:
         line = {"metric": METRIC, "value": b_s * 1.0, "unit": "s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": st_ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "n": w.n, "d": w.d, "alpha": w.alpha, "tau": 0.0,
-                           "R": w.R, "L": w.L, "nq": w.nq, "k": w.k, "screen": args.screen,
-                           "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "inputs larger than L2 (512 MB points)"},
+                "config": bench_config(w, args, ws),
                 "search": {"fixed": {"L": Ls, "qps": qps_f * ws, "recall_at_10": rec_f, "ms": f_ms,
                                      "hops_mean": hops_f},
                            "learned": {"L": Ll, "threshold": theta, "check_every": cev,

@@ -15,11 +15,10 @@
 //               accumulators (rows 0-127 and 128-255), K in steps of 16, into one of two TMEM
 //               buffers; tcgen05.commit frees each operand stage and publishes the buffer
 //   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of accumulator w / 4,
-//               so each thread owns one row; the row's 128 columns are loaded at once and the
-//               TMEM buffer is released before scoring; score = fma(-2, acc, ||y_b||^2); the
-//               minimum of each 32 scores is compared with the row threshold and only then are
-//               entries appended to the row's buffer; full buffers are compacted by the warp
-//               (radix select) which lowers the threshold
+//               so each thread owns one row; 32 columns per tcgen05.ld; score = fma(-2, acc,
+//               ||y_b||^2); the minimum of 32 scores is compared with the row threshold and
+//               only then are entries appended to the row's buffer; full buffers are compacted
+//               by the warp (radix select) which lowers the threshold
 // All CTAs sweep the columns in the same order, so B tiles are shared through L2.
 // Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT, drains its own
 // TMA copies and MMAs (bounded) and frees TMEM before returning.
@@ -332,83 +331,62 @@ CNG_DEV float4 lds_f4(uint32_t saddr) {
 
 CNG_DEV float fu(uint32_t x) { return __uint_as_float(x); }
 
-// Selection for one tile row (scores already in r): minimums per 32-column chunk and per
-// 4-column group against the row threshold; appends visit only chunks and groups that hold one;
-// every branch is warp-uniform.
-CNG_DEV void select_tile(const uint32_t (&r)[TC_BN], int64_t c0, bool live, const TcParams& P,
-                         float thr, int& cnt, uint64_t* rbuf) {
-  float cm[TC_BN / 32];
-#pragma unroll
-  for (int ch = 0; ch < TC_BN / 32; ++ch) {
-    float gm[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const int b0 = 32 * ch + 4 * g;
-      gm[g] = fminf(min3f(fu(r[b0]), fu(r[b0 + 1]), fu(r[b0 + 2])), fu(r[b0 + 3]));
-    }
-    cm[ch] = min3f(min3f(gm[0], gm[1], gm[2]), min3f(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-  }
-  float tmin = cm[0];
-#pragma unroll
-  for (int ch = 1; ch < TC_BN / 32; ++ch) tmin = fminf(tmin, cm[ch]);
-  const bool want = live && tmin < thr;
-  if (!__any_sync(FULL, want)) return;
-#pragma unroll
-  for (int ch = 0; ch < TC_BN / 32; ++ch) {
-    const bool wc = want && cm[ch] < thr;
-    if (!__any_sync(FULL, wc)) continue;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const int b0 = 32 * ch + 4 * g;
-      const float gmv = fminf(min3f(fu(r[b0]), fu(r[b0 + 1]), fu(r[b0 + 2])), fu(r[b0 + 3]));
-      const bool wg = wc && gmv < thr;
-      if (!__any_sync(FULL, wg)) continue;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float vj = fu(r[b0 + k]);
-        if (wg && vj < thr) {
-          if (cnt < P.cap)
-            rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(c0 + b0 + k);
-          else
-            atomicOr(P.status, ST_OVERFLOW);
-          ++cnt;
-        }
-      }
-    }
-  }
-}
-
-// One row's TC_BN accumulator columns [c0, c0 + TC_BN), already in registers: screened scores
-// fma(-2, acc, ||y_b||^2) (the column norms from the norm ring slot at `nbs`, released once
-// read), masking of out-of-range and self columns, then the selection (or, for the score-dump
-// test aid, the scores written out).
+// One row's 32 accumulator columns [cb, cb + 32): screened scores fma(-2, acc, ||y_b||^2) with
+// the column norms from the norm ring (shared memory, the same address in every lane), masking
+// of out-of-range and self columns, the minimum against the row threshold and appends below
+// it.  The minimum is taken per group of 4 columns first, so appends visit only groups that
+// hold one; every branch is warp-uniform.
 template <bool DUMP>
-CNG_DEV void process_tile(uint32_t (&r)[TC_BN], int64_t c0, bool edge, bool live, int64_t row,
-                          const TcParams& P, uint32_t nbs, uint64_t* nempty, int lane, float thr,
-                          int& cnt, uint64_t* rbuf, float* dump) {
+CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_t row,
+                           const TcParams& P, uint32_t nbs, float thr, int& cnt,
+                           uint64_t* rbuf, float* dump) {
+  float4 y[8];
 #pragma unroll
-  for (int q = 0; q < TC_BN / 4; ++q) {
-    const float4 y = lds_f4(nbs + 16 * q);
-    fma2(r[4 * q + 0], r[4 * q + 1], r[4 * q + 0], r[4 * q + 1], -2.f, y.x, y.y);
-    fma2(r[4 * q + 2], r[4 * q + 3], r[4 * q + 2], r[4 * q + 3], -2.f, y.z, y.w);
+  for (int q = 0; q < 8; ++q) y[q] = lds_f4(nbs + 16 * q);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    fma2(r[4 * q + 0], r[4 * q + 1], r[4 * q + 0], r[4 * q + 1], -2.f, y[q].x, y[q].y);
+    fma2(r[4 * q + 2], r[4 * q + 3], r[4 * q + 2], r[4 * q + 3], -2.f, y[q].z, y[q].w);
   }
-  // the norms are in registers: release the ring slot to the producer
-  __syncwarp();
-  if (lane == 0) mbar_arrive(nempty);
   if (edge) {
 #pragma unroll
-    for (int jj = 0; jj < TC_BN; ++jj) {
-      const int64_t col = c0 + jj;
+    for (int jj = 0; jj < 32; ++jj) {
+      const int64_t col = cb + jj;
       if (col >= P.n || (P.self_excl && col == row)) r[jj] = 0x7f800000u;
     }
   }
   if constexpr (DUMP) {
     if (live)
 #pragma unroll
-      for (int jj = 0; jj < TC_BN; ++jj)
-        if (c0 + jj < P.n) dump[row * P.n + c0 + jj] = fu(r[jj]);
+      for (int jj = 0; jj < 32; ++jj)
+        if (cb + jj < P.n) dump[row * P.n + cb + jj] = fu(r[jj]);
   } else {
-    select_tile(r, c0, live, P, thr, cnt, rbuf);
+    float gm[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      gm[g] = fminf(min3f(fu(r[4 * g]), fu(r[4 * g + 1]), fu(r[4 * g + 2])), fu(r[4 * g + 3]));
+    const float mall = min3f(min3f(gm[0], gm[1], gm[2]), min3f(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
+    // appends, under warp-uniform branches (all lanes of the warp are converged here)
+    const bool want = live && mall < thr;
+    if (__any_sync(FULL, want)) {
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const bool wg = want && gm[g] < thr;
+        if (__any_sync(FULL, wg)) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float vj = fu(r[4 * g + k]);
+            if (wg && vj < thr) {
+              if (cnt < P.cap)
+                rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + 4 * g + k);
+              else
+                atomicOr(P.status, ST_OVERFLOW);
+              ++cnt;
+            }
+          }
+        }
+      }
+    }
   }
 }
 
@@ -648,23 +626,29 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> TC_NBUF_LOG) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
-        // the whole tile row into registers, then the accumulator buffer goes back to the MMA
-        // at once: the MMA of tile tt + 2 overlaps the scoring and selection of this one
-        const uint32_t ta =
-            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * (2 * TC_BN) + accsel * TC_BN);
-        uint32_t r[TC_BN];
-#pragma unroll
-        for (int ch = 0; ch < TC_BN / 32; ++ch) tmem_ld32_nowait(ta + ch * 32, r + ch * 32);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&t_empty[b]);
+        // the tile's column norms: the producer's copy into the ring slot is complete
         ok = mbar_wait_warp(&n_full[ns], nph, abort_flag, P.status);
         if (!ok) break;
         const int64_t c0 = (int64_t)t * TC_BN;
         const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
-        process_tile<DUMP>(r, c0, edge, live, row, P, smem_u32(sNB + ns * TC_BN), &n_empty[ns], lane,
-                           thr, cnt, rbuf, dump);
+        const uint32_t ta =
+            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * (2 * TC_BN) + accsel * TC_BN);
+#pragma unroll 1
+        for (int ch = 0; ch < TC_BN / 32; ++ch) {
+          uint32_t r[32];
+          tmem_ld32_nowait(ta + ch * 32, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (ch == TC_BN / 32 - 1) {  // the last TMEM load of the tile: buffer back to the MMA
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[b]);
+          }
+          process_chunk<DUMP>(r, c0 + ch * 32, edge, live, row, P,
+                              smem_u32(sNB + ns * TC_BN + ch * 32), thr, cnt, rbuf, dump);
+        }
+        // the norms of this slot are no longer needed: release it to the producer
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&n_empty[ns]);
         if (++ns == TC_NR) {
           ns = 0;
           nph ^= 1u;

@@ -22,6 +22,9 @@ into islands that graphs built from exact neighbour lists cannot navigate betwee
                  clipped to [0, 255] and rounded to integers (float32).
 * ``deep``       256 centres; c0 a random unit vector; A entries N(0, 0.25 / (16 d));
                  e ~ N(0, 0.05^2 / d); x normalised to unit length.
+* ``sift_iso``   the isotropic alternative: 64 centres with coordinates uniform on the
+                 integers 40..215, x = centre + N(0, 25^2 I) in all d dimensions, clipped to
+                 [0, 255] and rounded (each cluster intrinsically d-dimensional).
 * ``gist``       100 centres N(0, 0.1^2 I); per (centre, dimension) standard deviation
                  sqrt(v), v log-uniform on [0.01, 1] (diagonal covariance).
 * ``bigann16``   1,024 centres; c0 = 0; A entries N(0, 0.25 / 16); e ~ N(0, 0.05^2); stored
@@ -72,6 +75,9 @@ WORKLOADS = {
     "gist1m": Workload("gist1m", "gist", 1_000_000, 960, 1_000, 10, 1.2, 32, 128, 2_000, 3),
     "bigann10m": Workload("bigann10m", "bigann16", 10_000_000, 128, 100_000, 10, 1.2, 32, 128,
                           200_000, 4, "float16"),
+    # the SIFT-like shape with isotropic clusters (reported beside the low-rank recipe)
+    "sift1m_iso": Workload("sift1m_iso", "sift_iso", 1_000_000, 128, 10_000, 10, 1.2, 32, 128,
+                           20_000, 5),
 }
 
 
@@ -92,6 +98,8 @@ def _centres(kind: str, d: int, seed: int):
         c0 = (g / np.linalg.norm(g)).astype(np.float32)
         A = (rng.standard_normal((d, m)) * (0.5 / np.sqrt(m * d))).astype(np.float32)
         return c0, A, rng.standard_normal((256, m)).astype(np.float32)
+    if kind == "sift_iso":
+        return rng.integers(40, 216, size=(64, d)).astype(np.float32), None, None
     if kind == "gist":
         c = (0.1 * rng.standard_normal((100, d))).astype(np.float32)
         v = np.exp(rng.uniform(np.log(0.01), np.log(1.0), size=(100, d))).astype(np.float32)
@@ -124,6 +132,10 @@ def generate(kind: str, n: int, d: int, seed: int, dtype: str = "float32",
                 blk = np.rint(np.clip(blk, 0.0, 255.0))
             elif kind == "deep":
                 blk = blk / np.linalg.norm(blk, axis=1, keepdims=True)
+        elif kind == "sift_iso":
+            a = rng.integers(0, c0.shape[0], size=m)
+            blk = c0[a] + 25.0 * rng.standard_normal((m, d), dtype=np.float32)
+            blk = np.rint(np.clip(blk, 0.0, 255.0))
         elif kind == "gist":
             a = rng.integers(0, c0.shape[0], size=m)
             blk = c0[a] + A[a] * rng.standard_normal((m, d), dtype=np.float32)
