@@ -39,6 +39,31 @@ CNG_DEV double canon_sqdist(const TA* x, const TB* y, int d) {
   }
   return s;
 }
+// FP32 rows: the same operations in the same order, with 16-byte loads when both rows are
+// 16-byte aligned (so the loads run ahead of the sequential FP64 sum).
+CNG_DEV double canon_sqdist(const float* x, const float* y, int d) {
+  double s = 0.0;
+  int i = 0;
+  if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0) {
+#pragma unroll 4
+    for (; i + 4 <= d; i += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(x + i);
+      const float4 b = *reinterpret_cast<const float4*>(y + i);
+      const double t0 = __dsub_rn((double)a.x, (double)b.x), t1 = __dsub_rn((double)a.y, (double)b.y);
+      const double t2 = __dsub_rn((double)a.z, (double)b.z), t3 = __dsub_rn((double)a.w, (double)b.w);
+      s = __dadd_rn(s, __dmul_rn(t0, t0));
+      s = __dadd_rn(s, __dmul_rn(t1, t1));
+      s = __dadd_rn(s, __dmul_rn(t2, t2));
+      s = __dadd_rn(s, __dmul_rn(t3, t3));
+    }
+  }
+  for (; i < d; ++i) {
+    const double t = __dsub_rn((double)x[i], (double)y[i]);
+    s = __dadd_rn(s, __dmul_rn(t, t));
+  }
+  return s;
+}
+
 template <typename TA, typename TB>
 CNG_DEV double canon_dist(const TA* x, const TB* y, int d) {
   return __dsqrt_rn(canon_sqdist(x, y, d));

@@ -438,55 +438,128 @@ CNG_DEV void warp_bitonic(uint64_t* a, int P2, int lane) {
 
 // Re-sort, by the canonical (D, id) order, every run of neighbours in keys[0..cnt) whose FP32
 // squared distances are pairwise near-tied and that starts before position `upto`.  `row` is
-// the stored row vector (exact values).  Returns the number of runs re-decided.
+// the stored row vector (exact values).  Runs are gathered in batches (up to 32 runs, RR_RUN
+// members); the canonical distances of a batch's members are computed in parallel, one per
+// lane, then lane 0 insertion-sorts each run.  rdesc: [3][32] ints of warp scratch (run start,
+// length, offset in d64).  Returns the number of runs re-decided.
 template <typename T>
 CNG_DEV int fix_runs_warp(uint64_t* keys, int cnt, int upto, const T* __restrict__ row,
                           const T* __restrict__ Xc, int dpad, int d, float band, double* d64,
-                          int lane, uint32_t* status) {
+                          int* rdesc, int lane, uint32_t* status) {
   int runs = 0;
   int i = 0;
   while (i < upto && i + 1 < cnt) {
-    // find the next run start >= i (lane-parallel scan, 32 pairs at a time)
-    int s = -1;
-    for (int b = i; b < upto && b + 1 < cnt && s < 0; b += 32) {
-      int t = b + lane;
-      bool nt = t < upto && t + 1 < cnt && near_tie(key_dist(keys[t]), key_dist(keys[t + 1]), band);
-      unsigned bal = __ballot_sync(FULL, nt);
-      if (bal) s = b + __ffs(bal) - 1;
+    int nb = 0, total = 0;
+    while (nb < 32 && i < upto && i + 1 < cnt) {
+      // the next run start >= i (lane-parallel scan, 32 pairs at a time)
+      int s = -1;
+      for (int b = i; b < upto && b + 1 < cnt && s < 0; b += 32) {
+        int t = b + lane;
+        bool nt = t < upto && t + 1 < cnt && near_tie(key_dist(keys[t]), key_dist(keys[t + 1]), band);
+        unsigned bal = __ballot_sync(FULL, nt);
+        if (bal) s = b + __ffs(bal) - 1;
+      }
+      if (s < 0) {
+        i = upto;
+        break;
+      }
+      int e = s + 1;  // run is [s, e]
+      while (e + 1 < cnt && near_tie(key_dist(keys[e]), key_dist(keys[e + 1]), band)) ++e;
+      int len = e - s + 1;
+      if (len > RR_RUN) {
+        if (lane == 0) set_status(status, ST_OVF_RUN);
+        len = RR_RUN;
+        e = s + len - 1;
+      }
+      if (total + len > RR_RUN) break;  // this run opens the next batch
+      if (lane == 0) {
+        rdesc[nb] = s;
+        rdesc[32 + nb] = len;
+        rdesc[64 + nb] = total;
+      }
+      total += len;
+      ++nb;
+      i = e + 1;
     }
-    if (s < 0) break;
-    int e = s + 1;  // run is [s, e]
-    while (e + 1 < cnt && near_tie(key_dist(keys[e]), key_dist(keys[e + 1]), band)) ++e;
-    int len = e - s + 1;
-    if (len > RR_RUN) {
-      if (lane == 0) set_status(status, ST_OVF_RUN);
-      len = RR_RUN;
-      e = s + len - 1;
-    }
-    for (int t = lane; t < len; t += 32) d64[t] = canon_dist(row, Xc + (int64_t)key_id(keys[s + t]) * dpad, d);
+    if (nb == 0) break;
     __syncwarp();
-    if (lane == 0) {  // insertion sort of the run by (d64, id)
-      for (int a = 1; a < len; ++a) {
-        double dv = d64[a];
-        uint64_t kv = keys[s + a];
-        int b = a - 1;
-        while (b >= 0 && (d64[b] > dv || (d64[b] == dv && key_id(keys[s + b]) > key_id(kv)))) {
-          d64[b + 1] = d64[b];
-          keys[s + b + 1] = keys[s + b];
-          --b;
+    for (int m = lane; m < total; m += 32) {
+      int k = 0;
+      while (k + 1 < nb && rdesc[64 + k + 1] <= m) ++k;
+      const int pos = rdesc[k] + (m - rdesc[64 + k]);
+      d64[m] = canon_dist(row, Xc + (int64_t)key_id(keys[pos]) * dpad, d);
+    }
+    __syncwarp();
+    if (lane == 0) {  // insertion sort of each run by (d64, id)
+      for (int k = 0; k < nb; ++k) {
+        const int s = rdesc[k], len = rdesc[32 + k];
+        double* dd = d64 + rdesc[64 + k];
+        for (int a = 1; a < len; ++a) {
+          double dv = dd[a];
+          uint64_t kv = keys[s + a];
+          int b = a - 1;
+          while (b >= 0 && (dd[b] > dv || (dd[b] == dv && key_id(keys[s + b]) > key_id(kv)))) {
+            dd[b + 1] = dd[b];
+            keys[s + b + 1] = keys[s + b];
+            --b;
+          }
+          dd[b + 1] = dv;
+          keys[s + b + 1] = kv;
         }
-        d64[b + 1] = dv;
-        keys[s + b + 1] = kv;
       }
     }
     __syncwarp();
-    ++runs;
-    i = e + 1;
+    runs += nb;
   }
   return runs;
 }
 
-template <typename T>
+// Squared FP32 distances of the query slice held in registers (lane l holds float4 chunks
+// l, l + 32, ..., NQ of them) to two stored rows read by the whole warp (coalesced 16-byte
+// loads), for rows wider than 256: two candidates per call keep 2 NQ loads in flight per lane.
+// Each lane sums its chunks in order with 2 accumulators (chain <= 2 NQ elements), then a
+// 5-level shuffle tree.
+template <int NQ>
+CNG_DEV void wide_sqdist2(const float4 (&qr)[NQ], const float* __restrict__ y0,
+                          const float* __restrict__ y1, int nch, int lane, float& r0, float& r1) {
+  const float4* a4 = reinterpret_cast<const float4*>(y0);
+  const float4* b4 = reinterpret_cast<const float4*>(y1);
+  float4 va[NQ], vb[NQ];
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const int c = lane + 32 * j;
+    va[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    vb[j] = va[j];
+    if (c < nch) {
+      if (y0) va[j] = __ldg(a4 + c);
+      if (y1) vb[j] = __ldg(b4 + c);
+    }
+  }
+  float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const int c = lane + 32 * j;
+    if (c < nch) {
+      if (j & 1) {
+        acc4(qr[j], va[j], s1);
+        acc4(qr[j], vb[j], t1);
+      } else {
+        acc4(qr[j], va[j], s0);
+        acc4(qr[j], vb[j], t0);
+      }
+    }
+  }
+  float a = s0 + s1, b = t0 + t1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(FULL, a, o);
+    b += __shfl_xor_sync(FULL, b, o);
+  }
+  r0 = a;
+  r1 = b;
+}
+
+template <typename T, int NQ>
 __global__ void __launch_bounds__(RR_WARPS * 32)
 rerank_kernel(const T* __restrict__ Xr, const T* __restrict__ Xc, int64_t m, int d, int dpad,
               const int32_t* __restrict__ sids, const uint32_t* __restrict__ sthr, int Lp, int L,
@@ -498,25 +571,48 @@ rerank_kernel(const T* __restrict__ Xr, const T* __restrict__ Xc, int64_t m, int
   const int P2 = Lp <= 64 ? 64 : (Lp <= 128 ? 128 : (Lp <= 256 ? 256 : 512));
   uint64_t* keys = reinterpret_cast<uint64_t*>(smem) + warp * RR_P2;
   double* d64 = reinterpret_cast<double*>(smem + RR_WARPS * RR_P2 * 8) + warp * RR_RUN;
-  float* q = reinterpret_cast<float*>(smem + RR_WARPS * (RR_P2 * 8 + RR_RUN * 8)) + warp * dpad;
+  int* rdesc = reinterpret_cast<int*>(smem + RR_WARPS * (RR_P2 * 8 + RR_RUN * 8)) + warp * 96;
+  float* q = reinterpret_cast<float*>(smem + RR_WARPS * (RR_P2 * 8 + RR_RUN * 8 + 96 * 4)) + warp * dpad;
   const int g = lane % RR_G, grp = lane / RR_G;
   unsigned long long ties = 0;
   float err_max = 0.f;
   for (int64_t row = blockIdx.x * (int64_t)RR_WARPS + warp; row < m;
        row += (int64_t)gridDim.x * RR_WARPS) {
-    load_row(q, Xr + row * dpad, dpad, lane, 32);
-    __syncwarp();
     const int32_t* ids = sids + row * Lp;
     int cnt = 0;
-    for (int t0 = 0; t0 < Lp; t0 += 32 / RR_G) {
-      int t = t0 + grp;
-      int32_t id = t < Lp ? ids[t] : -1;
-      float s = 0.f;
-      if (id >= 0) s = part_sqdist<RR_G>(q, Xc + (int64_t)id * dpad, dpad, g);
-      s = group_reduce<RR_G>(s);
-      if (g == 0 && t < Lp) keys[t] = id >= 0 ? pack_key(s, id) : ~0ull;
-      unsigned v = __ballot_sync(FULL, g == 0 && t < Lp && id >= 0);
-      cnt += __popc(v);
+    if constexpr (NQ > 0) {
+      // wide rows: the query slice in registers, one candidate per warp, two at a time
+      const int nch = dpad >> 2;
+      const float4* x4 = reinterpret_cast<const float4*>(Xr + row * dpad);
+      float4 qr[NQ];
+#pragma unroll
+      for (int j = 0; j < NQ; ++j)
+        qr[j] = lane + 32 * j < nch ? __ldg(x4 + lane + 32 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int t = 0; t < Lp; t += 2) {
+        const int32_t i0 = ids[t], i1 = t + 1 < Lp ? ids[t + 1] : -1;
+        float s0, s1;
+        wide_sqdist2<NQ>(qr, i0 >= 0 ? reinterpret_cast<const float*>(Xc + (int64_t)i0 * dpad) : nullptr,
+                         i1 >= 0 ? reinterpret_cast<const float*>(Xc + (int64_t)i1 * dpad) : nullptr, nch,
+                         lane, s0, s1);
+        if (lane == 0) {
+          keys[t] = i0 >= 0 ? pack_key(s0, i0) : ~0ull;
+          if (t + 1 < Lp) keys[t + 1] = i1 >= 0 ? pack_key(s1, i1) : ~0ull;
+        }
+        cnt += (i0 >= 0) + (t + 1 < Lp && i1 >= 0);
+      }
+    } else {
+      load_row(q, Xr + row * dpad, dpad, lane, 32);
+      __syncwarp();
+      for (int t0 = 0; t0 < Lp; t0 += 32 / RR_G) {
+        int t = t0 + grp;
+        int32_t id = t < Lp ? ids[t] : -1;
+        float s = 0.f;
+        if (id >= 0) s = part_sqdist<RR_G>(q, Xc + (int64_t)id * dpad, dpad, g);
+        s = group_reduce<RR_G>(s);
+        if (g == 0 && t < Lp) keys[t] = id >= 0 ? pack_key(s, id) : ~0ull;
+        unsigned v = __ballot_sync(FULL, g == 0 && t < Lp && id >= 0);
+        cnt += __popc(v);
+      }
     }
     for (int t = Lp + lane; t < P2; t += 32) keys[t] = ~0ull;
     __syncwarp();
@@ -554,7 +650,7 @@ rerank_kernel(const T* __restrict__ Xr, const T* __restrict__ Xc, int64_t m, int
       }
       continue;
     }
-    if (!exact) ties += fix_runs_warp(keys, cnt, L, Xr + row * dpad, Xc, dpad, d, band, d64, lane,
+    if (!exact) ties += fix_runs_warp(keys, cnt, L, Xr + row * dpad, Xc, dpad, d, band, d64, rdesc, lane,
                                       &ctr->status);
     for (int t = lane; t < L; t += 32) {
       uint64_t k = keys[t];
@@ -572,21 +668,30 @@ cudaError_t launch_rerank(const void* xr, const void* xc, int dtype, int64_t m, 
                           const ScreenModel& sm, float band, int exact, int32_t* out_ids,
                           float* out_dist, int32_t* fail_rows, float* fail_bound, Counters* ctr,
                           cudaStream_t s) {
-  size_t sh = RR_WARPS * (RR_P2 * 8 + RR_RUN * 8) + RR_WARPS * dpad * sizeof(float);
+  // rows wider than 256 (FP32 storage, up to 1024): the query slice in registers (wide path)
+  const int nq4 = dtype == CNG_F32 && dpad > 256 ? (dpad / 4 + 31) / 32 : 0;
+  const int NQ = nq4 == 0 ? 0 : (nq4 <= 4 ? 4 : (nq4 <= 8 ? 8 : 0));
+  size_t sh = RR_WARPS * (RR_P2 * 8 + RR_RUN * 8 + 96 * 4) + (NQ ? 0 : RR_WARPS * dpad * sizeof(float));
   int grid = (int)std::min<int64_t>((m + RR_WARPS - 1) / RR_WARPS, (int64_t)num_sms() * 32);
+#define CNG_RR(T, Q)                                                                          \
+  do {                                                                                        \
+    cudaFuncSetAttribute(rerank_kernel<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
+    count_launch();                                                                           \
+    rerank_kernel<T, Q><<<grid, RR_WARPS * 32, sh, s>>>((const T*)xr, (const T*)xc, m, d, dpad, sids, \
+                                                        sthr, Lp, L, sm, band, exact, out_ids, \
+                                                        out_dist, fail_rows, fail_bound, ctr); \
+  } while (0)
   if (dtype == CNG_F32) {
-    cudaFuncSetAttribute(rerank_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    count_launch();
-    rerank_kernel<float><<<grid, RR_WARPS * 32, sh, s>>>((const float*)xr, (const float*)xc, m, d,
-                                                         dpad, sids, sthr, Lp, L, sm, band, exact,
-                                                         out_ids, out_dist, fail_rows, fail_bound, ctr);
+    if (NQ == 8)
+      CNG_RR(float, 8);
+    else if (NQ == 4)
+      CNG_RR(float, 4);
+    else
+      CNG_RR(float, 0);
   } else {
-    cudaFuncSetAttribute(rerank_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    count_launch();
-    rerank_kernel<__half><<<grid, RR_WARPS * 32, sh, s>>>((const __half*)xr, (const __half*)xc, m,
-                                                          d, dpad, sids, sthr, Lp, L, sm, band,
-                                                          exact, out_ids, out_dist, fail_rows, fail_bound, ctr);
+    CNG_RR(__half, 0);
   }
+#undef CNG_RR
   return cudaGetLastError();
 }
 

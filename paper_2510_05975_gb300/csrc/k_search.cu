@@ -203,12 +203,18 @@ search_kernel(SearchArgs a) {
       __syncwarp();
       if (lane == 0) cur.e[idx] = 1;
       ++hops;
+      int ins = 0;          // points of this hop still in Q after it
+      bool chg = false;     // the first min(k, |Q|) ids changed
+      // rows wider than SQ_ROWSLOTS * 32 (a K-NN graph as G0) are taken in slices, each merged
+      // into Q before the next: Q keeps the L smallest of everything inserted, whatever the
+      // grouping, so the hop's result is Alg. 1's
+      for (int rc = 0; rc < a.R; rc += SQ_ROWSLOTS * 32) {
       // fresh neighbours -> Nv[0..nb); rows hold -1 past the degree, so the row alone is read
       int32_t row[SQ_ROWSLOTS];
-      const bool hit = u == pf_u;
+      const bool hit = rc == 0 && u == pf_u;
 #pragma unroll
       for (int r = 0; r < SQ_ROWSLOTS; ++r) {
-        const int j = r * 32 + lane;
+        const int j = rc + r * 32 + lane;
         row[r] = hit ? pf[r] : (j < a.R ? a.adj[(int64_t)u * a.R + j] : -1);
       }
       int nb = 0;
@@ -222,8 +228,6 @@ search_kernel(SearchArgs a) {
       }
       __syncwarp();
       ndc += nb;
-      int ins = 0;          // points of this hop still in Q after it
-      bool chg = false;     // the first min(k, |Q|) ids changed
       do {                  // merge of the hop's new points (skipped when there are none)
       if (nb == 0) break;
       int P2;
@@ -285,7 +289,7 @@ search_kernel(SearchArgs a) {
         }
         uint64_t kn = nidx >= 0 ? cur.k[nidx] : ~0ull;
         if (Nk[0] < kn) kn = Nk[0];
-        pf_u = kn == ~0ull ? -1 : key_id(kn);
+        pf_u = kn == ~0ull || a.R > SQ_ROWSLOTS * 32 ? -1 : key_id(kn);
         if (pf_u >= 0) {
 #pragma unroll
           for (int r = 0; r < SQ_ROWSLOTS; ++r) {
@@ -427,14 +431,15 @@ search_kernel(SearchArgs a) {
           lchg |= pos < ktop;
         }
       }
-      chg = __any_sync(FULL, lchg);
+      chg = chg || __any_sync(FULL, lchg);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) lins += __shfl_xor_sync(FULL, lins, o);
-      ins = lins;
+      ins = lins;  // one slice per hop whenever features are recorded (row stride <= 96)
       __syncwarp();
       QEnt t = cur; cur = nxt; nxt = t;
       len = nlen;
       } while (0);
+      }  // row slices
       // ---- search state after this hop (learned early stop) ----
       if (a.trace_feats || a.model) {
         const int kk = min(a.k, len);
