@@ -343,6 +343,10 @@ def main():
     ap.add_argument("--adaptive", action="store_true",
                     help="with --build-n: adaptive pruning (Alg. 4, alpha0 0.9, dalpha 0.05, "
                          "alpha_max 1.6) instead of the workload's fixed alpha")
+    ap.add_argument("--candidates", default="exact", choices=["exact", "beam"],
+                    help="with --build-n: exact L-NN candidates, or the paper's route (beam search "
+                         "on the exact K-NN graph G0, K = --knn-K, queue L + 1)")
+    ap.add_argument("--knn-K", type=int, default=200)
     ap.add_argument("--search-L", type=int, default=0,
                     help="only build the workload's index and run its queries at this fixed beam "
                          "width with 4 queries per CTA (no autotuning): a warm-up search, then the "
@@ -387,16 +391,22 @@ def main():
         return
     if args.build_n:
         Xs = torch.from_numpy(w.base(args.build_n).astype(np.float32)).cuda()
+        beam = args.candidates == "beam"
         for it in range(2):  # warm-up, then the reported build
             idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
-                                    adaptive=(0.9, 1.6, 0.05) if args.adaptive else None)
+                                    adaptive=(0.9, 1.6, 0.05) if args.adaptive else None,
+                                    candidates=cng.CNG_CAND_BEAM if beam else cng.CNG_CAND_EXACT,
+                                    knn_K=args.knn_K if beam else 0)
             torch.cuda.synchronize()
             cng.cng_free(idx)
-        print(json.dumps({"build_n": args.build_n, "d": w.d, "L": w.L, "R": w.R,
+        print(json.dumps({"build_n": args.build_n, "workload": args.workload, "d": w.d, "L": w.L,
+                          "R": w.R, "candidates": args.candidates,
+                          "knn_K": args.knn_K if beam else None,
                           **{k: st[k] for k in ("ms_total", "ms_order", "ms_screen", "ms_rerank",
-                                                "ms_prune", "ms_merge", "ms_connect", "rule_ties", "cert_fail_rows", "order_ties",
-                                                "alpha_mean",
-                                                "merge_repruned", "n_edges")}}), flush=True)
+                                                "ms_cand_search", "ms_prune", "ms_merge",
+                                                "ms_connect", "rule_ties", "cert_fail_rows",
+                                                "order_ties", "alpha_mean", "merge_repruned",
+                                                "n_edges", "screen_used")}}), flush=True)
         return
     if args.search_L:
         xs = torch.from_numpy(w.base()).cuda()

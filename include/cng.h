@@ -79,6 +79,17 @@ typedef enum {
  *                    unused.  The paper's setting (Sec. 4.4): alpha0 0.9, dalpha 0.05,
  *                    alpha_max 1.6.
  *   alpha0, alpha_max, dalpha   [alpha_0, alpha_max, Delta alpha] of Alg. 4 (adaptive only)
+ *   candidates       CNG_CAND_EXACT (0, default): the exact L nearest points of P \ {p};
+ *                    CNG_CAND_BEAM (1): the paper's route (Alg. 3 phase 2, Sec. 4.1): the L
+ *                    closest points other than p among those visited by a beam search (Alg. 1)
+ *                    for p on a K-NN graph G0 from the navigating node, with queue beam_L
+ *                    (0 = L + 1; L + 1 <= beam_L <= 256, so L <= 255).  Phases 3 and 4 follow
+ *                    as with exact candidates.
+ *   knn_K            [K] degree of G0 (0 = 200); L <= knn_K <= 256 and knn_K < n
+ *   beam_L           queue of the candidate searches (see candidates)
+ *   knn_graph        G0 as device int32 [n][knn_K] (each row's neighbours, -1 padded at its
+ *                    end; the paper builds an approximate K-NN graph), or NULL for the exact
+ *                    knn_K-NN graph computed by the library's candidate screen
  */
 typedef struct {
   double alpha;
@@ -96,7 +107,13 @@ typedef struct {
   double alpha0;
   double alpha_max;
   double dalpha;
+  int32_t candidates;
+  int32_t knn_K;
+  int32_t beam_L;
+  const int32_t *knn_graph;
 } cng_build_params;
+
+enum { CNG_CAND_EXACT = 0, CNG_CAND_BEAM = 1 };
 
 /* Per-phase times (device events, milliseconds) and near-tie / certification counts. */
 typedef struct {
@@ -115,15 +132,18 @@ typedef struct {
   double screen_err_max;      /* largest |screened - rerank| seen on kept candidates */
   double ms_order;            /* locality order of the screen's operands (part of ms_total) */
   double alpha_mean;          /* mean alpha of the phase-2 lists (alpha when not adaptive) */
+  double ms_cand_search;      /* CNG_CAND_BEAM: the candidate searches on G0 (ms_screen and
+                                 ms_rerank then time G0's exact K-NN, when the library builds it) */
 } cng_build_stats;
 
 typedef struct cng_index cng_index;
 
 /*
- * cng_build -- Alg. 3 with exact candidates (Sec. 4.1, 4.3):
+ * cng_build -- Alg. 3 (Sec. 4.1, 4.3):
  *   navigating node s = point nearest the centroid (phase 1);
- *   for each p: the exact L nearest points of P \ {p} by (D, id), then Alg. 2 with the rule
- *   of Def. 2 (Eq. 1) and the out-degree cut at R (phase 2);
+ *   for each p: its L candidates -- the exact L nearest points of P \ {p} by (D, id), or with
+ *   CNG_CAND_BEAM the L closest points visited by a beam search for p on G0 -- then Alg. 2
+ *   with the rule of Def. 2 (Eq. 1) and the out-degree cut at R (phase 2);
  *   reverse edges from the phase-2 snapshot, each node's merged set pruned once if it
  *   exceeds R, else kept in (D, id) order (phase 3, lazy pruning of Sec. 4.3);
  *   connectivity (phase 4): in rounds, every point p not reachable from s is searched for from

@@ -22,6 +22,7 @@ CNG_OK, CNG_E_INVAL, CNG_E_NOMEM, CNG_E_CUDA, CNG_E_TIMEOUT, CNG_E_UNSUPPORTED, 
 CNG_L2, CNG_IP_AS_L2, CNG_IP = 0, 1, 2
 CNG_F32, CNG_F16 = 0, 1
 CNG_SCREEN_FP32, CNG_SCREEN_TC, CNG_SCREEN_TC_BF16 = 0, 1, 2
+CNG_CAND_EXACT, CNG_CAND_BEAM = 0, 1
 CNG_SEARCH_FIXED, CNG_SEARCH_LEARNED = 0, 1
 
 EXPORTS = ("cng_build", "cng_free", "cng_last_error", "cng_graph", "cng_lists", "cng_search",
@@ -44,7 +45,9 @@ class BuildParams(ctypes.Structure):
                 ("keep_lists", ctypes.c_int32), ("connect_L", ctypes.c_int32),
                 ("input_order", ctypes.c_int32), ("adaptive", ctypes.c_int32),
                 ("alpha0", ctypes.c_double), ("alpha_max", ctypes.c_double),
-                ("dalpha", ctypes.c_double)]
+                ("dalpha", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("knn_K", ctypes.c_int32), ("beam_L", ctypes.c_int32),
+                ("knn_graph", ctypes.c_void_p)]
 
 
 class BuildStats(ctypes.Structure):
@@ -57,7 +60,7 @@ class BuildStats(ctypes.Structure):
                [("repair_rounds", ctypes.c_int32), ("screen_used", ctypes.c_int32),
                 ("entry", ctypes.c_int32), ("exact_int", ctypes.c_int32),
                 ("screen_err_max", ctypes.c_double), ("ms_order", ctypes.c_double),
-                ("alpha_mean", ctypes.c_double)]
+                ("alpha_mean", ctypes.c_double), ("ms_cand_search", ctypes.c_double)]
 
 
 class SearchParams(ctypes.Structure):
@@ -220,9 +223,12 @@ class Index:
 def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: int = CNG_L2,
               screen: int = CNG_SCREEN_TC, tie_band: float = 1e-5, margin: int = 32,
               keep_lists: bool = False, connect_L: int = 0, input_order: bool = False,
-              adaptive=None, stream=None):
+              adaptive=None, candidates: int = 0, knn_K: int = 0, beam_L: int = 0,
+              knn_graph: torch.Tensor | None = None, stream=None):
     """cng_build of include/cng.h.  points: CUDA tensor or host (numpy / CPU tensor), float32
-    or float16, shape [n, d].  Returns (Index, stats dict)."""
+    or float16, shape [n, d].  candidates: CNG_CAND_EXACT or CNG_CAND_BEAM (with knn_K,
+    beam_L and optionally knn_graph, a CUDA int32 tensor [n, knn_K]).  Returns (Index, stats
+    dict)."""
     if isinstance(points, torch.Tensor):
         dt = {torch.float32: CNG_F32, torch.float16: CNG_F16}[points.dtype]
         n, d = points.shape
@@ -231,8 +237,14 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
         dt = {np.dtype("float32"): CNG_F32, np.dtype("float16"): CNG_F16}[points.dtype]
         n, d = points.shape
     a0, am, da = adaptive if adaptive is not None else (0.0, 0.0, 0.0)
+    if knn_graph is not None:
+        if knn_graph.dtype != torch.int32 or not knn_graph.is_cuda or knn_graph.shape[0] != n:
+            raise ValueError("knn_graph must be a CUDA int32 tensor [n, knn_K]")
+        knn_K = knn_graph.shape[1]
+        knn_graph = knn_graph.contiguous()
     p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists), connect_L,
-                    int(input_order), int(adaptive is not None), a0, am, da)
+                    int(input_order), int(adaptive is not None), a0, am, da, int(candidates),
+                    int(knn_K), int(beam_L), None if knn_graph is None else knn_graph.data_ptr())
     st = BuildStats()
     h = ctypes.c_void_p()
     _check(lib().cng_build(_ptr(points), dt, n, d, ctypes.byref(p), _stream(stream),
@@ -250,7 +262,8 @@ def cng_tune_tau(points, alpha: float, R: int, L: int, queries, k: int, gt_ids, 
     else:
         dt = {np.dtype("float32"): CNG_F32, np.dtype("float16"): CNG_F16}[points.dtype]
     n, d = points.shape
-    p = BuildParams(alpha, 0.0, R, L, metric, screen, 1e-5, 32, 0, 0, 0, 0, 0.0, 0.0, 0.0)
+    p = BuildParams(alpha, 0.0, R, L, metric, screen, 1e-5, 32, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0, 0, 0,
+                    None)
     gt = np.ascontiguousarray(gt_ids, dtype=np.int32)
     Ls = np.ascontiguousarray(search_Ls, dtype=np.int32)
     best = ctypes.c_double()

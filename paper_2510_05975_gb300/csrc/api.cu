@@ -474,6 +474,17 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
       return fail(CNG_E_INVAL,
                   "adaptive pruning needs 0 < alpha0 <= alpha_max, dalpha > 0 and at most 1001 steps");
   }
+  if (p->candidates != CNG_CAND_EXACT && p->candidates != CNG_CAND_BEAM)
+    return fail(CNG_E_INVAL, "unknown candidates route");
+  if (p->candidates == CNG_CAND_BEAM) {
+    const int K = p->knn_K > 0 ? p->knn_K : 200, Lb = p->beam_L > 0 ? p->beam_L : p->L + 1;
+    if (p->L > 255) return fail(CNG_E_INVAL, "CNG_CAND_BEAM needs L <= 255");
+    if (K < p->L || K > 256 || K >= n) return fail(CNG_E_INVAL, "CNG_CAND_BEAM needs L <= knn_K <= 256 and knn_K < n");
+    if (Lb < p->L + 1 || Lb > 256) return fail(CNG_E_INVAL, "CNG_CAND_BEAM needs L + 1 <= beam_L <= 256");
+    if (p->metric == CNG_IP && p->knn_graph)
+      return fail(CNG_E_INVAL, "CNG_IP builds its own G0 (knn_graph must be NULL)");
+    if (p->knn_graph && !is_device_ptr(p->knn_graph)) return fail(CNG_E_INVAL, "knn_graph must be device memory");
+  }
   return CNG_OK;
 }
 
@@ -599,9 +610,36 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     st = apply_order(pool, &pr, dtype, n, d, dpad, kpad, &ki, &ms_order, s);
     if (st != CNG_OK) return st;
   }
-  double ms_screen = 0, ms_rerank = 0;
-  st = run_knn(ki, cand, cdist, ctr, &ms_screen, &ms_rerank, s);
-  if (st != CNG_OK) return st;
+  double ms_screen = 0, ms_rerank = 0, ms_cand = 0;
+  const bool beam = P.candidates == CNG_CAND_BEAM;
+  const int K0 = P.knn_K > 0 ? P.knn_K : 200;
+  int32_t* g0 = nullptr;  // beam route: G0 [n][K0]
+  if (beam && P.knn_graph) {
+    // the caller's G0 is checked before any search reads it
+    g0 = const_cast<int32_t*>(P.knn_graph);
+    uint32_t* gst;
+    CK(pool.alloc(&gst, 1));
+    CK(cudaMemsetAsync(gst, 0, 4, s));
+    CK(launch_check_knn_graph(g0, n, K0, gst, s));
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, gst, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hst) return fail(CNG_E_INVAL, "knn_graph holds an id outside [0, n), a self edge or -1 before a neighbour");
+  } else if (beam) {  // G0 = the exact K0-NN graph
+    float* g0d;
+    CK(pool.alloc(&g0, (size_t)n * K0));
+    CK(pool.alloc(&g0d, (size_t)n * K0));
+    KnnInputs kg = ki;
+    kg.L = K0;
+    kg.Lp = (int)std::min<int64_t>((int64_t)K0 + P.margin, n - 1);
+    st = run_knn(kg, g0, g0d, ctr, &ms_screen, &ms_rerank, s);
+    if (st != CNG_OK) return st;
+    cudaFree(g0d);
+    pool.release(g0d);
+  } else {
+    st = run_knn(ki, cand, cdist, ctr, &ms_screen, &ms_rerank, s);
+    if (st != CNG_OK) return st;
+  }
   // screening operands are no longer needed
   if (pr.tc) { cudaFree(pr.tc); pool.release(pr.tc); pr.tc = nullptr; }
   // integer data spanning <= 255: 8-bit rows for exact integer pair distances in K4 / K6
@@ -610,6 +648,72 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   if (u8w) {
     CK(pool.alloc(&u8, (size_t)n * u8w * 4));
     CK(launch_to_u8(pr.xs, dtype, n, d, dpad, key_to_float(pr.st.vmin_key), u8w, u8, s));
+  }
+  if (beam) {
+    // Alg. 3 phase 2 (Sec. 4.1): beam search for every point on G0 from the navigating node;
+    // its first L + 1 results hold the L closest visited points other than p
+    const int Lb = P.beam_L > 0 ? P.beam_L : L + 1;
+    Timer tc(s);
+    tc.mark();
+    int32_t h_entry0 = -1;
+    CK(cudaMemcpyAsync(&h_entry0, d_entry, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    int32_t *qid, *deg0, *bid;
+    float* bdist;
+    int* bcounter;
+    unsigned long long* btot;
+    uint32_t* bstatus;
+    CK(pool.alloc(&qid, (size_t)n));
+    CK(pool.alloc(&deg0, (size_t)n));
+    CK(pool.alloc(&bid, (size_t)n * (L + 1)));
+    CK(pool.alloc(&bdist, (size_t)n * (L + 1)));
+    CK(pool.alloc(&bcounter, SEARCH_COUNTER_INTS));
+    CK(pool.alloc(&btot, 4));
+    CK(pool.alloc(&bstatus, 1));
+    CK(cudaMemsetAsync(bstatus, 0, 4, s));
+    CK(launch_iota(qid, n, s));
+    CK(launch_fill(deg0, n, K0, s));  // rows are -1 padded; the search reads the row alone
+    CK(cudaStreamSynchronize(s));
+    SearchArgs sa{};
+    sa.X = pr.xs;
+    sa.dtype = dtype;
+    sa.n = n;
+    sa.d = d;
+    sa.dpad = dpad;
+    sa.adj = g0;
+    sa.deg = deg0;
+    sa.R = K0;
+    sa.entry = h_entry0;
+    sa.qids = qid;
+    sa.nq = n;
+    sa.k = L + 1;
+    sa.L = Lb;
+    sa.band = band;
+    sa.exact = exact;
+    if (u8 && exact) {
+      sa.U = u8;
+      sa.u8w = u8w;
+    }
+    sa.counter = bcounter;
+    sa.ids = bid;
+    sa.dists = bdist;
+    sa.tot = btot;
+    sa.status = bstatus;
+    SearchPlan plan;
+    if (!search_plan(sa, 4, Lb <= 64 ? 1024 : 2048, &plan))
+      return fail(CNG_E_UNSUPPORTED, "candidate search shape does not fit");
+    CK(cudaMemsetAsync(bcounter, 0, SEARCH_COUNTER_INTS * sizeof(int), s));
+    CK(launch_search(sa, plan, s));
+    CK(launch_strip_self(bid, bdist, n, L, cand, cdist, &ctr->status, s));
+    tc.mark();
+    uint32_t sst = 0;
+    CK(cudaMemcpyAsync(&sst, bstatus, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sst) return fail(CNG_E_INTERNAL, "candidate search exceeded n hop vertices");
+    ms_cand = tc.ms(0, 1);
+    cudaFree(bid);
+    pool.release(bid);
+    cudaFree(bdist);
+    pool.release(bdist);
   }
   tm.mark();  // 3
   // phase 2b: prune every candidate list
@@ -815,6 +919,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     stats->alpha_mean = P.adaptive ? P.alpha0 + P.dalpha * (double)hc.alpha_steps / (double)n
                                    : P.alpha;
     stats->ms_order = ms_order;
+    stats->ms_cand_search = ms_cand;
   }
   *out = ix;
   return CNG_OK;

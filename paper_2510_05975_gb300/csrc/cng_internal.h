@@ -125,6 +125,12 @@ cudaError_t launch_pick_add(const int32_t* U, const int32_t* r, int nu, int kc, 
                             int64_t n, int32_t* adj, int32_t* deg, int Rs, int* added_dev,
                             cudaStream_t st);
 cudaError_t launch_fill(int32_t* a, int64_t n, int32_t v, cudaStream_t st);
+
+// k_beam.cu: the paper's candidate route (beam search on a K-NN graph G0)
+cudaError_t launch_iota(int32_t* a, int64_t n, cudaStream_t s);
+cudaError_t launch_strip_self(const int32_t* ids, const float* dists, int64_t n, int C, int32_t* cand,
+                              float* cdist, uint32_t* status, cudaStream_t s);
+cudaError_t launch_check_knn_graph(const int32_t* g, int64_t n, int K, uint32_t* status, cudaStream_t s);
 constexpr int REPAIR_SLOTS = 8;   // adjacency row slots beyond R for phase-4 edges
 constexpr int CONNECT_L = 32;     // default beam width of the phase-4 searches
 

@@ -8,22 +8,17 @@
 //
 // CTA organisation (one CTA per SM, persistent over 256-row blocks):
 //   warp 8      TMA producer: for kpad <= 192 the row block's A tile once, then B tiles of 128
-//               columns through an NST-stage ring (full / empty mbarriers); for wider rows A and
-//               B together in 64-wide K chunks through the same ring; plus each tile's 128
-//               column norms into a 4-slot norm ring
+//               columns with their column norms through an NST-stage ring (full / empty
+//               mbarriers); for wider rows A and B together in 64-wide K chunks through the
+//               same ring, and each tile's 128 column norms into a 4-slot norm ring
 //   warp 9      TMEM owner (512 columns) and MMA issuer: per B tile, two M=128 x N=128
 //               accumulators (rows 0-127 and 128-255), K in steps of 16, into one of two TMEM
 //               buffers; tcgen05.commit frees each operand stage and publishes the buffer
 //   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of accumulator w / 4,
 //               so each thread owns one row; 32 columns per tcgen05.ld; score = fma(-2, acc,
 //               ||y_b||^2); the minimum of 32 scores is compared with the row threshold and
-//               only then are entries appended to one of the row's two append halves; a half
-//               that could overflow on the next tile is handed to the merge helpers and the
-//               row continues in the other half
-//   warps 10-11 merge helpers: each request merges a row's kept region with one append half
-//               (radix select of the L' smallest) and lowers the row's threshold, off the
-//               epilogue's critical path (a compaction took a warp ~8,600 cycles and stalled
-//               the TMEM hand-off for every warp)
+//               only then are entries appended to the row's buffer; full buffers are compacted
+//               by the warp (radix select) which lowers the threshold
 // All CTAs sweep the columns in the same order, so B tiles are shared through L2.
 // Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT, drains its own
 // TMA copies and MMAs (bounded) and frees TMEM before returning.
@@ -45,17 +40,12 @@ constexpr int TC_MAXST = TC_BN == 64 ? 8 : 4;  // operand stages at most
 constexpr int TC_NR = 4;            // column-norm ring slots (tiles whose norms are in flight)
 static_assert((2 * TC_MAXST + 2 * TC_NBUF + 2 * TC_NR + 3) * 8 + 8 <= 256,
               "barrier block exceeds its 256 bytes");
+static_assert(TC_MAXST >= TC_NR, "the column-norm area holds max(stages, ring slots) tiles");
 static_assert(TC_NBUF == 2 || TC_NBUF == 4, "two or four accumulator buffers");
 constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
-constexpr int TC_THREADS = 384;     // 8 epilogue warps + producer + MMA + 2 merge helpers
+constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
 constexpr int TC_PRODUCER = 8;
 constexpr int TC_MMA = 9;
-constexpr int TC_HELP0 = 10;        // warps 10 and 11 merge row buffers for the epilogue
-constexpr int TC_HALF = 256;        // each of a row buffer's two append halves
-constexpr int TC_RQ = TC_BM;        // merge request ring (one request per row in flight at most)
-// idle polls of a merge helper before it declares a timeout (each poll sleeps ~64 ns); larger
-// than any run of the kernel without a merge request
-constexpr uint32_t TC_HELP_SPIN = 1u << 30;
 // wait iterations before declaring a timeout (each try_wait may suspend the thread for a
 // system-dependent time; no suspend-time hint, so a completed phase is seen at once)
 constexpr uint32_t TC_SPIN = 1u << 19;
@@ -235,20 +225,17 @@ CNG_DEV void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-// Warp-cooperative merge of a row's kept entries K[0, kc) with an append half A[0, ca)
-// (kc + ca > Lp): keeps the Lp smallest keys in K[0, Lp) and returns the largest kept key.
-// Both segments are read into registers first; radix select on 8-bit digits with a 256-bin
-// shared histogram per warp (4 passes), then a stable compaction of the kept entries.
+// Warp-cooperative selection (same contract as warp_compact): keeps the Lp smallest of the
+// cnt buffered keys, moves them to the front and returns the largest kept key.  Radix select
+// on 8-bit digits with a 256-bin shared histogram per warp (4 passes).
 template <int CAP_PER_LANE>
-CNG_DEV uint32_t warp_merge_select(uint64_t* K, int kc, const uint64_t* A, int ca, int Lp, int lane,
-                                   uint32_t* hist) {
-  const int cnt = kc + ca;
+CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uint32_t* hist) {
   uint32_t k[CAP_PER_LANE];
   uint64_t e[CAP_PER_LANE];
 #pragma unroll
   for (int i = 0; i < CAP_PER_LANE; ++i) {
-    const int idx = i * 32 + lane;
-    e[i] = idx < kc ? K[idx] : (idx < cnt ? A[idx - kc] : ~0ull);
+    int idx = i * 32 + lane;
+    e[i] = idx < cnt ? buf[idx] : ~0ull;
     k[i] = (uint32_t)(e[i] >> 32);
   }
   __syncwarp();
@@ -275,7 +262,7 @@ CNG_DEV uint32_t warp_merge_select(uint64_t* K, int kc, const uint64_t* A, int c
       h[i] = hist[lane * 8 + i];
       tot += h[i];
     }
-    uint32_t inc = tot;
+    uint32_t inc = tot;  // inclusive scan of lane totals
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(FULL, inc, o);
@@ -300,7 +287,7 @@ CNG_DEV uint32_t warp_merge_select(uint64_t* K, int kc, const uint64_t* A, int c
     prefix |= (uint32_t)digit << shift;
     __syncwarp();
   }
-  const uint32_t kth = prefix;
+  const uint32_t kth = prefix;  // `need` entries equal to kth are kept
   int out = 0, eq_taken = 0;
 #pragma unroll
   for (int i = 0; i < CAP_PER_LANE; ++i) {
@@ -312,7 +299,7 @@ CNG_DEV uint32_t warp_merge_select(uint64_t* K, int kc, const uint64_t* A, int c
     bool keep = lt || (eq && eq_rank < need);
     eq_taken += __popc(beq);
     unsigned bk = __ballot_sync(FULL, keep);
-    if (keep) K[out + __popc(bk & ((1u << lane) - 1))] = e[i];
+    if (keep) buf[out + __popc(bk & ((1u << lane) - 1))] = e[i];
     out += __popc(bk);
   }
   __syncwarp();
@@ -353,7 +340,7 @@ CNG_DEV float fu(uint32_t x) { return __uint_as_float(x); }
 template <bool DUMP>
 CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_t row,
                            const TcParams& P, uint32_t nbs, float thr, int& cnt,
-                           uint64_t* rbuf, int cap, float* dump) {
+                           uint64_t* rbuf, float* dump) {
   float4 y[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) y[q] = lds_f4(nbs + 16 * q);
@@ -391,7 +378,7 @@ CNG_DEV void process_chunk(uint32_t* r, int64_t cb, bool edge, bool live, int64_
           for (int k = 0; k < 4; ++k) {
             const float vj = fu(r[4 * g + k]);
             if (wg && vj < thr) {
-              if (cnt < cap)
+              if (cnt < P.cap)
                 rbuf[cnt] = ((uint64_t)fkey(vj) << 32) | (uint32_t)(cb + 4 * g + k);
               else
                 atomicOr(P.status, ST_OVERFLOW);
@@ -422,8 +409,9 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   const int stage_bytes = KSTREAM ? (TC_BM + TC_BN) * TC_KC * 2 : TC_BN * P.kpad * 2;
   unsigned char* sA = smem;
   unsigned char* sB = smem + a_bytes;
-  float* sNB = reinterpret_cast<float*>(sB + P.nst * stage_bytes);  // [TC_NR][TC_BN] column norms
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sNB + TC_NR * TC_BN);
+  // column norms: per operand stage with a resident A tile, else a TC_NR-slot ring
+  float* sNB = reinterpret_cast<float*>(sB + P.nst * stage_bytes);  // [max(nst, TC_NR)][TC_BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sNB + TC_MAXST * TC_BN);
   uint64_t* b_full = bars;               // [nst]
   uint64_t* b_empty = bars + P.nst;      // [nst]
   uint64_t* t_full = bars + 2 * P.nst;   // [TC_NBUF]
@@ -435,14 +423,7 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   uint64_t* fin = a_empty + 1;           // [1] MMA drain at exit
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  uint32_t* hist_all = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);  // [12][256]
-  // merge state of the block's rows (TC_BM each) and the request ring
-  uint32_t* s_thrk = hist_all + 12 * 256;  // threshold key lowered by the helpers' merges
-  uint32_t* s_kcnt = s_thrk + TC_BM;       // entries in the kept region
-  uint32_t* s_busy = s_kcnt + TC_BM;       // 1 while a merge of the row is requested / running
-  uint32_t* q_ent = s_busy + TC_BM;        // request: row << 16 | half << 15 | count
-  uint32_t* q_seq = q_ent + TC_RQ;         // slot + 1 once the request is written
-  uint32_t* q_ctl = q_seq + TC_RQ;         // [0] head, [1] tail, [2] epilogue warps finished
+  uint32_t* hist_all = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);  // [8][256]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nrb = (P.m + TC_BM - 1) / TC_BM;
@@ -451,7 +432,9 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   if (tid == 0) {
     for (int i = 0; i < P.nst; ++i) {
       mbar_init(&b_full[i], 1);
-      mbar_init(&b_empty[i], 1);  // the MMA's commit
+      // the MMA's commit; with a resident A tile each stage also carries its tile's column
+      // norms, which the 8 epilogue warps release
+      mbar_init(&b_empty[i], KSTREAM ? 1 : 1 + 8);
     }
     for (int i = 0; i < TC_NBUF; ++i) {
       mbar_init(&t_full[i], 1);
@@ -465,7 +448,6 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     mbar_init(a_empty, 1);
     mbar_init(fin, 1);
     *abort_flag = 0;
-    q_ctl[0] = q_ctl[1] = q_ctl[2] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == TC_MMA) {
@@ -474,7 +456,6 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int i = tid; i < TC_RQ; i += TC_THREADS) q_seq[i] = 0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -503,27 +484,29 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         for (int ti = 0; ti < ntiles; ++ti, ++it) {
           const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
           wave_checkpoint(P, it, nrb, ntiles);
-          // the tile's column norms into the norm ring
-          ok = mbar_wait(&n_empty[ns], nph ^ 1, abort_flag, P.status);
-          if (!ok) break;
-          mbar_expect_tx(&n_full[ns], TC_BN * 4);
-          bulk_load(sNB + ns * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &n_full[ns]);
-          if (++ns == TC_NR) {
-            ns = 0;
-            nph ^= 1u;
-          }
           if (!KSTREAM) {
+            // the B tile and its column norms into one stage
             ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
             if (!ok) break;
-            mbar_expect_tx(&b_full[s], (uint32_t)stage_bytes);
+            mbar_expect_tx(&b_full[s], (uint32_t)(stage_bytes + TC_BN * 4));
             unsigned char* dst = sB + s * stage_bytes;
             for (int kc = 0; kc < P.nkc; ++kc)
               tma_load_2d(dst + kc * (TC_BN * 128), &mapB, kc * TC_KC, t * TC_BN, &b_full[s]);
+            bulk_load(sNB + s * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &b_full[s]);
             if (++s == P.nst) {
               s = 0;
               ph ^= 1u;
             }
           } else {
+            // the tile's column norms into the norm ring, then A and B in K chunks
+            ok = mbar_wait(&n_empty[ns], nph ^ 1, abort_flag, P.status);
+            if (!ok) break;
+            mbar_expect_tx(&n_full[ns], TC_BN * 4);
+            bulk_load(sNB + ns * TC_BN, P.nb + (int64_t)t * TC_BN, TC_BN * 4, &n_full[ns]);
+            if (++ns == TC_NR) {
+              ns = 0;
+              nph ^= 1u;
+            }
             for (int kc = 0; kc < P.nkc && ok; ++kc) {
               ok = mbar_wait(&b_empty[s], ph ^ 1, abort_flag, P.status);
               if (!ok) break;
@@ -627,104 +610,21 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       for (uint32_t i = 0; i < (1u << 24); ++i)
         if (mbar_try(fin, 0)) break;
     }
-  } else if (warp >= TC_HELP0) {
-    // ---- merge helpers: warps 10-11 ----
-    // A request hands over one append half of a row: the helper keeps the Lp smallest of the
-    // row's kept region and that half in the kept region, and lowers the row's threshold to
-    // the largest kept key.  The epilogue appends to the row's other half meanwhile.
-    uint32_t* hist = hist_all + warp * 256;
-    uint32_t idle = 0;
-    for (;;) {
-      int slot = -1;
-      if (lane == 0) {
-        const uint32_t h = *reinterpret_cast<volatile uint32_t*>(&q_ctl[0]);
-        const uint32_t tl = *reinterpret_cast<volatile uint32_t*>(&q_ctl[1]);
-        if (h != tl && atomicCAS(&q_ctl[0], h, h + 1u) == h) slot = (int)(h & 0x7fffffffu);
-      }
-      slot = __shfl_sync(FULL, slot, 0);
-      if (slot < 0) {
-        int stop = 0;
-        if (lane == 0)
-          stop = (*reinterpret_cast<volatile uint32_t*>(&q_ctl[2]) == 8u &&
-                  *reinterpret_cast<volatile uint32_t*>(&q_ctl[0]) ==
-                      *reinterpret_cast<volatile uint32_t*>(&q_ctl[1])) ||
-                 *abort_flag;
-        if (__shfl_sync(FULL, stop, 0)) break;
-        if (++idle > TC_HELP_SPIN) {
-          if (lane == 0) {
-            *abort_flag = 1;
-            atomicOr(P.status, ST_TIMEOUT);
-          }
-          break;
-        }
-        __nanosleep(64);
-        continue;
-      }
-      idle = 0;
-      const uint32_t si = (uint32_t)slot % TC_RQ;
-      bool ready = false;
-      for (uint32_t i = 0; i < TC_SPIN && !ready; ++i)
-        ready = *reinterpret_cast<volatile uint32_t*>(&q_seq[si]) == (uint32_t)slot + 1u;
-      if (!__all_sync(FULL, ready)) {
-        if (lane == 0) {
-          *abort_flag = 1;
-          atomicOr(P.status, ST_TIMEOUT);
-        }
-        break;
-      }
-      __threadfence_block();
-      const uint32_t ent = *reinterpret_cast<volatile uint32_t*>(&q_ent[si]);
-      const int rl = (int)(ent >> 16), half = (int)((ent >> 15) & 1u), ca = (int)(ent & 0x7fffu);
-      uint64_t* K = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rl) * P.cap;
-      const uint64_t* A = K + P.Lp + half * TC_HALF;
-      const int kc = (int)s_kcnt[rl];
-      if (kc + ca <= P.Lp) {
-        for (int i = lane; i < ca; i += 32) K[kc + i] = A[i];
-        if (lane == 0) s_kcnt[rl] = (uint32_t)(kc + ca);
-      } else {
-        const uint32_t k = warp_merge_select<CPL>(K, kc, A, ca, P.Lp, lane, hist);
-        if (lane == 0) {
-          s_kcnt[rl] = (uint32_t)P.Lp;
-          atomicMin(&s_thrk[rl], k);
-        }
-      }
-      __threadfence_block();
-      __syncwarp();
-      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&s_busy[rl]) = 0u;
-    }
   } else {
     // ---- epilogue: warps 0-7, one row per thread ----
     const int quarter = warp & 3, accsel = warp >> 2;
     const int rloc = accsel * 128 + quarter * 32 + lane;  // row within the block
-    uint64_t* kbuf = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rloc) * P.cap;  // kept region
+    uint64_t* rbuf = P.rowbuf + ((size_t)blockIdx.x * TC_BM + rloc) * P.cap;
     uint32_t* hist = hist_all + warp * 256;
-    volatile uint32_t* busy = reinterpret_cast<volatile uint32_t*>(&s_busy[rloc]);
     int64_t tt = 0;
-    int ns = 0;        // norm ring slot of tile tt (advanced without dividing)
+    int ns = 0;        // norm slot (stage, or ring slot) of tile tt, advanced without dividing
     uint32_t nph = 0;  // its phase
     bool ok = true;
-    // bounded wait until no merge of this lane's row is requested or running
-    auto wait_idle = [&]() -> bool {
-      bool idle_row = false;
-      for (uint32_t i = 0; i < TC_SPIN && !idle_row; ++i) {
-        idle_row = *busy == 0u;
-        if (!idle_row) __nanosleep(32);
-      }
-      if (!idle_row) {
-        *abort_flag = 1;
-        atomicOr(P.status, ST_TIMEOUT);
-      }
-      return __all_sync(FULL, idle_row);
-    };
     for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
       const int64_t row = rb * TC_BM + rloc;
       const bool live = row < P.m;
-      // the previous block left no request of this row pending
-      s_thrk[rloc] = 0xff800000u;  // fkey(+inf)
-      s_kcnt[rloc] = 0u;
-      *busy = 0u;
       float thr = __int_as_float(0x7f800000);
-      int cnt = 0, act = 0;
+      int cnt = 0;
       const int t0 = sweep_start(P, rb, ntiles);
       for (int ti = 0; ti < ntiles; ++ti, ++tt) {
         const int t = ti + t0 < ntiles ? ti + t0 : ti + t0 - ntiles;
@@ -732,12 +632,11 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         ok = mbar_wait_warp(&t_full[b], (uint32_t)((tt >> TC_NBUF_LOG) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
-        // the tile's column norms: the producer's copy into the ring slot is complete
-        ok = mbar_wait_warp(&n_full[ns], nph, abort_flag, P.status);
+        // the tile's column norms: the producer's copy (with the B stage, or into the ring
+        // slot) is complete; the stage cannot be refilled before this warp releases it
+        ok = KSTREAM ? mbar_wait_warp(&n_full[ns], nph, abort_flag, P.status)
+                     : mbar_wait_warp(&b_full[ns], nph, abort_flag, P.status);
         if (!ok) break;
-        // thresholds lowered by the helpers' merges
-        if (!DUMP) thr = fminf(thr, fkey_inv(*reinterpret_cast<volatile uint32_t*>(&s_thrk[rloc])));
-        uint64_t* abuf = kbuf + P.Lp + act * TC_HALF;
         const int64_t c0 = (int64_t)t * TC_BN;
         const bool edge = (c0 + TC_BN > P.n) || (P.self_excl && row >= c0 && row < c0 + TC_BN);
         const uint32_t ta =
@@ -753,78 +652,60 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             if (lane == 0) mbar_arrive(&t_empty[b]);
           }
           process_chunk<DUMP>(r, c0 + ch * 32, edge, live, row, P,
-                              smem_u32(sNB + ns * TC_BN + ch * 32), thr, cnt, abuf, TC_HALF, dump);
+                              smem_u32(sNB + ns * TC_BN + ch * 32), thr, cnt, rbuf, dump);
         }
-        // the norms of this slot are no longer needed: release it to the producer
+        // the norms of this slot (stage) are no longer needed: release it to the producer
         __syncwarp();
-        if (lane == 0) mbar_arrive(&n_empty[ns]);
-        if (++ns == TC_NR) {
+        if (lane == 0) mbar_arrive(KSTREAM ? &n_empty[ns] : &b_empty[ns]);
+        if (++ns == (KSTREAM ? TC_NR : P.nst)) {
           ns = 0;
           nph ^= 1u;
         }
         if (DUMP) continue;
-        // a half that could overflow on the next tile goes to the helpers; the row continues
-        // in its other half (whose previous merge must have finished)
-        const bool hand = cnt > TC_HALF - TC_BN;
-        if (__any_sync(FULL, hand)) {
-          ok = wait_idle();
-          if (!ok) break;
-          if (hand) {
-            *busy = 1u;
-            const uint32_t slot = atomicAdd(&q_ctl[1], 1u);
-            q_ent[slot % TC_RQ] = ((uint32_t)rloc << 16) | ((uint32_t)act << 15) | (uint32_t)cnt;
-            __threadfence_block();
-            *reinterpret_cast<volatile uint32_t*>(&q_seq[slot % TC_RQ]) = slot + 1u;
-            act ^= 1;
-            cnt = 0;
-          }
+        // compact every row whose buffer could overflow on the next tile
+        unsigned needc = __ballot_sync(FULL, cnt > P.cap - TC_BN);
+        while (needc) {
+          const int l = __ffs(needc) - 1;
+          needc &= needc - 1;
+          const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
+          uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
           __syncwarp();
+          const uint32_t k = warp_compact_hist<CPL>(buf_l, c_l, P.Lp, lane, hist);
+          if (lane == l) {
+            thr = fkey_inv(k);
+            cnt = P.Lp;
+          }
         }
       }
       if (!ok || DUMP) continue;
-      // final: wait for the row's merge, then keep Lp of the kept region and the active half
-      ok = wait_idle();
-      if (!ok) break;
-      __threadfence_block();
-      int kc = (int)s_kcnt[rloc];
-      uint32_t thk = s_thrk[rloc];
-      if (thk == 0xff800000u) thk = 0xffffffffu;  // no selection yet: everything was kept
-      unsigned needf = __ballot_sync(FULL, cnt > 0);
+      // final: keep Lp per row, write ids and the threshold key
+      uint32_t thk = fkey(thr);
+      if (isinf(thr) && thr > 0.f) thk = 0xffffffffu;
+      unsigned needf = __ballot_sync(FULL, cnt > P.Lp);
       while (needf) {
         const int l = __ffs(needf) - 1;
         needf &= needf - 1;
-        const int kc_l = __shfl_sync(FULL, kc, l), ca_l = min(__shfl_sync(FULL, cnt, l), TC_HALF);
-        uint64_t* K = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(kbuf), l));
-        const uint64_t* A = K + P.Lp + __shfl_sync(FULL, act, l) * TC_HALF;
+        const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
+        uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
         __syncwarp();
-        if (kc_l + ca_l <= P.Lp) {
-          for (int i = lane; i < ca_l; i += 32) K[kc_l + i] = A[i];
-          if (lane == l) kc = kc_l + ca_l;
-        } else {
-          const uint32_t k = warp_merge_select<CPL>(K, kc_l, A, ca_l, P.Lp, lane, hist);
-          if (lane == l) {
-            thk = k;
-            kc = P.Lp;
-          }
+        const uint32_t k = warp_compact_hist<CPL>(buf_l, c_l, P.Lp, lane, hist);
+        if (lane == l) {
+          thk = k;
+          cnt = P.Lp;
         }
-        __syncwarp();
       }
       __syncwarp();
       if (live) {
-        const int c = min(kc, P.Lp);
+        const int c = min(cnt, P.Lp);
         const int64_t orow = P.perm ? P.perm[row] : row;
         for (int t = 0; t < P.Lp; ++t) {
           int32_t id = -1;
-          if (t < c) id = P.perm ? P.perm[key_id(kbuf[t])] : key_id(kbuf[t]);
+          if (t < c) id = P.perm ? P.perm[key_id(rbuf[t])] : key_id(rbuf[t]);
           P.ids[orow * P.Lp + t] = id;
         }
         P.thr[orow] = thk;
       }
-      __syncwarp();
     }
-    // let the helpers finish once the queue is empty
-    __syncwarp();
-    if (lane == 0) atomicAdd(&q_ctl[2], 1u);
   }
   tc_fence_before();
   __syncthreads();
@@ -970,8 +851,7 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   p.nkc = kpad / 64;
   const int a_bytes = kstream ? 0 : TC_BM * kpad * 2;
   const int stage_bytes = kstream ? (TC_BM + TC_BN) * TC_KC * 2 : TC_BN * kpad * 2;
-  // alignment, norms, barriers, 12 histograms, merge state and request ring
-  const int fixed = 1024 + TC_NR * TC_BN * 4 + 256 + 12 * 256 * 4 + (3 * TC_BM + 2 * TC_RQ + 4) * 4;
+  const int fixed = 1024 + TC_MAXST * TC_BN * 4 + 256 + 8 * 256 * 4;  // alignment, norms, barriers, hist
   const int budget = 220 * 1024 - a_bytes - fixed;
   p.nst = std::min(TC_MAXST, budget / stage_bytes);
   if (p.nst < 2) {
@@ -980,13 +860,13 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   }
   p.Lp = a.Lp;
   int cpl = 0;
-  for (int c : {12, 16, 20, 24})  // a merge holds the kept region and one append half
-    if (c * 32 >= a.Lp + TC_HALF) { cpl = c; break; }
+  for (int c : {12, 16, 20, 24})
+    if (c * 32 >= a.Lp + TC_BN + 32) { cpl = c; break; }
   if (!cpl) {
     if (msg) *msg = "screened list too long; ";
     return cudaErrorInvalidValue;
   }
-  p.cap = a.Lp + 2 * TC_HALF;  // row buffer: kept region + two append halves
+  p.cap = cpl * 32;
   p.self_excl = a.self_excl;
   p.idesc = make_idesc(a.fp16);
   p.nb = a.nb;
@@ -1039,9 +919,10 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
 }
 
 size_t screen_tc_rowbuf_words(int64_t m, int64_t n, int Lp) {
+  const int cpl = 24;  // the largest capacity launch_impl may choose
   const int64_t nrb = (m + TC_BM - 1) / TC_BM;
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
-  return (size_t)grid * TC_BM * (Lp + 2 * TC_HALF) + sync_counter_words(m, n, grid);
+  return (size_t)grid * TC_BM * cpl * 32 + sync_counter_words(m, n, grid);
 }
 
 cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg) {

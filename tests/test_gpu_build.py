@@ -3,6 +3,7 @@ against the FP64 oracle: candidate lists, phase-2 lists and the final graph must
 element by element (every FP32 near-tie is re-decided in FP64 on the GPU)."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2510_05975_gb300 import synth
@@ -201,3 +202,61 @@ def test_tau_grid_search_matches_oracle():
     key = lambda ts: [(t["tau"], t["L"], t["recall"], t["hops_mean"]) for t in ts]
     assert key(trials) == key(otrials)
     assert best == obest
+
+
+@pytest.mark.parametrize("kind,n,d,R,C,K,Lb,screen", [
+    ("gauss", 3000, 32, 16, 48, 64, 49, 1),
+    ("sift", 3001, 128, 32, 96, 128, 128, 1),   # integer data: the 8-bit exact search path
+    ("gauss", 4000, 24, 16, 100, 200, 160, 0),  # G0 rows wider than 96 entries (read in slices)
+    ("deep", 2500, 96, 24, 80, 96, 81, 1),
+])
+def test_beam_candidates_match_oracle(kind, n, d, R, C, K, Lb, screen):
+    """The paper's candidate route (Alg. 3 phase 2, Sec. 4.1): candidates are the C closest
+    points visited by a beam search for p on the exact K-NN graph G0; candidate lists, phase-2
+    lists and the final graph equal the oracle's."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate(kind, n, d, seed=11)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=R, L=C, screen=screen, keep_lists=True,
+                            candidates=cng.CNG_CAND_BEAM, knn_K=K, beam_L=Lb)
+    G = oracle.build_graph_beam(X, 1.2, 0.0, R, C, K, Lb)
+    cand, _, fwd, fdeg = cng.cng_lists(idx)
+    adj, deg, _, entry = cng.cng_graph(idx)
+    assert entry == G.entry
+    bad = np.flatnonzero((host(cand) != G.cand).any(axis=1))
+    assert bad.size == 0, f"candidate lists differ at rows {bad[:10]}"
+    assert np.array_equal(host(fdeg), G.fdeg) and np.array_equal(host(fwd), G.fwd)
+    assert np.array_equal(host(deg), G.deg) and np.array_equal(host(adj), G.adj)
+    assert st["ms_cand_search"] > 0
+    cng.cng_free(idx)
+
+
+def test_beam_candidates_on_a_given_approximate_graph():
+    """G0 supplied by the caller (the paper builds an approximate K-NN graph): the exact 48-NN
+    lists with their last 16 entries replaced by random other points; the build equals the
+    oracle's route on the same G0.  A G0 with a self edge is rejected before any search."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate("gauss", 2500, 16, seed=12)
+    n, K = len(X), 48
+    G0, _ = oracle.knn(X, K)
+    rng = np.random.default_rng(3)
+    for p in range(n):
+        keep = set(G0[p, :32].tolist()) | {p}
+        extra = [v for v in rng.permutation(n)[:64].tolist() if v not in keep][:16]
+        G0[p, 32:] = extra
+    idx, _ = cng.cng_build(tensor(X), alpha=1.2, R=16, L=40, keep_lists=True,
+                           candidates=cng.CNG_CAND_BEAM, beam_L=41,
+                           knn_graph=torch.from_numpy(G0).cuda())
+    G = oracle.build_graph_beam(X, 1.2, 0.0, 16, 40, K, 41, knn_graph=G0)
+    cand, _, fwd, _ = cng.cng_lists(idx)
+    adj, deg, _, _ = cng.cng_graph(idx)
+    assert np.array_equal(host(cand), G.cand) and np.array_equal(host(fwd), G.fwd)
+    assert np.array_equal(host(adj), G.adj) and np.array_equal(host(deg), G.deg)
+    cng.cng_free(idx)
+    bad = G0.copy()
+    bad[7, 3] = 7
+    with pytest.raises(cng.CngError) as e:
+        cng.cng_build(tensor(X), alpha=1.2, R=16, L=40, candidates=cng.CNG_CAND_BEAM,
+                      knn_graph=torch.from_numpy(bad).cuda())
+    assert e.value.code == cng.CNG_E_INVAL
