@@ -147,7 +147,7 @@ typedef struct cng_index cng_index;
  *   reverse edges from the phase-2 snapshot, each node's merged set pruned once if it
  *   exceeds R, else kept in (D, id) order (phase 3, lazy pruning of Sec. 4.3);
  *   connectivity (phase 4): in rounds, every point p not reachable from s is searched for from
- *   s (Alg. 1, beam connect_L, k = min(8, connect_L)); its first result r whose row has a free
+ *   s (Alg. 1, beam connect_L, all connect_L results); its first result r whose row has a free
  *   slot names p, and each named r gets an edge to the smallest point naming it.  Rows hold up
  *   to R pruned edges plus up to 8 such edges.
  * points: host or device, n x d of `dtype`, borrowed for the call only (the index keeps its own

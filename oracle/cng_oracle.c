@@ -642,7 +642,7 @@ int or_build_beam(const float *X, int64_t n, int d, double alpha, double tau, in
  * The paper adds "necessary edges" from the DFS tree of s to every point outside it, in line
  * with NSG, without fixing which.  Our reading, in rounds until every point is reachable:
  *   reached = points reachable from s;
- *   for every unreached p: beam-search(G, x_p, s, Lc, kc) on the current graph, kc = min(8, Lc);
+ *   for every unreached p: beam-search(G, x_p, s, Lc, Lc) on the current graph (all Lc results);
  *     r(p) = the first of its results (nearest first; all reached points) whose row has a free
  *     slot (deg < Rs, degrees as at the start of the round); none: p waits for a later round;
  *   every reached r named by some r(p) gets the edge r -> (smallest such p).
@@ -679,7 +679,7 @@ int or_connect(const float *X, int64_t n, int d, int32_t *adj, int32_t *deg, int
             if (!reach[i]) U[nu++] = (int32_t)i;
         if (nu == 0) break;
         ++rounds;
-        const int kc = Lc < 8 ? Lc : 8;
+        const int kc = Lc;
         float *Qm = (float *)malloc(sizeof(float) * nu * d);
         int32_t *rid = (int32_t *)malloc(sizeof(int32_t) * nu * kc);
         double *rd = (double *)malloc(sizeof(double) * nu * kc);

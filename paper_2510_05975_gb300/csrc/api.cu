@@ -778,7 +778,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     CK(pool.alloc(&fa, (size_t)n));
     CK(pool.alloc(&fb, (size_t)n));
     CK(pool.alloc(&U, (size_t)n));
-    const int kc = std::min(8, Lc);
+    const int kc = Lc;  // every result of the search can name p
     CK(pool.alloc(&rid, (size_t)n * kc));
     CK(pool.alloc(&rdist, (size_t)n * kc));
     CK(pool.alloc(&best, (size_t)n));
@@ -835,7 +835,9 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
       CK(cudaMemcpyAsync(&hc_counts[3], counts + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (hc_counts[3] == 0)
-        return fail(CNG_E_UNSUPPORTED, "phase 4 could not connect the graph (connectivity slots full)");
+        return fail(CNG_E_UNSUPPORTED, "phase 4 could not connect the graph (connectivity slots full; round " +
+                                            std::to_string(round) + ", " + std::to_string(nu) +
+                                            " points unreachable)");
       repair_edges += hc_counts[3];
     }
     uint32_t sst = 0;
