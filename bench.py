@@ -122,7 +122,8 @@ def bench_config(w, args, ws: int) -> dict:
     ops = {"tc": "fp16 (power-of-two scaled, FP32 accumulate)", "tc-bf16": "bf16 (FP32 accumulate)",
            "fp32": "fp32 (CUDA cores)"}[args.screen]
     return {"workload": args.workload, "n": w.n, "d": w.d, "dtype": w.dtype, "alpha": w.alpha,
-            "tau": 0.0, "R": w.R, "L": w.L, "nq": w.nq, "k": w.k, "screen": args.screen,
+            "tau": 0.0, "R": w.R, "L": w.L, "repair_slots": w.repair_slots, "nq": w.nq, "k": w.k,
+            "screen": args.screen,
             "screen_operands": ops, "parallelism": "replicas" if ws > 1 else "single",
             "l2": f"inputs larger than L2 ({w.n * w.d * (2 if w.dtype == 'float16' else 4) >> 20} MB points)"}
 
@@ -134,7 +135,8 @@ def gpu_lists(w, X):
 
     import paper_2510_05975_gb300.cng as cng
 
-    idx, st = cng.cng_build(torch.from_numpy(X).cuda(), alpha=w.alpha, R=w.R, L=w.L, keep_lists=True)
+    idx, st = cng.cng_build(torch.from_numpy(X).cuda(), alpha=w.alpha, R=w.R, L=w.L, keep_lists=True,
+                            repair_slots=w.repair_slots)
     _, _, fwd, fdeg = cng.cng_lists(idx)
     adj, deg, _, entry = cng.cng_graph(idx)
     out = dict(fwd=fwd.cpu().numpy(), fdeg=fdeg.cpu().numpy(), adj=adj.cpu().numpy(),
@@ -396,7 +398,7 @@ def main():
             idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
                                     adaptive=(0.9, 1.6, 0.05) if args.adaptive else None,
                                     candidates=cng.CNG_CAND_BEAM if beam else cng.CNG_CAND_EXACT,
-                                    knn_K=args.knn_K if beam else 0)
+                                    knn_K=args.knn_K if beam else 0, repair_slots=w.repair_slots)
             torch.cuda.synchronize()
             cng.cng_free(idx)
         print(json.dumps({"build_n": args.build_n, "workload": args.workload, "d": w.d, "L": w.L,
@@ -411,7 +413,8 @@ def main():
     if args.search_L:
         xs = torch.from_numpy(w.base()).cuda()
         qs = torch.from_numpy(w.queries().astype(np.float32)).cuda()
-        idx, _ = cng.cng_build(xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+        idx, _ = cng.cng_build(xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
+                               repair_slots=w.repair_slots)
         for it in range(2):
             r = cng.cng_search(idx, qs, k=w.k, L=args.search_L, warps_per_block=4,
                                with_stats=True)
@@ -445,7 +448,8 @@ def main():
     base32 = xd.float() if dtype_t == torch.float16 else xd
     gt = cng.cng_knn(base32, w.k, rows=qd, screen=screen)[0].cpu().numpy()
     gt_cal = cng.cng_knn(base32, w.k, rows=Cq, screen=screen)[0].cpu().numpy()
-    idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+    idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
+                             repair_slots=w.repair_slots)
     TARGET = 0.955  # calibration target, a margin above the 0.95 reported on the evaluation set
 
     def timed_search(q, **kw):
@@ -512,7 +516,8 @@ def main():
             sampler.__enter__()
             torch.cuda.nvtx.range_push("timed")
         ev[0].record(stream)
-        idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+        idx, bst = cng.cng_build(xd, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
+                                 repair_slots=w.repair_slots)
         ev[1].record(stream)
         model, tst = cng.cng_stop_train(idx, Tq, k=w.k, L=Ll, seed=1)
         ev[2].record(stream)
@@ -595,7 +600,8 @@ def main():
         for step in range(1 + args.steps):
             barrier()
             t0 = time.perf_counter()
-            ix2, _ = cng.cng_build(Xh.numpy(), alpha=w.alpha, R=w.R, L=w.L, screen=screen)
+            ix2, _ = cng.cng_build(Xh.numpy(), alpha=w.alpha, R=w.R, L=w.L, screen=screen,
+                                   repair_slots=w.repair_slots)
             t1 = time.perf_counter()
             cng.cng_search(ix2, Qh.numpy(), k=w.k, L=Ls, out={k_: (v.numpy() if v is not None else None)
                                                                for k_, v in out.items()}, with_stats=False)

@@ -90,6 +90,8 @@ typedef enum {
  *   knn_graph        G0 as device int32 [n][knn_K] (each row's neighbours, -1 padded at its
  *                    end; the paper builds an approximate K-NN graph), or NULL for the exact
  *                    knn_K-NN graph computed by the library's candidate screen
+ *   repair_slots     adjacency slots per row for phase-4 edges (0 = 8, at most 64); the row
+ *                    stride of the final graph is R + repair_slots
  */
 typedef struct {
   double alpha;
@@ -111,6 +113,7 @@ typedef struct {
   int32_t knn_K;
   int32_t beam_L;
   const int32_t *knn_graph;
+  int32_t repair_slots;
 } cng_build_params;
 
 enum { CNG_CAND_EXACT = 0, CNG_CAND_BEAM = 1 };
@@ -149,7 +152,7 @@ typedef struct cng_index cng_index;
  *   connectivity (phase 4): in rounds, every point p not reachable from s is searched for from
  *   s (Alg. 1, beam connect_L, all connect_L results); its first result r whose row has a free
  *   slot names p, and each named r gets an edge to the smallest point naming it.  Rows hold up
- *   to R pruned edges plus up to 8 such edges.
+ *   to R pruned edges plus up to repair_slots (default 8) such edges.
  * points: host or device, n x d of `dtype`, borrowed for the call only (the index keeps its own
  * device copy).  *out receives a new index owned by the caller (free with cng_free).
  * stats may be NULL.  Synchronises `stream` before returning.

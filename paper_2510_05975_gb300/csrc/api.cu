@@ -93,7 +93,7 @@ struct cng_index {
   int d = 0, dpad = 0, dtype = 0, R = 0, L = 0;
   int metric = CNG_L2;      // CNG_IP: rows (and queries) are augmented by one coordinate
   double mips_M2 = 0.0;     // CNG_IP: the largest squared row norm
-  int rs = 0;               // adjacency row stride (R + REPAIR_SLOTS)
+  int rs = 0;               // adjacency row stride (R + repair slots)
   int32_t entry = -1;
   int exact = 0;
   float band = 1e-5f;
@@ -474,6 +474,7 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
       return fail(CNG_E_INVAL,
                   "adaptive pruning needs 0 < alpha0 <= alpha_max, dalpha > 0 and at most 1001 steps");
   }
+  if (p->repair_slots < 0 || p->repair_slots > 64) return fail(CNG_E_INVAL, "repair_slots must be in [0, 64]");
   if (p->candidates != CNG_CAND_EXACT && p->candidates != CNG_CAND_BEAM)
     return fail(CNG_E_INVAL, "unknown candidates route");
   if (p->candidates == CNG_CAND_BEAM) {
@@ -737,7 +738,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   CK(pool.alloc(&off, (size_t)n + 1));
   CK(pool.alloc(&bsum, (size_t)reverse_blocksums_len(n)));
   CK(pool.alloc(&inl, (size_t)n * R));
-  const int Rs = R + REPAIR_SLOTS;
+  const int Rs = R + (P.repair_slots > 0 ? P.repair_slots : REPAIR_SLOTS);
   CK(pool.alloc(&adj, (size_t)n * Rs));
   CK(pool.alloc(&deg, (size_t)n));
   int32_t* big_list;

@@ -821,7 +821,12 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
   for (int i = nv + tid; i < P2; i += PR_THREADS) ar.keys[i] = ~0ull;
   __syncthreads();
   cta_bitonic64(ar.keys, P2);
-  // FP64 re-decision of near-tied neighbours in the order (warp 0)
+  // FP64 re-decision of near-tied neighbours in the order (warp 0); runs longer than PR_RUN
+  // (large merged sets of hubs with concentrated distances) are recorded and re-sorted below
+  // by the whole CTA
+  __shared__ int s_lr_start[8], s_lr_len[8], s_nlr;
+  if (tid == 0) s_nlr = 0;
+  __syncthreads();
   if (!exact && warp == 0) {
     int i = 0;
     while (i + 1 < nv) {
@@ -837,9 +842,19 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
       while (e + 1 < nv && near_tie(key_dist(ar.keys[e]), key_dist(ar.keys[e + 1]), ra.band)) ++e;
       int len = e - s + 1;
       if (len > PR_RUN) {
-        if (lane == 0) set_status(&ctr->status, ST_OVF_RUN);
-        len = PR_RUN;
-        e = s + len - 1;
+        if (lane == 0) {
+          if (s_nlr < 8) {
+            s_lr_start[s_nlr] = s;
+            s_lr_len[s_nlr] = len;
+            ++s_nlr;
+          } else {
+            set_status(&ctr->status, ST_OVF_RUN);
+          }
+        }
+        __syncwarp();
+        ++ordties;
+        i = e + 1;
+        continue;
       }
       for (int t = lane; t < len; t += 32) {
         rid[t] = key_id(ar.keys[s + t]);
@@ -869,6 +884,28 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
     }
   }
   __syncthreads();
+  // long runs: canonical distances of the whole run (in the id / dist arrays, free until they
+  // are filled below), then an odd-even transposition sort of the run by (D, id)
+  for (int r = 0; r < s_nlr; ++r) {
+    const int s0 = s_lr_start[r], len = s_lr_len[r];
+    double* D = reinterpret_cast<double*>(ar.ids);  // ids and dist: 8 bytes per entry, contiguous
+    for (int t = tid; t < len; t += PR_THREADS)
+      D[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)key_id(ar.keys[s0 + t]) * dpad, d);
+    __syncthreads();
+    for (int ph = 0; ph < len; ++ph) {
+      for (int t = 2 * tid + (ph & 1); t + 1 < len; t += 2 * PR_THREADS) {
+        const uint64_t ka = ar.keys[s0 + t], kb = ar.keys[s0 + t + 1];
+        if (D[t + 1] < D[t] || (D[t + 1] == D[t] && key_id(kb) < key_id(ka))) {
+          const double tdv = D[t];
+          D[t] = D[t + 1];
+          D[t + 1] = tdv;
+          ar.keys[s0 + t] = kb;
+          ar.keys[s0 + t + 1] = ka;
+        }
+      }
+      __syncthreads();
+    }
+  }
   for (int i = tid; i < nv; i += PR_THREADS) {
     ar.ids[i] = key_id(ar.keys[i]);
     ar.dist[i] = sqrtf(key_dist(ar.keys[i]));

@@ -54,6 +54,7 @@ class Workload:
     n_train: int
     seed: int
     dtype: str = "float32"
+    repair_slots: int = 8  # phase-4 slots per row
 
     def base(self, n: int | None = None) -> np.ndarray:
         return generate(self.kind, self.n if n is None else n, self.d, self.seed, self.dtype)
@@ -72,7 +73,9 @@ WORKLOADS = {
     "gauss10k": Workload("gauss10k", "gauss", 10_000, 32, 100, 10, 1.2, 32, 64, 2_000, 0),
     "sift1m": Workload("sift1m", "sift", 1_000_000, 128, 10_000, 10, 1.2, 32, 128, 20_000, 1),
     "deep1m": Workload("deep1m", "deep", 1_000_000, 96, 10_000, 10, 1.3, 48, 160, 20_000, 2),
-    "gist1m": Workload("gist1m", "gist", 1_000_000, 960, 1_000, 10, 1.2, 32, 128, 2_000, 3),
+    # at d = 960 many points get no in-edge from exact candidate lists; phase 4 needs room
+    "gist1m": Workload("gist1m", "gist", 1_000_000, 960, 1_000, 10, 1.2, 32, 128, 2_000, 3,
+                       repair_slots=32),
     "bigann10m": Workload("bigann10m", "bigann16", 10_000_000, 128, 100_000, 10, 1.2, 32, 128,
                           200_000, 4, "float16"),
     # the SIFT-like shape with isotropic clusters (reported beside the low-rank recipe)

@@ -260,3 +260,43 @@ def test_beam_candidates_on_a_given_approximate_graph():
         cng.cng_build(tensor(X), alpha=1.2, R=16, L=40, candidates=cng.CNG_CAND_BEAM,
                       knn_graph=torch.from_numpy(bad).cuda())
     assert e.value.code == cng.CNG_E_INVAL
+
+
+@pytest.mark.parametrize("M", [600, 2500])
+def test_long_near_tie_run_in_merge(M):
+    """A hub whose merged set is one long run of near-tied distances: M points on a sphere of
+    radius 1 (+- 2e-7) around point 0 in 32 dimensions all keep point 0 (their nearest point),
+    so its merged set holds M entries whose FP32 distances cannot order them; the GPU re-sorts
+    the whole run by the canonical FP64 distance (M = 2500 exceeds the shared-memory merge and
+    takes the global-scratch pass) and the graph equals the oracle's."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal((M, 32))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    v *= 1.0 + 2e-7 * rng.standard_normal((M, 1))
+    X = np.concatenate([np.zeros((1, 32)), v]).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=16, L=48, keep_lists=True)
+    G = oracle.build_graph(X, 1.2, 0.0, 16, 48)
+    assert int((G.fwd == 0).sum()) == M  # every sphere point keeps the hub
+    _check_graph(X, G, idx, cng, 16, 48)
+    assert st["order_ties"] > 0
+    cng.cng_free(idx)
+
+
+@pytest.mark.parametrize("slots", [2, 24])
+def test_repair_slots(slots):
+    """Phase 4 with a given number of repair slots per row (row stride R + slots): separated
+    clusters need repair edges; the final graph equals the oracle's with the same slots."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(9)
+    centres = rng.standard_normal((12, 16)) * 40.0
+    X = (centres[rng.integers(0, 12, 1500)] + rng.standard_normal((1500, 16))).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=12, L=40, keep_lists=True, repair_slots=slots)
+    G = oracle.build_graph(X, 1.2, 0.0, 12, 40, repair_slots=slots)
+    assert st["repair_edges"] == G.repair_edges > 0
+    adj, deg, Rs, _ = cng.cng_graph(idx)
+    assert Rs == 12 + slots
+    assert np.array_equal(host(adj), G.adj) and np.array_equal(host(deg), G.deg)
+    cng.cng_free(idx)
