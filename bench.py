@@ -314,7 +314,7 @@ def hbm_kernels(w, X, st, ndc_sum, hops_sum, search_ms, peak, src):
 # DRAM bytes (read + write) of one full-size screen launch from a one-pass ncu capture, keyed by
 # (workload, digest of the screen kernel's source): a changed kernel has no entry, so its
 # traffic is reported as null until it is captured again.
-SCREEN_DRAM_BYTES = {}
+SCREEN_DRAM_BYTES = {("sift1m", "9cf3ca3d15b07b39"): 45.26e9 + 23.11e9}
 
 
 def screen_digest() -> str:

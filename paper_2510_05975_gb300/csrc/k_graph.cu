@@ -822,89 +822,100 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
   __syncthreads();
   cta_bitonic64(ar.keys, P2);
   // FP64 re-decision of near-tied neighbours in the order (warp 0); runs longer than PR_RUN
-  // (large merged sets of hubs with concentrated distances) are recorded and re-sorted below
-  // by the whole CTA
-  __shared__ int s_lr_start[8], s_lr_len[8], s_nlr;
-  if (tid == 0) s_nlr = 0;
-  __syncthreads();
-  if (!exact && warp == 0) {
-    int i = 0;
-    while (i + 1 < nv) {
-      int s = -1;
-      for (int b = i; b + 1 < nv && s < 0; b += 32) {
-        int t = b + lane;
-        bool nt = t + 1 < nv && near_tie(key_dist(ar.keys[t]), key_dist(ar.keys[t + 1]), ra.band);
-        unsigned bal = __ballot_sync(FULL, nt);
-        if (bal) s = b + __ffs(bal) - 1;
-      }
-      if (s < 0) break;
-      int e = s + 1;
-      while (e + 1 < nv && near_tie(key_dist(ar.keys[e]), key_dist(ar.keys[e + 1]), ra.band)) ++e;
-      int len = e - s + 1;
-      if (len > PR_RUN) {
-        if (lane == 0) {
-          if (s_nlr < 8) {
+  // (large merged sets of hubs with concentrated distances) are recorded, up to 8 per pass,
+  // and re-sorted by the whole CTA, then warp 0 continues after the last recorded one
+  __shared__ int s_lr_start[8], s_lr_len[8], s_nlr, s_next;
+  int from = 0;
+  while (!exact && from + 1 < nv) {
+    if (tid == 0) {
+      s_nlr = 0;
+      s_next = nv;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int i = from;
+      while (i + 1 < nv) {
+        int s = -1;
+        for (int b = i; b + 1 < nv && s < 0; b += 32) {
+          int t = b + lane;
+          bool nt = t + 1 < nv && near_tie(key_dist(ar.keys[t]), key_dist(ar.keys[t + 1]), ra.band);
+          unsigned bal = __ballot_sync(FULL, nt);
+          if (bal) s = b + __ffs(bal) - 1;
+        }
+        if (s < 0) break;
+        int e = s + 1;
+        while (e + 1 < nv && near_tie(key_dist(ar.keys[e]), key_dist(ar.keys[e + 1]), ra.band)) ++e;
+        int len = e - s + 1;
+        if (len > PR_RUN) {
+          const bool full = s_nlr == 8;  // warp-uniform (written by lane 0 before a __syncwarp)
+          if (full) {
+            if (lane == 0) s_next = s;
+            break;
+          }
+          __syncwarp();
+          if (lane == 0) {
             s_lr_start[s_nlr] = s;
             s_lr_len[s_nlr] = len;
             ++s_nlr;
-          } else {
-            set_status(&ctr->status, ST_OVF_RUN);
+          }
+          __syncwarp();
+          ++ordties;
+          i = e + 1;
+          continue;
+        }
+        for (int t = lane; t < len; t += 32) {
+          rid[t] = key_id(ar.keys[s + t]);
+          d64[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)rid[t] * dpad, d);
+        }
+        __syncwarp();
+        if (lane == 0) {  // insertion sort of the run by (D, id)
+          for (int a = 1; a < len; ++a) {
+            double dv = d64[a];
+            int32_t iv = rid[a];
+            uint64_t kv = ar.keys[s + a];
+            int b = a - 1;
+            while (b >= 0 && (d64[b] > dv || (d64[b] == dv && rid[b] > iv))) {
+              d64[b + 1] = d64[b];
+              rid[b + 1] = rid[b];
+              ar.keys[s + b + 1] = ar.keys[s + b];
+              --b;
+            }
+            d64[b + 1] = dv;
+            rid[b + 1] = iv;
+            ar.keys[s + b + 1] = kv;
           }
         }
         __syncwarp();
         ++ordties;
         i = e + 1;
-        continue;
       }
-      for (int t = lane; t < len; t += 32) {
-        rid[t] = key_id(ar.keys[s + t]);
-        d64[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)rid[t] * dpad, d);
-      }
-      __syncwarp();
-      if (lane == 0) {  // insertion sort of the run by (D, id)
-        for (int a = 1; a < len; ++a) {
-          double dv = d64[a];
-          int32_t iv = rid[a];
-          uint64_t kv = ar.keys[s + a];
-          int b = a - 1;
-          while (b >= 0 && (d64[b] > dv || (d64[b] == dv && rid[b] > iv))) {
-            d64[b + 1] = d64[b];
-            rid[b + 1] = rid[b];
-            ar.keys[s + b + 1] = ar.keys[s + b];
-            --b;
-          }
-          d64[b + 1] = dv;
-          rid[b + 1] = iv;
-          ar.keys[s + b + 1] = kv;
-        }
-      }
-      __syncwarp();
-      ++ordties;
-      i = e + 1;
     }
-  }
-  __syncthreads();
-  // long runs: canonical distances of the whole run (in the id / dist arrays, free until they
-  // are filled below), then an odd-even transposition sort of the run by (D, id)
-  for (int r = 0; r < s_nlr; ++r) {
-    const int s0 = s_lr_start[r], len = s_lr_len[r];
-    double* D = reinterpret_cast<double*>(ar.ids);  // ids and dist: 8 bytes per entry, contiguous
-    for (int t = tid; t < len; t += PR_THREADS)
-      D[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)key_id(ar.keys[s0 + t]) * dpad, d);
     __syncthreads();
-    for (int ph = 0; ph < len; ++ph) {
-      for (int t = 2 * tid + (ph & 1); t + 1 < len; t += 2 * PR_THREADS) {
-        const uint64_t ka = ar.keys[s0 + t], kb = ar.keys[s0 + t + 1];
-        if (D[t + 1] < D[t] || (D[t + 1] == D[t] && key_id(kb) < key_id(ka))) {
-          const double tdv = D[t];
-          D[t] = D[t + 1];
-          D[t + 1] = tdv;
-          ar.keys[s0 + t] = kb;
-          ar.keys[s0 + t + 1] = ka;
-        }
-      }
+    // long runs: canonical distances of the whole run (in the id / dist arrays, free until they
+    // are filled below), then an odd-even transposition sort of the run by (D, id)
+    const int nlr = s_nlr;
+    for (int r = 0; r < nlr; ++r) {
+      const int s0 = s_lr_start[r], len = s_lr_len[r];
+      double* D = reinterpret_cast<double*>(ar.ids);  // ids and dist: 8 bytes per entry, contiguous
+      for (int t = tid; t < len; t += PR_THREADS)
+        D[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)key_id(ar.keys[s0 + t]) * dpad, d);
       __syncthreads();
+      for (int ph = 0; ph < len; ++ph) {
+        for (int t = 2 * tid + (ph & 1); t + 1 < len; t += 2 * PR_THREADS) {
+          const uint64_t ka = ar.keys[s0 + t], kb = ar.keys[s0 + t + 1];
+          if (D[t + 1] < D[t] || (D[t + 1] == D[t] && key_id(kb) < key_id(ka))) {
+            const double tdv = D[t];
+            D[t] = D[t + 1];
+            D[t + 1] = tdv;
+            ar.keys[s0 + t] = kb;
+            ar.keys[s0 + t + 1] = ka;
+          }
+        }
+        __syncthreads();
+      }
     }
+    from = s_next;
+    __syncthreads();
   }
   for (int i = tid; i < nv; i += PR_THREADS) {
     ar.ids[i] = key_id(ar.keys[i]);
