@@ -63,16 +63,17 @@ struct TcParams {
   uint32_t* status;
   const int32_t* perm;  // rows and columns are positions of a locality order: perm[pos] = id
   int wave_start;       // 1: each wave of row blocks starts its column sweep at its own rows
+  int64_t row_off;      // position of row 0 in the order (a tuning trial on a row sample)
   uint32_t* sync;       // zeroed checkpoint counters (producers of a wave stay close), or null
+  int sync_d;           // checkpoint lag in windows
 };
 
 // Producers meet at checkpoints every TC_SYNC_K tiles of their own sequence; a producer at
-// checkpoint c waits until every CTA that reaches checkpoint c - TC_SYNC_D has reached it, so
-// the CTAs of a wave stay within TC_SYNC_D * TC_SYNC_K B tiles of each other and share the tiles
+// checkpoint c waits until every CTA that reaches checkpoint c - sync_d has reached it, so
+// the CTAs of a wave stay within sync_d * TC_SYNC_K B tiles of each other and share the tiles
 // through L2 instead of each streaming them from DRAM.  The wait only serves the cache: it is
 // bounded (about 2 ms) and the producer proceeds when it expires.
 constexpr int TC_SYNC_K = 256 * 128 / TC_BN;  // tiles per checkpoint window (32,768 columns)
-constexpr int TC_SYNC_D = 8;
 constexpr uint32_t TC_SYNC_SPIN = 8192;
 
 CNG_DEV uint32_t ld_acquire_u32(const uint32_t* p) {
@@ -85,8 +86,8 @@ CNG_DEV void wave_checkpoint(const TcParams& P, int64_t it, int64_t nrb, int nti
   if (!P.sync || it == 0 || it % TC_SYNC_K != 0) return;
   const int64_t c = it / TC_SYNC_K;
   atomicAdd(&P.sync[c], 1u);
-  if (c <= TC_SYNC_D) return;
-  const int64_t cw = c - TC_SYNC_D;
+  if (c <= P.sync_d) return;
+  const int64_t cw = c - P.sync_d;
   // CTAs reaching tile index cw * K: those with a row block in wave (cw * K) / ntiles
   const int64_t w = (cw * TC_SYNC_K) / ntiles;
   const int64_t left = nrb - w * (int64_t)gridDim.x;
@@ -102,7 +103,7 @@ CNG_DEV void wave_checkpoint(const TcParams& P, int64_t it, int64_t nrb, int nti
 CNG_DEV int sweep_start(const TcParams& P, int64_t rb, int ntiles) {
   if (!P.wave_start) return 0;
   const int64_t w0 = rb - rb % gridDim.x;
-  const int64_t t0 = (w0 * TC_BM) / TC_BN;
+  const int64_t t0 = (P.row_off + w0 * TC_BM) / TC_BN;
   return t0 < ntiles ? (int)t0 : ntiles - 1;
 }
 
