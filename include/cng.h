@@ -92,6 +92,11 @@ typedef enum {
  *                    knn_K-NN graph computed by the library's candidate screen
  *   repair_slots     adjacency slots per row for phase-4 edges (0 = 8, at most 64); the row
  *                    stride of the final graph is R + repair_slots
+ *   screen_variant   0 (default): the tensor-core screen's pipeline variant (operand stages,
+ *                    row-buffer capacity, checkpoint lag) is chosen by the library's
+ *                    autotuner, which times the variants on a sample of row blocks the first
+ *                    time a problem shape is built in the process; v >= 1 forces variant v - 1
+ *                    (fewer than 8 variants; results never depend on the variant)
  */
 typedef struct {
   double alpha;
@@ -114,6 +119,7 @@ typedef struct {
   int32_t beam_L;
   const int32_t *knn_graph;
   int32_t repair_slots;
+  int32_t screen_variant;
 } cng_build_params;
 
 enum { CNG_CAND_EXACT = 0, CNG_CAND_BEAM = 1 };
@@ -137,6 +143,10 @@ typedef struct {
   double alpha_mean;          /* mean alpha of the phase-2 lists (alpha when not adaptive) */
   double ms_cand_search;      /* CNG_CAND_BEAM: the candidate searches on G0 (ms_screen and
                                  ms_rerank then time G0's exact K-NN, when the library builds it) */
+  int32_t screen_variant;     /* tensor-core screen: the pipeline variant used, its operand */
+  int32_t screen_stages;      /* stages, row-buffer capacity (entries per row) and checkpoint */
+  int32_t screen_cap;         /* lag (windows of 256 column tiles); -1 for the FP32 screen */
+  int32_t screen_sync;
 } cng_build_stats;
 
 typedef struct cng_index cng_index;

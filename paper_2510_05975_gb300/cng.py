@@ -47,7 +47,8 @@ class BuildParams(ctypes.Structure):
                 ("alpha0", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("dalpha", ctypes.c_double), ("candidates", ctypes.c_int32),
                 ("knn_K", ctypes.c_int32), ("beam_L", ctypes.c_int32),
-                ("knn_graph", ctypes.c_void_p), ("repair_slots", ctypes.c_int32)]
+                ("knn_graph", ctypes.c_void_p), ("repair_slots", ctypes.c_int32),
+                ("screen_variant", ctypes.c_int32)]
 
 
 class BuildStats(ctypes.Structure):
@@ -60,7 +61,9 @@ class BuildStats(ctypes.Structure):
                [("repair_rounds", ctypes.c_int32), ("screen_used", ctypes.c_int32),
                 ("entry", ctypes.c_int32), ("exact_int", ctypes.c_int32),
                 ("screen_err_max", ctypes.c_double), ("ms_order", ctypes.c_double),
-                ("alpha_mean", ctypes.c_double), ("ms_cand_search", ctypes.c_double)]
+                ("alpha_mean", ctypes.c_double), ("ms_cand_search", ctypes.c_double),
+                ("screen_variant", ctypes.c_int32), ("screen_stages", ctypes.c_int32),
+                ("screen_cap", ctypes.c_int32), ("screen_sync", ctypes.c_int32)]
 
 
 class SearchParams(ctypes.Structure):
@@ -224,7 +227,8 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
               screen: int = CNG_SCREEN_TC, tie_band: float = 1e-5, margin: int = 32,
               keep_lists: bool = False, connect_L: int = 0, input_order: bool = False,
               adaptive=None, candidates: int = 0, knn_K: int = 0, beam_L: int = 0,
-              knn_graph: torch.Tensor | None = None, repair_slots: int = 0, stream=None):
+              knn_graph: torch.Tensor | None = None, repair_slots: int = 0, screen_variant: int = 0,
+              stream=None):
     """cng_build of include/cng.h.  points: CUDA tensor or host (numpy / CPU tensor), float32
     or float16, shape [n, d].  candidates: CNG_CAND_EXACT or CNG_CAND_BEAM (with knn_K,
     beam_L and optionally knn_graph, a CUDA int32 tensor [n, knn_K]).  Returns (Index, stats
@@ -245,7 +249,7 @@ def cng_build(points, alpha: float, R: int, L: int, tau: float = 0.0, metric: in
     p = BuildParams(alpha, tau, R, L, metric, screen, tie_band, margin, int(keep_lists), connect_L,
                     int(input_order), int(adaptive is not None), a0, am, da, int(candidates),
                     int(knn_K), int(beam_L), None if knn_graph is None else knn_graph.data_ptr(),
-                    int(repair_slots))
+                    int(repair_slots), int(screen_variant))
     st = BuildStats()
     h = ctypes.c_void_p()
     _check(lib().cng_build(_ptr(points), dt, n, d, ctypes.byref(p), _stream(stream),

@@ -226,10 +226,12 @@ struct KnnInputs {
   // locality order of the tensor-core operands (tc_rows / tc_cols / nb_cols hold positions)
   const int32_t* perm;
   int wave_start;
+  int variant = -1;  // tensor-core screen pipeline variant (-1: autotuned)
 };
 
 static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist, Counters* ctr,
-                          double* ms_screen, double* ms_rerank, cudaStream_t s) {
+                          double* ms_screen, double* ms_rerank, cudaStream_t s,
+                          TcShape* shape = nullptr) {
   DevPool pool;
   int32_t* sids;
   uint32_t* sthr;
@@ -255,9 +257,15 @@ static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist
     ta.rowbuf_words = screen_tc_rowbuf_words(in.m, in.n, in.Lp);
     ta.perm = in.perm;
     ta.wave_start = in.wave_start;
+    ta.variant = in.variant;
     CK(pool.alloc(&ta.rowbuf, ta.rowbuf_words));
     std::string msg;
-    cudaError_t e = launch_screen_tc(ta, s, &msg);
+    if (in.variant < 0) {  // a first use of this shape times the variants (outside the timing)
+      cudaError_t te = launch_screen_tc_tune(ta, s, &msg, &ta.variant);
+      if (te != cudaSuccess) return fail(CNG_E_CUDA, "tensor-core screen: " + msg + cudaGetErrorString(te));
+      tm.mark();  // the screen's time starts after the tuning trials
+    }
+    cudaError_t e = launch_screen_tc(ta, s, &msg, shape);
     if (e != cudaSuccess) return fail(CNG_E_CUDA, "tensor-core screen: " + msg + cudaGetErrorString(e));
     sm.kind = 1;
     sm.nb = in.nb_rows;
@@ -291,8 +299,9 @@ static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist
                    fail_rows, fail_bound, ctr, out_ids, out_dist, s));
   tm.mark();
   CK(cudaStreamSynchronize(s));
-  if (ms_screen) *ms_screen = tm.ms(0, 1);
-  if (ms_rerank) *ms_rerank = tm.ms(1, 2);
+  const int m0 = tm.n - 3;  // marks: [tuning start,] screen start, screen end, rerank end
+  if (ms_screen) *ms_screen = tm.ms(m0, m0 + 1);
+  if (ms_rerank) *ms_rerank = tm.ms(m0 + 1, m0 + 2);
   return CNG_OK;
 }
 
@@ -475,6 +484,8 @@ static cng_status validate_build(const void* points, int32_t dtype, int64_t n, i
                   "adaptive pruning needs 0 < alpha0 <= alpha_max, dalpha > 0 and at most 1001 steps");
   }
   if (p->repair_slots < 0 || p->repair_slots > 64) return fail(CNG_E_INVAL, "repair_slots must be in [0, 64]");
+  if (p->screen_variant < 0 || p->screen_variant > screen_tc_variants())
+    return fail(CNG_E_INVAL, "screen_variant must be in [0, " + std::to_string(screen_tc_variants()) + "]");
   if (p->candidates != CNG_CAND_EXACT && p->candidates != CNG_CAND_BEAM)
     return fail(CNG_E_INVAL, "unknown candidates route");
   if (p->candidates == CNG_CAND_BEAM) {
@@ -605,6 +616,8 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   ki.rb_rows = pr.rb;
   ki.rbmax = bits_to_float(pr.st.rbmax_bits);
   ki.normmax = std::sqrt(bits_to_float(pr.st.nbmax_bits));
+  ki.variant = P.screen_variant > 0 ? P.screen_variant - 1 : -1;
+  TcShape tshape{-1, -1, -1, -1};
   // locality order of the screen's operands (speed only; the lists are exact either way)
   double ms_order = 0;
   if (screen == CNG_SCREEN_TC && !P.input_order) {
@@ -633,12 +646,12 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     KnnInputs kg = ki;
     kg.L = K0;
     kg.Lp = (int)std::min<int64_t>((int64_t)K0 + P.margin, n - 1);
-    st = run_knn(kg, g0, g0d, ctr, &ms_screen, &ms_rerank, s);
+    st = run_knn(kg, g0, g0d, ctr, &ms_screen, &ms_rerank, s, &tshape);
     if (st != CNG_OK) return st;
     cudaFree(g0d);
     pool.release(g0d);
   } else {
-    st = run_knn(ki, cand, cdist, ctr, &ms_screen, &ms_rerank, s);
+    st = run_knn(ki, cand, cdist, ctr, &ms_screen, &ms_rerank, s, &tshape);
     if (st != CNG_OK) return st;
   }
   // screening operands are no longer needed
@@ -792,7 +805,11 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     (void)qhops;
     CK(launch_fill(best, n, 0x7fffffff, s));
     int hc_counts[4] = {0, 0, 0, 0};
-    for (int round = 0; round < 64; ++round) {
+    // rounds until every point is reachable (each adds at least one edge, else the phase
+    // fails); the cap only bounds a pathological input
+    constexpr int kMaxRounds = 4096;
+    int round = 0;
+    for (; round < kMaxRounds; ++round) {
       CK(launch_bfs(adj, deg, Rs, n, h_entry, reached, fa, fb, counts, hc_counts, s));
       CK(launch_collect(reached, n, U, counts + 2, s));
       CK(cudaMemcpyAsync(&hc_counts[2], counts + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -841,6 +858,9 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
                                             " points unreachable)");
       repair_edges += hc_counts[3];
     }
+    if (round == kMaxRounds)
+      return fail(CNG_E_UNSUPPORTED, "phase 4 did not connect the graph within " +
+                                         std::to_string(kMaxRounds) + " rounds");
     uint32_t sst = 0;
     CK(cudaMemcpyAsync(&sst, sc_status, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -923,6 +943,10 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
                                    : P.alpha;
     stats->ms_order = ms_order;
     stats->ms_cand_search = ms_cand;
+    stats->screen_variant = tshape.variant;
+    stats->screen_stages = tshape.stages;
+    stats->screen_cap = tshape.cap;
+    stats->screen_sync = tshape.sync_d;
   }
   *out = ix;
   return CNG_OK;

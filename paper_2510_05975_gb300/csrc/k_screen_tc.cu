@@ -30,6 +30,9 @@
 #include "device_common.cuh"
 #include "screen_tc.h"
 
+#include <mutex>
+#include <vector>
+
 namespace cng {
 
 constexpr int TC_BM = 256;          // rows per CTA block (two M=128 accumulators)
@@ -838,7 +841,24 @@ static cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const 
   return cudaGetLastError();
 }
 
-static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::string* msg, float* dump) {
+// Pipeline variants the autotuner times: operand stages (0 = as many as shared memory holds,
+// else that many fewer), row-buffer capacity step (0 = the smallest that fits, 1 = the next),
+// checkpoint lag in windows of 256 tiles.
+struct TcVariant {
+  int stages_less, cap_step, sync_d;
+};
+constexpr TcVariant TC_VARIANTS[] = {{0, 0, 8}, {0, 0, 4}, {0, 0, 16}, {1, 0, 8}, {0, 1, 8}, {2, 0, 8}};
+constexpr int TC_NVARIANTS = (int)(sizeof(TC_VARIANTS) / sizeof(TC_VARIANTS[0]));
+
+int screen_tc_variants() { return TC_NVARIANTS; }
+
+static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::string* msg, float* dump,
+                               int variant, TcShape* shape) {
+  if (variant < 0 || variant >= TC_NVARIANTS) {
+    if (msg) *msg = "unknown screen variant; ";
+    return cudaErrorInvalidValue;
+  }
+  const TcVariant v = TC_VARIANTS[variant];
   const int kpad = a.kpad;
   if (kpad % 64 != 0 || kpad < 64 || kpad > TC_KPAD_MAX) {
     if (msg) *msg = "kpad must be a multiple of 64 in [64, 4096]; ";
@@ -854,20 +874,23 @@ static cudaError_t launch_impl(const TcScreenArgs& a, cudaStream_t s, std::strin
   const int stage_bytes = kstream ? (TC_BM + TC_BN) * TC_KC * 2 : TC_BN * kpad * 2;
   const int fixed = 1024 + TC_MAXST * TC_BN * 4 + 256 + 8 * 256 * 4;  // alignment, norms, barriers, hist
   const int budget = 220 * 1024 - a_bytes - fixed;
-  p.nst = std::min(TC_MAXST, budget / stage_bytes);
+  p.nst = std::min(TC_MAXST, budget / stage_bytes) - v.stages_less;
   if (p.nst < 2) {
     if (msg) *msg = "shared memory too small for two operand stages; ";
     return cudaErrorInvalidValue;
   }
   p.Lp = a.Lp;
-  int cpl = 0;
+  int cpl = 0, step = v.cap_step;
   for (int c : {12, 16, 20, 24})
-    if (c * 32 >= a.Lp + TC_BN + 32) { cpl = c; break; }
+    if (c * 32 >= a.Lp + TC_BN + 32 && step-- == 0) { cpl = c; break; }
   if (!cpl) {
     if (msg) *msg = "screened list too long; ";
     return cudaErrorInvalidValue;
   }
   p.cap = cpl * 32;
+  p.sync_d = v.sync_d;
+  p.row_off = a.row_off;
+  if (shape) *shape = TcShape{variant, p.nst, p.cap, p.sync_d};
   p.self_excl = a.self_excl;
   p.idesc = make_idesc(a.fp16);
   p.nb = a.nb;
@@ -926,13 +949,119 @@ size_t screen_tc_rowbuf_words(int64_t m, int64_t n, int Lp) {
   return (size_t)grid * TC_BM * cpl * 32 + sync_counter_words(m, n, grid);
 }
 
-cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg) {
-  return launch_impl(a, s, msg, nullptr);
+// ---- autotuner -----------------------------------------------------------------------------------
+// The pipeline variant is chosen once per (device, kpad, L', operand type, self or rows, n
+// rounded to a power of two) by timing every valid variant on a sample of two waves of row
+// blocks (rows from the middle of the order, their sweep starting where theirs would) against
+// all the columns; smaller problems use variant 0.  The results of a screen never depend on
+// the variant (the lists are certified and reranked the same way).
+struct TunedScreen {
+  int dev, kpad, Lp, fp16, self, nlog;
+  int variant;
+};
+static std::mutex g_tc_mu;
+static std::vector<TunedScreen> g_tc_tuned;
+
+static int tune_key_nlog(int64_t n) {
+  int l = 0;
+  while (((int64_t)1 << l) < n) ++l;
+  return l;
+}
+
+static cudaError_t tune_variant(const TcScreenArgs& a, cudaStream_t s, std::string* msg, int* chosen) {
+  *chosen = 0;
+  const int64_t grid = std::min<int64_t>((a.m + TC_BM - 1) / TC_BM, num_sms());
+  const int64_t sample = 2 * grid * TC_BM;
+  if (a.m < 4 * sample) return cudaSuccess;  // small problems: the default variant
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TunedScreen key{dev, a.kpad, a.Lp, a.fp16, a.self_excl, tune_key_nlog(a.n), 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    for (const auto& t : g_tc_tuned)
+      if (t.dev == key.dev && t.kpad == key.kpad && t.Lp == key.Lp && t.fp16 == key.fp16 &&
+          t.self == key.self && t.nlog == key.nlog) {
+        *chosen = t.variant;
+        return cudaSuccess;
+      }
+  }
+  int32_t* ids = nullptr;
+  uint32_t *thr = nullptr, *st = nullptr;
+  cudaError_t e = cudaMalloc(&ids, (size_t)sample * a.Lp * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&thr, (size_t)sample * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&st, sizeof(uint32_t));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  if (e == cudaSuccess) {
+    TcScreenArgs t = a;
+    const int64_t off = (a.m / 2 / TC_BM) * TC_BM;
+    t.row_off = std::min<int64_t>(off, (a.m - sample) / TC_BM * TC_BM);
+    t.A = static_cast<const char*>(a.A) + (size_t)t.row_off * a.kpad * 2;
+    t.m = sample;
+    t.self_excl = 0;
+    t.perm = nullptr;
+    t.ids = ids;
+    t.thr = thr;
+    t.status = st;
+    for (int v = 0; v < TC_NVARIANTS && e == cudaSuccess; ++v) {
+      for (int rep = 0; rep < (v == 0 ? 2 : 1) && e == cudaSuccess; ++rep) {  // variant 0 warms up
+        e = cudaMemsetAsync(st, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) break;
+        cudaEventRecord(e0, s);
+        std::string m2;
+        const cudaError_t le = launch_impl(t, s, &m2, nullptr, v, nullptr);
+        cudaEventRecord(e1, s);
+        if (le == cudaErrorInvalidValue) {  // variant not valid for this shape
+          (void)cudaGetLastError();
+          break;
+        }
+        e = le;
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        uint32_t hst = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost);
+        float ms = 0.f;
+        if (e == cudaSuccess && hst == 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            (v > 0 || rep == 1) && ms < best) {
+          best = ms;
+          *chosen = v;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(ids);
+  cudaFree(thr);
+  cudaFree(st);
+  if (e != cudaSuccess) {
+    if (msg) *msg = "screen autotuning failed; ";
+    return e;
+  }
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  TunedScreen r = key;
+  r.variant = *chosen;
+  g_tc_tuned.push_back(r);
+  return cudaSuccess;
+}
+
+cudaError_t launch_screen_tc_tune(const TcScreenArgs& a, cudaStream_t s, std::string* msg, int* variant) {
+  return tune_variant(a, s, msg, variant);
+}
+
+cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg, TcShape* shape) {
+  int variant = a.variant;
+  if (variant < 0) {
+    cudaError_t e = tune_variant(a, s, msg, &variant);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_impl(a, s, msg, nullptr, variant, shape);
 }
 
 cudaError_t launch_screen_tc_dump(const TcScreenArgs& a, float* dump, cudaStream_t s,
                                   std::string* msg) {
-  return launch_impl(a, s, msg, dump);
+  return launch_impl(a, s, msg, dump, 0, nullptr);
 }
 
 }  // namespace cng

@@ -28,12 +28,26 @@ struct TcScreenArgs {
   // perm[col]).  wave_start = 1 starts each wave of row blocks at its own column tile.
   const int32_t* perm;
   int wave_start;
+  int64_t row_off = 0;  // position of row 0 in the order (tuning trials on a row sample)
+  int variant = -1;     // pipeline variant; -1: the autotuner's choice
 };
+
+// Pipeline shape a screen ran with: variant index, operand stages, row-buffer capacity,
+// checkpoint lag (windows of 256 tiles).
+struct TcShape {
+  int variant, stages, cap, sync_d;
+};
+int screen_tc_variants();
+// The autotuned variant for a's shape (timing the variants on first use; synchronises `s`).
+cudaError_t launch_screen_tc_tune(const TcScreenArgs& a, cudaStream_t s, std::string* msg, int* variant);
 
 bool tc_screen_supported(int d, bool fp16);
 // Scratch words for m rows against n columns: row buffers plus checkpoint counters.
 size_t screen_tc_rowbuf_words(int64_t m, int64_t n, int Lp);
-cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg);
+// The screen (launch on `s`); with a.variant < 0 the autotuned variant for this shape, timed
+// on first use (synchronises `s` then).  *shape, if given, receives the shape used.
+cudaError_t launch_screen_tc(const TcScreenArgs& a, cudaStream_t s, std::string* msg,
+                             TcShape* shape = nullptr);
 // Test aid: writes every screened score s(x, y) to dump[m][n] instead of selecting.
 // One warp runs the screen's bounded waits on a barrier and a flag that never complete; they
 // must run out and leave ST_TIMEOUT in *status (never_set: a zeroed device word).

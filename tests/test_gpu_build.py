@@ -300,3 +300,43 @@ def test_repair_slots(slots):
     assert Rs == 12 + slots
     assert np.array_equal(host(adj), G.adj) and np.array_equal(host(deg), G.deg)
     cng.cng_free(idx)
+
+
+def test_screen_variants_give_identical_lists():
+    """Every pipeline variant of the tensor-core screen (operand stages, row-buffer capacity,
+    checkpoint lag) yields the same candidate lists, phase-2 lists and graph; the stats report
+    the shape used."""
+    need_gpu()
+    cng = lib()
+    X = tensor(synth.generate("sift", 40_001, 128, seed=13))
+    ref = None
+    shapes = set()
+    for v in range(1, 7):
+        idx, st = cng.cng_build(X, alpha=1.2, R=32, L=128, keep_lists=True, screen_variant=v)
+        assert st["screen_variant"] == v - 1 and st["screen_stages"] >= 2
+        shapes.add((st["screen_stages"], st["screen_cap"], st["screen_sync"]))
+        cand, _, fwd, _ = cng.cng_lists(idx)
+        adj, deg, _, _ = cng.cng_graph(idx)
+        got = [host(a) for a in (cand, fwd, adj, deg)]
+        cng.cng_free(idx)
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), v
+    assert len(shapes) == 6
+
+
+def test_screen_autotuner_picks_a_variant():
+    """At 400k points the first build of the shape times the variants on a row sample and uses
+    the fastest; the lists equal those of a forced variant."""
+    need_gpu()
+    cng = lib()
+    X = tensor(synth.generate("sift", 400_000, 128, seed=14))
+    idx, st = cng.cng_build(X, alpha=1.2, R=32, L=128, keep_lists=True)
+    assert 0 <= st["screen_variant"] < 6 and st["screen_cap"] >= 288
+    cand_a = host(cng.cng_lists(idx)[0])
+    cng.cng_free(idx)
+    idx, st2 = cng.cng_build(X, alpha=1.2, R=32, L=128, keep_lists=True, screen_variant=1)
+    assert np.array_equal(cand_a, host(cng.cng_lists(idx)[0]))
+    cng.cng_free(idx)
