@@ -349,6 +349,8 @@ def main():
                     help="with --build-n: exact L-NN candidates, or the paper's route (beam search "
                          "on the exact K-NN graph G0, K = --knn-K, queue L + 1)")
     ap.add_argument("--knn-K", type=int, default=200)
+    ap.add_argument("--connect-L", type=int, default=0,
+                    help="with --build-n: beam width of the phase-4 searches (0 = 32)")
     ap.add_argument("--search-L", type=int, default=0,
                     help="only build the workload's index and run its queries at this fixed beam "
                          "width with 4 queries per CTA (no autotuning): a warm-up search, then the "
@@ -398,7 +400,8 @@ def main():
             idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen,
                                     adaptive=(0.9, 1.6, 0.05) if args.adaptive else None,
                                     candidates=cng.CNG_CAND_BEAM if beam else cng.CNG_CAND_EXACT,
-                                    knn_K=args.knn_K if beam else 0, repair_slots=w.repair_slots)
+                                    knn_K=args.knn_K if beam else 0, repair_slots=w.repair_slots,
+                                    connect_L=args.connect_L)
             torch.cuda.synchronize()
             cng.cng_free(idx)
         print(json.dumps({"build_n": args.build_n, "workload": args.workload, "d": w.d, "L": w.L,
@@ -408,7 +411,9 @@ def main():
                                                 "ms_cand_search", "ms_prune", "ms_merge",
                                                 "ms_connect", "rule_ties", "cert_fail_rows",
                                                 "order_ties", "alpha_mean", "merge_repruned",
-                                                "n_edges", "screen_used")}}), flush=True)
+                                                "n_edges", "screen_used", "screen_variant",
+                                                "screen_stages", "screen_cap", "screen_sync",
+                                                "repair_edges", "repair_rounds")}}), flush=True)
         return
     if args.search_L:
         xs = torch.from_numpy(w.base()).cuda()
@@ -670,7 +675,8 @@ def main():
                 "build_counts": {k_: last_stats[k_] for k_ in
                                  ("n_edges", "cert_fail_rows", "order_ties", "rule_ties",
                                   "merge_repruned", "merge_max_list", "repair_edges", "repair_rounds",
-                                  "exact_int", "screen_used")} if last_stats else None,
+                                  "exact_int", "screen_used", "screen_variant", "screen_stages",
+                                  "screen_cap", "screen_sync")} if last_stats else None,
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "hbm_kernels": hbm,
                 "cpu_baseline": cpu,
                 "clocks": clocks}
