@@ -55,6 +55,7 @@ class Workload:
     seed: int
     dtype: str = "float32"
     repair_slots: int = 8  # phase-4 slots per row
+    connect_L: int = 0  # phase-4 search beam (0: the library default, 32)
 
     def base(self, n: int | None = None) -> np.ndarray:
         return generate(self.kind, self.n if n is None else n, self.d, self.seed, self.dtype)
@@ -74,8 +75,9 @@ WORKLOADS = {
     "sift1m": Workload("sift1m", "sift", 1_000_000, 128, 10_000, 10, 1.2, 32, 128, 20_000, 1),
     "deep1m": Workload("deep1m", "deep", 1_000_000, 96, 10_000, 10, 1.3, 48, 160, 20_000, 2),
     # at d = 960 many points get no in-edge from exact candidate lists; phase 4 needs room
+    # and a wider search (a beam of 32 stalls with tens of thousands of points unreached)
     "gist1m": Workload("gist1m", "gist", 1_000_000, 960, 1_000, 10, 1.2, 32, 128, 2_000, 3,
-                       repair_slots=32),
+                       repair_slots=32, connect_L=128),
     "bigann10m": Workload("bigann10m", "bigann16", 10_000_000, 128, 100_000, 10, 1.2, 32, 128,
                           200_000, 4, "float16"),
     # the SIFT-like shape with isotropic clusters (reported beside the low-rank recipe)
