@@ -63,7 +63,8 @@ class BuildStats(ctypes.Structure):
                 ("screen_err_max", ctypes.c_double), ("ms_order", ctypes.c_double),
                 ("alpha_mean", ctypes.c_double), ("ms_cand_search", ctypes.c_double),
                 ("screen_variant", ctypes.c_int32), ("screen_stages", ctypes.c_int32),
-                ("screen_cap", ctypes.c_int32), ("screen_sync", ctypes.c_int32)]
+                ("screen_cap", ctypes.c_int32), ("screen_sync", ctypes.c_int32),
+                ("prune_path", ctypes.c_int32)]
 
 
 class SearchParams(ctypes.Structure):

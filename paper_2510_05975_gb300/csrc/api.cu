@@ -757,8 +757,15 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   int32_t* big_list;
   CK(pool.alloc(&big_list, 2 * (size_t)n));  // big list + the 8-bit merge's middle list
   CK(launch_reverse(fwd, fdeg, n, R, indeg, off, cursor, inl, bsum, ctr, s));
+  MergeScratch ms{};  // the 8-bit merge's listed sets for the pipelined Gram re-prune
+  if (!P.adaptive && gram_prune_ok(u8, u8w, 128, R)) {
+    CK(pool.alloc(&ms.mlist, (size_t)n * 128));
+    CK(pool.alloc(&ms.mdist, (size_t)n * 128));
+    CK(pool.alloc(&ms.mlen, (size_t)n));
+    CK(pool.alloc(&ms.rlist, (size_t)n));
+  }
   CK(launch_merge(pr.xs, dtype, n, d, dpad, fwd, fdeg, off, inl, P.alpha, P.tau, ag, R, band, exact, adj,
-                  deg, Rs, ctr, big_list, u8, u8w, s));
+                  deg, Rs, ctr, big_list, u8, u8w, ms, s));
   {
     Counters hc0;
     CK(cudaMemcpyAsync(&hc0, ctr, sizeof(hc0), cudaMemcpyDeviceToHost, s));
@@ -947,6 +954,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     stats->screen_stages = tshape.stages;
     stats->screen_cap = tshape.cap;
     stats->screen_sync = tshape.sync_d;
+    stats->prune_path = gram_prune_ok(u8, u8w, L, R) ? 2 : (u8 && L <= 256 ? 1 : 0);
   }
   *out = ix;
   return CNG_OK;

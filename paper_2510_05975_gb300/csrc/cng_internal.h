@@ -41,6 +41,16 @@ struct Counters {
   int max_indeg;
   int nmid;        // 8-bit merge: nodes deferred from the 128-entry to the 256-entry pass
   unsigned long long alpha_steps;  // adaptive pruning: sum over phase-2 points of the alpha step
+  int nre;         // 8-bit merge: nodes listed for the pipelined Gram re-prune
+};
+
+// Scratch of the 8-bit merge's pipelined re-prune: merged lists of up to 128 entries per node
+// ([n][128] ids and FP32 distances), their lengths and the listed nodes.  All null: not used.
+struct MergeScratch {
+  int32_t* mlist;
+  float* mdist;
+  int32_t* mlen;
+  int32_t* rlist;
 };
 
 // Alg. 4 grid of adaptive pruning: alpha_i = alpha0 + i * dalpha, i = 0 .. imax (imax < 0:
@@ -107,7 +117,7 @@ cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* inl, double alpha, double tau, const AlphaGrid& ag,
                          int R, float band, int exact, int32_t* adj, int32_t* deg, int rs,
                          Counters* ctr, int32_t* big_list, const uint8_t* u8, int u8_words,
-                         cudaStream_t s);
+                         const MergeScratch& ms, cudaStream_t s);
 // Merge of the listed nodes with per-CTA global scratch of 17 * big_cap bytes (grid CTAs).
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
@@ -135,6 +145,9 @@ constexpr int REPAIR_SLOTS = 8;   // adjacency row slots beyond R for phase-4 ed
 constexpr int CONNECT_L = 32;     // default beam width of the phase-4 searches
 
 int num_sms();
+// True when the tensor-core Gram-tile prune (k_prune_tc.cu) takes lists of L entries with
+// out-degree bound R on 8-bit rows of dw 32-bit words (U non-null).
+bool gram_prune_ok(const uint8_t* U, int dw, int L, int R);
 // k_entry_noalloc.cu: the navigating node using a fixed file-scope device array as scratch.
 int64_t entry_noalloc_need(int64_t n, int d);      // doubles of scratch a call needs
 int64_t entry_noalloc_capacity();                  // doubles the array holds

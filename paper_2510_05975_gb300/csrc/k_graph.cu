@@ -15,6 +15,8 @@
 #include "launch_count.h"
 #include "cng_internal.h"
 #include "device_common.cuh"
+#include "prune_rule.cuh"
+#include "prune_tc.h"
 
 namespace cng {
 
@@ -25,55 +27,6 @@ constexpr int PR_VMAX = 2048;                 // merged-list capacity
 constexpr int PR_STAGE_BYTES = 96 * 1024;     // candidate vectors staged in shared memory
 constexpr int PR_MERGE_STAGE_BYTES = 64 * 1024;
 
-struct RuleArgs {
-  float alpha32, t32, band;
-  double alpha64, t64;
-  int R;   // out-degree bound
-  int rs;  // row stride of the final adjacency (R + connectivity slots)
-  // adaptive pruning (Alg. 4): alpha_i = alpha0 + i * dalpha for i = 0 .. imax; imax < 0: fixed
-  double alpha0, dalpha, tau64;
-  int imax;
-};
-
-// The rule at step i of Alg. 4, in the oracle's operation order (no contraction).
-CNG_DEV RuleArgs rule_step(const RuleArgs& ra, int i) {
-  RuleArgs r = ra;
-  r.alpha64 = __dadd_rn(ra.alpha0, __dmul_rn((double)i, ra.dalpha));
-  r.t64 = __dmul_rn(__dadd_rn(r.alpha64, 1.0), ra.tau64);
-  r.alpha32 = (float)r.alpha64;
-  r.t32 = (float)r.t64;
-  return r;
-}
-
-// Alg. 2 with the fixed alpha, or Alg. 4: sweeps with alpha_0, alpha_1, ... until the kept set
-// holds at least R/2 points (its first R are kept) or alpha_max was tried.  `sweep(rule)` runs
-// one Alg. 2 pass and returns |S| (uniform over the CTA).  *steps receives the last i.
-template <typename F>
-CNG_DEV int prune_with_rule(const RuleArgs& ra, F&& sweep, int* steps) {
-  int ns = 0, i = 0;
-  for (;; ++i) {
-    ns = sweep(ra.imax >= 0 ? rule_step(ra, i) : ra);
-    if (ra.imax < 0 || 2 * ns >= ra.R || i >= ra.imax) break;
-  }
-  *steps = ra.imax >= 0 ? i : 0;
-  return ns;
-}
-
-static RuleArgs rule_args(double alpha, double tau, int R, float band, int rs, const AlphaGrid& g) {
-  RuleArgs ra;
-  ra.rs = rs;
-  ra.alpha64 = alpha;
-  ra.t64 = (alpha + 1.0) * tau;
-  ra.alpha32 = (float)alpha;
-  ra.t32 = (float)ra.t64;
-  ra.band = band;
-  ra.R = R;
-  ra.alpha0 = g.alpha0;
-  ra.dalpha = g.dalpha;
-  ra.tau64 = tau;
-  ra.imax = g.imax;
-  return ra;
-}
 
 CNG_DEV float part_sqdist_ss(const float* __restrict__ a, const float* __restrict__ b, int dpad,
                              int g) {
@@ -580,6 +533,9 @@ cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dp
                              double tau, const AlphaGrid& ag, int R, float band, int32_t* fwd, int32_t* fdeg,
                              Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s) {
   RuleArgs ra = rule_args(alpha, tau, R, band, R, ag);
+  if (gram_prune_ok(u8, u8_words, L, R))  // 8-bit rows, lists of <= 128: Gram tile on tcgen05
+    return launch_prune_gram_u8(u8, u8_words, xs, dtype, n, d, dpad, cand, cdist, L, ra, fwd, fdeg,
+                                ctr, s);
   if (dtype == CNG_F32 ? launch_prune_u8(u8, u8_words, (const float*)xs, n, d, dpad, cand, cdist, L,
                                          ra, fwd, fdeg, ctr, s)
                        : launch_prune_u8(u8, u8_words, (const __half*)xs, n, d, dpad, cand, cdist,
@@ -1147,7 +1103,8 @@ static cudaError_t merge_t(const uint8_t* U, int dw, const void* xs, int64_t n, 
                            const int32_t* fwd, const int32_t* fdeg, const int64_t* off,
                            const int32_t* inl, const RuleArgs& ra, int exact, int32_t* adj,
                            int32_t* deg, Counters* ctr, int32_t* big_list,
-                           unsigned char* big_scratch, int big_cap, int grid, cudaStream_t s) {
+                           unsigned char* big_scratch, int big_cap, int grid,
+                           const MergeScratch& ms, cudaStream_t s) {
   const int dl4 = dpad % 32 == 0 ? dpad / 32 : 0;
   constexpr bool half = sizeof(T) == 2;
   if constexpr (!BIG) {
@@ -1155,11 +1112,20 @@ static cudaError_t merge_t(const uint8_t* U, int dw, const void* xs, int64_t n, 
       const int g1 = (int)std::min<int64_t>(n, (int64_t)num_sms() * 16);
       const int g2 = num_sms() * 4;
       int32_t* mid_list = big_list + n;
+      // first pass (sets of <= 128) on the tcgen05 Gram tile when the rule fits it
+      const bool gram = gram_prune_ok(U, dw, 128, ra.R);
 #define CNG_MU(DWV)                                                                                \
   if (dw == DWV) {                                                                                 \
-    count_launch();                                                                                \
-    merge_u8_kernel<T, DWV, 128><<<g1, 128, 0, s>>>(U, (const T*)xs, n, d, dpad, fwd, fdeg, off,    \
-                                                    inl, ra, adj, deg, ctr, mid_list, big_list);   \
+    if (gram) {                                                                                    \
+      cudaError_t e = launch_merge_gram_u8(U, dw, xs, sizeof(T) == 4 ? CNG_F32 : CNG_F16, n, d,    \
+                                           dpad, fwd, fdeg, off, inl, ra, adj, deg, ctr, mid_list, \
+                                           ms, s);                                                 \
+      if (e != cudaSuccess) return e;                                                              \
+    } else {                                                                                       \
+      count_launch();                                                                              \
+      merge_u8_kernel<T, DWV, 128><<<g1, 128, 0, s>>>(U, (const T*)xs, n, d, dpad, fwd, fdeg, off,  \
+                                                      inl, ra, adj, deg, ctr, mid_list, big_list); \
+    }                                                                                              \
     count_launch();                                                                                \
     merge_u8_kernel<T, DWV, 256><<<g2, 256, 0, s>>>(U, (const T*)xs, n, d, dpad, fwd, fdeg, off,    \
                                                     inl, ra, adj, deg, ctr, mid_list, big_list);   \
@@ -1195,14 +1161,14 @@ cudaError_t launch_merge(const void* xs, int dtype, int64_t n, int d, int dpad,
                          const int32_t* inl, double alpha, double tau, const AlphaGrid& ag,
                          int R, float band, int exact, int32_t* adj, int32_t* deg, int rs,
                          Counters* ctr, int32_t* big_list, const uint8_t* u8, int u8_words,
-                         cudaStream_t s) {
+                         const MergeScratch& ms, cudaStream_t s) {
   RuleArgs ra = rule_args(alpha, tau, R, band, rs, ag);
   int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
   return dtype == CNG_F32
              ? merge_t<float, false>(u8, u8_words, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
-                                     adj, deg, ctr, big_list, nullptr, 0, grid, s)
+                                     adj, deg, ctr, big_list, nullptr, 0, grid, ms, s)
              : merge_t<__half, false>(u8, u8_words, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
-                                      adj, deg, ctr, big_list, nullptr, 0, grid, s);
+                                      adj, deg, ctr, big_list, nullptr, 0, grid, ms, s);
 }
 
 cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dpad,
@@ -1215,9 +1181,10 @@ cudaError_t launch_merge_big(const void* xs, int dtype, int64_t n, int d, int dp
   (void)nbig;
   return dtype == CNG_F32
              ? merge_t<float, true>(nullptr, 0, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj,
-                                    deg, ctr, big_list, scratch, big_cap, grid, s)
+                                    deg, ctr, big_list, scratch, big_cap, grid, MergeScratch{}, s)
              : merge_t<__half, true>(nullptr, 0, xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact,
-                                     adj, deg, ctr, big_list, scratch, big_cap, grid, s);
+                                     adj, deg, ctr, big_list, scratch, big_cap, grid, MergeScratch{},
+                                     s);
 }
 
 }  // namespace cng

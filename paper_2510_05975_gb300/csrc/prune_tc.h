@@ -1,0 +1,28 @@
+// prune_tc.h -- tensor-core Alg. 2 for 8-bit integer rows (k_prune_tc.cu): the K4 prune of
+// lists of up to 128 candidates and the first (<= 128-entry) pass of the K6 merge.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cng_internal.h"
+#include "prune_rule.cuh"
+
+namespace cng {
+
+// K4 on the Gram tile: fwd / fdeg as launch_prune_fwd writes them.
+cudaError_t launch_prune_gram_u8(const uint8_t* U, int dw, const void* xs, int dtype, int64_t n,
+                                 int d, int dpad, const int32_t* cand, const float* cdist, int L,
+                                 const RuleArgs& ra, int32_t* fwd, int32_t* fdeg, Counters* ctr,
+                                 cudaStream_t s);
+
+// K6 first pass on the Gram tile: merged sets of up to 128 entries; larger ones are appended to
+// mid_list (count in ctr->nmid) for the 256-entry pass.  With the fixed rule and scratch given
+// (ms.mlist non-null) the sets are listed first and re-pruned by the pipelined Gram kernel.
+cudaError_t launch_merge_gram_u8(const uint8_t* U, int dw, const void* xs, int dtype, int64_t n,
+                                 int d, int dpad, const int32_t* fwd, const int32_t* fdeg,
+                                 const int64_t* off, const int32_t* inl, const RuleArgs& ra,
+                                 int32_t* adj, int32_t* deg, Counters* ctr, int32_t* mid_list,
+                                 const MergeScratch& ms, cudaStream_t s);
+
+}  // namespace cng

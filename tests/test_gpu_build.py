@@ -340,3 +340,68 @@ def test_screen_autotuner_picks_a_variant():
     idx, st2 = cng.cng_build(X, alpha=1.2, R=32, L=128, keep_lists=True, screen_variant=1)
     assert np.array_equal(cand_a, host(cng.cng_lists(idx)[0]))
     cng.cng_free(idx)
+
+
+def _int_clusters(n, d, seed, k=20):
+    """Integer coordinates in 0..255 around k integer centres (8-bit rows, exact distances)."""
+    rng = np.random.default_rng(seed)
+    c = rng.integers(64, 192, (k, d))
+    X = c[rng.integers(0, k, n)] + np.rint(rng.normal(0.0, 20.0, (n, d)))
+    return np.clip(X, 0, 255).astype(np.float32)
+
+
+@pytest.mark.parametrize("d,n,R,L,alpha,tau,seed", [
+    (20, 2500, 16, 64, 1.2, 0.0, 1),     # 8-bit rows of 8 words: K = 32
+    (64, 2500, 24, 100, 1.2, 0.3, 2),    # 16 words, tau > 0, list length not a multiple of 32
+    (96, 2000, 32, 128, 1.3, 0.0, 3),    # 24 words: K = 96 (a partial second K atom)
+    (128, 3001, 64, 128, 1.2, 0.0, 4),   # 32 words, R = 64
+    (128, 2000, 32, 37, 1.0, 0.0, 5),    # a short ragged list, alpha = 1
+])
+def test_gram_prune_matches_oracle(d, n, R, L, alpha, tau, seed):
+    """Integer data through the tensor-core Gram-tile prune and merge (phase 2b and phase 3):
+    lists and graph identical to the oracle's."""
+    need_gpu()
+    cng = lib()
+    X = _int_clusters(n, d, seed)
+    idx, st = cng.cng_build(tensor(X), alpha=alpha, R=R, L=L, tau=tau, keep_lists=True)
+    assert st["prune_path"] == 2
+    G = oracle.build_graph(X, alpha, tau, R, L)
+    _check_graph(X, G, idx, cng, R, L)
+    cng.cng_free(idx)
+
+
+def test_gram_prune_lattice_ties():
+    """Lattice points (coordinates 0..2 in 24 dimensions, 100 of them duplicated) with alpha = 1:
+    many pairs fall exactly on the rule's boundary D(p,v) = D(u,v) and duplicates sit at
+    D(p,v) = 0, so the Gram tile's near-tie masks are exercised; the FP64 re-decisions give the
+    oracle's lists and graph."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(11)
+    X = rng.integers(0, 3, (1400, 24))
+    X = np.concatenate([X, X[:100]]).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.0, R=12, L=48, keep_lists=True)
+    assert st["prune_path"] == 2
+    G = oracle.build_graph(X, 1.0, 0.0, 12, 48)
+    _check_graph(X, G, idx, cng, 12, 48)
+    assert st["rule_ties"] > 0
+    cng.cng_free(idx)
+
+
+def test_gram_merge_with_a_hub():
+    """A hub with 700 near points keeps them all in its merged set (beyond the Gram tile's 128
+    and the 256-entry pass), beside ordinary nodes of the Gram pass: graph equals the oracle's."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(12)
+    d = 32
+    hub = np.full((1, d), 128)
+    near = 128 + rng.integers(-3, 4, (700, d))
+    far = rng.integers(0, 256, (800, d))
+    X = np.concatenate([hub, near, far]).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=16, L=64, keep_lists=True)
+    assert st["prune_path"] == 2
+    G = oracle.build_graph(X, 1.2, 0.0, 16, 64)
+    assert st["merge_max_list"] > 256
+    _check_graph(X, G, idx, cng, 16, 64)
+    cng.cng_free(idx)
