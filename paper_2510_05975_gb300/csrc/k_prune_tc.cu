@@ -255,6 +255,31 @@ CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restric
     uint32_t kc = 0u;
     bool full = false;
     uint32_t live_m = __ballot_sync(FULL, alive);
+    if (!__any_sync(FULL, alive && btc != 0u)) {
+      // no near-tie inside the chunk: transpose the chunk's masks (prb[b] = the entries b prunes)
+      // and run the greedy on bits, all lanes alike
+      uint32_t prb[32];
+#pragma unroll
+      for (int b = 0; b < 32; ++b) prb[b] = __ballot_sync(FULL, (bpc >> b) & 1u);
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        if ((live_m >> b) & 1u) {
+          kc |= 1u << b;
+          live_m &= ~prb[b];
+        }
+      }
+      const int room = r.R - ns;
+      if (__popc(kc) >= room) {  // S fills up inside this chunk: its first `room` members
+        uint32_t t = kc;
+        for (int i = 1; i < room; ++i) t &= t - 1u;  // lowest set bit of t: the room-th member
+        const int pos = __ffs(t) - 1;
+        kc &= pos == 31 ? 0xffffffffu : ((2u << pos) - 1u);
+        full = true;
+      }
+      if ((kc >> lane) & 1u) S[ns + __popc(kc & ((1u << lane) - 1u))] = sm.ids[c * 32 + lane];
+      ns += __popc(kc);
+      live_m = 0u;
+    }
     while (live_m) {
       const int b = __ffs(live_m) - 1;
       kc |= 1u << b;

@@ -11,10 +11,6 @@
 namespace cng {
 namespace tcx {
 
-// wait iterations before a wait is declared expired (each try_wait may suspend the thread for
-// a system-dependent time)
-constexpr uint32_t SPIN = 1u << 20;
-
 CNG_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 CNG_DEV void mbar_init(uint64_t* b, uint32_t count) {
@@ -32,11 +28,25 @@ CNG_DEV bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps until the phase completes or about
+// `ns` nanoseconds pass, instead of spinning on issue slots other warps need.
+CNG_DEV bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint32_t SLEEP_NS = 20000;
+constexpr uint32_t SLEEP_TRIES = 1u << 16;  // a wait gives up after about 1.3 s
+
 // Warp-uniform bounded wait: the warp leaves together (before .sync.aligned TMEM loads).
 // Returns false if the phase did not complete within the bound.
 CNG_DEV bool mbar_wait_warp(uint64_t* b, uint32_t parity) {
-  for (uint32_t i = 0; i < SPIN; ++i)
-    if (__all_sync(FULL, mbar_try(b, parity))) return true;
+  for (uint32_t i = 0; i < SLEEP_TRIES; ++i)
+    if (__all_sync(FULL, mbar_try_sleep(b, parity, SLEEP_NS))) return true;
   return false;
 }
 
