@@ -304,6 +304,12 @@ def hbm_kernels(w, X, st, ndc_sum, hops_sum, search_ms, peak, src):
         " + n L (id, dist) + n R ids written")
     put("merge", n * (2 * R * prow * 2 + 2 * R * 4 + (R + 8) * 4), st["ms_merge"],
         "each phase-2 edge's row read from both ends, twice (order, sweep) + lists")
+    if st.get("prune_path") == 2:  # candidate-pair Gram tiles on the tensor cores (8-bit rows)
+        k = (d + 15) // 16 * 16
+        gram = 2.0 * 128 * 128 * k  # one 128 x 128 x K tile per list
+        for name, lists in (("prune", n), ("merge", st["merge_repruned"])):
+            out[name]["gram_tiles"] = int(lists)
+            out[name]["gram_tflops"] = lists * gram / (out[name]["ms"] / 1e3) / 1e12
     put("search_fixed", ndc_sum * prow + hops_sum * (R + 8) * 4 + w.nq * (d * 4 + w.k * 8),
         search_ms, ("sum NDC rows of d bytes (8-bit rows)" if u8 else "sum NDC rows of 4 dpad B") +
         " + sum hops adjacency rows + queries + results")
