@@ -227,6 +227,8 @@ struct KnnInputs {
   const int32_t* perm;
   int wave_start;
   int variant = -1;  // tensor-core screen pipeline variant (-1: autotuned)
+  const uint8_t* u8 = nullptr;  // 8-bit rows of the points (rows = columns), or null
+  int u8w = 0;
 };
 
 static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist, Counters* ctr,
@@ -294,7 +296,8 @@ static cng_status run_knn(const KnnInputs& in, int32_t* out_ids, float* out_dist
   CK(pool.alloc(&fail_rows, (size_t)in.m));
   CK(pool.alloc(&fail_bound, (size_t)in.m));
   CK(launch_rerank(in.xr, in.xc, in.dtype, in.m, in.d, in.dpad, sids, sthr, in.Lp, in.L, sm,
-                   in.band, in.exact, out_ids, out_dist, fail_rows, fail_bound, ctr, s));
+                   in.band, in.exact, out_ids, out_dist, fail_rows, fail_bound, ctr, in.u8, in.u8w,
+                   s));
   CK(launch_rescan(in.xr, in.xc, in.dtype, in.m, in.n, in.d, in.dpad, in.self_excl, in.L,
                    fail_rows, fail_bound, ctr, out_ids, out_dist, s));
   tm.mark();
@@ -624,6 +627,16 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     st = apply_order(pool, &pr, dtype, n, d, dpad, kpad, &ki, &ms_order, s);
     if (st != CNG_OK) return st;
   }
+  // integer data spanning <= 255: 8-bit rows for exact integer pair distances in the rerank
+  // (K2), prune (K4) and merge (K6)
+  uint8_t* u8 = nullptr;
+  const int u8w = u8_rows_ok(pr.st, d) ? u8_words(d) : 0;
+  if (u8w) {
+    CK(pool.alloc(&u8, (size_t)n * u8w * 4));
+    CK(launch_to_u8(pr.xs, dtype, n, d, dpad, key_to_float(pr.st.vmin_key), u8w, u8, s));
+    ki.u8 = u8;
+    ki.u8w = u8w;
+  }
   double ms_screen = 0, ms_rerank = 0, ms_cand = 0;
   const bool beam = P.candidates == CNG_CAND_BEAM;
   const int K0 = P.knn_K > 0 ? P.knn_K : 200;
@@ -656,13 +669,6 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   }
   // screening operands are no longer needed
   if (pr.tc) { cudaFree(pr.tc); pool.release(pr.tc); pr.tc = nullptr; }
-  // integer data spanning <= 255: 8-bit rows for exact integer pair distances in K4 / K6
-  uint8_t* u8 = nullptr;
-  const int u8w = u8_rows_ok(pr.st, d) ? u8_words(d) : 0;
-  if (u8w) {
-    CK(pool.alloc(&u8, (size_t)n * u8w * 4));
-    CK(launch_to_u8(pr.xs, dtype, n, d, dpad, key_to_float(pr.st.vmin_key), u8w, u8, s));
-  }
   if (beam) {
     // Alg. 3 phase 2 (Sec. 4.1): beam search for every point on G0 from the navigating node;
     // its first L + 1 results hold the L closest visited points other than p

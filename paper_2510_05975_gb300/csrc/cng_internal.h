@@ -88,11 +88,13 @@ cudaError_t launch_knn_simt(const void* xr, int64_t m, const void* xc, int64_t n
                             int dpad, int Lp, int self_excl, uint64_t* rowbuf, int cpl,
                             int grid, int32_t* ids, uint32_t* thr, uint32_t* status,
                             cudaStream_t s);
+// u8 (8-bit rows of the points, u8w words each) may be null; when given for rows = columns of
+// exact integer data the distances come from the 8-bit rows.
 cudaError_t launch_rerank(const void* xr, const void* xc, int dtype, int64_t m, int d, int dpad,
                           const int32_t* sids, const uint32_t* sthr, int Lp, int L,
                           const ScreenModel& sm, float band, int exact, int32_t* out_ids,
                           float* out_dist, int32_t* fail_rows, float* fail_bound, Counters* ctr,
-                          cudaStream_t s);
+                          const uint8_t* u8, int u8w, cudaStream_t s);
 cudaError_t launch_rescan(const void* xr, const void* xc, int dtype, int64_t m, int64_t n, int d,
                           int dpad, int self_excl, int L, const int32_t* fail_rows,
                           const float* fail_bound, Counters* ctr, int32_t* out_ids,

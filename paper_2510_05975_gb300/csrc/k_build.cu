@@ -559,6 +559,58 @@ CNG_DEV void wide_sqdist2(const float4 (&qr)[NQ], const float* __restrict__ y0,
   r1 = b;
 }
 
+// Sorts a row's keys [0, Lp) (FP32 D^2, id), then certifies the list: every unscreened point
+// is provably farther than the L-th candidate.  Rows that fail are queued for the exact rescan
+// (returns false, uniform over the warp).
+CNG_DEV bool rerank_sort_certify(uint64_t* keys, int P2, int cnt, int64_t row, int Lp, int L,
+                                 const uint32_t* __restrict__ sthr, const ScreenModel& sm,
+                                 float band, int exact, int32_t* fail_rows, float* fail_bound,
+                                 Counters* ctr, int lane) {
+  for (int t = Lp + lane; t < P2; t += 32) keys[t] = ~0ull;
+  __syncwarp();
+  warp_bitonic(keys, P2, lane);
+  bool ok = true;
+  const uint32_t th = sthr[row];
+  if (th != 0xffffffffu && cnt >= L) {
+    const float dL = key_dist(keys[L - 1]);
+    const float sc = fkey_inv(th);
+    if (sm.kind == 0) {
+      float lb = sc * (1.f - sm.rel_err);
+      ok = exact ? (sc > dL) : (lb > dL * (1.f + 2.f * band));
+    } else {
+      // scores are in units of scale^2 (operands scale * x, scale a power of two): compare
+      // with dL scaled exactly
+      const float nx = sm.nb[row];
+      const float dLs = dL * sm.scale2;
+      if (exact) {
+        ok = (sc + nx) > dLs;
+      } else {
+        float nrm = sqrtf(fmaxf(nx, 0.f));
+        float eacc = sm.acc_err * (nrm + sm.normmax) * (nrm + sm.normmax);
+        float db = sqrtf(fmaxf(sc + nx - eacc, 0.f)) - (sm.rb[row] + sm.rbmax);
+        ok = db > 0.f && db * db > dLs * (1.f + 2.f * band);
+      }
+    }
+  }
+  if (cnt < L) ok = false;
+  if (!ok && lane == 0) {
+    int slot = atomicAdd(&ctr->nfail, 1);
+    fail_rows[slot] = (int32_t)row;
+    fail_bound[slot] = cnt >= L ? key_dist(keys[L - 1]) * (1.f + 4.f * band) : INFINITY;
+  }
+  return ok;
+}
+
+CNG_DEV void rerank_write(const uint64_t* keys, int64_t row, int L, int32_t* __restrict__ out_ids,
+                          float* __restrict__ out_dist, int lane) {
+  for (int t = lane; t < L; t += 32) {
+    uint64_t k = keys[t];
+    out_ids[row * L + t] = key_id(k);
+    out_dist[row * L + t] = sqrtf(key_dist(k));
+  }
+  __syncwarp();
+}
+
 template <typename T, int NQ>
 __global__ void __launch_bounds__(RR_WARPS * 32)
 rerank_kernel(const T* __restrict__ Xr, const T* __restrict__ Xc, int64_t m, int d, int dpad,
@@ -614,60 +666,92 @@ rerank_kernel(const T* __restrict__ Xr, const T* __restrict__ Xc, int64_t m, int
         cnt += __popc(v);
       }
     }
-    for (int t = Lp + lane; t < P2; t += 32) keys[t] = ~0ull;
-    __syncwarp();
-    warp_bitonic(keys, P2, lane);
-    // certification: every unscreened point is provably farther than the L-th candidate
-    bool ok = true;
-    const uint32_t th = sthr[row];
-    if (th != 0xffffffffu && cnt >= L) {
-      const float dL = key_dist(keys[L - 1]);
-      const float sc = fkey_inv(th);
-      if (sm.kind == 0) {
-        float lb = sc * (1.f - sm.rel_err);
-        ok = exact ? (sc > dL) : (lb > dL * (1.f + 2.f * band));
-      } else {
-        // scores are in units of scale^2 (operands scale * x, scale a power of two): compare
-        // with dL scaled exactly
-        const float nx = sm.nb[row];
-        const float dLs = dL * sm.scale2;
-        if (exact) {
-          ok = (sc + nx) > dLs;
-        } else {
-          float nrm = sqrtf(fmaxf(nx, 0.f));
-          float eacc = sm.acc_err * (nrm + sm.normmax) * (nrm + sm.normmax);
-          float db = sqrtf(fmaxf(sc + nx - eacc, 0.f)) - (sm.rb[row] + sm.rbmax);
-          ok = db > 0.f && db * db > dLs * (1.f + 2.f * band);
-        }
-      }
-    }
-    if (cnt < L) ok = false;
-    if (!ok) {
-      if (lane == 0) {
-        int slot = atomicAdd(&ctr->nfail, 1);
-        fail_rows[slot] = (int32_t)row;
-        fail_bound[slot] = cnt >= L ? key_dist(keys[L - 1]) * (1.f + 4.f * band) : INFINITY;
-      }
+    if (!rerank_sort_certify(keys, P2, cnt, row, Lp, L, sthr, sm, band, exact, fail_rows, fail_bound,
+                             ctr, lane))
       continue;
-    }
     if (!exact) ties += fix_runs_warp(keys, cnt, L, Xr + row * dpad, Xc, dpad, d, band, d64, rdesc, lane,
                                       &ctr->status);
-    for (int t = lane; t < L; t += 32) {
-      uint64_t k = keys[t];
-      out_ids[row * L + t] = key_id(k);
-      out_dist[row * L + t] = sqrtf(key_dist(k));
-    }
-    __syncwarp();
+    rerank_write(keys, row, L, out_ids, out_dist, lane);
   }
   if (lane == 0 && ties) atomicAdd(&ctr->order_ties, ties);
   (void)err_max;
+}
+
+// 8-bit rows (integer data spanning <= 255, rows and columns the same points): D^2 as the exact
+// integer sum of dp4a(|u - v|, |u - v|) over 16-byte chunks, 8 lanes per candidate (one
+// coalesced 128-byte row read per group) -- the value the FP32 difference form gives for such
+// data, from a quarter of the bytes.  (One candidate per lane with the whole row per lane was
+// slower: 11.2 against 9.0 ms at 1M x 128.)
+template <int DW>
+__global__ void __launch_bounds__(RR_WARPS * 32)
+rerank_u8_kernel(const uint8_t* __restrict__ U, int64_t m, const int32_t* __restrict__ sids,
+                 const uint32_t* __restrict__ sthr, int Lp, int L, ScreenModel sm, float band,
+                 int32_t* __restrict__ out_ids, float* __restrict__ out_dist,
+                 int32_t* __restrict__ fail_rows, float* __restrict__ fail_bound, Counters* ctr) {
+  constexpr int NC = DW / 4;  // 16-byte chunks per row, <= RR_G
+  static_assert(NC <= RR_G, "one chunk per lane of a group");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P2 = Lp <= 64 ? 64 : (Lp <= 128 ? 128 : (Lp <= 256 ? 256 : 512));
+  uint64_t* keys = reinterpret_cast<uint64_t*>(smem) + warp * RR_P2;
+  const int g = lane % RR_G, grp = lane / RR_G;
+  for (int64_t row = blockIdx.x * (int64_t)RR_WARPS + warp; row < m;
+       row += (int64_t)gridDim.x * RR_WARPS) {
+    const int32_t* ids = sids + row * Lp;
+    const uint4 q = g < NC ? __ldg(reinterpret_cast<const uint4*>(U + row * (DW * 4)) + g)
+                           : make_uint4(0u, 0u, 0u, 0u);
+    int cnt = 0;
+    for (int t0 = 0; t0 < Lp; t0 += 32 / RR_G) {
+      const int t = t0 + grp;
+      const int32_t id = t < Lp ? ids[t] : -1;
+      uint32_t s = 0;
+      if (id >= 0 && g < NC) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(U + (int64_t)id * (DW * 4)) + g);
+        uint32_t a = __vabsdiffu4(q.x, v.x);
+        s = __dp4a(a, a, s);
+        a = __vabsdiffu4(q.y, v.y);
+        s = __dp4a(a, a, s);
+        a = __vabsdiffu4(q.z, v.z);
+        s = __dp4a(a, a, s);
+        a = __vabsdiffu4(q.w, v.w);
+        s = __dp4a(a, a, s);
+      }
+#pragma unroll
+      for (int o = 1; o < RR_G; o <<= 1) s += __shfl_xor_sync(FULL, s, o);
+      if (g == 0 && t < Lp) keys[t] = id >= 0 ? pack_key((float)s, id) : ~0ull;
+      cnt += __popc(__ballot_sync(FULL, g == 0 && t < Lp && id >= 0));
+    }
+    if (!rerank_sort_certify(keys, P2, cnt, row, Lp, L, sthr, sm, band, 1, fail_rows, fail_bound,
+                             ctr, lane))
+      continue;
+    rerank_write(keys, row, L, out_ids, out_dist, lane);
+  }
 }
 
 cudaError_t launch_rerank(const void* xr, const void* xc, int dtype, int64_t m, int d, int dpad,
                           const int32_t* sids, const uint32_t* sthr, int Lp, int L,
                           const ScreenModel& sm, float band, int exact, int32_t* out_ids,
                           float* out_dist, int32_t* fail_rows, float* fail_bound, Counters* ctr,
-                          cudaStream_t s) {
+                          const uint8_t* u8, int u8w, cudaStream_t s) {
+  if (u8 && exact && xr == xc && Lp <= RR_P2) {  // 8-bit rows of the same points
+    const size_t sh8 = RR_WARPS * RR_P2 * 8;
+    const int grid8 = (int)std::min<int64_t>((m + RR_WARPS - 1) / RR_WARPS, (int64_t)num_sms() * 32);
+#define CNG_RU(DW)                                                                                 \
+    if (u8w == DW) {                                                                               \
+      cudaFuncSetAttribute(rerank_u8_kernel<DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                           (int)sh8);                                                              \
+      count_launch();                                                                              \
+      rerank_u8_kernel<DW><<<grid8, RR_WARPS * 32, sh8, s>>>(u8, m, sids, sthr, Lp, L, sm, band,   \
+                                                             out_ids, out_dist, fail_rows,         \
+                                                             fail_bound, ctr);                     \
+      return cudaGetLastError();                                                                   \
+    }
+    CNG_RU(8)
+    CNG_RU(16)
+    CNG_RU(24)
+    CNG_RU(32)
+#undef CNG_RU
+  }
   // rows wider than 256 (FP32 storage, up to 1024): the query slice in registers (wide path)
   const int nq4 = dtype == CNG_F32 && dpad > 256 ? (dpad / 4 + 31) / 32 : 0;
   const int NQ = nq4 == 0 ? 0 : (nq4 <= 4 ? 4 : (nq4 <= 8 ? 8 : 0));
