@@ -388,7 +388,7 @@ def main():
     screen = {"tc": cng.CNG_SCREEN_TC, "tc-bf16": cng.CNG_SCREEN_TC_BF16,
               "fp32": cng.CNG_SCREEN_FP32}[args.screen]
     if args.knn_n:
-        Xs = torch.from_numpy(w.base(args.knn_n).astype(np.float32)).cuda()
+        Xs = torch.from_numpy(w.base(args.knn_n).astype(np.float32)).cuda()  # cng_knn takes FP32
         cng.cng_knn(Xs, w.L, screen=screen)  # warm-up
         torch.cuda.synchronize()
         ids, _, st = cng.cng_knn(Xs, w.L, screen=screen)
@@ -401,7 +401,7 @@ def main():
                           "cert_fail_rows": st["cert_fail_rows"]}), flush=True)
         return
     if args.build_n:
-        Xs = torch.from_numpy(w.base(args.build_n).astype(np.float32)).cuda()
+        Xs = torch.from_numpy(w.base(args.build_n)).cuda()  # the workload's storage type
         beam = args.candidates == "beam"
         for it in range(2):  # warm-up, then the reported build
             idx, st = cng.cng_build(Xs, alpha=w.alpha, R=w.R, L=w.L, screen=screen,

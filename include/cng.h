@@ -147,8 +147,9 @@ typedef struct {
   int32_t screen_stages;      /* stages, row-buffer capacity (entries per row) and checkpoint */
   int32_t screen_cap;         /* lag (windows of 256 column tiles); -1 for the FP32 screen */
   int32_t screen_sync;
-  int32_t prune_path;         /* phase-2b sweep: 0 FP32 rows (SIMT), 1 8-bit rows (dp4a SIMT),
-                                 2 8-bit rows, candidate-pair Gram tile on the tensor cores */
+  int32_t prune_path;         /* phase-2b sweep: 0 float rows (SIMT), 1 8-bit rows (dp4a SIMT),
+                                 2 8-bit rows, candidate-pair Gram tile on the tensor cores,
+                                 3 FP16 rows, Gram tile with certified decision windows */
 } cng_build_stats;
 
 typedef struct cng_index cng_index;

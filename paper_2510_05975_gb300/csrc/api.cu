@@ -746,8 +746,11 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     ag.dalpha = P.dalpha;
     ag.imax = (int)std::floor((P.alpha_max - P.alpha0) / P.dalpha + 0.5);
   }
+  float* half_norms = nullptr;  // FP16 rows on the Gram tile: |x|^2 per point
+  if (!u8 && gram_prune_f16_ok(dtype, dpad, L, R, P.adaptive != 0))
+    CK(pool.alloc(&half_norms, (size_t)n));
   CK(launch_prune_fwd(pr.xs, dtype, n, d, dpad, cand, cdist, L, P.alpha, P.tau, ag, R, band, fwd, fdeg,
-                      ctr, u8, u8w, s));
+                      ctr, u8, u8w, half_norms, s));
   tm.mark();  // 4
   // phase 3: reverse edges + lazy pruning
   int32_t *indeg, *cursor, *inl, *adj, *deg;
@@ -960,7 +963,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     stats->screen_stages = tshape.stages;
     stats->screen_cap = tshape.cap;
     stats->screen_sync = tshape.sync_d;
-    stats->prune_path = gram_prune_ok(u8, u8w, L, R) ? 2 : (u8 && L <= 256 ? 1 : 0);
+    stats->prune_path = gram_prune_ok(u8, u8w, L, R) ? 2 : (u8 && L <= 256 ? 1 : (half_norms ? 3 : 0));
   }
   *out = ix;
   return CNG_OK;

@@ -99,11 +99,13 @@ cudaError_t launch_rescan(const void* xr, const void* xc, int dtype, int64_t m, 
                           int dpad, int self_excl, int L, const int32_t* fail_rows,
                           const float* fail_bound, Counters* ctr, int32_t* out_ids,
                           float* out_dist, cudaStream_t s);
+// half_norms: scratch of n floats for the FP16 Gram-tile prune, or null.
 cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* cand, const float* cdist, int L, double alpha,
                              double tau, const AlphaGrid& ag, int R, float band, int32_t* fwd,
                              int32_t* fdeg,
-                             Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s);
+                             Counters* ctr, const uint8_t* u8, int u8_words, float* half_norms,
+                             cudaStream_t s);
 // 8-bit rows (integer data spanning <= 255): words per row for d (0: unsupported), conversion.
 int u8_words(int d);
 cudaError_t launch_to_u8(const void* xs, int dtype, int64_t n, int d, int dpad, float vmin, int dw,
@@ -150,6 +152,8 @@ int num_sms();
 // True when the tensor-core Gram-tile prune (k_prune_tc.cu) takes lists of L entries with
 // out-degree bound R on 8-bit rows of dw 32-bit words (U non-null).
 bool gram_prune_ok(const uint8_t* U, int dw, int L, int R);
+// The same for FP16 rows (dtype CNG_F16, dpad 64 or 128, fixed alpha).
+bool gram_prune_f16_ok(int dtype, int dpad, int L, int R, bool adaptive);
 // k_entry_noalloc.cu: the navigating node using a fixed file-scope device array as scratch.
 int64_t entry_noalloc_need(int64_t n, int d);      // doubles of scratch a call needs
 int64_t entry_noalloc_capacity();                  // doubles the array holds

@@ -531,11 +531,14 @@ static bool launch_prune_reg(const T* xs, int64_t n, int d, int dpad, const int3
 cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dpad,
                              const int32_t* cand, const float* cdist, int L, double alpha,
                              double tau, const AlphaGrid& ag, int R, float band, int32_t* fwd, int32_t* fdeg,
-                             Counters* ctr, const uint8_t* u8, int u8_words, cudaStream_t s) {
+                             Counters* ctr, const uint8_t* u8, int u8_words, float* half_norms,
+                             cudaStream_t s) {
   RuleArgs ra = rule_args(alpha, tau, R, band, R, ag);
   if (gram_prune_ok(u8, u8_words, L, R))  // 8-bit rows, lists of <= 128: Gram tile on tcgen05
     return launch_prune_gram_u8(u8, u8_words, xs, dtype, n, d, dpad, cand, cdist, L, ra, fwd, fdeg,
                                 ctr, s);
+  if (half_norms && gram_prune_f16_ok(dtype, dpad, L, R, ag.imax >= 0))  // FP16 rows, same tile
+    return launch_prune_gram_f16(xs, n, d, dpad, cand, cdist, L, ra, fwd, fdeg, half_norms, ctr, s);
   if (dtype == CNG_F32 ? launch_prune_u8(u8, u8_words, (const float*)xs, n, d, dpad, cand, cdist, L,
                                          ra, fwd, fdeg, ctr, s)
                        : launch_prune_u8(u8, u8_words, (const __half*)xs, n, d, dpad, cand, cdist,

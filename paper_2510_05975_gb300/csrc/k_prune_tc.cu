@@ -143,8 +143,11 @@ CNG_DEV void issue_gram(const unsigned char* A, uint32_t tmem, uint64_t* bar) {
 
 // ---- epilogue: masks ----------------------------------------------------------------------
 // Thread j decides the pairs (i, j), i < j < V, from row j of G.  check: verify G_jj = |u_j|^2.
+// With cE > 0 (FP16 rows: G from FP32 accumulation) D^2 carries an error of at most
+// cE (|v_i|^2 + |v_j|^2); the window then adds alpha^2 times that and 2^-22 of the magnitudes, and
+// the near-tie mask marks the pairs to decide again from the FP32 difference form (then FP64).
 CNG_DEV void gram_masks(const GramList& sm, uint32_t tmem, int V, const RuleArgs& r, int warp, int lane,
-                        uint32_t* check_status) {
+                        uint32_t* check_status, float cE = 0.f) {
   const int j = warp * 32 + lane;
   const bool live = j < V;
   const float dj = live ? sm.dist[j] : 0.f;
@@ -155,6 +158,7 @@ CNG_DEV void gram_masks(const GramList& sm, uint32_t tmem, int V, const RuleArgs
   const float T = tj * tj;
   const float w = 2.f * r.band * dj * tj;
   const float A2 = r.alpha32 * r.alpha32;
+  const float A2cE = A2 * cE;
   const int nch = min(warp + 1, (V + 31) >> 5);  // warp-uniform; chunks past the row's own unused
   bool bad = false;
 #pragma unroll 1
@@ -170,10 +174,12 @@ CNG_DEV void gram_masks(const GramList& sm, uint32_t tmem, int V, const RuleArgs
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const float g = v[k];
-        const float d2 = (nj - g) + (ni[k] - g);  // exact: integers below 2^24
+        const float d2 = (nj - g) + (ni[k] - g);  // exact for 8-bit rows: integers below 2^24
         const float e = fmaf(-A2, d2, T);
-        pb |= e > w ? (1u << (h * 16 + k)) : 0u;
-        tb |= fabsf(e) <= w ? (1u << (h * 16 + k)) : 0u;
+        float win = w;
+        if (cE > 0.f) win = fmaf(2.384185791015625e-7f, fmaf(A2, fabsf(d2), T), fmaf(A2cE, nj + ni[k], w));
+        pb |= e > win ? (1u << (h * 16 + k)) : 0u;
+        tb |= fabsf(e) <= win ? (1u << (h * 16 + k)) : 0u;
       }
       if (diag) {
 #pragma unroll
@@ -185,7 +191,7 @@ CNG_DEV void gram_masks(const GramList& sm, uint32_t tmem, int V, const RuleArgs
       sm.bp[j][c] = cls == 0 ? (pb & valid) : 0u;
       sm.bt[j][c] = cls == 0 ? (tb & valid) : (cls == 2 ? valid : 0u);
     }
-    if (check_status && diag) bad = live && gjj != nj;
+    if (check_status && diag && cE == 0.f) bad = live && gjj != nj;
   }
   if (bad) atomicOr(check_status, ST_SCREEN);
 }
@@ -200,6 +206,37 @@ CNG_DEV bool prunes64(const GramList& sm, const T* __restrict__ Xs, int d, int d
   return rule64(Dpj, Dij, r.alpha64, r.t64);
 }
 
+// A pair the masks left open.  Exact D^2 (8-bit rows): a near-tie, re-decided in FP64.  FP16
+// rows: D(v_i, v_j) from the FP32 difference form (4 accumulators, chain <= d / 4 + 3), then
+// the rule with the relative band, FP64 inside it.  Counts the FP64 decisions.
+template <typename T, bool EXACT>
+CNG_DEV bool decide_pair(const GramList& sm, const T* __restrict__ Xs, int d, int dpad, int64_t p,
+                         int i, int j, const RuleArgs& r, unsigned long long& ties) {
+  if constexpr (!EXACT) {
+    const T* xi = Xs + (int64_t)sm.ids[i] * dpad;
+    const T* xj = Xs + (int64_t)sm.ids[j] * dpad;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int k = 0;
+    for (; k + 4 <= d; k += 4) {
+      float t;
+      t = to_f(xi[k]) - to_f(xj[k]); s0 = fmaf(t, t, s0);
+      t = to_f(xi[k + 1]) - to_f(xj[k + 1]); s1 = fmaf(t, t, s1);
+      t = to_f(xi[k + 2]) - to_f(xj[k + 2]); s2 = fmaf(t, t, s2);
+      t = to_f(xi[k + 3]) - to_f(xj[k + 3]); s3 = fmaf(t, t, s3);
+    }
+    for (; k < d; ++k) {
+      const float t = to_f(xi[k]) - to_f(xj[k]);
+      s0 = fmaf(t, t, s0);
+    }
+    const float Dij = sqrtf((s0 + s1) + (s2 + s3));
+    const float rhs = r.alpha32 * Dij + r.t32;
+    const float dj = sm.dist[j];
+    if (!near_tie(dj, rhs, r.band)) return dj > rhs;
+  }
+  ++ties;
+  return prunes64(sm, Xs, d, dpad, p, i, j, r);
+}
+
 CNG_DEV uint32_t word(const uint4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 CNG_DEV void set_word(uint4& v, int q, uint32_t x) {
   v.x = q == 0 ? x : v.x;
@@ -210,7 +247,7 @@ CNG_DEV void set_word(uint4& v, int q, uint32_t x) {
 
 // Returns |S| (uniform over the warp); S written to S[].  Entry j's words q of bp / bt cover the
 // entries of chunk q; only q <= j / 32 are read.
-template <typename T>
+template <typename T, bool EXACT = true>
 CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restrict__ Xs, int d, int dpad,
                        int64_t p, const RuleArgs& r, int lane, unsigned long long& ties) {
   uint4 K = make_uint4(0u, 0u, 0u, 0u);  // members of S by chunk (uniform)
@@ -241,9 +278,8 @@ CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restric
             const int b = __ffs(m) - 1;
             if ((bq >> b) & 1u) {
               alive = false;
-            } else {
-              ++ties;
-              if (prunes64(sm, Xs, d, dpad, p, q * 32 + b, j, r)) alive = false;
+            } else if (decide_pair<T, EXACT>(sm, Xs, d, dpad, p, q * 32 + b, j, r, ties)) {
+              alive = false;
             }
             m &= m - 1u;
           }
@@ -293,8 +329,7 @@ CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restric
         if ((bpc >> b) & 1u) {
           alive = false;
         } else if ((btc >> b) & 1u) {
-          ++ties;
-          if (prunes64(sm, Xs, d, dpad, p, c * 32 + b, j, r)) alive = false;
+          if (decide_pair<T, EXACT>(sm, Xs, d, dpad, p, c * 32 + b, j, r, ties)) alive = false;
         }
       }
       live_m = __ballot_sync(FULL, alive) & ~((2u << b) - 1u);
@@ -444,6 +479,7 @@ struct GramJob {
   int out_stride;
   int32_t* out_deg;
   int merge;           // count edges and re-pruned nodes (phase 3)
+  const float* nrm;    // FP16 rows: |x|^2 of every point (FP32, one rounding)
 };
 
 constexpr int GP_THREADS = 160;
@@ -485,6 +521,7 @@ struct RowAhead {
   int V;
   int32_t id;
   float dist;
+  float nrm;  // FP16 rows: |x_id|^2
 };
 
 CNG_DEV int32_t job_point(const GramJob& J, int64_t q) { return J.pts ? J.pts[q] : (int32_t)q; }
@@ -497,10 +534,31 @@ CNG_DEV void job_list(const GramJob& J, RowAhead& r, int tid) {
   }
 }
 
-template <typename T, int DW>
+// FP16 row r of the operand tile straight from global memory: K / 8 16-byte chunks, element k in
+// atom k / 64, chunk (k % 64) / 8 of the row's 128 bytes, position XOR (r % 8).
+template <int K>
+CNG_DEV void stage_row_async(const __half* __restrict__ Xs, int dpad, int32_t id, int r,
+                             unsigned char* A) {
+  const uint4* src = reinterpret_cast<const uint4*>(Xs + (int64_t)id * dpad);
+#pragma unroll
+  for (int c = 0; c < K / 8; ++c)
+    tcx::cp_async16(A + (c >> 3) * (GT_N * 128) + r * 128 + (((c & 7) ^ (r & 7)) << 4), src + c);
+}
+
+// The Gram error coefficient of K-element FP16 rows: |D^2_est - D^2| <= cE (|u|^2 + |v|^2) with
+// products exact, at most K additions at 2^-22 of the magnitudes each in the accumulators, norms
+// rounded once and three FP32 additions forming D^2.
+constexpr float gram_ce(int K) { return (float)(4 * K + 8) * 5.9604644775390625e-8f; }
+
+// HALF = false: 8-bit rows (U, K = 4 DW bytes per row, exact Gram values).  HALF = true: the
+// FP16 point rows themselves (Xs, K = dpad <= 128), copied to the operand tile with cp.async,
+// norms from J.nrm, decisions with the certified window of gram_ce(K).
+template <typename T, int K, bool HALF>
 __global__ void __launch_bounds__(GP_THREADS, 4)
 gram_pipe_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int d, int dpad,
                  GramJob J, RuleArgs ra, Counters* ctr) {
+  constexpr int DW = K / 4;
+  static_assert(!HALF || K <= 128, "FP16 rows of at most two K atoms");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* A = align1024(smem_raw);
   PipeSmem& sm = *reinterpret_cast<PipeSmem*>(A + GT_ABYTES);
@@ -519,36 +577,43 @@ gram_pipe_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int d,
   __syncthreads();
   tcx::fence_after();
   const uint32_t tmem = sm.tmem;
+  const float cE = HALF ? gram_ce(K) : 0.f;
   // this CTA's rows q_k = blockIdx.x + k * gridDim.x, k < K
   const int64_t nq = J.count ? (int64_t)*J.count : J.n;
-  const int64_t K = (int64_t)blockIdx.x < nq ? (nq - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t NK = (int64_t)blockIdx.x < nq ? (nq - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t G = gridDim.x;
   unsigned long long ties = 0, edges = 0;
   uint32_t issued = 0, completed = 0;  // Gram MMAs (meaningful in thread 0)
   if (warp < 4) {
     bool ok = true;
-    RowAhead r1{0, 0, 0, 0.f}, r2{0, 0, 0, 0.f};  // rows k+1 and k+2
-    int32_t p3 = 0;                              // row k+3's point
-    if (K > 0) {  // row 0 staged, its MMA started; rows 1, 2 (lists) and 3 (point) in flight
-      RowAhead r0{job_point(J, blockIdx.x), 0, 0, 0.f};
-      if (K > 1) r1.p = job_point(J, blockIdx.x + G);
-      if (K > 2) r2.p = job_point(J, blockIdx.x + 2 * G);
-      if (K > 3) p3 = job_point(J, blockIdx.x + 3 * G);
+    RowAhead r1{0, 0, 0, 0.f, 0.f}, r2{0, 0, 0, 0.f, 0.f};  // rows k+1 and k+2
+    int32_t p3 = 0;                                        // row k+3's point
+    if (NK > 0) {  // row 0 staged, its MMA started; rows 1, 2 (lists) and 3 (point) in flight
+      RowAhead r0{job_point(J, blockIdx.x), 0, 0, 0.f, 0.f};
+      if (NK > 1) r1.p = job_point(J, blockIdx.x + G);
+      if (NK > 2) r2.p = job_point(J, blockIdx.x + 2 * G);
+      if (NK > 3) p3 = job_point(J, blockIdx.x + 3 * G);
       job_list(J, r0, tid);
-      if (K > 1) job_list(J, r1, tid);
-      if (K > 2) job_list(J, r2, tid);
+      if (NK > 1) job_list(J, r1, tid);
+      if (NK > 2) job_list(J, r2, tid);
       if (tid < r0.V) {
-        uint4 w[DW / 4];
-        load_row<DW>(U, r0.id, w);
         sm.ids[0][tid] = r0.id;
         sm.dist[0][tid] = r0.dist;
-        sm.nrm[0][tid] = (float)row_norm<DW>(w);
-        store_row_f16<DW>(w, tid, A);
+        if constexpr (HALF) {
+          sm.nrm[0][tid] = J.nrm[r0.id];
+          stage_row_async<K>(reinterpret_cast<const __half*>(Xs), dpad, r0.id, tid, A);
+        } else {
+          uint4 w[DW / 4];
+          load_row<DW>(U, r0.id, w);
+          sm.nrm[0][tid] = (float)row_norm<DW>(w);
+          store_row_f16<DW>(w, tid, A);
+        }
       }
       if (tid == 0) {
         sm.P[0] = r0.p;
         sm.V[0] = r0.V;
       }
+      if constexpr (HALF) tcx::cp_async_wait_all();
       tcx::fence_async_smem();
       tile_bar();
       if (tid == 0) {
@@ -556,37 +621,53 @@ gram_pipe_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int d,
         ++issued;
       }
     }
-    for (int64_t k = 0; k < K; ++k) {
+    for (int64_t k = 0; k < NK; ++k) {
       const int b = (int)(k & 1);
-      const bool next = k + 1 < K;
-      // loads ahead: rows of k+1, the list of k+3, the point of k+4
-      uint4 w[DW / 4];
-      if (ok && next && tid < r1.V) load_row<DW>(U, r1.id, w);
-      RowAhead r3{p3, 0, 0, 0.f};
-      if (ok && k + 3 < K) job_list(J, r3, tid);
-      const int32_t p4 = (ok && k + 4 < K) ? job_point(J, blockIdx.x + (k + 4) * G) : 0;
+      const bool next = k + 1 < NK;
+      // loads ahead: rows of k+1 (8-bit rows), the list of k+3, the point of k+4
+      uint4 w[HALF ? 1 : DW / 4];
+      if constexpr (!HALF) {
+        if (ok && next && tid < r1.V) load_row<DW>(U, r1.id, w);
+      }
+      float nrm1 = 0.f;
+      if constexpr (HALF) {
+        if (ok && next && tid < r1.V) nrm1 = J.nrm[r1.id];
+      }
+      RowAhead r3{p3, 0, 0, 0.f, 0.f};
+      if (ok && k + 3 < NK) job_list(J, r3, tid);
+      const int32_t p4 = (ok && k + 4 < NK) ? job_point(J, blockIdx.x + (k + 4) * G) : 0;
       if (ok) ok = pipe_wait(sm, &sm.mma, (uint32_t)(k & 1), &ctr->status, lane);
       if (ok && tid == 0) ++completed;
       tcx::fence_after();
+      if constexpr (HALF) {  // the operand tile is free: row k+1's rows go in while G(k) is read
+        if (ok && next && tid < r1.V)
+          stage_row_async<K>(reinterpret_cast<const __half*>(Xs), dpad, r1.id, tid, A);
+        tcx::cp_async_commit();
+      }
       // masks of row k into buffer b, once row k-2's sweep released it
       if (ok && k >= 2) ok = pipe_wait(sm, &sm.freed[b], (uint32_t)(((k - 2) >> 1) & 1), &ctr->status, lane);
-      if (ok) gram_masks(list_of(sm, b), tmem, sm.V[b], ra, warp, lane, &ctr->status);
+      if (ok) gram_masks(list_of(sm, b), tmem, sm.V[b], ra, warp, lane, &ctr->status, cE);
       tcx::fence_before();
-      // row k+1 into buffer b ^ 1 and the operand tile, once row k-1's sweep released it
+      // row k+1 into buffer b ^ 1 (and the operand tile), once row k-1's sweep released it
       if (ok && next && k >= 1)
         ok = pipe_wait(sm, &sm.freed[b ^ 1], (uint32_t)(((k - 1) >> 1) & 1), &ctr->status, lane);
       if (ok && next) {
         if (tid < r1.V) {
           sm.ids[b ^ 1][tid] = r1.id;
           sm.dist[b ^ 1][tid] = r1.dist;
-          sm.nrm[b ^ 1][tid] = (float)row_norm<DW>(w);
-          store_row_f16<DW>(w, tid, A);
+          if constexpr (HALF) {
+            sm.nrm[b ^ 1][tid] = nrm1;
+          } else {
+            sm.nrm[b ^ 1][tid] = (float)row_norm<DW>(w);
+            store_row_f16<DW>(w, tid, A);
+          }
         }
         if (tid == 0) {
           sm.P[b ^ 1] = r1.p;
           sm.V[b ^ 1] = r1.V;
         }
       }
+      if constexpr (HALF) tcx::cp_async_wait_all();
       tcx::fence_async_smem();
       tile_bar();
       if (tid == 0 && ok) {
@@ -603,12 +684,12 @@ gram_pipe_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, int d,
   } else {
     bool ok = true;
     unsigned long long rows = 0;
-    for (int64_t k = 0; k < K && ok; ++k) {
+    for (int64_t k = 0; k < NK && ok; ++k) {
       const int b = (int)(k & 1);
       ok = pipe_wait(sm, &sm.ready[b], (uint32_t)((k >> 1) & 1), &ctr->status, lane);
       if (!ok) break;
       const int64_t p = sm.P[b];
-      const int ns = gram_sweep(list_of(sm, b), sm.S, sm.V[b], Xs, d, dpad, p, ra, lane, ties);
+      const int ns = gram_sweep<T, !HALF>(list_of(sm, b), sm.S, sm.V[b], Xs, d, dpad, p, ra, lane, ties);
       for (int t = lane; t < J.out_stride; t += 32) J.out[p * J.out_stride + t] = t < ns ? sm.S[t] : -1;
       if (lane == 0) J.out_deg[p] = ns;
       edges += ns;
@@ -819,18 +900,59 @@ bool gram_prune_ok(const uint8_t* U, int dw, int L, int R) {
   return U && L >= 1 && L <= GT_N && R <= 64 && (dw == 8 || dw == 16 || dw == 24 || dw == 32);
 }
 
+bool gram_prune_f16_ok(int dtype, int dpad, int L, int R, bool adaptive) {
+  return dtype == CNG_F16 && !adaptive && (dpad == 64 || dpad == 128) && L >= 1 && L <= GT_N &&
+         R <= 64;
+}
+
+// |x|^2 of every FP16 row: FP64 sum of the exact squares, rounded once to FP32.
+__global__ void half_norms_kernel(const __half* __restrict__ X, int64_t n, int d, int dpad,
+                                  float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const __half* x = X + i * dpad;
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double v = (double)__half2float(x[k]);
+      s = fma(v, v, s);
+    }
+    out[i] = (float)s;
+  }
+}
+
+cudaError_t launch_prune_gram_f16(const void* xs, int64_t n, int d, int dpad, const int32_t* cand,
+                                  const float* cdist, int L, const RuleArgs& ra, int32_t* fwd,
+                                  int32_t* fdeg, float* norms, Counters* ctr, cudaStream_t s) {
+  const __half* X = static_cast<const __half*>(xs);
+  count_launch();
+  half_norms_kernel<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
+      X, n, d, dpad, norms);
+  const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
+  const GramJob J{cand, cdist, L, nullptr, L, nullptr, nullptr, n, fwd, ra.R, fdeg, 0, norms};
+  count_launch();
+  if (dpad == 128) {
+    prepare(gram_pipe_kernel<__half, 128, true>);
+    gram_pipe_kernel<__half, 128, true><<<grid, GP_THREADS, GT_SMEM, s>>>(nullptr, X, d, dpad, J, ra, ctr);
+  } else {
+    prepare(gram_pipe_kernel<__half, 64, true>);
+    gram_pipe_kernel<__half, 64, true><<<grid, GP_THREADS, GT_SMEM, s>>>(nullptr, X, d, dpad, J, ra, ctr);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t prune_gram_t(const uint8_t* U, int dw, const T* xs, int64_t n, int d, int dpad,
                                 const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
                                 int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
-  const GramJob J{cand, cdist, L, nullptr, L, nullptr, nullptr, n, fwd, ra.R, fdeg, 0};
+  const GramJob J{cand, cdist, L, nullptr, L, nullptr, nullptr, n, fwd, ra.R, fdeg, 0, nullptr};
 #define CNG_PG(DW)                                                                                \
   if (dw == DW) {                                                                                 \
     count_launch();                                                                               \
     if (ra.imax < 0) {                                                                            \
-      prepare(gram_pipe_kernel<T, DW>);                                                           \
-      gram_pipe_kernel<T, DW><<<grid, GP_THREADS, GT_SMEM, s>>>(U, xs, d, dpad, J, ra, ctr);     \
+      prepare(gram_pipe_kernel<T, 4 * DW, false>);                                                \
+      gram_pipe_kernel<T, 4 * DW, false><<<grid, GP_THREADS, GT_SMEM, s>>>(U, xs, d, dpad, J, ra, \
+                                                                           ctr);                  \
     } else {                                                                                      \
       prepare(prune_gram_u8_kernel<T, DW>);                                                       \
       prune_gram_u8_kernel<T, DW><<<grid, GT_THREADS, GT_SMEM, s>>>(U, xs, n, d, dpad, cand,      \
@@ -864,7 +986,8 @@ static cudaError_t merge_gram_t(const uint8_t* U, int dw, const T* xs, int64_t n
                                 cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
   const bool pipe = ra.imax < 0 && ms.mlist;
-  const GramJob J{ms.mlist, ms.mdist, GT_N, ms.mlen, 0, ms.rlist, &ctr->nre, n, adj, ra.rs, deg, 1};
+  const GramJob J{ms.mlist, ms.mdist, GT_N, ms.mlen, 0, ms.rlist, &ctr->nre, n, adj, ra.rs, deg, 1,
+                  nullptr};
   const int glist = (int)std::min<int64_t>(n, (int64_t)num_sms() * 16);
 #define CNG_MG(DW)                                                                                 \
   if (dw == DW) {                                                                                  \
@@ -873,10 +996,10 @@ static cudaError_t merge_gram_t(const uint8_t* U, int dw, const T* xs, int64_t n
       merge_lists_u8_kernel<DW><<<glist, 128, 0, s>>>(U, n, fwd, fdeg, off, inl, ra.R, ra.rs, adj,  \
                                                       deg, ms.mlist, ms.mdist, ms.mlen, ms.rlist,  \
                                                       mid_list, ctr);                              \
-      prepare(gram_pipe_kernel<T, DW>);                                                            \
+      prepare(gram_pipe_kernel<T, 4 * DW, false>);                                                 \
       count_launch();                                                                              \
-      gram_pipe_kernel<T, DW><<<num_sms() * 4, GP_THREADS, GT_SMEM, s>>>(U, xs, d, dpad, J, ra,    \
-                                                                         ctr);                     \
+      gram_pipe_kernel<T, 4 * DW, false><<<num_sms() * 4, GP_THREADS, GT_SMEM, s>>>(U, xs, d, dpad, \
+                                                                                    J, ra, ctr);   \
     } else {                                                                                       \
       prepare(merge_gram_u8_kernel<T, DW>);                                                        \
       count_launch();                                                                              \

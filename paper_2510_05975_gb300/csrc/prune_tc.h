@@ -16,6 +16,12 @@ cudaError_t launch_prune_gram_u8(const uint8_t* U, int dw, const void* xs, int d
                                  const RuleArgs& ra, int32_t* fwd, int32_t* fdeg, Counters* ctr,
                                  cudaStream_t s);
 
+// K4 on the Gram tile for FP16 rows (dpad 64 or 128, fixed rule): |x|^2 into norms[n], then the
+// pipelined prune with certified decision windows.
+cudaError_t launch_prune_gram_f16(const void* xs, int64_t n, int d, int dpad, const int32_t* cand,
+                                  const float* cdist, int L, const RuleArgs& ra, int32_t* fwd,
+                                  int32_t* fdeg, float* norms, Counters* ctr, cudaStream_t s);
+
 // K6 first pass on the Gram tile: merged sets of up to 128 entries; larger ones are appended to
 // mid_list (count in ctr->nmid) for the 256-entry pass.  With the fixed rule and scratch given
 // (ms.mlist non-null) the sets are listed first and re-pruned by the pipelined Gram kernel.

@@ -115,6 +115,13 @@ CNG_DEV void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 16-byte global -> shared copies without registers (cp.async, L2 only), committed as a group.
+CNG_DEV void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+CNG_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+CNG_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // 16 consecutive FP32 columns of the warp's 32 TMEM lanes; waits for the load.
 CNG_DEV void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];

@@ -71,7 +71,7 @@ def test_gauss10k_full_size():
 def test_host_points_and_fp16():
     need_gpu()
     cng = lib()
-    X = synth.generate("bigann16", 2000, 64, seed=3)  # float16 storage
+    X = synth.generate("bigann16", 2000, 64, seed=3, dtype="float16")  # FP16 storage
     idx, st = cng.cng_build(X, alpha=1.2, R=16, L=48, keep_lists=True)  # host array
     G = oracle.build_graph(X.astype(np.float32), 1.2, 0.0, 16, 48)
     _check_graph(X.astype(np.float32), G, idx, cng, 16, 48)
@@ -404,4 +404,43 @@ def test_gram_merge_with_a_hub():
     G = oracle.build_graph(X, 1.2, 0.0, 16, 64)
     assert st["merge_max_list"] > 256
     _check_graph(X, G, idx, cng, 16, 64)
+    cng.cng_free(idx)
+
+
+@pytest.mark.parametrize("d,n,R,L,tau,seed", [
+    (128, 3001, 32, 128, 0.0, 21),   # K = 128, full tile
+    (64, 2500, 24, 100, 0.3, 22),    # K = 64, tau > 0, list length not a multiple of 32
+    (128, 1000, 64, 64, 0.0, 23),    # short lists, R = 64
+])
+def test_gram_prune_fp16_matches_oracle(d, n, R, L, tau, seed):
+    """FP16 storage through the Gram-tile prune (FP32 accumulation, certified decision windows;
+    pairs inside them decided again by the FP32 difference form, then FP64): lists and graph
+    identical to the oracle's."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate("bigann16", n, d, seed=seed, dtype="float16")
+    assert X.dtype == np.float16
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=R, L=L, tau=tau, keep_lists=True)
+    assert st["prune_path"] == 3
+    Xf = X.astype(np.float32)
+    G = oracle.build_graph(Xf, 1.2, tau, R, L)
+    _check_graph(Xf, G, idx, cng, R, L)
+    cng.cng_free(idx)
+
+
+def test_gram_prune_fp16_ties():
+    """Half-integer lattice points in FP16 (0, 0.5, 1, 1.5 in 64 dimensions; 100 duplicated) with
+    alpha = 1: exact rule boundaries and D(p,v) = 0 entries go through the open-pair path (FP32
+    difference form, then FP64) and give the oracle's lists."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(24)
+    X = rng.integers(0, 4, (1400, 64)) * 0.5
+    X = np.concatenate([X, X[:100]]).astype(np.float16)
+    idx, st = cng.cng_build(tensor(X), alpha=1.0, R=12, L=48, keep_lists=True)
+    assert st["prune_path"] == 3
+    Xf = X.astype(np.float32)
+    G = oracle.build_graph(Xf, 1.0, 0.0, 12, 48)
+    _check_graph(Xf, G, idx, cng, 12, 48)
+    assert st["rule_ties"] > 0
     cng.cng_free(idx)

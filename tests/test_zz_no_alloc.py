@@ -40,7 +40,8 @@ def test_entry_noalloc_matches_build_on_consecutive_calls():
 def test_entry_noalloc_fp16_and_limits():
     need_gpu()
     cng = lib()
-    H = synth.generate("bigann16", 5000, 64, seed=33)  # float16 storage
+    H = synth.generate("bigann16", 5000, 64, seed=33, dtype="float16")
+    assert H.dtype == np.float16
     ref = _reference_entry(cng, H)
     out = torch.empty((1,), dtype=torch.int32, device="cuda")
     cng.cng_entry_noalloc(tensor(H), out)
