@@ -420,7 +420,7 @@ def main():
                                                 "order_ties", "alpha_mean", "merge_repruned",
                                                 "n_edges", "screen_used", "screen_variant",
                                                 "screen_stages", "screen_cap", "screen_sync",
-                                                "repair_edges", "repair_rounds")}}), flush=True)
+                                                "repair_edges", "repair_rounds", "prune_path")}}), flush=True)
         return
     if args.search_L:
         xs = torch.from_numpy(w.base()).cuda()
@@ -683,7 +683,7 @@ def main():
                                  ("n_edges", "cert_fail_rows", "order_ties", "rule_ties",
                                   "merge_repruned", "merge_max_list", "repair_edges", "repair_rounds",
                                   "exact_int", "screen_used", "screen_variant", "screen_stages",
-                                  "screen_cap", "screen_sync")} if last_stats else None,
+                                  "screen_cap", "screen_sync", "prune_path")} if last_stats else None,
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "hbm_kernels": hbm,
                 "cpu_baseline": cpu,
                 "clocks": clocks}
