@@ -159,8 +159,62 @@ extern "C" void cng_stop_free(cng_stop_model* m) {
   delete m;
 }
 
+// Search scratch (staging areas, deferred-query lists) of freed indexes, kept for the next
+// index on the same device so its first host-buffer search allocates nothing.  Bounded: at most
+// kScratchKeep buffers; a buffer beyond that is freed.
+namespace {
+struct ScratchBuf {
+  int dev;
+  void* p;
+  size_t bytes;
+};
+constexpr size_t kScratchKeep = 8;
+std::mutex g_scratch_mu;
+std::vector<ScratchBuf> g_scratch;
+}  // namespace
+
+static void scratch_give(void* p, size_t bytes) {
+  if (!p) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (g_scratch.size() >= kScratchKeep) {
+    cudaFree(p);
+    return;
+  }
+  g_scratch.push_back({dev, p, bytes});
+}
+
+// The smallest cached buffer of at least `bytes` on the current device, or a new allocation.
+static cudaError_t scratch_take(size_t bytes, void** p, size_t* got) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    int best = -1;
+    for (int i = 0; i < (int)g_scratch.size(); ++i)
+      if (g_scratch[i].dev == dev && g_scratch[i].bytes >= bytes &&
+          (best < 0 || g_scratch[i].bytes < g_scratch[best].bytes))
+        best = i;
+    if (best >= 0) {
+      *p = g_scratch[best].p;
+      *got = g_scratch[best].bytes;
+      g_scratch.erase(g_scratch.begin() + best);
+      return cudaSuccess;
+    }
+  }
+  *got = bytes;
+  return cudaMalloc(p, bytes);
+}
+
 extern "C" void cng_free(cng_index* ix) {
   if (!ix) return;
+  // the scratch goes back to the cache: the index's last call must be complete
+  if (ix->has_last) cudaEventSynchronize(ix->done);
+  scratch_give(ix->stage, ix->stage_cap);
+  scratch_give(ix->defer, (size_t)ix->defer_cap * sizeof(int32_t));
+  ix->stage = nullptr;
+  ix->defer = nullptr;
   for (auto& g : ix->graphs) cudaGraphExecDestroy(g.exec);
   cudaFree(ix->xs);
   cudaFree(ix->adj);
@@ -1024,8 +1078,13 @@ static cudaError_t ensure_stage(cng_index* ix, size_t bytes) {
   cudaFree(ix->stage);
   ix->stage = nullptr;
   ix->stage_cap = 0;
-  const cudaError_t e = cudaMalloc(&ix->stage, bytes);
-  if (e == cudaSuccess) ix->stage_cap = bytes;
+  void* p = nullptr;
+  size_t got = 0;
+  const cudaError_t e = scratch_take(bytes, &p, &got);
+  if (e == cudaSuccess) {
+    ix->stage = static_cast<char*>(p);
+    ix->stage_cap = got;
+  }
   return e;
 }
 
@@ -1035,8 +1094,13 @@ static cudaError_t ensure_defer(cng_index* ix, int64_t nq) {
   cudaFree(ix->defer);
   ix->defer = nullptr;
   ix->defer_cap = 0;
-  const cudaError_t e = cudaMalloc(&ix->defer, (size_t)nq * sizeof(int32_t));
-  if (e == cudaSuccess) ix->defer_cap = nq;
+  void* p = nullptr;
+  size_t got = 0;
+  const cudaError_t e = scratch_take((size_t)nq * sizeof(int32_t), &p, &got);
+  if (e == cudaSuccess) {
+    ix->defer = static_cast<int32_t*>(p);
+    ix->defer_cap = (int64_t)(got / sizeof(int32_t));
+  }
   return e;
 }
 
