@@ -194,7 +194,9 @@ cng_status cng_build(const void *points, int32_t dtype, int64_t n, int32_t d,
 cng_status cng_entry_noalloc(const void *points_dev, int32_t dtype, int64_t n, int32_t d,
                              int32_t *entry_dev, void *stream);
 
-/* Release an index and its device memory.  NULL-safe. */
+/* Release an index and its device memory.  NULL-safe.  Waits for the index's last search to
+ * finish; its search scratch (host staging, deferred-query list) is kept in a small per-process
+ * cache (at most 8 buffers) for the next index on the same device. */
 void cng_free(cng_index *index);
 
 /* Thread-local message describing the last failure of this thread (never NULL). */
