@@ -149,7 +149,8 @@ typedef struct {
   int32_t screen_sync;
   int32_t prune_path;         /* phase-2b sweep: 0 float rows (SIMT), 1 8-bit rows (dp4a SIMT),
                                  2 8-bit rows, candidate-pair Gram tile on the tensor cores,
-                                 3 FP16 rows, Gram tile with certified decision windows */
+                                 3 FP16 rows, Gram tile with certified decision windows,
+                                 4 float rows, all-pairs Gram blocks on CUDA cores */
 } cng_build_stats;
 
 typedef struct cng_index cng_index;

@@ -1017,7 +1017,11 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     stats->screen_stages = tshape.stages;
     stats->screen_cap = tshape.cap;
     stats->screen_sync = tshape.sync_d;
-    stats->prune_path = gram_prune_ok(u8, u8w, L, R) ? 2 : (u8 && L <= 256 ? 1 : (half_norms ? 3 : 0));
+    stats->prune_path = gram_prune_ok(u8, u8w, L, R)                 ? 2
+                        : (u8 && L <= 256)                             ? 1
+                        : half_norms                                   ? 3
+                        : (!u8 && pairs_prune_ok(L, R, P.adaptive != 0)) ? 4
+                                                                       : 0;
   }
   *out = ix;
   return CNG_OK;

@@ -154,6 +154,8 @@ int num_sms();
 bool gram_prune_ok(const uint8_t* U, int dw, int L, int R);
 // The same for FP16 rows (dtype CNG_F16, dpad 64 or 128, fixed alpha).
 bool gram_prune_f16_ok(int dtype, int dpad, int L, int R, bool adaptive);
+// True when the CUDA-core all-pairs prune takes lists of L with bound R (float rows).
+bool pairs_prune_ok(int L, int R, bool adaptive);
 // k_entry_noalloc.cu: the navigating node using a fixed file-scope device array as scratch.
 int64_t entry_noalloc_need(int64_t n, int d);      // doubles of scratch a call needs
 int64_t entry_noalloc_capacity();                  // doubles the array holds

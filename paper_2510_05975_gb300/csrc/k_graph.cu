@@ -539,6 +539,8 @@ cudaError_t launch_prune_fwd(const void* xs, int dtype, int64_t n, int d, int dp
                                 ctr, s);
   if (half_norms && gram_prune_f16_ok(dtype, dpad, L, R, ag.imax >= 0))  // FP16 rows, same tile
     return launch_prune_gram_f16(xs, n, d, dpad, cand, cdist, L, ra, fwd, fdeg, half_norms, ctr, s);
+  if (!u8 && pairs_prune_ok(L, R, ag.imax >= 0))  // float rows: all pairs on CUDA cores
+    return launch_prune_pairs(xs, dtype, n, d, dpad, cand, cdist, L, ra, fwd, fdeg, ctr, s);
   if (dtype == CNG_F32 ? launch_prune_u8(u8, u8_words, (const float*)xs, n, d, dpad, cand, cdist, L,
                                          ra, fwd, fdeg, ctr, s)
                        : launch_prune_u8(u8, u8_words, (const __half*)xs, n, d, dpad, cand, cdist,

@@ -889,6 +889,310 @@ merge_gram_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, in
   gram_teardown(sm, tmem, phase, warp);
 }
 
+// ---- K4 for float rows on CUDA cores: all pairs of a list in 32 x 32 blocks ----------------------
+// Lists of up to 256 entries (FP32 or FP16 rows of any width, fixed alpha).  A warp computes a
+// block of the list's Gram matrix (i in rows 32a..32a+31, j in 32b..32b+31, a <= b): lane l owns
+// entry j = 32b + l and accumulates <x_i, x_j> for the 32 rows i, broadcast from shared memory
+// in double-buffered chunks of PP_KC dimensions (cp.async), one FFMA per pair and dimension (a
+// chain of d); each warp carries two blocks per pass.  With |x|^2 from FP32 chains too,
+// D^2 = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j> is off by at most cE (|x_i|^2 + |x_j|^2),
+// cE = (2 d + 8) 2^-24 (the |x_ik x_jk| sum to at most the mean of the two squared norms),
+// and the rule is decided in the squared form with the certified window of the FP16 Gram tiles;
+// open pairs are decided again when Alg. 2 meets them by the FP32 difference form with the band,
+// then FP64.  Lane l keeps the 32 decisions of its entry as one word of the "prunes" / "open"
+// masks; warp 0 runs Alg. 2 on them.
+constexpr int PP_THREADS = 256;
+constexpr int PP_VMAX = 256;
+constexpr int PP_NW = PP_VMAX / 32;  // mask words per entry
+constexpr int PP_KC = 32;            // dimensions per staged chunk
+constexpr int PP_LD = PP_KC + 4;     // row stride in floats: rows r..r+7 in distinct bank groups
+
+struct __align__(16) PairsSmem {
+  float xs[2][PP_VMAX][PP_LD];  // double-buffered dimension chunks of the list's rows
+  int32_t ids[PP_VMAX];
+  float dist[PP_VMAX];
+  float nrm[PP_VMAX];
+  uint32_t bp[PP_VMAX][PP_NW];
+  uint32_t bt[PP_VMAX][PP_NW];
+  int32_t S[64];
+  int ns;
+};
+constexpr int PP_SMEM = (int)sizeof(PairsSmem);
+
+// Alg. 2 on masks of nw words per entry (entries [0, V), V <= 32 nw).  Same order and near-tie
+// treatment as gram_sweep.
+template <typename T>
+CNG_DEV int pairs_sweep(PairsSmem& sm, int V, const T* __restrict__ Xs, int d, int dpad, int64_t p,
+                        const RuleArgs& r, int lane, unsigned long long& ties) {
+  const GramList gl{sm.ids, sm.dist, sm.nrm, nullptr, nullptr};
+  uint32_t K[PP_NW];
+#pragma unroll
+  for (int q = 0; q < PP_NW; ++q) K[q] = 0u;
+  int ns = 0;
+  const int nch = (V + 31) >> 5;
+#pragma unroll 1
+  for (int c = 0; c < nch; ++c) {
+    const int j = c * 32 + lane;
+    bool alive = j < V;
+    if (alive && c > 0) {  // members of S from earlier chunks
+      uint32_t hit = 0u, tie = 0u;
+#pragma unroll
+      for (int q = 0; q < PP_NW; ++q)
+        if (q < c) {
+          hit |= sm.bp[j][q] & K[q];
+          tie |= sm.bt[j][q] & K[q];
+        }
+      if (tie == 0u) {
+        alive = hit == 0u;
+      } else {  // ascending over the members that prune or tie, until one prunes
+#pragma unroll
+        for (int q = 0; q < PP_NW; ++q) {
+          if (q >= c || !alive) continue;
+          const uint32_t bq = sm.bp[j][q];
+          uint32_t m = (bq | sm.bt[j][q]) & K[q];
+          while (m && alive) {
+            const int b = __ffs(m) - 1;
+            if ((bq >> b) & 1u) {
+              alive = false;
+            } else if (decide_pair<T, false>(gl, Xs, d, dpad, p, q * 32 + b, j, r, ties)) {
+              alive = false;
+            }
+            m &= m - 1u;
+          }
+        }
+      }
+    }
+    const uint32_t bpc = j < V ? sm.bp[j][c] : 0u, btc = j < V ? sm.bt[j][c] : 0u;
+    uint32_t kc = 0u;
+    bool full = false;
+    uint32_t live_m = __ballot_sync(FULL, alive);
+    if (!__any_sync(FULL, alive && btc != 0u)) {  // no near-tie inside the chunk: bit greedy
+      uint32_t prb[32];
+#pragma unroll
+      for (int b = 0; b < 32; ++b) prb[b] = __ballot_sync(FULL, (bpc >> b) & 1u);
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        if ((live_m >> b) & 1u) {
+          kc |= 1u << b;
+          live_m &= ~prb[b];
+        }
+      }
+      const int room = r.R - ns;
+      if (__popc(kc) >= room) {
+        uint32_t t = kc;
+        for (int i = 1; i < room; ++i) t &= t - 1u;
+        const int pos = __ffs(t) - 1;
+        kc &= pos == 31 ? 0xffffffffu : ((2u << pos) - 1u);
+        full = true;
+      }
+      if ((kc >> lane) & 1u) sm.S[ns + __popc(kc & ((1u << lane) - 1u))] = sm.ids[c * 32 + lane];
+      ns += __popc(kc);
+      live_m = 0u;
+    }
+    while (live_m) {
+      const int b = __ffs(live_m) - 1;
+      kc |= 1u << b;
+      if (lane == 0) sm.S[ns] = sm.ids[c * 32 + b];
+      ++ns;
+      if (ns >= r.R) {
+        full = true;
+        break;
+      }
+      if (alive && lane > b) {
+        if ((bpc >> b) & 1u) {
+          alive = false;
+        } else if ((btc >> b) & 1u) {
+          if (decide_pair<T, false>(gl, Xs, d, dpad, p, c * 32 + b, j, r, ties)) alive = false;
+        }
+      }
+      live_m = __ballot_sync(FULL, alive) & ~((2u << b) - 1u);
+    }
+#pragma unroll
+    for (int q = 0; q < PP_NW; ++q)
+      if (q == c) K[q] = kc;
+    if (full) break;
+  }
+  __syncwarp();
+  return ns;
+}
+
+// Block t of the lower triangle (a <= b) of an nb x nb block grid: t = b (b + 1) / 2 + a.
+CNG_DEV void block_of(int t, int& a, int& b) {
+  b = 0;
+  while ((b + 1) * (b + 2) / 2 <= t) ++b;
+  a = t - b * (b + 1) / 2;
+}
+
+// Four consecutive elements of row `row` from dimension k as floats (zero at k >= d).
+CNG_DEV float4 load4(const float* __restrict__ row, int k, int d) {
+  if (k + 4 <= d) return __ldg(reinterpret_cast<const float4*>(row + k));
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (k < d) v.x = row[k];
+  if (k + 1 < d) v.y = row[k + 1];
+  if (k + 2 < d) v.z = row[k + 2];
+  return v;
+}
+CNG_DEV float4 load4(const __half* __restrict__ row, int k, int d) {
+  if (k + 4 <= d) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(row + k));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (k < d) v.x = __half2float(row[k]);
+  if (k + 1 < d) v.y = __half2float(row[k + 1]);
+  if (k + 2 < d) v.z = __half2float(row[k + 2]);
+  return v;
+}
+
+// Dimensions [k0, k0 + PP_KC) of every entry's row into chunk buffer buf: 16-byte cp.async copies
+// of the zero-padded stored rows (FP32), or converted loads (FP16).
+template <typename T>
+CNG_DEV void stage_chunk(PairsSmem& sm, int buf, const T* __restrict__ Xs, int d, int dpad, int V,
+                         int k0) {
+  for (int e = threadIdx.x; e < V * (PP_KC / 4); e += PP_THREADS) {
+    const int i = e / (PP_KC / 4), q = e - i * (PP_KC / 4);
+    const T* row = Xs + (int64_t)sm.ids[i] * dpad;
+    if constexpr (sizeof(T) == 4) {
+      tcx::cp_async16(&sm.xs[buf][i][4 * q], row + k0 + 4 * q);  // k0 + 4q + 4 <= dpad
+    } else {
+      *reinterpret_cast<float4*>(&sm.xs[buf][i][4 * q]) = load4(row, k0 + 4 * q, d);
+    }
+  }
+  tcx::cp_async_commit();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PP_THREADS, 2)
+pairs_prune_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
+                   const int32_t* __restrict__ cand, const float* __restrict__ cdist, int L,
+                   RuleArgs ra, int32_t* __restrict__ fwd, int32_t* __restrict__ fdeg, Counters* ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PairsSmem& sm = *reinterpret_cast<PairsSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int V = L;
+  const int nb = (V + 31) >> 5;
+  const int nblocks = nb * (nb + 1) / 2;
+  const int nchunk = (d + PP_KC - 1) / PP_KC;
+  // Gram and norms both FP32 chains of d: cE = (2 d + 8) 2^-24
+  const float cE = (float)(2 * d + 8) * 5.9604644775390625e-8f;
+  const float A2 = ra.alpha32 * ra.alpha32, A2cE = A2 * cE;
+  unsigned long long ties = 0;
+  for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
+    for (int t = tid; t < V; t += PP_THREADS) {
+      sm.ids[t] = cand[p * L + t];
+      sm.dist[t] = cdist[p * L + t];
+    }
+    float nn = 0.f;  // |x_tid|^2 (pass 0)
+    // two blocks per warp per pass: (blk0, blk1) = (16 pass + warp, 16 pass + 8 + warp)
+    for (int pass = 0; pass * 16 < nblocks; ++pass) {
+      const int blk0 = pass * 16 + warp, blk1 = blk0 + 8;
+      const bool has0 = blk0 < nblocks, has1 = blk1 < nblocks;
+      int a0 = 0, b0 = 0, a1 = 0, b1 = 0;
+      if (has0) block_of(blk0, a0, b0);
+      if (has1) block_of(blk1, a1, b1);
+      float acc0[32], acc1[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc0[r] = acc1[r] = 0.f;
+      __syncthreads();  // ids written; both chunk buffers free
+      stage_chunk(sm, 0, Xs, d, dpad, V, 0);
+      for (int c = 0; c < nchunk; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunk) {
+          stage_chunk(sm, buf ^ 1, Xs, d, dpad, V, (c + 1) * PP_KC);
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          tcx::cp_async_wait_all();
+        }
+        __syncthreads();  // chunk c visible to every warp
+        if (pass == 0 && tid < V) {
+#pragma unroll
+          for (int k = 0; k < PP_KC; k += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(&sm.xs[buf][tid][k]);
+            nn = fmaf(x.x, x.x, nn);
+            nn = fmaf(x.y, x.y, nn);
+            nn = fmaf(x.z, x.z, nn);
+            nn = fmaf(x.w, x.w, nn);
+          }
+        }
+        if (has0) {
+          const float* xj0 = sm.xs[buf][32 * b0 + lane];
+          const float* xj1 = sm.xs[buf][32 * b1 + lane];
+#pragma unroll 1
+          for (int k = 0; k < PP_KC; k += 4) {
+            const float4 y0 = *reinterpret_cast<const float4*>(xj0 + k);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+              const float4 x = *reinterpret_cast<const float4*>(&sm.xs[buf][32 * a0 + r][k]);
+              acc0[r] = fmaf(x.x, y0.x, acc0[r]);
+              acc0[r] = fmaf(x.y, y0.y, acc0[r]);
+              acc0[r] = fmaf(x.z, y0.z, acc0[r]);
+              acc0[r] = fmaf(x.w, y0.w, acc0[r]);
+            }
+            if (has1) {
+              const float4 y1 = *reinterpret_cast<const float4*>(xj1 + k);
+#pragma unroll
+              for (int r = 0; r < 32; ++r) {
+                const float4 x = *reinterpret_cast<const float4*>(&sm.xs[buf][32 * a1 + r][k]);
+                acc1[r] = fmaf(x.x, y1.x, acc1[r]);
+                acc1[r] = fmaf(x.y, y1.y, acc1[r]);
+                acc1[r] = fmaf(x.z, y1.z, acc1[r]);
+                acc1[r] = fmaf(x.w, y1.w, acc1[r]);
+              }
+            }
+          }
+        }
+        __syncthreads();  // chunk c consumed: its buffer may be refilled
+      }
+      if (pass == 0 && tid < V) sm.nrm[tid] = nn;
+      __syncthreads();  // norms visible
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {  // decisions of the blocks' pairs (i, j), i < j < V
+        const bool has = h == 0 ? has0 : has1;
+        if (!has) continue;
+        const int a = h == 0 ? a0 : a1, b = h == 0 ? b0 : b1;
+        const int j = 32 * b + lane;
+        if (j >= V) continue;
+        const float dj = sm.dist[j], nj = sm.nrm[j];
+        const float tj = dj - ra.t32;
+        const float lim = 2.f * ra.band * dj;
+        const int cls = tj > lim ? 0 : (tj < -lim ? 1 : 2);
+        const float T2 = tj * tj, w = 2.f * ra.band * dj * tj;
+        uint32_t pb = 0u, tb = 0u;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int i = 32 * a + r;
+          const float g = h == 0 ? acc0[r] : acc1[r];
+          if (i < j) {
+            const float ni = sm.nrm[i];
+            const float d2 = (nj - g) + (ni - g);
+            const float e = fmaf(-A2, d2, T2);
+            const float win =
+                fmaf(2.384185791015625e-7f, fmaf(A2, fabsf(d2), T2), fmaf(A2cE, nj + ni, w));
+            if (cls == 2 || (cls == 0 && fabsf(e) <= win)) tb |= 1u << r;
+            else if (cls == 0 && e > win) pb |= 1u << r;
+          }
+        }
+        sm.bp[j][a] = pb;
+        sm.bt[j][a] = tb;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int k = pairs_sweep(sm, V, Xs, d, dpad, p, ra, lane, ties);
+      if (lane == 0) sm.ns = k;
+    }
+    __syncthreads();
+    const int ns = sm.ns;
+    for (int t = tid; t < ra.R; t += PP_THREADS) fwd[p * ra.R + t] = t < ns ? sm.S[t] : -1;
+    if (tid == 0) fdeg[p] = ns;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
+  if (lane == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+}
+
 template <typename K>
 static void prepare(K kernel) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
@@ -918,6 +1222,25 @@ __global__ void half_norms_kernel(const __half* __restrict__ X, int64_t n, int d
     }
     out[i] = (float)s;
   }
+}
+
+bool pairs_prune_ok(int L, int R, bool adaptive) { return !adaptive && L >= 1 && L <= PP_VMAX && R <= 64; }
+
+cudaError_t launch_prune_pairs(const void* xs, int dtype, int64_t n, int d, int dpad,
+                               const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
+                               int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 2);
+  count_launch();
+  if (dtype == CNG_F32) {
+    cudaFuncSetAttribute(pairs_prune_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PP_SMEM);
+    pairs_prune_kernel<float><<<grid, PP_THREADS, PP_SMEM, s>>>((const float*)xs, n, d, dpad, cand, cdist,
+                                                               L, ra, fwd, fdeg, ctr);
+  } else {
+    cudaFuncSetAttribute(pairs_prune_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, PP_SMEM);
+    pairs_prune_kernel<__half><<<grid, PP_THREADS, PP_SMEM, s>>>((const __half*)xs, n, d, dpad, cand,
+                                                                cdist, L, ra, fwd, fdeg, ctr);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prune_gram_f16(const void* xs, int64_t n, int d, int dpad, const int32_t* cand,

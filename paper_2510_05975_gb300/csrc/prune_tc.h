@@ -22,6 +22,12 @@ cudaError_t launch_prune_gram_f16(const void* xs, int64_t n, int d, int dpad, co
                                   const float* cdist, int L, const RuleArgs& ra, int32_t* fwd,
                                   int32_t* fdeg, float* norms, Counters* ctr, cudaStream_t s);
 
+// K4 for float rows on CUDA cores (lists of up to 256, fixed rule): all pairs of a list in
+// 32 x 32 Gram blocks with certified decision windows, Alg. 2 on the masks.
+cudaError_t launch_prune_pairs(const void* xs, int dtype, int64_t n, int d, int dpad,
+                               const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
+                               int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s);
+
 // K6 first pass on the Gram tile: merged sets of up to 128 entries; larger ones are appended to
 // mid_list (count in ctr->nmid) for the 256-entry pass.  With the fixed rule and scratch given
 // (ms.mlist non-null) the sets are listed first and re-pruned by the pipelined Gram kernel.

@@ -444,3 +444,40 @@ def test_gram_prune_fp16_ties():
     _check_graph(Xf, G, idx, cng, 12, 48)
     assert st["rule_ties"] > 0
     cng.cng_free(idx)
+
+
+@pytest.mark.parametrize("kind,d,n,R,L,alpha,tau,seed", [
+    ("deep", 96, 3000, 48, 160, 1.3, 0.0, 31),    # the DEEP-like shape: lists of 160
+    ("gauss", 32, 3000, 48, 250, 1.2, 0.0, 32),   # eight 32-entry chunks, ragged
+    ("gauss", 20, 2500, 16, 64, 1.2, 0.25, 33),   # tau > 0, rows narrower than a chunk
+    ("gist", 960, 1500, 32, 128, 1.2, 0.0, 34),   # rows of 30 chunks
+])
+def test_pairs_prune_matches_oracle(kind, d, n, R, L, alpha, tau, seed):
+    """Float rows through the CUDA-core all-pairs prune (Gram blocks with certified windows, open
+    pairs decided again by the FP32 difference form, then FP64): lists and graph identical to the
+    oracle's."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate(kind, n, d, seed=seed)
+    idx, st = cng.cng_build(tensor(X), alpha=alpha, R=R, L=L, tau=tau, keep_lists=True)
+    assert st["prune_path"] == 4
+    G = oracle.build_graph(X, alpha, tau, R, L)
+    _check_graph(X, G, idx, cng, R, L)
+    cng.cng_free(idx)
+
+
+def test_pairs_prune_ties():
+    """Half-integer lattice points in FP32 (0 .. 1.5 in 40 dimensions, 100 duplicated), alpha = 1:
+    exact rule boundaries and D(p,v) = 0 entries take the open-pair path; lists equal the
+    oracle's."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(35)
+    X = rng.integers(0, 4, (1400, 40)) * 0.5
+    X = np.concatenate([X, X[:100]]).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.0, R=12, L=48, keep_lists=True)
+    assert st["prune_path"] == 4
+    G = oracle.build_graph(X, 1.0, 0.0, 12, 48)
+    _check_graph(X, G, idx, cng, 12, 48)
+    assert st["rule_ties"] > 0
+    cng.cng_free(idx)
