@@ -820,10 +820,11 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   int32_t* big_list;
   CK(pool.alloc(&big_list, 2 * (size_t)n));  // big list + the 8-bit merge's middle list
   CK(launch_reverse(fwd, fdeg, n, R, indeg, off, cursor, inl, bsum, ctr, s));
-  MergeScratch ms{};  // the 8-bit merge's listed sets for the pipelined Gram re-prune
-  if (!P.adaptive && gram_prune_ok(u8, u8w, 128, R)) {
-    CK(pool.alloc(&ms.mlist, (size_t)n * 128));
-    CK(pool.alloc(&ms.mdist, (size_t)n * 128));
+  MergeScratch ms{};  // merged sets listed for the Gram-tile (8-bit rows) or all-pairs re-prune
+  if (!P.adaptive && (gram_prune_ok(u8, u8w, 128, R) || (!u8 && pairs_prune_ok(256, R, false)))) {
+    ms.stride = u8 ? 128 : 256;
+    CK(pool.alloc(&ms.mlist, (size_t)n * ms.stride));
+    CK(pool.alloc(&ms.mdist, (size_t)n * ms.stride));
     CK(pool.alloc(&ms.mlen, (size_t)n));
     CK(pool.alloc(&ms.rlist, (size_t)n));
   }

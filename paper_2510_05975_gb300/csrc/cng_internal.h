@@ -44,13 +44,15 @@ struct Counters {
   int nre;         // 8-bit merge: nodes listed for the pipelined Gram re-prune
 };
 
-// Scratch of the 8-bit merge's pipelined re-prune: merged lists of up to 128 entries per node
-// ([n][128] ids and FP32 distances), their lengths and the listed nodes.  All null: not used.
+// Scratch of the merge's re-prune by the Gram-tile / all-pairs kernels: merged lists in (D, id)
+// order of up to `stride` entries per node ([n][stride] ids and FP32 distances; 128 for 8-bit
+// rows, 256 for float rows), their lengths and the listed nodes.  All null: not used.
 struct MergeScratch {
   int32_t* mlist;
   float* mdist;
   int32_t* mlen;
   int32_t* rlist;
+  int stride;
 };
 
 // Alg. 4 grid of adaptive pruning: alpha_i = alpha0 + i * dalpha, i = 0 .. imax (imax < 0:

@@ -745,7 +745,8 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
                        int64_t i0, int nin, const RuleArgs& ra, int exact, const MergeArrays& ar,
                        PruneSmem& sm, double* d64, int32_t* rid, int stage_cap, int* s_nv,
                        int32_t* __restrict__ adj_row, Counters* ctr, unsigned long long& ties,
-                       unsigned long long& ordties, unsigned long long& repruned) {
+                       unsigned long long& ordties, unsigned long long& repruned,
+                       const MergeScratch& ms) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = tid % PR_G, grp = tid / PR_G;
   sm.ids = ar.ids;
@@ -883,6 +884,19 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
     ar.dist[i] = sqrtf(key_dist(ar.keys[i]));
   }
   __syncthreads();
+  if (ms.mlist && nv > ra.R && nv <= ms.stride) {
+    // listed in (D, id) order for the all-pairs re-prune, which writes the row and its degree
+    for (int i = tid; i < nv; i += PR_THREADS) {
+      ms.mlist[p * ms.stride + i] = ar.ids[i];
+      ms.mdist[p * ms.stride + i] = ar.dist[i];
+    }
+    if (tid == 0) {
+      ms.mlen[p] = nv;
+      ms.rlist[atomicAdd(&ctr->nre, 1)] = (int32_t)p;
+    }
+    __syncthreads();
+    return -1;
+  }
   int na;
   if (nv <= ra.R) {
     na = nv;
@@ -917,7 +931,7 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
              const int32_t* __restrict__ fdeg, const int64_t* __restrict__ off,
              const int32_t* __restrict__ inl, RuleArgs ra, int exact, int32_t* __restrict__ adj,
              int32_t* __restrict__ deg, Counters* ctr, int32_t* __restrict__ big_list,
-             unsigned char* __restrict__ big_scratch, int big_cap) {
+             unsigned char* __restrict__ big_scratch, int big_cap, MergeScratch ms) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_nv;
   PruneSmem sm;
@@ -958,7 +972,8 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
     }
     maxlist = max(maxlist, (unsigned long long)(nf + nin));
     int na = merge_node<T, NS, DL>(Xs, d, dpad, p, fwd + p * ra.R, nf, inl, i0, nin, ra, exact, ar, sm, d64,
-                        rid, stage_cap, &s_nv, adj + p * ra.rs, ctr, ties, ordties, repruned);
+                        rid, stage_cap, &s_nv, adj + p * ra.rs, ctr, ties, ordties, repruned, ms);
+    if (na < 0) continue;  // listed for the all-pairs re-prune
     if (tid == 0) deg[p] = na;
     edges += na;
   }
@@ -1088,17 +1103,21 @@ static cudaError_t merge_t2(const void* xs, int64_t n, int d, int dpad, const in
                            const int32_t* fdeg, const int64_t* off, const int32_t* inl,
                            const RuleArgs& ra, int exact, int32_t* adj, int32_t* deg,
                            Counters* ctr, int32_t* big_list, unsigned char* big_scratch,
-                           int big_cap, int grid, cudaStream_t s) {
+                           int big_cap, int grid, const MergeScratch& ms, cudaStream_t s) {
   const int stage_cap = PR_MERGE_STAGE_BYTES / (dpad * 4);
   size_t sh = 2 * (size_t)dpad * 4 + 256 + PR_RUN * 12 + (BIG ? 0 : (size_t)PR_VMAX * 17) +
               (size_t)stage_cap * dpad * 4 + 16;
   cudaFuncSetAttribute(merge_kernel<T, BIG, NS, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sh);
   count_launch();
+  const MergeScratch mk = BIG ? MergeScratch{} : ms;
   merge_kernel<T, BIG, NS, DL><<<grid, PR_THREADS, sh, s>>>((const T*)xs, n, d, dpad, fwd, fdeg, off,
                                                             inl, ra, exact, adj, deg, ctr, big_list,
-                                                            big_scratch, big_cap);
-  return cudaGetLastError();
+                                                            big_scratch, big_cap, mk);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && mk.mlist)
+    e = launch_merge_pairs(xs, sizeof(T) == 4 ? CNG_F32 : CNG_F16, n, d, dpad, mk, ra, adj, deg, ctr, s);
+  return e;
 }
 
 // Merged lists of up to 128 entries are pruned from registers when 16-byte chunks per lane
@@ -1147,7 +1166,7 @@ static cudaError_t merge_t(const uint8_t* U, int dw, const void* xs, int64_t n, 
   if constexpr (!half || DLV % 2 == 0) {                                                           \
     if (dl4 == DLV)                                                                                \
       return merge_t2<T, BIG, 4, DLV>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg,    \
-                                      ctr, big_list, big_scratch, big_cap, grid, s);               \
+                                      ctr, big_list, big_scratch, big_cap, grid, ms, s);           \
   }
   if constexpr (!BIG) {
     CNG_MG(1)
@@ -1157,7 +1176,7 @@ static cudaError_t merge_t(const uint8_t* U, int dw, const void* xs, int64_t n, 
   }
 #undef CNG_MG
   return merge_t2<T, BIG, 0, 0>(xs, n, d, dpad, fwd, fdeg, off, inl, ra, exact, adj, deg, ctr,
-                                big_list, big_scratch, big_cap, grid, s);
+                                big_list, big_scratch, big_cap, grid, ms, s);
 }
 
 

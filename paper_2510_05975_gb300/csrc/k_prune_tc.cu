@@ -1063,26 +1063,27 @@ CNG_DEV void stage_chunk(PairsSmem& sm, int buf, const T* __restrict__ Xs, int d
   tcx::cp_async_commit();
 }
 
+// One job (the GramJob contract): rows q < count, the list of point p = pts[q] (or q) at row p.
 template <typename T>
 __global__ void __launch_bounds__(PP_THREADS, 2)
-pairs_prune_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
-                   const int32_t* __restrict__ cand, const float* __restrict__ cdist, int L,
-                   RuleArgs ra, int32_t* __restrict__ fwd, int32_t* __restrict__ fdeg, Counters* ctr) {
+pairs_prune_kernel(const T* __restrict__ Xs, int d, int dpad, GramJob J, RuleArgs ra, Counters* ctr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PairsSmem& sm = *reinterpret_cast<PairsSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int V = L;
-  const int nb = (V + 31) >> 5;
-  const int nblocks = nb * (nb + 1) / 2;
   const int nchunk = (d + PP_KC - 1) / PP_KC;
   // Gram and norms both FP32 chains of d: cE = (2 d + 8) 2^-24
   const float cE = (float)(2 * d + 8) * 5.9604644775390625e-8f;
   const float A2 = ra.alpha32 * ra.alpha32, A2cE = A2 * cE;
-  unsigned long long ties = 0;
-  for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
+  unsigned long long ties = 0, rows = 0, edges = 0;
+  const int64_t nq = J.count ? (int64_t)*J.count : J.n;
+  for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int64_t p = J.pts ? (int64_t)J.pts[q] : q;
+    const int V = J.len ? J.len[p] : J.L;
+    const int nb = (V + 31) >> 5;
+    const int nblocks = nb * (nb + 1) / 2;
     for (int t = tid; t < V; t += PP_THREADS) {
-      sm.ids[t] = cand[p * L + t];
-      sm.dist[t] = cdist[p * L + t];
+      sm.ids[t] = J.ids[p * J.list_stride + t];
+      sm.dist[t] = J.dist[p * J.list_stride + t];
     }
     float nn = 0.f;  // |x_tid|^2 (pass 0)
     // two blocks per warp per pass: (blk0, blk1) = (16 pass + warp, 16 pass + 8 + warp)
@@ -1185,12 +1186,18 @@ pairs_prune_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad,
     }
     __syncthreads();
     const int ns = sm.ns;
-    for (int t = tid; t < ra.R; t += PP_THREADS) fwd[p * ra.R + t] = t < ns ? sm.S[t] : -1;
-    if (tid == 0) fdeg[p] = ns;
+    for (int t = tid; t < J.out_stride; t += PP_THREADS) J.out[p * J.out_stride + t] = t < ns ? sm.S[t] : -1;
+    if (tid == 0) J.out_deg[p] = ns;
+    edges += ns;
+    ++rows;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(FULL, ties, o);
   if (lane == 0 && ties) atomicAdd(&ctr->rule_ties, ties);
+  if (tid == 0 && J.merge && rows) {
+    atomicAdd(&ctr->merge_repruned, rows);
+    atomicAdd(&ctr->edges, edges);
+  }
 }
 
 template <typename K>
@@ -1226,21 +1233,33 @@ __global__ void half_norms_kernel(const __half* __restrict__ X, int64_t n, int d
 
 bool pairs_prune_ok(int L, int R, bool adaptive) { return !adaptive && L >= 1 && L <= PP_VMAX && R <= 64; }
 
-cudaError_t launch_prune_pairs(const void* xs, int dtype, int64_t n, int d, int dpad,
-                               const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
-                               int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s) {
-  const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 2);
+static cudaError_t pairs_job(const void* xs, int dtype, int d, int dpad, const GramJob& J,
+                             const RuleArgs& ra, Counters* ctr, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(J.n, (int64_t)num_sms() * 2);
   count_launch();
   if (dtype == CNG_F32) {
     cudaFuncSetAttribute(pairs_prune_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PP_SMEM);
-    pairs_prune_kernel<float><<<grid, PP_THREADS, PP_SMEM, s>>>((const float*)xs, n, d, dpad, cand, cdist,
-                                                               L, ra, fwd, fdeg, ctr);
+    pairs_prune_kernel<float><<<grid, PP_THREADS, PP_SMEM, s>>>((const float*)xs, d, dpad, J, ra, ctr);
   } else {
     cudaFuncSetAttribute(pairs_prune_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, PP_SMEM);
-    pairs_prune_kernel<__half><<<grid, PP_THREADS, PP_SMEM, s>>>((const __half*)xs, n, d, dpad, cand,
-                                                                cdist, L, ra, fwd, fdeg, ctr);
+    pairs_prune_kernel<__half><<<grid, PP_THREADS, PP_SMEM, s>>>((const __half*)xs, d, dpad, J, ra, ctr);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_prune_pairs(const void* xs, int dtype, int64_t n, int d, int dpad,
+                               const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
+                               int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s) {
+  const GramJob J{cand, cdist, L, nullptr, L, nullptr, nullptr, n, fwd, ra.R, fdeg, 0, nullptr};
+  return pairs_job(xs, dtype, d, dpad, J, ra, ctr, s);
+}
+
+cudaError_t launch_merge_pairs(const void* xs, int dtype, int64_t n, int d, int dpad,
+                               const MergeScratch& ms, const RuleArgs& ra, int32_t* adj, int32_t* deg,
+                               Counters* ctr, cudaStream_t s) {
+  const GramJob J{ms.mlist, ms.mdist, ms.stride, ms.mlen, 0, ms.rlist, &ctr->nre, n, adj, ra.rs, deg, 1,
+                  nullptr};
+  return pairs_job(xs, dtype, d, dpad, J, ra, ctr, s);
 }
 
 cudaError_t launch_prune_gram_f16(const void* xs, int64_t n, int d, int dpad, const int32_t* cand,
@@ -1309,7 +1328,7 @@ static cudaError_t merge_gram_t(const uint8_t* U, int dw, const T* xs, int64_t n
                                 cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(n, (int64_t)num_sms() * 4);
   const bool pipe = ra.imax < 0 && ms.mlist;
-  const GramJob J{ms.mlist, ms.mdist, GT_N, ms.mlen, 0, ms.rlist, &ctr->nre, n, adj, ra.rs, deg, 1,
+  const GramJob J{ms.mlist, ms.mdist, ms.stride, ms.mlen, 0, ms.rlist, &ctr->nre, n, adj, ra.rs, deg, 1,
                   nullptr};
   const int glist = (int)std::min<int64_t>(n, (int64_t)num_sms() * 16);
 #define CNG_MG(DW)                                                                                 \

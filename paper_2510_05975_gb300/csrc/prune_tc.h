@@ -28,6 +28,11 @@ cudaError_t launch_prune_pairs(const void* xs, int dtype, int64_t n, int d, int 
                                const int32_t* cand, const float* cdist, int L, const RuleArgs& ra,
                                int32_t* fwd, int32_t* fdeg, Counters* ctr, cudaStream_t s);
 
+// K6 re-prune of the float merged sets listed in ms (count ctr->nre) by the all-pairs kernel.
+cudaError_t launch_merge_pairs(const void* xs, int dtype, int64_t n, int d, int dpad,
+                               const MergeScratch& ms, const RuleArgs& ra, int32_t* adj, int32_t* deg,
+                               Counters* ctr, cudaStream_t s);
+
 // K6 first pass on the Gram tile: merged sets of up to 128 entries; larger ones are appended to
 // mid_list (count in ctr->nmid) for the 256-entry pass.  With the fixed rule and scratch given
 // (ms.mlist non-null) the sets are listed first and re-pruned by the pipelined Gram kernel.
