@@ -481,3 +481,18 @@ def test_pairs_prune_ties():
     _check_graph(X, G, idx, cng, 12, 48)
     assert st["rule_ties"] > 0
     cng.cng_free(idx)
+
+
+def test_pairs_prune_fp16_wide_rows():
+    """FP16 storage with rows wider than the FP16 Gram tile (d = 200, dpad = 256) takes the
+    all-pairs path with converted FP16 loads; the merge re-prunes its sets the same way."""
+    need_gpu()
+    cng = lib()
+    X = synth.generate("bigann16", 2000, 200, seed=36, dtype="float16")
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=24, L=96, keep_lists=True)
+    assert st["prune_path"] == 4
+    Xf = X.astype(np.float32)
+    G = oracle.build_graph(Xf, 1.2, 0.0, 24, 96)
+    _check_graph(Xf, G, idx, cng, 24, 96)
+    assert st["merge_repruned"] > 0
+    cng.cng_free(idx)
