@@ -1,5 +1,10 @@
-// k_prune_tc.cu -- Alg. 2 on the tensor cores for 8-bit integer rows (sm_103a): the K4 prune of
-// every candidate list (Alg. 3 phase 2b) and the lazy re-prune of the K6 merge (phase 3).
+// k_prune_tc.cu -- Alg. 2 on whole-list pair tiles (sm_103a): the K4 prune of every candidate
+// list (Alg. 3 phase 2b) and the lazy re-prune of the K6 merge (phase 3).
+//   8-bit integer rows  tcgen05 Gram tile, exact (below); FP16 storage: the same tile from the
+//                       stored rows, FP32-accumulated, with certified decision windows
+//   other float rows    all pairs in 32 x 32 Gram blocks on CUDA cores, certified windows
+//                       (pairs_prune_kernel, further down)
+// All of them decide every pair of a list into bit masks and run Alg. 2 on the masks in one warp.
 //
 // Per point p its list V -- the L candidates in (D, id) order, or the merged set V'(p) ranked by
 // (D, id) -- of up to 128 entries is staged as FP16 rows in 128-byte-swizzled shared memory, and

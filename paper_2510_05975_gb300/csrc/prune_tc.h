@@ -1,5 +1,6 @@
-// prune_tc.h -- tensor-core Alg. 2 for 8-bit integer rows (k_prune_tc.cu): the K4 prune of
-// lists of up to 128 candidates and the first (<= 128-entry) pass of the K6 merge.
+// prune_tc.h -- Alg. 2 on whole-list pair tiles (k_prune_tc.cu): tcgen05 Gram tiles for 8-bit
+// rows (K4 and the K6 first pass) and FP16 storage (K4), CUDA-core Gram blocks for other float
+// rows (K4 and the K6 re-prune of listed sets).
 #pragma once
 
 #include <cuda_runtime.h>
