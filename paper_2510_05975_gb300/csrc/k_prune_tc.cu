@@ -899,7 +899,8 @@ merge_gram_u8_kernel(const uint8_t* __restrict__ U, const T* __restrict__ Xs, in
 // block of the list's Gram matrix (i in rows 32a..32a+31, j in 32b..32b+31, a <= b): lane l owns
 // entry j = 32b + l and accumulates <x_i, x_j> for the 32 rows i, broadcast from shared memory
 // in double-buffered chunks of PP_KC dimensions (cp.async), one FFMA per pair and dimension (a
-// chain of d); each warp carries two blocks per pass.  With |x|^2 from FP32 chains too,
+// chain of d); each warp carries two blocks per pass, sharing the row loads when their row
+// blocks agree.  With |x|^2 from FP32 chains too,
 // D^2 = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j> is off by at most cE (|x_i|^2 + |x_j|^2),
 // cE = (2 d + 8) 2^-24 (the |x_ik x_jk| sum to at most the mean of the two squared norms),
 // and the rule is decided in the squared form with the certified window of the FP16 Gram tiles;
@@ -1021,11 +1022,15 @@ CNG_DEV int pairs_sweep(PairsSmem& sm, int V, const T* __restrict__ Xs, int d, i
   return ns;
 }
 
-// Block t of the lower triangle (a <= b) of an nb x nb block grid: t = b (b + 1) / 2 + a.
-CNG_DEV void block_of(int t, int& a, int& b) {
-  b = 0;
-  while ((b + 1) * (b + 2) / 2 <= t) ++b;
-  a = t - b * (b + 1) / 2;
+// Block t of the blocks (a, b), a <= b < nb, in row-major order (a outer): consecutive blocks
+// share their row block a except across row boundaries.
+CNG_DEV void block_of(int t, int nb, int& a, int& b) {
+  a = 0;
+  while (t >= nb - a) {
+    t -= nb - a;
+    ++a;
+  }
+  b = a + t;
 }
 
 // Four consecutive elements of row `row` from dimension k as floats (zero at k >= d).
@@ -1091,13 +1096,17 @@ pairs_prune_kernel(const T* __restrict__ Xs, int d, int dpad, GramJob J, RuleArg
       sm.dist[t] = J.dist[p * J.list_stride + t];
     }
     float nn = 0.f;  // |x_tid|^2 (pass 0)
-    // two blocks per warp per pass: (blk0, blk1) = (16 pass + warp, 16 pass + 8 + warp)
+    // up to 16 blocks per pass over the 8 warps: with P blocks in the pass, the first P - 8
+    // warps take two consecutive blocks (row-major order: when they share their row block a,
+    // each broadcast row load serves both), the others one
     for (int pass = 0; pass * 16 < nblocks; ++pass) {
-      const int blk0 = pass * 16 + warp, blk1 = blk0 + 8;
-      const bool has0 = blk0 < nblocks, has1 = blk1 < nblocks;
+      const int P = min(16, nblocks - pass * 16), np = max(0, P - 8);
+      const int blk0 = pass * 16 + (warp < np ? 2 * warp : np + warp);
+      const int blk1 = warp < np ? blk0 + 1 : nblocks;
+      const bool has0 = warp < np || np + warp < P, has1 = warp < np;
       int a0 = 0, b0 = 0, a1 = 0, b1 = 0;
-      if (has0) block_of(blk0, a0, b0);
-      if (has1) block_of(blk1, a1, b1);
+      if (has0) block_of(blk0, nb, a0, b0);
+      if (has1) block_of(blk1, nb, a1, b1);
       float acc0[32], acc1[32];
 #pragma unroll
       for (int r = 0; r < 32; ++r) acc0[r] = acc1[r] = 0.f;
@@ -1122,7 +1131,27 @@ pairs_prune_kernel(const T* __restrict__ Xs, int d, int dpad, GramJob J, RuleArg
             nn = fmaf(x.w, x.w, nn);
           }
         }
-        if (has0) {
+        if (has1 && a1 == a0) {  // shared rows
+          const float* xj0 = sm.xs[buf][32 * b0 + lane];
+          const float* xj1 = sm.xs[buf][32 * b1 + lane];
+#pragma unroll 1
+          for (int k = 0; k < PP_KC; k += 4) {
+            const float4 y0 = *reinterpret_cast<const float4*>(xj0 + k);
+            const float4 y1 = *reinterpret_cast<const float4*>(xj1 + k);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+              const float4 x = *reinterpret_cast<const float4*>(&sm.xs[buf][32 * a0 + r][k]);
+              acc0[r] = fmaf(x.x, y0.x, acc0[r]);
+              acc1[r] = fmaf(x.x, y1.x, acc1[r]);
+              acc0[r] = fmaf(x.y, y0.y, acc0[r]);
+              acc1[r] = fmaf(x.y, y1.y, acc1[r]);
+              acc0[r] = fmaf(x.z, y0.z, acc0[r]);
+              acc1[r] = fmaf(x.z, y1.z, acc1[r]);
+              acc0[r] = fmaf(x.w, y0.w, acc0[r]);
+              acc1[r] = fmaf(x.w, y1.w, acc1[r]);
+            }
+          }
+        } else if (has0) {
           const float* xj0 = sm.xs[buf][32 * b0 + lane];
           const float* xj1 = sm.xs[buf][32 * b1 + lane];
 #pragma unroll 1
