@@ -243,47 +243,55 @@ CNG_DEV bool decide_pair(const GramList& sm, const T* __restrict__ Xs, int d, in
 }
 
 CNG_DEV uint32_t word(const uint4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
-CNG_DEV void set_word(uint4& v, int q, uint32_t x) {
-  v.x = q == 0 ? x : v.x;
-  v.y = q == 1 ? x : v.y;
-  v.z = q == 2 ? x : v.z;
-  v.w = q == 3 ? x : v.w;
-}
 
-// Returns |S| (uniform over the warp); S written to S[].  Entry j's words q of bp / bt cover the
-// entries of chunk q; only q <= j / 32 are read.
-template <typename T, bool EXACT = true>
-CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restrict__ Xs, int d, int dpad,
-                       int64_t p, const RuleArgs& r, int lane, unsigned long long& ties) {
-  uint4 K = make_uint4(0u, 0u, 0u, 0u);  // members of S by chunk (uniform)
+// Alg. 2 on the masks of the list [0, V), V <= 128 NV: bp[j] / bt[j] hold NV uint4 (4 NV words),
+// word q covering the entries of chunk q (only q <= j / 32 are read).  Returns |S| (uniform over
+// the warp); S written to S[].
+template <typename T, bool EXACT, int NV>
+CNG_DEV int mask_sweep(const GramList& gl, const uint4* bp, const uint4* bt, int32_t* S, int V,
+                       const T* __restrict__ Xs, int d, int dpad, int64_t p, const RuleArgs& r, int lane,
+                       unsigned long long& ties) {
+  constexpr int NW = 4 * NV;
+  const uint32_t* bpw = reinterpret_cast<const uint32_t*>(bp);
+  const uint32_t* btw = reinterpret_cast<const uint32_t*>(bt);
+  uint32_t K[NW];  // members of S by chunk (uniform)
+#pragma unroll
+  for (int q = 0; q < NW; ++q) K[q] = 0u;
   int ns = 0;
   const int nch = (V + 31) >> 5;
 #pragma unroll 1
   for (int c = 0; c < nch; ++c) {
     const int j = c * 32 + lane;
     bool alive = j < V;
+    // the entry's mask words: one list's four words held in registers, longer lists' read as used
     uint4 p4 = make_uint4(0u, 0u, 0u, 0u), t4 = p4;
-    if (alive) {
-      p4 = *reinterpret_cast<const uint4*>(sm.bp[j]);
-      t4 = *reinterpret_cast<const uint4*>(sm.bt[j]);
+    if (NV == 1 && alive) {
+      p4 = bp[j];
+      t4 = bt[j];
     }
+    auto pw = [&](int q) { return NV == 1 ? word(p4, q) : bpw[j * NW + q]; };
+    auto tw = [&](int q) { return NV == 1 ? word(t4, q) : btw[j * NW + q]; };
     if (alive && c > 0) {  // members of S from earlier chunks
       uint32_t hit = 0u, tie = 0u;
-      for (int q = 0; q < c; ++q) {
-        hit |= word(p4, q) & word(K, q);
-        tie |= word(t4, q) & word(K, q);
-      }
+#pragma unroll
+      for (int q = 0; q < NW; ++q)
+        if (q < c) {
+          hit |= pw(q) & K[q];
+          tie |= tw(q) & K[q];
+        }
       if (tie == 0u) {
         alive = hit == 0u;
       } else {  // ascending over the members that prune or tie, until one prunes
-        for (int q = 0; q < c && alive; ++q) {
-          const uint32_t bq = word(p4, q);
-          uint32_t m = (bq | word(t4, q)) & word(K, q);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+          if (q >= c || !alive) continue;
+          const uint32_t bq = pw(q);
+          uint32_t m = (bq | tw(q)) & K[q];
           while (m && alive) {
             const int b = __ffs(m) - 1;
             if ((bq >> b) & 1u) {
               alive = false;
-            } else if (decide_pair<T, EXACT>(sm, Xs, d, dpad, p, q * 32 + b, j, r, ties)) {
+            } else if (decide_pair<T, EXACT>(gl, Xs, d, dpad, p, q * 32 + b, j, r, ties)) {
               alive = false;
             }
             m &= m - 1u;
@@ -292,7 +300,7 @@ CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restric
       }
     }
     // this chunk in order: the first alive entry joins S and tests the later ones
-    const uint32_t bpc = word(p4, c), btc = word(t4, c);
+    const uint32_t bpc = j < V ? pw(c) : 0u, btc = j < V ? tw(c) : 0u;
     uint32_t kc = 0u;
     bool full = false;
     uint32_t live_m = __ballot_sync(FULL, alive);
@@ -317,14 +325,14 @@ CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restric
         kc &= pos == 31 ? 0xffffffffu : ((2u << pos) - 1u);
         full = true;
       }
-      if ((kc >> lane) & 1u) S[ns + __popc(kc & ((1u << lane) - 1u))] = sm.ids[c * 32 + lane];
+      if ((kc >> lane) & 1u) S[ns + __popc(kc & ((1u << lane) - 1u))] = gl.ids[c * 32 + lane];
       ns += __popc(kc);
       live_m = 0u;
     }
     while (live_m) {
       const int b = __ffs(live_m) - 1;
       kc |= 1u << b;
-      if (lane == 0) S[ns] = sm.ids[c * 32 + b];
+      if (lane == 0) S[ns] = gl.ids[c * 32 + b];
       ++ns;
       if (ns >= r.R) {
         full = true;
@@ -334,16 +342,26 @@ CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restric
         if ((bpc >> b) & 1u) {
           alive = false;
         } else if ((btc >> b) & 1u) {
-          if (decide_pair<T, EXACT>(sm, Xs, d, dpad, p, c * 32 + b, j, r, ties)) alive = false;
+          if (decide_pair<T, EXACT>(gl, Xs, d, dpad, p, c * 32 + b, j, r, ties)) alive = false;
         }
       }
       live_m = __ballot_sync(FULL, alive) & ~((2u << b) - 1u);
     }
-    set_word(K, c, kc);
+#pragma unroll
+    for (int q = 0; q < NW; ++q)
+      if (q == c) K[q] = kc;
     if (full) break;
   }
   __syncwarp();
   return ns;
+}
+
+// The Gram tiles' lists: 4 words per entry (V <= 128).
+template <typename T, bool EXACT = true>
+CNG_DEV int gram_sweep(const GramList& sm, int32_t* S, int V, const T* __restrict__ Xs, int d, int dpad,
+                       int64_t p, const RuleArgs& r, int lane, unsigned long long& ties) {
+  return mask_sweep<T, EXACT, 1>(sm, reinterpret_cast<const uint4*>(sm.bp),
+                                 reinterpret_cast<const uint4*>(sm.bt), S, V, Xs, d, dpad, p, r, lane, ties);
 }
 
 // Masks and sweep for the list [0, V) with the fixed rule, or with Alg. 4's alpha steps.
@@ -925,101 +943,15 @@ struct __align__(16) PairsSmem {
 };
 constexpr int PP_SMEM = (int)sizeof(PairsSmem);
 
-// Alg. 2 on masks of nw words per entry (entries [0, V), V <= 32 nw).  Same order and near-tie
-// treatment as gram_sweep.
+// Alg. 2 on the all-pairs masks: PP_NW words per entry (V <= 256), near-ties re-decided by the
+// FP32 difference form with the band, then FP64.
 template <typename T>
 CNG_DEV int pairs_sweep(PairsSmem& sm, int V, const T* __restrict__ Xs, int d, int dpad, int64_t p,
                         const RuleArgs& r, int lane, unsigned long long& ties) {
   const GramList gl{sm.ids, sm.dist, sm.nrm, nullptr, nullptr};
-  uint32_t K[PP_NW];
-#pragma unroll
-  for (int q = 0; q < PP_NW; ++q) K[q] = 0u;
-  int ns = 0;
-  const int nch = (V + 31) >> 5;
-#pragma unroll 1
-  for (int c = 0; c < nch; ++c) {
-    const int j = c * 32 + lane;
-    bool alive = j < V;
-    if (alive && c > 0) {  // members of S from earlier chunks
-      uint32_t hit = 0u, tie = 0u;
-#pragma unroll
-      for (int q = 0; q < PP_NW; ++q)
-        if (q < c) {
-          hit |= sm.bp[j][q] & K[q];
-          tie |= sm.bt[j][q] & K[q];
-        }
-      if (tie == 0u) {
-        alive = hit == 0u;
-      } else {  // ascending over the members that prune or tie, until one prunes
-#pragma unroll
-        for (int q = 0; q < PP_NW; ++q) {
-          if (q >= c || !alive) continue;
-          const uint32_t bq = sm.bp[j][q];
-          uint32_t m = (bq | sm.bt[j][q]) & K[q];
-          while (m && alive) {
-            const int b = __ffs(m) - 1;
-            if ((bq >> b) & 1u) {
-              alive = false;
-            } else if (decide_pair<T, false>(gl, Xs, d, dpad, p, q * 32 + b, j, r, ties)) {
-              alive = false;
-            }
-            m &= m - 1u;
-          }
-        }
-      }
-    }
-    const uint32_t bpc = j < V ? sm.bp[j][c] : 0u, btc = j < V ? sm.bt[j][c] : 0u;
-    uint32_t kc = 0u;
-    bool full = false;
-    uint32_t live_m = __ballot_sync(FULL, alive);
-    if (!__any_sync(FULL, alive && btc != 0u)) {  // no near-tie inside the chunk: bit greedy
-      uint32_t prb[32];
-#pragma unroll
-      for (int b = 0; b < 32; ++b) prb[b] = __ballot_sync(FULL, (bpc >> b) & 1u);
-#pragma unroll
-      for (int b = 0; b < 32; ++b) {
-        if ((live_m >> b) & 1u) {
-          kc |= 1u << b;
-          live_m &= ~prb[b];
-        }
-      }
-      const int room = r.R - ns;
-      if (__popc(kc) >= room) {
-        uint32_t t = kc;
-        for (int i = 1; i < room; ++i) t &= t - 1u;
-        const int pos = __ffs(t) - 1;
-        kc &= pos == 31 ? 0xffffffffu : ((2u << pos) - 1u);
-        full = true;
-      }
-      if ((kc >> lane) & 1u) sm.S[ns + __popc(kc & ((1u << lane) - 1u))] = sm.ids[c * 32 + lane];
-      ns += __popc(kc);
-      live_m = 0u;
-    }
-    while (live_m) {
-      const int b = __ffs(live_m) - 1;
-      kc |= 1u << b;
-      if (lane == 0) sm.S[ns] = sm.ids[c * 32 + b];
-      ++ns;
-      if (ns >= r.R) {
-        full = true;
-        break;
-      }
-      if (alive && lane > b) {
-        if ((bpc >> b) & 1u) {
-          alive = false;
-        } else if ((btc >> b) & 1u) {
-          if (decide_pair<T, false>(gl, Xs, d, dpad, p, c * 32 + b, j, r, ties)) alive = false;
-        }
-      }
-      live_m = __ballot_sync(FULL, alive) & ~((2u << b) - 1u);
-    }
-#pragma unroll
-    for (int q = 0; q < PP_NW; ++q)
-      if (q == c) K[q] = kc;
-    if (full) break;
-  }
-  __syncwarp();
-  return ns;
+  return mask_sweep<T, false, PP_NW / 4>(gl, reinterpret_cast<const uint4*>(sm.bp),
+                                         reinterpret_cast<const uint4*>(sm.bt), sm.S, V, Xs, d, dpad, p, r,
+                                         lane, ties);
 }
 
 // Block t of the blocks (a, b), a <= b < nb, in row-major order (a outer): consecutive blocks

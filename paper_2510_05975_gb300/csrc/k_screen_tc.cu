@@ -46,6 +46,7 @@ static_assert((2 * TC_MAXST + 2 * TC_NBUF + 2 * TC_NR + 3) * 8 + 8 <= 256,
 static_assert(TC_MAXST >= TC_NR, "the column-norm area holds max(stages, ring slots) tiles");
 static_assert(TC_NBUF == 2 || TC_NBUF == 4, "two or four accumulator buffers");
 constexpr int TC_KC = 64;           // K elements per 128-byte swizzle chunk
+constexpr int TC_SLACK = 16;        // keys past the Lp-th a thinning may keep (one digit pass)
 constexpr int TC_THREADS = 320;     // 8 epilogue warps + producer + MMA
 constexpr int TC_PRODUCER = 8;
 constexpr int TC_MMA = 9;
@@ -308,6 +309,122 @@ CNG_DEV uint32_t warp_compact_hist(uint64_t* buf, int cnt, int Lp, int lane, uin
   }
   __syncwarp();
   return kth;
+}
+
+// Warp-cooperative thinning of a row's buffer between tiles: keeps every buffered key up to a
+// cut, with Lp <= kept <= Lp + slack, moves them to the front and returns the largest kept key
+// (the row's new threshold); *kept = their number.  Each dropped key lies above every kept one,
+// so at least Lp buffered keys stay at or below the threshold and no dropped column can be
+// among the row's Lp smallest.  The radix select runs on the keys relative to the buffer's
+// minimum, shifted left until the range fills 32 bits, so the first 8-bit digit already spans
+// the buffer: one histogram pass usually places the cut (a bucket of at most `slack` keys past
+// the Lp-th is kept whole).  Otherwise the next digit refines it, and after the last digit
+// the ties at the Lp-th key are kept in buffer order as in warp_compact_hist.
+template <int CAP_PER_LANE>
+CNG_DEV uint32_t warp_thin_hist(uint64_t* buf, int cnt, int Lp, int slack, int lane, uint32_t* hist,
+                                int* kept) {
+  uint32_t k[CAP_PER_LANE];
+  uint64_t e[CAP_PER_LANE];
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll
+  for (int i = 0; i < CAP_PER_LANE; ++i) {
+    const int idx = i * 32 + lane;
+    e[i] = idx < cnt ? buf[idx] : ~0ull;
+    k[i] = (uint32_t)(e[i] >> 32);
+    if (idx < cnt) {
+      kmin = min(kmin, k[i]);
+      kmax = max(kmax, k[i]);
+    }
+  }
+  kmin = __reduce_min_sync(FULL, kmin);
+  kmax = __reduce_max_sync(FULL, kmax);
+  const uint32_t range = kmax - kmin;
+  const int sh = range ? __clz(range) : 0;
+#pragma unroll
+  for (int i = 0; i < CAP_PER_LANE; ++i) k[i] = (k[i] - kmin) << sh;  // order kept: no overflow
+  __syncwarp();
+  uint32_t prefix = 0;
+  int need = Lp, shift = 24;
+  bool whole = false;
+  const uint32_t hist_s = smem_u32(hist);
+#pragma unroll 1
+  for (int pass = 0; pass < 4; ++pass) {
+    shift = 24 - 8 * pass;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < CAP_PER_LANE; ++i) {
+      const bool valid = i * 32 + lane < cnt;
+      const bool match = pass == 0 || ((k[i] ^ prefix) >> (shift + 8)) == 0;
+      if (valid && match)
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(hist_s + 4u * ((k[i] >> shift) & 255u)) : "memory");
+    }
+    __syncwarp();
+    uint32_t h[8], tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = hist[lane * 8 + i];
+      tot += h[i];
+    }
+    uint32_t inc = tot;  // inclusive scan of lane totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const uint32_t excl = inc - tot;
+    const unsigned hit = __ballot_sync(FULL, excl < (uint32_t)need && inc >= (uint32_t)need);
+    const int src = __ffs(hit) - 1;
+    int digit = 0, below = 0, hd = 0;
+    if (lane == src) {
+      uint32_t acc = excl;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (acc + h[i] >= (uint32_t)need) {
+          digit = lane * 8 + i;
+          hd = (int)h[i];
+          break;
+        }
+        acc += h[i];
+      }
+      below = (int)acc;
+    }
+    digit = __shfl_sync(FULL, digit, src);
+    below = __shfl_sync(FULL, below, src);
+    hd = __shfl_sync(FULL, hd, src);
+    need -= below;  // keys still needed from the bucket `digit` (1 .. hd)
+    prefix |= (uint32_t)digit << shift;
+    __syncwarp();
+    if (hd - need <= slack) {
+      whole = true;
+      break;
+    }
+  }
+  // whole: keep every key up to the bucket's end; else keep the keys below prefix and the first
+  // `need` equal to it
+  const uint32_t cut = whole ? (prefix | ((1u << shift) - 1u)) : prefix;
+  int out = 0, eq_taken = 0;
+  uint32_t kmx = 0u;
+#pragma unroll
+  for (int i = 0; i < CAP_PER_LANE; ++i) {
+    const bool valid = i * 32 + lane < cnt;
+    const bool lt = valid && (whole ? k[i] <= cut : k[i] < cut);
+    const bool eq = !whole && valid && k[i] == cut;
+    const unsigned beq = __ballot_sync(FULL, eq);
+    const int eq_rank = eq_taken + __popc(beq & ((1u << lane) - 1));
+    const bool keep = lt || (eq && eq_rank < need);
+    eq_taken += __popc(beq);
+    const unsigned bk = __ballot_sync(FULL, keep);
+    if (keep) {
+      buf[out + __popc(bk & ((1u << lane) - 1))] = e[i];
+      kmx = max(kmx, (uint32_t)(e[i] >> 32));
+    }
+    out += __popc(bk);
+  }
+  __syncwarp();
+  *kept = out;
+  return __reduce_max_sync(FULL, kmx);
 }
 
 CNG_DEV float min3f(float a, float b, float c) {
@@ -674,10 +791,11 @@ screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           const int c_l = min(__shfl_sync(FULL, cnt, l), P.cap);
           uint64_t* buf_l = reinterpret_cast<uint64_t*>(__shfl_sync(FULL, reinterpret_cast<uintptr_t>(rbuf), l));
           __syncwarp();
-          const uint32_t k = warp_compact_hist<CPL>(buf_l, c_l, P.Lp, lane, hist);
+          int kept;
+          const uint32_t k = warp_thin_hist<CPL>(buf_l, c_l, P.Lp, TC_SLACK, lane, hist, &kept);
           if (lane == l) {
             thr = fkey_inv(k);
-            cnt = P.Lp;
+            cnt = kept;
           }
         }
       }
