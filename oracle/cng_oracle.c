@@ -645,7 +645,11 @@ int or_build_beam(const float *X, int64_t n, int d, double alpha, double tau, in
  *   for every unreached p: beam-search(G, x_p, s, Lc, Lc) on the current graph (all Lc results);
  *     r(p) = the first of its results (nearest first; all reached points) whose row has a free
  *     slot (deg < Rs, degrees as at the start of the round); none: p waits for a later round;
- *   every reached r named by some r(p) gets the edge r -> (smallest such p).
+ *   if some unreached p without any in-edge has an r(p): each such p (ascending) gets the edge
+ *     r(p) -> p while r(p)'s row has a free slot (such a p can be reached in no other way, so
+ *     every one of these edges is necessary; the other unreached points wait, as the new edges
+ *     may reach them);
+ *   otherwise every reached r named by some r(p) gets the edge r -> (smallest such p).
  * adj rows have stride Rs; phase-3 rows use at most R < Rs of them.  Returns the number of
  * edges added (rounds in *rounds_out), or -3 if a round could add no edge.
  */
@@ -656,7 +660,8 @@ int or_connect(const float *X, int64_t n, int d, int32_t *adj, int32_t *deg, int
     int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * n);
     int32_t *U = (int32_t *)malloc(sizeof(int32_t) * n);
     int32_t *best = (int32_t *)malloc(sizeof(int32_t) * n);
-    if (!reach || !stack || !U || !best) return OR_E_NOMEM;
+    unsigned char *has_in = (unsigned char *)malloc((size_t)n);
+    if (!reach || !stack || !U || !best || !has_in) return OR_E_NOMEM;
     for (int64_t i = 0; i < n; ++i) best[i] = -1;
     int total = 0, rounds = 0, rc = 0;
     for (;;) {
@@ -686,21 +691,41 @@ int or_connect(const float *X, int64_t n, int d, int32_t *adj, int32_t *deg, int
         if (!Qm || !rid || !rd) return OR_E_NOMEM;
         for (int64_t i = 0; i < nu; ++i) memcpy(Qm + i * d, X + (int64_t)U[i] * d, sizeof(float) * d);
         or_search(X, n, d, adj, deg, Rs, s, Qm, nu, kc, Lc, rid, rd, NULL, NULL);
-        for (int64_t i = 0; i < nu; ++i) { /* U ascending: the first p naming r is the smallest */
+        memset(has_in, 0, (size_t)n);
+        for (int64_t u = 0; u < n; ++u)
+            for (int j = 0; j < deg[u]; ++j) has_in[adj[u * Rs + j]] = 1;
+        /* r(p) with the degrees at the start of the round, kept in rid[i * kc] */
+        int64_t nz = 0;
+        for (int64_t i = 0; i < nu; ++i) {
             int32_t r = -1;
             for (int t = 0; t < kc && r < 0; ++t) {
                 int32_t c = rid[i * kc + t];
                 if (c >= 0 && deg[c] < Rs) r = c;
             }
-            if (r >= 0 && best[r] < 0) best[r] = U[i];
+            rid[i * kc] = r;
+            if (r >= 0 && !has_in[U[i]]) ++nz;
         }
         int added = 0;
-        for (int64_t r = 0; r < n; ++r) {
-            if (best[r] < 0) continue;
-            adj[r * Rs + deg[r]] = best[r];
-            deg[r] += 1;
-            ++added;
-            best[r] = -1;
+        if (nz > 0) { /* U ascending: each r takes its points without in-edges, smallest first */
+            for (int64_t i = 0; i < nu; ++i) {
+                const int32_t r = rid[i * kc];
+                if (r < 0 || has_in[U[i]] || deg[r] >= Rs) continue;
+                adj[(int64_t)r * Rs + deg[r]] = U[i];
+                deg[r] += 1;
+                ++added;
+            }
+        } else {
+            for (int64_t i = 0; i < nu; ++i) { /* the first p naming r is the smallest */
+                const int32_t r = rid[i * kc];
+                if (r >= 0 && best[r] < 0) best[r] = U[i];
+            }
+            for (int64_t r = 0; r < n; ++r) {
+                if (best[r] < 0) continue;
+                adj[r * Rs + deg[r]] = best[r];
+                deg[r] += 1;
+                ++added;
+                best[r] = -1;
+            }
         }
         free(Qm);
         free(rid);
@@ -712,6 +737,7 @@ int or_connect(const float *X, int64_t n, int d, int32_t *adj, int32_t *deg, int
         total += added;
     }
     free(reach);
+    free(has_in);
     free(stack);
     free(U);
     free(best);

@@ -117,6 +117,22 @@ def test_knn_rows_vs_oracle(kind, d, screen):
     assert np.allclose(host(ds), rd, rtol=2e-6)
 
 
+def test_knn_screen_heavy_ties():
+    """Lattice points (coordinates 0..3 in 8 dimensions): squared distances take fewer than 80
+    values, so the screen's row buffers hold runs of equal keys far longer than the thinning
+    slack between tiles.  The selection then keeps ties in buffer order, and the rerank's
+    certification (with exact rescans) must still give the exact (distance, id) lists."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(17)
+    X = rng.integers(0, 4, size=(6000, 8)).astype(np.float32)
+    ids, ds, st = cng.cng_knn(tensor(X), 100, screen=cng.CNG_SCREEN_TC)
+    ref, rd = oracle.knn(X, 100)
+    assert st["screen_used"] == 1
+    assert np.array_equal(host(ids), ref)
+    assert np.allclose(host(ds), rd, rtol=0, atol=0)
+
+
 @pytest.mark.parametrize("kind,n,d,R,L", [
     ("sift", 60_001, 128, 32, 128),   # two waves of 152 row blocks and a ragged tail
     ("deep", 41_000, 96, 24, 80),

@@ -180,19 +180,35 @@ def test_connectivity_repair_on_clusters():
     assert np.all(G.deg <= 12 + oracle.REPAIR_SLOTS)
     for p in range(n):  # phase-3 edges kept in place, repair edges appended
         assert np.array_equal(G.adj[p, : G.deg3[p]], G.adj3[p, : G.deg3[p]])
-    # the first round's edges: r -> smallest p whose search from the entry ends at r
+    # the first round's edges, from the searches for the unreached points on the phase-3 graph:
+    # r(p) = the first result with a free slot; points without in-edges go first, each to its
+    # r(p) while that row has room, else each named r takes the smallest p naming it
     reach0 = _reachable(G.adj3, G.deg3, G.entry)
     U = np.array(sorted(set(range(n)) - reach0), np.int32)
-    ids, _, _, _ = oracle.search(X, G.adj3, G.deg3, G.entry, X[U], 8, oracle.CONNECT_L)
-    first = {}
+    ids, _, _, _ = oracle.search(X, G.adj3, G.deg3, G.entry, X[U], oracle.CONNECT_L,
+                                 oracle.CONNECT_L)
     Rs = 12 + oracle.REPAIR_SLOTS
+    has_in = np.zeros(n, bool)
+    for u in range(n):
+        has_in[G.adj3[u, : G.deg3[u]]] = True
+    rp = {}
     for p, row in zip(U, ids):
         r = next((int(c) for c in row if c >= 0 and G.deg3[c] < Rs), None)
         if r is not None:
-            first.setdefault(r, int(p))
-    for r, p in first.items():
-        assert int(r) in reach0
-        assert G.adj[r, G.deg3[r]] == p
+            rp[int(p)] = r
+    taken = {}
+    if any(not has_in[p] for p in rp):
+        for p in sorted(rp):
+            r = rp[p]
+            if not has_in[p] and G.deg3[r] + len(taken.get(r, [])) < Rs:
+                taken.setdefault(r, []).append(p)
+    else:
+        for p in sorted(rp):
+            taken.setdefault(rp[p], [p])
+    assert taken
+    for r, ps in taken.items():
+        assert r in reach0
+        assert G.adj[r, G.deg3[r]: G.deg3[r] + len(ps)].tolist() == ps
 
 
 ADAPT = (0.9, 1.6, 0.05)  # the paper's setting (Sec. 4.4): alpha0, alpha_max, dalpha
