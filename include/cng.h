@@ -165,8 +165,10 @@ typedef struct cng_index cng_index;
  *   exceeds R, else kept in (D, id) order (phase 3, lazy pruning of Sec. 4.3);
  *   connectivity (phase 4): in rounds, every point p not reachable from s is searched for from
  *   s (Alg. 1, beam connect_L, all connect_L results); its first result r whose row has a free
- *   slot names p, and each named r gets an edge to the smallest point naming it.  Rows hold up
- *   to R pruned edges plus up to repair_slots (default 8) such edges.
+ *   slot names p.  Points without in-edges get the edge r -> p, a row taking them in ascending
+ *   order while it has free slots; in a round where none of them can be linked, each named r
+ *   gets an edge to the smallest point naming it.  Rows hold up to R pruned edges plus up to
+ *   repair_slots (default 8) such edges.
  * points: host or device, n x d of `dtype`, borrowed for the call only (the index keeps its own
  * device copy).  *out receives a new index owned by the caller (free with cng_free).
  * stats may be NULL.  Synchronises `stream` before returning.

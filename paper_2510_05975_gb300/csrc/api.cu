@@ -853,7 +853,7 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
   int repair_rounds = 0;
   if (P.connect_L >= 0) {
     const int Lc = P.connect_L > 0 ? P.connect_L : CONNECT_L;
-    int32_t *reached, *fa, *fb, *U, *rid, *best, *qdeg, *qhops;
+    int32_t *reached, *fa, *fb, *U, *rid, *best, *rp, *has_in, *qdeg, *qhops;
     float* rdist;
     int* counts;
     int *sc_counter;
@@ -867,6 +867,8 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
     CK(pool.alloc(&rid, (size_t)n * kc));
     CK(pool.alloc(&rdist, (size_t)n * kc));
     CK(pool.alloc(&best, (size_t)n));
+    CK(pool.alloc(&rp, (size_t)n));
+    CK(pool.alloc(&has_in, (size_t)n));
     CK(pool.alloc(&counts, 4));
     CK(pool.alloc(&sc_counter, SEARCH_COUNTER_INTS));
     CK(pool.alloc(&sc_tot, 4));
@@ -920,14 +922,26 @@ extern "C" cng_status cng_build(const void* points, int32_t dtype, int64_t n, in
         return fail(CNG_E_UNSUPPORTED, "connectivity search shape does not fit");
       CK(cudaMemsetAsync(sc_counter, 0, SEARCH_COUNTER_INTS * sizeof(int), s));
       CK(launch_search(sa, plan, s));
-      CK(launch_pick_add(U, rid, nu, kc, best, n, adj, deg, Rs, counts + 3, s));
+      // points without in-edges first (each edge necessary), several per row while its slots
+      // last; else one edge per named row to the smallest point naming it
+      CK(launch_has_in(adj, deg, Rs, n, has_in, s));
+      CK(launch_pick(U, rid, nu, kc, deg, Rs, has_in, rp, counts + 3, s));
       CK(cudaMemcpyAsync(&hc_counts[3], counts + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      if (hc_counts[3] == 0)
+      const int zonly = hc_counts[3] > 0;
+      int64_t added = 0;
+      for (int step = 0; step <= Rs; ++step) {  // a row takes at most Rs edges
+        CK(launch_claim_link(U, rp, nu, has_in, zonly, best, adj, deg, Rs, counts + 3, s));
+        CK(cudaMemcpyAsync(&hc_counts[3], counts + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        added += hc_counts[3];
+        if (!zonly || hc_counts[3] == 0) break;
+      }
+      if (added == 0)
         return fail(CNG_E_UNSUPPORTED, "phase 4 could not connect the graph (connectivity slots full; round " +
                                             std::to_string(round) + ", " + std::to_string(nu) +
                                             " points unreachable)");
-      repair_edges += hc_counts[3];
+      repair_edges += added;
     }
     if (round == kMaxRounds)
       return fail(CNG_E_UNSUPPORTED, "phase 4 did not connect the graph within " +

@@ -137,9 +137,20 @@ cudaError_t launch_bfs(const int32_t* adj, const int32_t* deg, int Rs, int64_t n
                        int* counts_host, cudaStream_t st);
 cudaError_t launch_collect(const int32_t* reached, int64_t n, int32_t* U, int* nu_dev,
                            cudaStream_t st);
-cudaError_t launch_pick_add(const int32_t* U, const int32_t* r, int nu, int kc, int32_t* best,
-                            int64_t n, int32_t* adj, int32_t* deg, int Rs, int* added_dev,
-                            cudaStream_t st);
+// has_in[v] = 1 for every edge u -> v of the current rows (0 elsewhere).
+cudaError_t launch_has_in(const int32_t* adj, const int32_t* deg, int Rs, int64_t n, int32_t* has_in,
+                          cudaStream_t st);
+// rp[i] = the first of U[i]'s kc search results whose row has a free slot, or -1; *nz_dev (zeroed
+// here) = how many of them have no in-edge.
+cudaError_t launch_pick(const int32_t* U, const int32_t* r, int nu, int kc, const int32_t* deg,
+                        int Rs, const int32_t* has_in, int32_t* rp, int* nz_dev, cudaStream_t st);
+// One claim-and-link step: every row r with a free slot named by a live rp[i] (only points
+// without in-edges when zonly) gets the edge r -> (smallest such U[i]); the linked entries are
+// retired (rp = -1).  best: n ints, all 0x7fffffff between calls.  *added_dev (zeroed here) =
+// edges added.
+cudaError_t launch_claim_link(const int32_t* U, int32_t* rp, int nu, const int32_t* has_in, int zonly,
+                              int32_t* best, int32_t* adj, int32_t* deg, int Rs, int* added_dev,
+                              cudaStream_t st);
 cudaError_t launch_fill(int32_t* a, int64_t n, int32_t v, cudaStream_t st);
 
 // k_beam.cu: the paper's candidate route (beam search on a K-NN graph G0)

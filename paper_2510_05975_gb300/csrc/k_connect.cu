@@ -3,10 +3,14 @@
 // The paper adds "necessary edges" from the DFS tree of the navigating node s to every point
 // outside it, in line with NSG.  Reading used here, in rounds until every point is reachable:
 //   reached = points reachable from s (frontier BFS);
-//   for every unreached p: r(p) = the nearest result of beam-search(G, x_p, s, Lc, 1) on the
-//     current graph (the batched search kernel with point ids as queries);
-//   every reached r named by some r(p) gets the edge r -> (smallest such p) if its row has a
-//   free slot; rows have stride R + 8 so that phase-3 rows keep all of their edges.
+//   for every unreached p: r(p) = the first result of beam-search(G, x_p, s, Lc, Lc) on the
+//     current graph whose row has a free slot at the start of the round (the batched search
+//     kernel with point ids as queries);
+//   if some unreached p without any in-edge has an r(p): each such p gets the edge r(p) -> p,
+//     a row taking its points in ascending order while it has free slots (one claim-and-link
+//     step per slot; such a p can be reached in no other way);
+//   otherwise every r named by some r(p) gets the edge r -> (smallest such p).
+// Rows have stride R + slots so that phase-3 rows keep all of their edges.
 #include "launch_count.h"
 #include "cng_internal.h"
 #include "device_common.cuh"
@@ -45,31 +49,61 @@ __global__ void collect_unreached_kernel(const int32_t* __restrict__ reached, in
   if (i < n && !reached[i]) U[atomicAdd(nu, 1)] = (int32_t)i;
 }
 
-// deg is read before add_edges_kernel changes it: the snapshot of the round's start.
-__global__ void pick_kernel(const int32_t* __restrict__ U, const int32_t* __restrict__ r, int nu,
-                            int kc, const int32_t* __restrict__ deg, int Rs,
-                            int32_t* __restrict__ best) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nu) return;
-  for (int t = 0; t < kc; ++t) {
-    int32_t c = r[(int64_t)i * kc + t];
-    if (c >= 0 && deg[c] < Rs) {
-      atomicMin(&best[c], U[i]);
-      return;
-    }
-  }
+__global__ void has_in_kernel(const int32_t* __restrict__ adj, const int32_t* __restrict__ deg, int Rs,
+                              int64_t n, int32_t* __restrict__ has_in) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * Rs) return;
+  const int64_t u = e / Rs;
+  const int j = (int)(e - u * Rs);
+  if (j < deg[u]) has_in[adj[e]] = 1;
 }
 
-__global__ void add_edges_kernel(int32_t* __restrict__ best, int64_t n, int32_t* __restrict__ adj,
-                                 int32_t* __restrict__ deg, int Rs, int* __restrict__ added) {
-  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int32_t p = best[r];
-  if (p == 0x7fffffff) return;
-  best[r] = 0x7fffffff;
-  int dg = deg[r];  // < Rs: pick_kernel only names rows with a free slot
-  adj[r * Rs + dg] = p;
+// r(p) with the degrees at the start of the round (before any edge of the round is added)
+__global__ void pick_kernel(const int32_t* __restrict__ U, const int32_t* __restrict__ r, int nu,
+                            int kc, const int32_t* __restrict__ deg, int Rs,
+                            const int32_t* __restrict__ has_in, int32_t* __restrict__ rp,
+                            int* __restrict__ nz) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  int32_t pick = -1;
+  for (int t = 0; t < kc; ++t) {
+    const int32_t c = r[(int64_t)i * kc + t];
+    if (c >= 0 && deg[c] < Rs) {
+      pick = c;
+      break;
+    }
+  }
+  rp[i] = pick;
+  if (pick >= 0 && !has_in[U[i]]) atomicAdd(nz, 1);
+}
+
+__global__ void claim_kernel(const int32_t* __restrict__ U, const int32_t* __restrict__ rp, int nu,
+                             const int32_t* __restrict__ has_in, int zonly,
+                             const int32_t* __restrict__ deg, int Rs, int32_t* __restrict__ best) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  const int32_t r = rp[i];
+  if (r < 0 || deg[r] >= Rs) return;
+  const int32_t p = U[i];
+  if (zonly && has_in[p]) return;
+  atomicMin(&best[r], p);
+}
+
+// The claim of row r is decided (the previous launch finished): its winner alone writes row r.
+__global__ void link_kernel(const int32_t* __restrict__ U, int32_t* __restrict__ rp, int nu,
+                            int32_t* __restrict__ best, int32_t* __restrict__ adj,
+                            int32_t* __restrict__ deg, int Rs, int* __restrict__ added) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  const int32_t r = rp[i];
+  if (r < 0) return;
+  const int32_t p = U[i];
+  if (best[r] != p) return;
+  const int dg = deg[r];  // < Rs: claim_kernel checked it
+  adj[(int64_t)r * Rs + dg] = p;
   deg[r] = dg + 1;
+  best[r] = 0x7fffffff;
+  rp[i] = -1;
   atomicAdd(added, 1);
 }
 
@@ -109,14 +143,33 @@ cudaError_t launch_collect(const int32_t* reached, int64_t n, int32_t* U, int* n
   return cudaGetLastError();
 }
 
-cudaError_t launch_pick_add(const int32_t* U, const int32_t* r, int nu, int kc, int32_t* best,
-                            int64_t n, int32_t* adj, int32_t* deg, int Rs, int* added_dev,
-                            cudaStream_t st) {
-  cudaMemsetAsync(added_dev, 0, sizeof(int), st);
+cudaError_t launch_has_in(const int32_t* adj, const int32_t* deg, int Rs, int64_t n, int32_t* has_in,
+                          cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(has_in, 0, (size_t)n * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
   count_launch();
-  pick_kernel<<<blocks(nu), 256, 0, st>>>(U, r, nu, kc, deg, Rs, best);
+  has_in_kernel<<<blocks(n * Rs), 256, 0, st>>>(adj, deg, Rs, n, has_in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pick(const int32_t* U, const int32_t* r, int nu, int kc, const int32_t* deg,
+                        int Rs, const int32_t* has_in, int32_t* rp, int* nz_dev, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(nz_dev, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   count_launch();
-  add_edges_kernel<<<blocks(n), 256, 0, st>>>(best, n, adj, deg, Rs, added_dev);
+  pick_kernel<<<blocks(nu), 256, 0, st>>>(U, r, nu, kc, deg, Rs, has_in, rp, nz_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_claim_link(const int32_t* U, int32_t* rp, int nu, const int32_t* has_in, int zonly,
+                              int32_t* best, int32_t* adj, int32_t* deg, int Rs, int* added_dev,
+                              cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(added_dev, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  claim_kernel<<<blocks(nu), 256, 0, st>>>(U, rp, nu, has_in, zonly, deg, Rs, best);
+  count_launch();
+  link_kernel<<<blocks(nu), 256, 0, st>>>(U, rp, nu, best, adj, deg, Rs, added_dev);
   return cudaGetLastError();
 }
 

@@ -130,7 +130,7 @@ def test_knn_screen_heavy_ties():
     ref, rd = oracle.knn(X, 100)
     assert st["screen_used"] == 1
     assert np.array_equal(host(ids), ref)
-    assert np.allclose(host(ds), rd, rtol=0, atol=0)
+    assert np.allclose(host(ds), rd, rtol=2e-7, atol=0)  # exact D^2, one FP32 square root
 
 
 @pytest.mark.parametrize("kind,n,d,R,L", [
