@@ -725,6 +725,7 @@ CNG_DEV void cta_bitonic64(uint64_t* a, int P2) {
 }
 
 constexpr int PR_RUN = 256;  // longest near-tie run re-sorted in FP64
+constexpr int PR_PREFIX = 512;  // entries of a large merged set ordered and pruned first
 
 // Per-node working arrays of the merge (shared memory for ordinary nodes, global scratch for
 // nodes whose merged set exceeds the shared capacity).
@@ -746,7 +747,7 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
                        PruneSmem& sm, double* d64, int32_t* rid, int stage_cap, int* s_nv,
                        int32_t* __restrict__ adj_row, Counters* ctr, unsigned long long& ties,
                        unsigned long long& ordties, unsigned long long& repruned,
-                       const MergeScratch& ms) {
+                       const MergeScratch& ms, int lim0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = tid % PR_G, grp = tid / PR_G;
   sm.ids = ar.ids;
@@ -783,141 +784,168 @@ CNG_DEV int merge_node(const T* __restrict__ Xs, int d, int dpad, int64_t p,
   for (int i = nv + tid; i < P2; i += PR_THREADS) ar.keys[i] = ~0ull;
   __syncthreads();
   cta_bitonic64(ar.keys, P2);
-  // FP64 re-decision of near-tied neighbours in the order (warp 0); runs longer than PR_RUN
-  // (large merged sets of hubs with concentrated distances) are recorded, up to 8 per pass,
-  // and re-sorted by the whole CTA, then warp 0 continues after the last recorded one
-  __shared__ int s_lr_start[8], s_lr_len[8], s_nlr, s_next;
-  int from = 0;
-  while (!exact && from + 1 < nv) {
-    if (tid == 0) {
-      s_nlr = 0;
-      s_next = nv;
-    }
+  // FP64 re-decision of near-tied neighbours in the order (warp 0), for the runs that start in
+  // [from, lim); runs longer than PR_RUN (large merged sets of hubs with concentrated
+  // distances) are recorded, up to 8 per pass, and re-sorted by the whole CTA, then warp 0
+  // continues after the last recorded one.  Returns q >= lim: [0, q) is in (D, id) order and
+  // keys[q - 1], keys[q] are not near-tied (or q = nv), so the entries beyond q all follow it.
+  __shared__ int s_lr_start[8], s_lr_len[8], s_nlr, s_next, s_qend;
+  auto resolve_runs = [&](int from, int lim) -> int {
+    if (tid == 0) s_qend = lim;
     __syncthreads();
-    if (warp == 0) {
-      int i = from;
-      while (i + 1 < nv) {
-        int s = -1;
-        for (int b = i; b + 1 < nv && s < 0; b += 32) {
-          int t = b + lane;
-          bool nt = t + 1 < nv && near_tie(key_dist(ar.keys[t]), key_dist(ar.keys[t + 1]), ra.band);
-          unsigned bal = __ballot_sync(FULL, nt);
-          if (bal) s = b + __ffs(bal) - 1;
-        }
-        if (s < 0) break;
-        int e = s + 1;
-        while (e + 1 < nv && near_tie(key_dist(ar.keys[e]), key_dist(ar.keys[e + 1]), ra.band)) ++e;
-        int len = e - s + 1;
-        if (len > PR_RUN) {
-          const bool full = s_nlr == 8;  // warp-uniform (written by lane 0 before a __syncwarp)
-          if (full) {
-            if (lane == 0) s_next = s;
-            break;
+    while (!exact && from + 1 < nv && from < lim) {
+      if (tid == 0) {
+        s_nlr = 0;
+        s_next = nv;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        int i = from;
+        while (i + 1 < nv && i < lim) {
+          int s = -1;
+          for (int b = i; b + 1 < nv && b < lim && s < 0; b += 32) {
+            int t = b + lane;
+            bool nt = t + 1 < nv && t < lim &&
+                      near_tie(key_dist(ar.keys[t]), key_dist(ar.keys[t + 1]), ra.band);
+            unsigned bal = __ballot_sync(FULL, nt);
+            if (bal) s = b + __ffs(bal) - 1;
+          }
+          if (s < 0) break;
+          int e = s + 1;
+          while (e + 1 < nv && near_tie(key_dist(ar.keys[e]), key_dist(ar.keys[e + 1]), ra.band)) ++e;
+          int len = e - s + 1;
+          if (len > PR_RUN) {
+            const bool full = s_nlr == 8;  // warp-uniform (written by lane 0 before a __syncwarp)
+            if (full) {
+              if (lane == 0) s_next = s;
+              break;
+            }
+            __syncwarp();
+            if (lane == 0) {
+              s_lr_start[s_nlr] = s;
+              s_lr_len[s_nlr] = len;
+              ++s_nlr;
+              s_qend = max(s_qend, e + 1);
+            }
+            __syncwarp();
+            ++ordties;
+            i = e + 1;
+            continue;
+          }
+          for (int t = lane; t < len; t += 32) {
+            rid[t] = key_id(ar.keys[s + t]);
+            d64[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)rid[t] * dpad, d);
           }
           __syncwarp();
-          if (lane == 0) {
-            s_lr_start[s_nlr] = s;
-            s_lr_len[s_nlr] = len;
-            ++s_nlr;
+          if (lane == 0) {  // insertion sort of the run by (D, id)
+            for (int a = 1; a < len; ++a) {
+              double dv = d64[a];
+              int32_t iv = rid[a];
+              uint64_t kv = ar.keys[s + a];
+              int b = a - 1;
+              while (b >= 0 && (d64[b] > dv || (d64[b] == dv && rid[b] > iv))) {
+                d64[b + 1] = d64[b];
+                rid[b + 1] = rid[b];
+                ar.keys[s + b + 1] = ar.keys[s + b];
+                --b;
+              }
+              d64[b + 1] = dv;
+              rid[b + 1] = iv;
+              ar.keys[s + b + 1] = kv;
+            }
+            s_qend = max(s_qend, e + 1);
           }
           __syncwarp();
           ++ordties;
           i = e + 1;
-          continue;
         }
-        for (int t = lane; t < len; t += 32) {
-          rid[t] = key_id(ar.keys[s + t]);
-          d64[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)rid[t] * dpad, d);
-        }
-        __syncwarp();
-        if (lane == 0) {  // insertion sort of the run by (D, id)
-          for (int a = 1; a < len; ++a) {
-            double dv = d64[a];
-            int32_t iv = rid[a];
-            uint64_t kv = ar.keys[s + a];
-            int b = a - 1;
-            while (b >= 0 && (d64[b] > dv || (d64[b] == dv && rid[b] > iv))) {
-              d64[b + 1] = d64[b];
-              rid[b + 1] = rid[b];
-              ar.keys[s + b + 1] = ar.keys[s + b];
-              --b;
-            }
-            d64[b + 1] = dv;
-            rid[b + 1] = iv;
-            ar.keys[s + b + 1] = kv;
-          }
-        }
-        __syncwarp();
-        ++ordties;
-        i = e + 1;
       }
-    }
-    __syncthreads();
-    // long runs: canonical distances of the whole run (in the id / dist arrays, free until they
-    // are filled below), then an odd-even transposition sort of the run by (D, id)
-    const int nlr = s_nlr;
-    for (int r = 0; r < nlr; ++r) {
-      const int s0 = s_lr_start[r], len = s_lr_len[r];
-      double* D = reinterpret_cast<double*>(ar.ids);  // ids and dist: 8 bytes per entry, contiguous
-      for (int t = tid; t < len; t += PR_THREADS)
-        D[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)key_id(ar.keys[s0 + t]) * dpad, d);
       __syncthreads();
-      for (int ph = 0; ph < len; ++ph) {
-        for (int t = 2 * tid + (ph & 1); t + 1 < len; t += 2 * PR_THREADS) {
-          const uint64_t ka = ar.keys[s0 + t], kb = ar.keys[s0 + t + 1];
-          if (D[t + 1] < D[t] || (D[t + 1] == D[t] && key_id(kb) < key_id(ka))) {
-            const double tdv = D[t];
-            D[t] = D[t + 1];
-            D[t + 1] = tdv;
-            ar.keys[s0 + t] = kb;
-            ar.keys[s0 + t + 1] = ka;
-          }
-        }
+      // long runs: canonical distances of the whole run (in the id / dist arrays, free until
+      // they are filled below), then an odd-even transposition sort of the run by (D, id)
+      const int nlr = s_nlr;
+      for (int r = 0; r < nlr; ++r) {
+        const int s0 = s_lr_start[r], len = s_lr_len[r];
+        double* D = reinterpret_cast<double*>(ar.ids);  // ids and dist: 8 bytes per entry, contiguous
+        for (int t = tid; t < len; t += PR_THREADS)
+          D[t] = canon_dist(Xs + p * dpad, Xs + (int64_t)key_id(ar.keys[s0 + t]) * dpad, d);
         __syncthreads();
+        for (int ph = 0; ph < len; ++ph) {
+          for (int t = 2 * tid + (ph & 1); t + 1 < len; t += 2 * PR_THREADS) {
+            const uint64_t ka = ar.keys[s0 + t], kb = ar.keys[s0 + t + 1];
+            if (D[t + 1] < D[t] || (D[t + 1] == D[t] && key_id(kb) < key_id(ka))) {
+              const double tdv = D[t];
+              D[t] = D[t + 1];
+              D[t + 1] = tdv;
+              ar.keys[s0 + t] = kb;
+              ar.keys[s0 + t + 1] = ka;
+            }
+          }
+          __syncthreads();
+        }
       }
+      from = s_next;
+      __syncthreads();
     }
-    from = s_next;
     __syncthreads();
-  }
-  for (int i = tid; i < nv; i += PR_THREADS) {
-    ar.ids[i] = key_id(ar.keys[i]);
-    ar.dist[i] = sqrtf(key_dist(ar.keys[i]));
-  }
-  __syncthreads();
-  if (ms.mlist && nv > ra.R && nv <= ms.stride) {
-    // listed in (D, id) order for the all-pairs re-prune, which writes the row and its degree
+    const int q = min(s_qend, nv);
+    __syncthreads();
+    return q;
+  };
+  // A set that will be pruned needs its order only as far as Alg. 2 reads it, which stops at R
+  // kept entries: large sets are ordered and pruned on a prefix first, and only if the sweep
+  // runs out of it with fewer than R kept is the whole set ordered and pruned again.  (With
+  // Alg. 4's alpha steps an early step's count decides whether later steps run, so a sweep that
+  // ran out of the prefix in any step would not do; those sets are ordered whole.)
+  const bool prefix_first =
+      nv > lim0 && nv > ra.R && ra.imax < 0 && !(ms.mlist && nv <= ms.stride);
+  int from = 0, lim = prefix_first ? lim0 : nv, na = 0;
+  for (;;) {
+    const int q = resolve_runs(from, lim);
     for (int i = tid; i < nv; i += PR_THREADS) {
-      ms.mlist[p * ms.stride + i] = ar.ids[i];
-      ms.mdist[p * ms.stride + i] = ar.dist[i];
-    }
-    if (tid == 0) {
-      ms.mlen[p] = nv;
-      ms.rlist[atomicAdd(&ctr->nre, 1)] = (int32_t)p;
+      ar.ids[i] = key_id(ar.keys[i]);
+      ar.dist[i] = sqrtf(key_dist(ar.keys[i]));
     }
     __syncthreads();
-    return -1;
-  }
-  int na;
-  if (nv <= ra.R) {
-    na = nv;
-    for (int i = tid; i < nv; i += PR_THREADS) sm.S[i] = ar.ids[i];
-    __syncthreads();
-  } else if (NS > 0 && nv <= NS * PR_GROUPS) {
+    if (ms.mlist && nv > ra.R && nv <= ms.stride) {
+      // listed in (D, id) order for the all-pairs re-prune, which writes the row and its degree
+      for (int i = tid; i < nv; i += PR_THREADS) {
+        ms.mlist[p * ms.stride + i] = ar.ids[i];
+        ms.mdist[p * ms.stride + i] = ar.dist[i];
+      }
+      if (tid == 0) {
+        ms.mlen[p] = nv;
+        ms.rlist[atomicAdd(&ctr->nre, 1)] = (int32_t)p;
+      }
+      __syncthreads();
+      return -1;
+    }
+    if (nv <= ra.R) {
+      na = nv;
+      for (int i = tid; i < nv; i += PR_THREADS) sm.S[i] = ar.ids[i];
+      __syncthreads();
+      break;
+    }
     int steps;
-    na = prune_with_rule(ra, [&](const RuleArgs& r) {
-      return prune_sweep_reg<T, (NS > 0 ? NS : 1), (DL > 0 ? DL : 1)>(
-          Xs, d, dpad, p, ar.ids, ar.dist, ar.flags, sm.S, sm.vq, nv, r, ties);
-    }, &steps);
-    ++repruned;
-  } else {
-    const int nstage = min(nv, stage_cap);
-    stage_vectors(Xs, dpad, ar.ids, nstage, sm.stage);
-    __syncthreads();
-    int steps;
-    na = prune_with_rule(
-        ra, [&](const RuleArgs& r) { return prune_sweep(Xs, d, dpad, p, sm, nv, nstage, r, ties); },
-        &steps);
-    ++repruned;
+    if (NS > 0 && q <= NS * PR_GROUPS) {
+      na = prune_with_rule(ra, [&](const RuleArgs& r) {
+        return prune_sweep_reg<T, (NS > 0 ? NS : 1), (DL > 0 ? DL : 1)>(
+            Xs, d, dpad, p, ar.ids, ar.dist, ar.flags, sm.S, sm.vq, q, r, ties);
+      }, &steps);
+    } else {
+      const int nstage = min(q, stage_cap);
+      stage_vectors(Xs, dpad, ar.ids, nstage, sm.stage);
+      __syncthreads();
+      na = prune_with_rule(
+          ra, [&](const RuleArgs& r) { return prune_sweep(Xs, d, dpad, p, sm, q, nstage, r, ties); },
+          &steps);
+    }
+    if (na >= ra.R || q >= nv) {
+      ++repruned;
+      break;
+    }
+    from = q;  // the prefix ran out with fewer than R kept: order the rest, prune the whole set
+    lim = nv;
   }
   for (int i = tid; i < ra.rs; i += PR_THREADS) adj_row[i] = i < na ? sm.S[i] : -1;
   __syncthreads();
@@ -972,7 +1000,8 @@ merge_kernel(const T* __restrict__ Xs, int64_t n, int d, int dpad, const int32_t
     }
     maxlist = max(maxlist, (unsigned long long)(nf + nin));
     int na = merge_node<T, NS, DL>(Xs, d, dpad, p, fwd + p * ra.R, nf, inl, i0, nin, ra, exact, ar, sm, d64,
-                        rid, stage_cap, &s_nv, adj + p * ra.rs, ctr, ties, ordties, repruned, ms);
+                        rid, stage_cap, &s_nv, adj + p * ra.rs, ctr, ties, ordties, repruned, ms,
+                        PR_PREFIX);
     if (na < 0) continue;  // listed for the all-pairs re-prune
     if (tid == 0) deg[p] = na;
     edges += na;

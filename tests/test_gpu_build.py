@@ -300,6 +300,51 @@ def test_long_near_tie_run_in_merge(M):
     cng.cng_free(idx)
 
 
+@pytest.mark.parametrize("M", [1200, 5000])
+def test_merge_prefix_of_a_large_set(M):
+    """A hub whose merged set (well over 512 entries; over 2,048 for M = 5000) fills R early:
+    half of M points on a sphere around point 0 at distinct radii 1 .. 1.25, the other half at
+    radius 1.3 (+- 2e-7), one long near-tie run at the end of the hub's order.  Nothing is pruned
+    around the hub, so Alg. 2 keeps its first R entries; the GPU orders and prunes a prefix of
+    the set, never re-sorting the tail run, and the graph equals the oracle's."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal((M, 32))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    h = M // 2
+    r = np.concatenate([1.0 + 0.25 * np.arange(h) / h, 1.3 * (1.0 + 2e-7 * rng.standard_normal(M - h))])
+    X = np.concatenate([np.zeros((1, 32)), v * r[:, None]]).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=16, L=48, keep_lists=True)
+    G = oracle.build_graph(X, 1.2, 0.0, 16, 48)
+    assert int((G.fwd == 0).sum()) > 512 and G.deg[0] == 16
+    _check_graph(X, G, idx, cng, 16, 48)
+    cng.cng_free(idx)
+
+
+def test_merge_prefix_runs_out():
+    """A hub with 1,196 in-edges from 30 tight clusters (40 points each around a random
+    direction, radius 1 .. 1.1): in the hub's sweep the first point of each cluster prunes the
+    rest of it, so only 30 < R = 32 are kept and Alg. 2 reads the whole set; the GPU's prefix
+    runs out, it orders the rest and prunes the set again, and the graph equals the oracle's."""
+    need_gpu()
+    cng = lib()
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((30, 32))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    pts = [np.zeros((1, 32))]
+    for k in range(30):
+        dirs = u[k] + 0.01 * rng.standard_normal((40, 32))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        pts.append(dirs * rng.uniform(1.0, 1.1, (40, 1)))
+    X = np.concatenate(pts).astype(np.float32)
+    idx, st = cng.cng_build(tensor(X), alpha=1.2, R=32, L=64, keep_lists=True)
+    G = oracle.build_graph(X, 1.2, 0.0, 32, 64)
+    assert int((G.fwd == 0).sum()) > 512 and G.deg[0] == 30
+    _check_graph(X, G, idx, cng, 32, 64)
+    cng.cng_free(idx)
+
+
 @pytest.mark.parametrize("slots", [2, 24])
 def test_repair_slots(slots):
     """Phase 4 with a given number of repair slots per row (row stride R + slots): separated
