@@ -211,6 +211,40 @@ def test_connectivity_repair_on_clusters():
         assert G.adj[r, G.deg3[r]: G.deg3[r] + len(ps)].tolist() == ps
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_connect_links_every_source_once(seed):
+    """Phase 4 on random sparse graphs in which most points have no in-edge (every row points
+    into 120 'popular' points): at the end every point is reachable from the entry, the
+    phase-3 edges are in place, no point receives more than one repair edge (a linked point is
+    reached and never named again), and every point without an in-edge other than the entry
+    receives exactly one (nothing else can reach it)."""
+    rng = np.random.default_rng(seed)
+    n, d, R = 400, 8, 4
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    adj3 = np.full((n, R), -1, np.int32)
+    deg3 = np.zeros(n, np.int32)
+    targets = rng.choice(n, 120, replace=False)
+    for u in range(n):
+        k = int(rng.integers(0, R + 1))
+        vs = rng.choice(targets[targets != u], k, replace=False)
+        adj3[u, :k] = vs
+        deg3[u] = k
+    entry = int(targets[0])
+    adj, deg, added, rounds = oracle.connect(X, adj3, deg3, entry, slots=8, Lc=16)
+    assert len(_reachable(adj, deg, entry)) == n and rounds >= 1
+    rep_in = np.zeros(n, np.int64)
+    for u in range(n):
+        assert np.array_equal(adj[u, : deg3[u]], adj3[u, : deg3[u]])
+        np.add.at(rep_in, adj[u, deg3[u]: deg[u]], 1)
+    assert rep_in.sum() == added and rep_in.max() == 1
+    has_in = np.zeros(n, bool)
+    for u in range(n):
+        has_in[adj3[u, : deg3[u]]] = True
+    sources = [p for p in range(n) if not has_in[p] and p != entry]
+    assert len(sources) > n // 2
+    assert all(rep_in[p] == 1 for p in sources)
+
+
 ADAPT = (0.9, 1.6, 0.05)  # the paper's setting (Sec. 4.4): alpha0, alpha_max, dalpha
 
 
